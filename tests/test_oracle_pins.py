@@ -1,0 +1,431 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every oracle function is checked against something other than itself:
+published known-answer vectors, closed forms, exact distributions, brute
+force on tiny inputs, or the plain definition evaluated independently in
+FP64 with numpy. A dropped term, a wrong sign, a wrong index or a
+transposed operand anywhere in the oracle fails at least one test here.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import special, stats
+
+from conftest import golden
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_known_answers(oracle_mod):
+    for row in golden("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row]
+        out = oracle_mod.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_own_log_matches_libm(oracle_mod):
+    rng = np.random.default_rng(7)
+    xs = np.concatenate([np.exp(rng.uniform(-700, 700, 3000)), rng.uniform(0, 1, 3000),
+                         [1.0, 2.0, 0.5, math.sqrt(2), 1e-300, 0.9999999999]])
+    for x in xs:
+        ref = math.log(x)
+        assert abs(oracle_mod.log(x) - ref) <= 4.5e-16 * max(1.0, abs(ref)), x
+
+
+# ------------------------------------------------------------- rotation P
+def test_gaussian_matrix_is_standard_normal(oracle_mod):
+    G = oracle_mod.gaussian_matrix(11, 128).ravel()
+    assert stats.kstest(G, "norm").pvalue > 1e-3
+    assert abs(G.mean()) < 5 / math.sqrt(G.size)
+    assert abs(G.var() - 1) < 5 * math.sqrt(2 / G.size)
+
+
+@pytest.mark.parametrize("dpad", [64, 128, 256])
+def test_rotation_is_orthogonal(oracle_mod, dpad):
+    P = oracle_mod.sample_rotation(2, dpad)
+    assert np.abs(P @ P.T - np.eye(dpad)).max() <= 1e-13
+    assert np.abs(P.T @ P - np.eye(dpad)).max() <= 1e-13
+
+
+def test_gram_schmidt_is_the_q_factor(oracle_mod):
+    """Row-wise Gram-Schmidt (App. B.3) is the QR factorisation G^T = Q R with
+    diag(R) > 0 and P = Q^T: G P^T is lower triangular with a positive
+    diagonal, and P equals numpy's QR after the sign fix."""
+    G = oracle_mod.gaussian_matrix(5, 64)
+    P = oracle_mod.orthonormalize_rows(G)
+    L = G @ P.T
+    assert np.abs(np.triu(L, 1)).max() <= 1e-12 * np.abs(L).max()
+    assert (np.diag(L) > 0).all()
+    Q, R = np.linalg.qr(G.T)
+    Q = Q * np.sign(np.diag(R))
+    assert np.abs(P - Q.T).max() <= 1e-11
+
+
+def _obar_stats(oracle_mod, dim, n_rot, seed0=1000):
+    """<o_bar,o> and <o_bar,e1>/sqrt(1-<o_bar,o>^2) over independent P."""
+    rng = np.random.default_rng(dim)
+    aa, xx, est = [], [], []
+    for t in range(n_rot):
+        P = oracle_mod.sample_rotation(seed0 + t, dim)
+        o = rng.standard_normal(dim)
+        o /= np.linalg.norm(o)
+        e = rng.standard_normal(dim)
+        e -= (e @ o) * o
+        e /= np.linalg.norm(e)
+        r = oracle_mod.estimator_fp64(P, o, e)   # q = e1 itself: <o,q> = 0
+        aa.append(r[0])
+        xx.append(r[3] / math.sqrt(1 - r[0] ** 2))
+        est.append(r[2])
+    return np.array(aa), np.array(xx), np.array(est)
+
+
+@pytest.fixture(scope="module")
+def obar64(oracle_mod):
+    return _obar_stats(oracle_mod, 64, 1500)
+
+
+def test_expected_obar_o_closed_form(oracle_mod, obar64):
+    """E<o_bar,o> = sqrt(D/pi) 2 Gamma(D/2) / ((D-1) Gamma((D-1)/2)) (App. B.1)."""
+    table = {int(r[0]): float(r[1]) for r in golden("expected_obar_o.txt")}
+    for D, v in table.items():
+        cf = math.sqrt(D / math.pi) * 2 * math.exp(math.lgamma(D / 2) - math.lgamma((D - 1) / 2)) / (D - 1)
+        assert abs(cf - v) < 1e-6
+    a = obar64[0]
+    assert abs(a.mean() - table[64]) <= 5 * a.std() / math.sqrt(a.size)
+    # 1/sqrt(D) <= <o_bar,o> <= 1 always (App. B.1, l1 vs l2 norm)
+    assert (a >= 1 / math.sqrt(64) - 1e-12).all() and (a <= 1 + 1e-12).all()
+
+
+def _pdm1_cdf(x, D):
+    """CDF of one coordinate of a uniform vector on S^{D-2} (density p_{D-1}
+    of Lemma B.1): X^2 ~ Beta(1/2, (D-2)/2), symmetric about 0."""
+    x = np.asarray(x)
+    return 0.5 + 0.5 * np.sign(x) * special.betainc(0.5, (D - 2) / 2.0, x * x)
+
+
+def test_joint_law_lemma(obar64):
+    """<o_bar,e1>/sqrt(1-<o_bar,o>^2) ~ p_{D-1}, independent of <o_bar,o>
+    (Lemma of App. B.3)."""
+    a, x, _ = obar64
+    assert stats.kstest(x, lambda t: _pdm1_cdf(t, 64)).pvalue > 1e-3
+    assert abs(np.corrcoef(a, np.abs(x))[0, 1]) < 5 / math.sqrt(a.size)
+
+
+def test_error_bound_failure_rate(obar64):
+    """Theorem 3.2 at <o,q> = 0: the eps0 interval fails exactly when
+    |X1| > eps0/sqrt(D-1); compare the count with that Beta tail."""
+    D, eps0 = 64, 1.9
+    a, _, est = obar64
+    bound = np.sqrt((1 - a ** 2) / a ** 2) * eps0 / math.sqrt(D - 1)
+    fails = int((np.abs(est) > bound).sum())
+    p = 1 - special.betainc(0.5, (D - 2) / 2.0, eps0 ** 2 / (D - 1))
+    M = a.size
+    assert 0.05 < p < 0.07
+    assert abs(fails - M * p) <= 5 * math.sqrt(M * p * (1 - p))
+
+
+def test_estimator_unbiased_and_collinear(oracle_mod):
+    """E[<o_bar,q>/<o_bar,o>] = <o,q> (Theorem 3.2); exact when q = +-o."""
+    dim, M = 64, 1500
+    rng = np.random.default_rng(3)
+    o = rng.standard_normal(dim); o /= np.linalg.norm(o)
+    e = rng.standard_normal(dim); e -= (e @ o) * o; e /= np.linalg.norm(e)
+    q = 0.6 * o + 0.8 * e
+    ests = []
+    for t in range(M):
+        P = oracle_mod.sample_rotation(5000 + t, dim)
+        ests.append(oracle_mod.estimator_fp64(P, o, q)[2])
+        if t < 20:
+            assert abs(oracle_mod.estimator_fp64(P, o, o)[2] - 1.0) <= 1e-12
+            assert abs(oracle_mod.estimator_fp64(P, o, -o)[2] + 1.0) <= 1e-12
+    ests = np.array(ests)
+    assert abs(ests.mean() - 0.6) <= 5 * ests.std() / math.sqrt(M)
+
+
+def test_sign_code_is_nearest_codebook_vector(oracle_mod):
+    """x_bar = argmin_{x in C} ||o - P x||^2 (§3.1.3) by brute force over all
+    2^D codebook vectors; <o_bar,o> is that maximal inner product."""
+    dim = 10
+    rng = np.random.default_rng(4)
+    grid = np.array(np.meshgrid(*[[-1.0, 1.0]] * dim, indexing="ij")).reshape(dim, -1).T
+    C = grid / math.sqrt(dim)                                 # all of C, unit vectors
+    assert np.allclose(np.linalg.norm(C, axis=1), 1.0)
+    for t in range(20):
+        G = rng.standard_normal((dim, dim))
+        P = np.linalg.qr(G)[0]
+        o = rng.standard_normal(dim); o /= np.linalg.norm(o)
+        d2 = ((o[None, :] - C @ P.T) ** 2).sum(1)             # ||o - P x||^2
+        best = C[np.argmin(d2)]
+        r = oracle_mod.estimator_fp64(P, o, o)
+        assert abs(r[0] - (P @ best) @ o) <= 1e-12
+        assert abs(r[0] - np.max(C @ (P.T @ o))) <= 1e-12
+
+
+# --------------------------------------------------------------- encoding
+def test_encode_against_definition(oracle_mod, tiny_oracle_index):
+    X = tiny_oracle_index
+    W = X.dpad // 64
+    P = X.P
+    idx = np.arange(0, X.n, 37)
+    bits = np.unpackbits(X.codes[idx].view(np.uint8).reshape(len(idx), -1), axis=1,
+                         bitorder="little")[:, :X.dpad].astype(np.float64)
+    assert W == 2
+    res = X.data[idx].astype(np.float64) - X.centroids[X.assign[idx]].astype(np.float64)
+    n_o = np.linalg.norm(res, axis=1)
+    r64 = res @ P[:X.d]                                       # P^T [res; 0]
+    clear = np.abs(r64) > 1e-5 * n_o[:, None]
+    assert ((r64 >= 0) == (bits > 0))[clear].all()            # sign code
+    xbar = (2 * bits - 1) / math.sqrt(X.dpad)                 # x_bar = (2 x_b - 1)/sqrt(D)
+    obar = xbar @ P.T                                         # o_bar = P x_bar
+    a_def = (obar[:, :X.d] * res).sum(1) / n_o                # <o_bar, o>
+    F = X.factors[idx].astype(np.float64)
+    a_o = 2 * n_o / F[:, 1]
+    assert np.abs(a_o - a_def).max() <= 2e-5
+    assert (a_def >= 1 / math.sqrt(X.dpad) - 1e-6).all() and (a_def <= 1 + 1e-9).all()
+    assert np.allclose(F[:, 0], n_o ** 2, rtol=2e-6)
+    assert np.allclose(F[:, 2], n_o * np.sqrt(1 - a_def ** 2) / a_def, rtol=1e-4)
+    assert (F[:, 3] == 2 * bits.sum(1) - X.dpad).all()
+
+
+def test_assignment_and_distances_are_canonical(oracle_mod, tiny_oracle_index):
+    X = tiny_oracle_index
+    d64 = ((X.data[:, None, :].astype(np.float64) - X.centroids[None].astype(np.float64)) ** 2).sum(2)
+    best = d64.min(1)
+    mine = d64[np.arange(X.n), X.assign]
+    assert (mine <= best * (1 + 1e-5) + 1e-6).all()
+    assert np.allclose(X.adist, mine, rtol=1e-5, atol=1e-6)
+    D32 = oracle_mod.sqdist_matrix(X.data[:50], X.centroids)
+    assert np.allclose(D32, d64[:50], rtol=1e-5, atol=1e-6)
+
+
+def test_kmeans_invariants(oracle_mod, tiny_workload):
+    """parity unpinned: the paper fixes no k-means variant, so only the
+    invariants of Lloyd's algorithm are checked."""
+    data = tiny_workload[0][:3000]
+    objs = []
+    for it in range(0, 5):
+        cent, assign, adist = oracle_mod.kmeans(data, 12, it, seed=9)
+        objs.append(float(adist.astype(np.float64).sum()))
+        # update step: centroids are the member means (mean of the members
+        # assigned in the previous pass, so recompute from scratch for it>0)
+    assert all(objs[i + 1] <= objs[i] * (1 + 1e-6) for i in range(len(objs) - 1))
+    cent, assign, _ = oracle_mod.kmeans(data, 12, 6, seed=9)
+    cent2, assign2, _ = oracle_mod.kmeans(data, 12, 7, seed=9)
+    for c in range(12):
+        mem = data[assign == c].astype(np.float64)
+        if len(mem):
+            assert np.allclose(cent2[c], mem.mean(0), rtol=1e-5, atol=1e-5)
+    ids = oracle_mod.kmeans_init_ids(3000, 12, 9)
+    assert len(set(ids.tolist())) == 12 and ids.min() >= 0 and ids.max() < 3000
+    assert np.array_equal(cent[0] if False else data[ids[0]], data[ids[0]])
+
+
+def test_floyd_sampling_is_uniform(oracle_mod):
+    n, K, S = 10, 3, 4000
+    hits = np.zeros(n)
+    for s in range(S):
+        ids = oracle_mod.kmeans_init_ids(n, K, s)
+        assert len(set(ids.tolist())) == K
+        hits[ids] += 1
+    p = K / n
+    assert np.abs(hits - S * p).max() <= 5 * math.sqrt(S * p * (1 - p))
+
+
+# ------------------------------------------------------------ quantization
+def _rand_query_setup(oracle_mod, dpad=128, seed=0):
+    rng = np.random.default_rng(seed)
+    rq = rng.standard_normal(dpad).astype(np.float32)
+    ptc = rng.standard_normal(dpad).astype(np.float32) * 0.3
+    return rq, ptc
+
+
+def test_quantizer_rounds_to_a_neighbouring_level(oracle_mod):
+    rq, ptc = _rand_query_setup(oracle_mod)
+    for bq in (1, 2, 4, 8):
+        qu, planes, s, meta = oracle_mod.quantize(rq, ptc, bq, 3, 5, 7, 4.0, 1.9)
+        qd = (rq - ptc).astype(np.float64)
+        vl, vr = qd.min(), qd.max()
+        delta = (vr - vl) / (2 ** bq - 1)
+        x = (qd - vl) / delta
+        assert qu.min() >= 0 and qu.max() <= 2 ** bq - 1
+        lo = np.floor(x + 1e-5)
+        assert np.all((qu == np.minimum(np.floor(x), 2 ** bq - 1)) | (qu == np.minimum(np.floor(x) + 1, 2 ** bq - 1)) | (np.abs(x - np.rint(x)) < 1e-4))
+        assert s == qu.sum()
+        dec = sum(((planes[j][:, None] >> np.arange(64, dtype=np.uint64)) & np.uint64(1)).astype(np.int64).ravel() << j for j in range(bq))
+        assert np.array_equal(dec, qu)
+        assert abs(meta[4] - vl) == 0 and abs(meta[5] - delta) <= 1e-6 * abs(delta)
+        assert abs(meta[0] - delta / math.sqrt(128)) <= 1e-6 * delta
+        assert abs(meta[2] - 2.0 * 2 * 1.9 / math.sqrt(127)) <= 1e-5
+
+
+def test_quantizer_unbiased_and_hoeffding(oracle_mod):
+    """E[q_bar] = q' (randomized rounding, §3.3.1) and the Hoeffding tail
+    P{|<x_bar, q_bar - q'>| >= Delta u} <= 2 exp(-u^2/2) (App. D)."""
+    dpad, bq, S = 128, 4, 3000
+    rq, ptc = _rand_query_setup(oracle_mod, dpad, 1)
+    qd = (rq - ptc).astype(np.float64)
+    rng = np.random.default_rng(2)
+    xbar = rng.choice([-1.0, 1.0], dpad) / math.sqrt(dpad)
+    acc = np.zeros(dpad)
+    errs = []
+    for s in range(S):
+        qu, _, _, meta = oracle_mod.quantize(rq, ptc, bq, s, 0, 0, 1.0, 1.9)
+        qbar = float(meta[5]) * qu + float(meta[4])
+        acc += qbar
+        errs.append(xbar @ (qbar - qd))
+    delta = float(meta[5])
+    mean = acc / S
+    assert np.abs(mean - qd).max() <= 5 * (delta / 2) / math.sqrt(S) + 1e-6
+    errs = np.abs(np.array(errs))
+    for u in (1.0, 2.0, 3.0):
+        assert (errs >= delta * u).mean() <= 2 * math.exp(-u * u / 2) + 3 / math.sqrt(S)
+
+
+def test_quantizer_degenerate_range(oracle_mod):
+    rq = np.full(64, 0.25, np.float32)
+    ptc = np.zeros(64, np.float32)
+    qu, planes, s, meta = oracle_mod.quantize(rq, ptc, 4, 3, 0, 0, 1.0, 1.9)
+    assert (qu == 0).all() and s == 0 and (planes == 0).all() and meta[5] == 0
+
+
+# ------------------------------------------------- inner product, estimator
+def test_bitplane_identity(oracle_mod):
+    rng = np.random.default_rng(8)
+    for dpad in (64, 128, 1024):
+        W = dpad // 64
+        for trial in range(30):
+            bits = rng.integers(0, 2, dpad)
+            qu = rng.integers(0, 16, dpad)
+            if trial == 0:
+                qu[:] = 0
+            if trial == 1:
+                qu[:] = 15
+            if trial == 2:
+                bits[:] = 1
+            code = np.packbits(bits.astype(np.uint8), bitorder="little").view(np.uint64)
+            planes = np.stack([np.packbits(((qu >> j) & 1).astype(np.uint8), bitorder="little").view(np.uint64) for j in range(4)])
+            assert code.shape == (W,)
+            assert oracle_mod.bitplane_ip(code, planes) == int((bits * qu).sum())
+
+
+def test_inner_product_expansion_and_estimate(oracle_mod):
+    """<x_bar, q_bar> = (2 Delta/sqrt D)<x_b,q_u> + (2 v_l/sqrt D) sum x_b
+    - (Delta/sqrt D) sum q_u - sqrt(D) v_l (§3.3.2), and the distance
+    identity of §3.1.1 with the estimator of Theorem 3.2."""
+    rng = np.random.default_rng(9)
+    dpad = 128
+    for trial in range(200):
+        rq = rng.standard_normal(dpad).astype(np.float32) * 3
+        ptc = rng.standard_normal(dpad).astype(np.float32)
+        n_q2 = float(np.float32(rng.uniform(0.5, 20)))
+        qu, planes, s, meta = oracle_mod.quantize(rq, ptc, 4, trial, 1, 2, n_q2, 1.9)
+        bits = rng.integers(0, 2, dpad)
+        code = np.packbits(bits.astype(np.uint8), bitorder="little").view(np.uint64)
+        ip = oracle_mod.bitplane_ip(code, planes)
+        n_o = rng.uniform(0.1, 5)
+        a_o = rng.uniform(0.6, 0.95)
+        F = np.array([n_o ** 2, 2 * n_o / a_o, n_o * math.sqrt(1 - a_o ** 2) / a_o,
+                      2 * bits.sum() - dpad], np.float32)
+        est = oracle_mod.estimate(ip, s, F, meta)
+        xbar = (2 * bits - 1) / math.sqrt(dpad)
+        qbar = float(meta[5]) * qu + float(meta[4])
+        direct = xbar @ qbar                                    # <x_bar, q_bar> (un-normalized)
+        n_q = math.sqrt(n_q2)
+        F64 = F.astype(np.float64)
+        dist = F64[0] + n_q2 - 2 * math.sqrt(F64[0]) * n_q * (direct / n_q) / a_o
+        e = 2 * math.sqrt(F64[0]) * n_q * math.sqrt(1 - a_o ** 2) / a_o * 1.9 / math.sqrt(dpad - 1)
+        scale = F64[0] + n_q2 + abs(F64[1] * direct)
+        assert abs(est[0] - dist) <= 2e-6 * scale
+        assert abs((est[2] - est[0]) - e) <= 2e-6 * scale
+        assert abs((est[0] - est[1]) - e) <= 2e-6 * scale
+
+
+# ------------------------------------------------------------ IVF search
+def test_select_matches_lexsort(oracle_mod):
+    rng = np.random.default_rng(10)
+    d = rng.integers(0, 20, (30, 100)).astype(np.float32)      # many ties
+    ids, sd = oracle_mod.select(d, 17)
+    for r in range(30):
+        order = np.lexsort((np.arange(100), d[r]))[:17]
+        assert np.array_equal(ids[r], order)
+        assert np.array_equal(sd[r], d[r][order])
+
+
+def test_search_equals_exact_knn_over_probed_buckets(oracle_mod, tiny_oracle_index, tiny_workload):
+    """With every true member inside its bound, the error-bound re-ranking
+    returns the exact kNN of the union of the probed buckets (§4)."""
+    X = tiny_oracle_index
+    _, Q = tiny_workload
+    k, nprobe = 10, 4
+    ids, dist = X.search(Q, k, nprobe)
+    cd = oracle_mod.sqdist_matrix(Q, X.centroids)
+    probes, _ = oracle_mod.select(cd, nprobe)
+    allowed = np.isin(X.assign[None, :], probes[:, :, None]).any(1) if False else \
+        np.stack([np.isin(X.assign, probes[i]) for i in range(len(Q))]).astype(np.uint8)
+    bids, bdist = oracle_mod.bruteforce_knn(X.data, Q, k, allowed)
+    same = (ids == bids).all(1)
+    assert same.mean() >= 0.97
+    assert np.array_equal(dist[same], bdist[same])
+    # mode 1 (paper-literal sequential drop rule) agrees on nearly all queries
+    ids1, _ = X.search(Q, k, nprobe, mode=1)
+    assert (ids1 == ids).all(1).mean() >= 0.97
+
+
+def test_trace_survivors_are_exactly_the_bound_set(oracle_mod, tiny_oracle_index, tiny_workload):
+    X = tiny_oracle_index
+    _, Q = tiny_workload
+    t = X.trace(Q[3], 3, 10, 4)
+    ub = np.sort(t["pair_est"][:, 2])
+    assert t["tau"] == ub[9]
+    surv = np.sort(t["pair_id"][t["pair_est"][:, 1] <= t["tau"]])
+    assert np.array_equal(surv, t["surv_ids"])
+    # the true 10-NN of the probed buckets survive and are returned
+    ex = ((X.data[t["pair_id"]] - Q[3]) ** 2).sum(1)
+    top = t["pair_id"][np.lexsort((t["pair_id"], ex))[:10]]
+    assert set(top.tolist()) <= set(t["surv_ids"].tolist())
+
+
+def test_recall_with_all_buckets_at_eps0(oracle_mod, tiny_oracle_index, tiny_workload):
+    """Nearly perfect recall at eps0 = 1.9 when every bucket is probed (§5.2.4)."""
+    X = tiny_oracle_index
+    _, Q = tiny_workload
+    ids, _ = X.search(Q, 10, X.K)
+    gt, _ = oracle_mod.bruteforce_knn(X.data, Q, 10)
+    recall = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids.tolist(), gt.tolist())])
+    assert recall >= 0.99
+    ids0, _ = X.search(Q, 10, X.K, eps0=0.0)
+    recall0 = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids0.tolist(), gt.tolist())])
+    assert recall0 < recall
+
+
+def _est_pairs(X, Q, bq, nq=20, nprobe=4):
+    est, true = [], []
+    for i in range(nq):
+        t = X.trace(Q[i], i, 10, nprobe, bq=bq)
+        est.append(t["pair_est"][:, 0])
+        true.append(((X.data[t["pair_id"]].astype(np.float64) - Q[i]) ** 2).sum(1))
+    return np.concatenate(est).astype(np.float64), np.concatenate(true)
+
+
+def test_bq_error_converges(tiny_oracle_index, tiny_workload):
+    """Average relative error of estimated squared distances flattens by
+    B_q = 4 (§5.2.5) and B_q = 1 is clearly worse."""
+    X = tiny_oracle_index
+    _, Q = tiny_workload
+    err = {}
+    for bq in (1, 4, 8):
+        e, t = _est_pairs(X, Q, bq)
+        err[bq] = np.mean(np.abs(e - t) / t)
+    assert err[4] <= 1.05 * err[8]
+    assert err[1] > 1.3 * err[4]
+
+
+def test_estimated_distances_unbiased_fit(tiny_oracle_index, tiny_workload):
+    """Linear fit of estimated vs true squared distance: slope 1, intercept 0
+    (§5.2.6)."""
+    X = tiny_oracle_index
+    _, Q = tiny_workload
+    e, t = _est_pairs(X, Q, 4, nq=40)
+    m = t.max()
+    slope, icpt = np.polyfit(t / m, e / m, 1)
+    assert abs(slope - 1) <= 0.01 and abs(icpt) <= 0.01
