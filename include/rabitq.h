@@ -1,0 +1,206 @@
+/*
+ * rabitq.h -- C-ABI of the GB300 (sm_103a) RaBitQ IVF library.
+ *
+ * RaBitQ (Gao & Long, SIGMOD 2024) quantizes each data vector to a D'-bit
+ * sign code of its inverse-rotated residual and estimates squared distances
+ * with an unbiased estimator whose error bound decides which candidates are
+ * re-ranked with exact distances. This library builds the IVF index (Alg. 1
+ * and §4 of the paper) and answers k-nearest-neighbour queries (Alg. 2 and
+ * §4) entirely in its own CUDA kernels.
+ *
+ * Conventions for every call:
+ *  - Return value: RABITQ_OK (0) or a negative rabitq_status; the message of
+ *    the last failure on the calling thread is rabitq_last_error().
+ *  - Inputs are caller-owned and read-only; the library copies what it keeps.
+ *  - Outputs are caller-allocated; on error their contents are undefined.
+ *  - Host pointers unless the options say a pointer is device memory.
+ *  - Matrices are row-major, float32 unless stated.
+ *  - An index is owned by the library from rabitq_build/rabitq_index_load
+ *    until rabitq_free. Searches on one const index may run concurrently
+ *    from several host threads on distinct streams.
+ */
+#ifndef RABITQ_H
+#define RABITQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rabitq_index rabitq_index;
+
+typedef enum {
+  RABITQ_OK = 0,
+  RABITQ_EINVAL = -1,       /* invalid argument (sizes, ranges, null pointer)  */
+  RABITQ_ENOMEM = -2,       /* device or host allocation failed               */
+  RABITQ_ECUDA = -3,        /* a CUDA runtime call or kernel failed            */
+  RABITQ_ETIMEOUT = -4,     /* a bounded device wait expired                  */
+  RABITQ_EIO = -5,          /* file missing, truncated or corrupt             */
+  RABITQ_EUNSUPPORTED = -6, /* option not supported on this device/build      */
+  RABITQ_EOVERFLOW = -7     /* a query's candidate list exceeded its capacity */
+} rabitq_status;
+
+/* Precision of the query rotation P^{-1} q (§3.3 of the paper). FP32 is the
+ * canonical, bit-reproducible path; TF32 and BF16 run on tensor cores with
+ * FP32 accumulation. */
+enum { RABITQ_ROT_FP32 = 0, RABITQ_ROT_TF32 = 1, RABITQ_ROT_BF16 = 2 };
+
+/* Bucket-scan implementation of <x_b, q_u> (§3.3.2): bit-plane popcount or
+ * an exact integer product on tensor cores; AUTO picks per shape. */
+enum { RABITQ_SCAN_AUTO = 0, RABITQ_SCAN_POPC = 1, RABITQ_SCAN_TC = 2 };
+
+typedef struct {
+  int32_t kmeans_iters;     /* Lloyd iterations (default 10)                    */
+  int64_t kmeans_sample;    /* train k-means on about this many points, 0 = all */
+  int32_t code_bits;        /* D' (multiple of 64, >= d); 0 = ceil(d/64)*64     */
+  int32_t data_on_device;   /* `data` is a device pointer                       */
+  void* stream;             /* cudaStream_t to run on; NULL = the legacy stream */
+  const float* centroids;   /* optional K x d centroids (host or device, as
+                               `data`); when given, k-means is skipped          */
+} rabitq_build_opts;
+
+typedef struct {
+  int32_t rot_precision;    /* RABITQ_ROT_*                                      */
+  int32_t scan_path;        /* RABITQ_SCAN_*                                     */
+  uint64_t quant_seed;      /* seed of the randomized query rounding (default 3) */
+  int32_t io_on_device;     /* queries and outputs are device pointers           */
+  void* stream;             /* cudaStream_t; NULL = the legacy default stream    */
+  const int32_t* per_query_nprobe; /* optional nq probe counts (same memory kind
+                               as the queries), each clamped to [1, nprobe]      */
+  int32_t max_candidates;   /* per-query capacity of the candidate list that
+                               survives the error bound (0 = 16384)              */
+  int32_t collect_stats;    /* record per-stage device times (rabitq_last_stats) */
+} rabitq_search_opts;
+
+/* Fill the option structs with their defaults. */
+void rabitq_build_opts_default(rabitq_build_opts* opts);
+void rabitq_search_opts_default(rabitq_search_opts* opts);
+
+/*
+ * rabitq_build -- index phase (Alg. 1 of the paper with the IVF of §4).
+ *   data        n x d float32 raw vectors o_r
+ *   n, d        n >= 1, 1 <= d <= 4096
+ *   n_clusters  K, 1 <= K <= n, K <= 65536: IVF k-means clusters; each
+ *               vector is normalized by its own centroid c (§3.1.1)
+ *   seed        seeds the k-means initialization and the random orthogonal
+ *               matrix P (§3.1.2); the whole build is deterministic
+ *   opts        NULL = defaults
+ *   out         receives the new index
+ * Produces the centroids, P (D' x D', FP64, row-major; the code of o is the
+ * sign vector of P^{-1}(o_r - c), §3.1.3), the packed D'-bit codes and the
+ * factors ||o_r - c|| and <o_bar, o> (Alg. 1 line 4).
+ * Errors: EINVAL on bad sizes or a non-finite input; ENOMEM; ECUDA.
+ */
+int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, uint64_t seed,
+                 const rabitq_build_opts* opts, rabitq_index** out);
+
+/*
+ * rabitq_search -- query phase (Alg. 2 with the IVF probing and error-bound
+ * re-ranking of §4).
+ *   queries   nq x d float32 raw query vectors q_r
+ *   nq        >= 0 (0 is a no-op)
+ *   k         1..1024 neighbours per query
+ *   nprobe    1..K buckets probed per query (the nearest centroids)
+ *   bq        1..8 bits of the randomized query quantization (§3.3.1)
+ *   eps0      >= 0, confidence parameter of the error bound (Theorem 3.2)
+ *   out_ids   nq x k int64 ids, ascending by (distance, id); -1 pads
+ *   out_dist  nq x k float32 exact squared distances; +inf pads
+ * A candidate is re-ranked iff its distance lower bound is at most the k-th
+ * smallest upper bound over all estimated codes of its query.
+ * Errors: EINVAL; ENOMEM; ECUDA; EOVERFLOW when more than max_candidates
+ * codes of one query pass the bound (raise max_candidates).
+ */
+int rabitq_search(const rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
+                  int32_t nprobe, int32_t bq, float eps0, int64_t* out_ids, float* out_dist,
+                  const rabitq_search_opts* opts);
+
+/*
+ * rabitq_search_trace -- rabitq_search that also writes the intermediates of
+ * every stage, for staged verification. All pointers are DEVICE memory (the
+ * queries and outputs too); any trace pointer may be NULL to skip it.
+ *   probe_ids, probe_dist  nq x nprobe: probed clusters by (distance, id)
+ *                          and ||q_r - c||^2
+ *   rq                     nq x D': P^{-1} [q_r; 0]
+ *   planes                 nq x nprobe x bq x (D'/64) bit-planes of q_u
+ *   sum_qu                 nq x nprobe: sum of q_u
+ *   meta                   nq x nprobe x 4: Delta/sqrt(D'), v_l/sqrt(D'),
+ *                          ||q_r-c|| 2 eps0/sqrt(D'-1), ||q_r-c||^2
+ *   pair_cap               per-query capacity of the pair arrays
+ *   n_pairs                nq: codes estimated per query
+ *   pair_id, pair_ip       nq x pair_cap: id and <x_b, q_u> per pair, in
+ *                          probe order then bucket order (ascending id)
+ *   pair_est               nq x pair_cap x 3: estimated distance, LB, UB
+ *   tau                    nq: k-th smallest UB (+inf if fewer than k)
+ *   surv_cap, n_surv, surv_ids  survivors (LB <= tau), in no particular order
+ */
+typedef struct {
+  int32_t* probe_ids;
+  float* probe_dist;
+  float* rq;
+  uint64_t* planes;
+  int32_t* sum_qu;
+  float* meta;
+  int32_t pair_cap;
+  int32_t* n_pairs;
+  int32_t* pair_id;
+  int32_t* pair_ip;
+  float* pair_est;
+  float* tau;
+  int32_t surv_cap;
+  int32_t* n_surv;
+  int32_t* surv_ids;
+} rabitq_trace;
+
+int rabitq_search_trace(const rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
+                        int32_t nprobe, int32_t bq, float eps0, int64_t* out_ids,
+                        float* out_dist, const rabitq_search_opts* opts,
+                        const rabitq_trace* trace);
+
+/* Per-stage device times (milliseconds) of the last search on this thread
+ * with collect_stats set. Stages: 0 centroid distances, 1 probe selection,
+ * 2 query rotation, 3 quantize + scan + prune + re-rank, 4 total (including
+ * host<->device copies). Returns the number of stages written (<= cap). */
+int rabitq_last_stats(float* ms, int32_t cap);
+
+/* Sizes of an index: n, d, D' (code bits), K. Any pointer may be NULL. */
+int rabitq_index_info(const rabitq_index* idx, int64_t* n, int32_t* d, int32_t* d_pad,
+                      int32_t* n_clusters);
+
+/* Accessors: copy to caller-owned HOST buffers, original id order. */
+int rabitq_get_centroids(const rabitq_index* idx, float* out /* K x d */);
+int rabitq_get_rotation(const rabitq_index* idx, double* out /* D' x D', P row-major */);
+int rabitq_get_codes(const rabitq_index* idx, uint64_t* out /* n x D'/64; bit i of the
+                     code is word i>>6, bit i&63 */);
+/* factors: n x 4 = {||o_r-c||^2, 2||o_r-c||/<o_bar,o>,
+ * ||o_r-c|| sqrt(1-<o_bar,o>^2)/<o_bar,o>, 2 popcount(code) - D'} */
+int rabitq_get_factors(const rabitq_index* idx, float* out /* n x 4 */);
+int rabitq_get_assign(const rabitq_index* idx, int32_t* cluster /* n */);
+/* Bucket layout: offsets (K+1) and the ids of each bucket, ascending. */
+int rabitq_get_buckets(const rabitq_index* idx, int32_t* offsets /* K+1 */,
+                       int32_t* ids /* n */);
+
+/*
+ * rabitq_sample_rotation -- the random orthogonal P of §3.1.2 on its own:
+ * a D' x D' matrix of standard Gaussians (Philox4x32-10 keyed by seed,
+ * Marsaglia polar method) orthonormalized row by row by Gram-Schmidt
+ * (App. B.3), in FP64 on the device. out: D' x D' HOST buffer, row-major.
+ */
+int rabitq_sample_rotation(uint64_t seed, int32_t d_pad, double* out);
+
+/* Save / load an index (versioned binary with a CRC-32 of the payload).
+ * Errors: EIO on a missing, truncated or corrupt file. */
+int rabitq_index_save(const rabitq_index* idx, const char* path);
+int rabitq_index_load(const char* path, const rabitq_build_opts* opts, rabitq_index** out);
+
+/* Release an index (NULL is a no-op). */
+void rabitq_free(rabitq_index* idx);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* rabitq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RABITQ_H */

@@ -1,0 +1,544 @@
+// api.cu -- the C-ABI entry points of include/rabitq.h: argument checks,
+// device memory of the index, host<->device copies, stream handling, stats,
+// accessors and the index file format.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace rbq {
+
+namespace {
+thread_local std::string g_err;
+thread_local float g_stats[5] = {0, 0, 0, 0, 0};
+thread_local int g_nstats = 0;
+}  // namespace
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+namespace {
+
+template <class T>
+int dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(RABITQ_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  return RABITQ_OK;
+}
+
+void free_index_arrays(rabitq_index* X) {
+  cudaFree(X->data_b);
+  cudaFree(X->codes);
+  cudaFree(X->factors);
+  cudaFree(X->perm);
+  cudaFree(X->bucket_off);
+  cudaFree(X->assign);
+  cudaFree(X->centroids);
+  cudaFree(X->centroids_t);
+  cudaFree(X->ptc);
+  cudaFree(X->P64);
+  cudaFree(X->P32);
+}
+
+int alloc_index_arrays(rabitq_index* X) {
+  const int64_t n = X->n;
+  RBQ_CHECK(dev_alloc(&X->data_b, (size_t)n * X->d));
+  RBQ_CHECK(dev_alloc(&X->codes, (size_t)n * X->W));
+  RBQ_CHECK(dev_alloc(&X->factors, (size_t)n));
+  RBQ_CHECK(dev_alloc(&X->perm, (size_t)n));
+  RBQ_CHECK(dev_alloc(&X->bucket_off, (size_t)X->K + 1));
+  RBQ_CHECK(dev_alloc(&X->assign, (size_t)n));
+  RBQ_CHECK(dev_alloc(&X->centroids, (size_t)X->K * X->d));
+  RBQ_CHECK(dev_alloc(&X->centroids_t, (size_t)X->K * X->d));
+  RBQ_CHECK(dev_alloc(&X->ptc, (size_t)X->K * X->dpad));
+  RBQ_CHECK(dev_alloc(&X->P64, (size_t)X->dpad * X->dpad));
+  RBQ_CHECK(dev_alloc(&X->P32, (size_t)X->dpad * X->dpad));
+  return RABITQ_OK;
+}
+
+int max_bucket_size(rabitq_index* X, cudaStream_t s) {
+  std::vector<int32_t> off(X->K + 1);
+  RBQ_CUDA(cudaMemcpyAsync(off.data(), X->bucket_off, sizeof(int32_t) * (X->K + 1),
+                           cudaMemcpyDeviceToHost, s));
+  RBQ_CUDA(cudaStreamSynchronize(s));
+  int mx = 0;
+  for (int c = 0; c < X->K; ++c) mx = std::max(mx, off[c + 1] - off[c]);
+  X->max_bucket = mx;
+  return RABITQ_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---- CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320) for index files
+uint32_t crc32_update(uint32_t crc, const void* data, size_t len) {
+  static uint32_t table[256];
+  static bool init = false;
+  if (!init) {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t c = i;
+      for (int k = 0; k < 8; ++k) c = (c & 1) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+      table[i] = c;
+    }
+    init = true;
+  }
+  const uint8_t* p = static_cast<const uint8_t*>(data);
+  crc = ~crc;
+  for (size_t i = 0; i < len; ++i) crc = table[(crc ^ p[i]) & 0xff] ^ (crc >> 8);
+  return ~crc;
+}
+
+struct FileHeader {
+  char magic[8];  // "RABITQ\0\1"
+  uint32_t version;
+  uint32_t reserved;
+  int64_t n;
+  int32_t d, dpad, K, W;
+  uint64_t payload_bytes;
+  uint32_t payload_crc;
+  uint32_t header_crc;
+};
+
+}  // namespace
+}  // namespace rbq
+
+using namespace rbq;
+
+extern "C" {
+
+void rabitq_build_opts_default(rabitq_build_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->kmeans_iters = 10;
+}
+
+void rabitq_search_opts_default(rabitq_search_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->quant_seed = 3;
+  o->max_candidates = 16384;
+}
+
+const char* rabitq_last_error(void) { return g_err.c_str(); }
+
+int rabitq_last_stats(float* ms, int32_t cap) {
+  if (!ms || cap < 0) return fail(RABITQ_EINVAL, "rabitq_last_stats: null output");
+  const int m = std::min<int>(cap, g_nstats);
+  for (int i = 0; i < m; ++i) ms[i] = g_stats[i];
+  return m;
+}
+
+int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, uint64_t seed,
+                 const rabitq_build_opts* opts_in, rabitq_index** out) {
+  g_err.clear();
+  if (!out) return fail(RABITQ_EINVAL, "rabitq_build: out is null");
+  *out = nullptr;
+  rabitq_build_opts opts;
+  rabitq_build_opts_default(&opts);
+  if (opts_in) opts = *opts_in;
+  if (!data) return fail(RABITQ_EINVAL, "rabitq_build: data is null");
+  if (n < 1 || n > 0x7fffffffLL) return fail(RABITQ_EINVAL, "rabitq_build: need 1 <= n < 2^31");
+  if (d < 1 || d > 4096) return fail(RABITQ_EINVAL, "rabitq_build: need 1 <= d <= 4096");
+  if (n_clusters < 1 || n_clusters > n || n_clusters > 65536)
+    return fail(RABITQ_EINVAL, "rabitq_build: need 1 <= n_clusters <= min(n, 65536)");
+  if (opts.kmeans_iters < 0) return fail(RABITQ_EINVAL, "rabitq_build: kmeans_iters < 0");
+  int32_t dpad = opts.code_bits ? opts.code_bits : (d + 63) / 64 * 64;
+  if (dpad % 64 != 0 || dpad < d || dpad > 4096)
+    return fail(RABITQ_EINVAL, "rabitq_build: code_bits must be a multiple of 64, >= d, <= 4096");
+  if (int64_t(n_clusters) * (n + 2047) / 2048 > (int64_t(1) << 31))
+    return fail(RABITQ_EINVAL, "rabitq_build: n_clusters too large for n");
+  cudaStream_t s = static_cast<cudaStream_t>(opts.stream);
+
+  auto* X = new rabitq_index();
+  X->n = n;
+  X->d = d;
+  X->dpad = dpad;
+  X->K = n_clusters;
+  X->W = dpad / 64;
+  RBQ_CUDA(cudaGetDevice(&X->device));
+  int st = alloc_index_arrays(X);
+  if (st != RABITQ_OK) {
+    free_index_arrays(X);
+    delete X;
+    return st;
+  }
+  auto body = [&]() -> int {
+    DevBuf dbuf, adist, adist_b;
+    const float* ddata = data;
+    if (!opts.data_on_device) {
+      RBQ_CHECK(dbuf.alloc(sizeof(float) * n * d, s));
+      RBQ_CUDA(cudaMemcpyAsync(dbuf.p, data, sizeof(float) * n * d, cudaMemcpyHostToDevice, s));
+      ddata = dbuf.as<float>();
+    }
+    bool finite = true;
+    RBQ_CHECK(check_finite(ddata, n * d, s, &finite));
+    if (!finite) return fail(RABITQ_EINVAL, "rabitq_build: data has a non-finite value");
+    if (opts.centroids) {
+      RBQ_CUDA(cudaMemcpyAsync(X->centroids, opts.centroids, sizeof(float) * n_clusters * d,
+                               opts.data_on_device ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyHostToDevice,
+                               s));
+      RBQ_CHECK(check_finite(X->centroids, (int64_t)n_clusters * d, s, &finite));
+      if (!finite) return fail(RABITQ_EINVAL, "rabitq_build: centroids have a non-finite value");
+    } else {
+      RBQ_CHECK(kmeans_dev(ddata, n, d, n_clusters, opts.kmeans_iters, opts.kmeans_sample, seed,
+                           X->centroids, s));
+    }
+    RBQ_CHECK(transpose_f32(X->centroids, n_clusters, d, X->centroids_t, s));
+    RBQ_CHECK(adist.alloc(sizeof(float) * n, s));
+    RBQ_CHECK(argmin_sqdist(ddata, d, X->centroids_t, n_clusters, n, n_clusters, d, X->assign,
+                            adist.as<float>(), s));
+    RBQ_CHECK(counting_sort(X->assign, n, n_clusters, X->perm, X->bucket_off, s));
+    RBQ_CHECK(gather_rows_f32(ddata, d, X->perm, n, d, X->data_b, s));
+    RBQ_CHECK(adist_b.alloc(sizeof(float) * n, s));
+    RBQ_CHECK(gather_rows_f32(adist.as<float>(), 1, X->perm, n, 1, adist_b.as<float>(), s));
+    RBQ_CHECK(sample_rotation_dev(seed, dpad, X->P64, X->P32, s));
+    RBQ_CHECK(gemm_canon(kDot, X->centroids, d, nullptr, nullptr, 0, nullptr, X->P32, dpad,
+                         X->ptc, dpad, n_clusters, dpad, d, s));
+    RBQ_CHECK(encode_dev(X, adist_b.as<float>(), s));
+    RBQ_CHECK(max_bucket_size(X, s));
+    RBQ_CUDA(cudaStreamSynchronize(s));
+    return RABITQ_OK;
+  };
+  st = body();
+  if (st != RABITQ_OK) {
+    cudaStreamSynchronize(s);
+    free_index_arrays(X);
+    delete X;
+    return st;
+  }
+  *out = X;
+  return RABITQ_OK;
+}
+
+static int search_common(const rabitq_index* X, const float* queries, int64_t nq, int32_t k,
+                         int32_t nprobe, int32_t bq, float eps0, int64_t* out_ids,
+                         float* out_dist, const rabitq_search_opts* opts_in,
+                         const rabitq_trace* trace) {
+  g_err.clear();
+  g_nstats = 0;
+  if (!X) return fail(RABITQ_EINVAL, "rabitq_search: index is null");
+  rabitq_search_opts opts;
+  rabitq_search_opts_default(&opts);
+  if (opts_in) opts = *opts_in;
+  if (opts.max_candidates == 0) opts.max_candidates = 16384;
+  if (nq < 0) return fail(RABITQ_EINVAL, "rabitq_search: nq < 0");
+  if (nq == 0) return RABITQ_OK;
+  if (!queries || !out_ids || !out_dist) return fail(RABITQ_EINVAL, "rabitq_search: null pointer");
+  if (k < 1 || k > 1024) return fail(RABITQ_EINVAL, "rabitq_search: need 1 <= k <= 1024");
+  if (nprobe < 1 || nprobe > X->K || nprobe > 16384)
+    return fail(RABITQ_EINVAL, "rabitq_search: need 1 <= nprobe <= min(K, 16384)");
+  if (bq < 1 || bq > 8) return fail(RABITQ_EINVAL, "rabitq_search: need 1 <= bq <= 8");
+  if (!(eps0 >= 0.0f) || !std::isfinite(eps0))
+    return fail(RABITQ_EINVAL, "rabitq_search: eps0 must be finite and >= 0");
+  if (opts.max_candidates < 1024 || opts.max_candidates > (1 << 26))
+    return fail(RABITQ_EINVAL, "rabitq_search: max_candidates must be in [1024, 2^26]");
+  if (opts.rot_precision != RABITQ_ROT_FP32)
+    return fail(RABITQ_EUNSUPPORTED, "rabitq_search: only FP32 rotation in this build");
+  if (opts.scan_path != RABITQ_SCAN_AUTO && opts.scan_path != RABITQ_SCAN_POPC)
+    return fail(RABITQ_EUNSUPPORTED, "rabitq_search: only the popcount scan in this build");
+  if (trace && (trace->pair_id || trace->pair_ip || trace->pair_est) &&
+      (!trace->pair_id || !trace->pair_ip || !trace->pair_est || trace->pair_cap < 0))
+    return fail(RABITQ_EINVAL, "rabitq_search_trace: pair arrays must be given together");
+  if (trace && trace->surv_ids && trace->surv_cap < 0)
+    return fail(RABITQ_EINVAL, "rabitq_search_trace: surv_cap < 0");
+  cudaStream_t s = static_cast<cudaStream_t>(opts.stream);
+  const bool on_dev = trace ? true : opts.io_on_device != 0;
+
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (opts.collect_stats) {
+    RBQ_CUDA(cudaEventCreate(&t0));
+    RBQ_CUDA(cudaEventCreate(&t1));
+    RBQ_CUDA(cudaEventRecord(t0, s));
+  }
+  DevBuf qb, ib, db, nb;
+  const float* dq = queries;
+  int64_t* dids = out_ids;
+  float* ddist = out_dist;
+  const int32_t* dnp = opts.per_query_nprobe;
+  if (!on_dev) {
+    RBQ_CHECK(qb.alloc(sizeof(float) * nq * X->d, s));
+    RBQ_CHECK(ib.alloc(sizeof(int64_t) * nq * k, s));
+    RBQ_CHECK(db.alloc(sizeof(float) * nq * k, s));
+    RBQ_CUDA(cudaMemcpyAsync(qb.p, queries, sizeof(float) * nq * X->d, cudaMemcpyHostToDevice, s));
+    if (dnp) {
+      RBQ_CHECK(nb.alloc(sizeof(int32_t) * nq, s));
+      RBQ_CUDA(cudaMemcpyAsync(nb.p, dnp, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, s));
+      dnp = nb.as<int32_t>();
+    }
+    dq = qb.as<float>();
+    dids = ib.as<int64_t>();
+    ddist = db.as<float>();
+  } else if (!is_device_ptr(queries) || !is_device_ptr(out_ids) || !is_device_ptr(out_dist)) {
+    return fail(RABITQ_EINVAL, "rabitq_search: io_on_device set but a pointer is not device memory");
+  }
+  SearchArgs a;
+  a.X = X;
+  a.queries = dq;
+  a.nq = nq;
+  a.k = k;
+  a.nprobe = nprobe;
+  a.bq = bq;
+  a.eps0 = eps0;
+  a.seed = opts.quant_seed;
+  a.per_query_nprobe = dnp;
+  a.cand_cap = opts.max_candidates;
+  a.out_ids = dids;
+  a.out_dist = ddist;
+  a.trace = trace;
+  a.rot_precision = opts.rot_precision;
+  a.scan_path = opts.scan_path;
+  float stage[5] = {0, 0, 0, 0, 0};
+  a.stage_ms = opts.collect_stats ? stage : nullptr;
+  RBQ_CHECK(search_dev(a, s));
+  if (!on_dev) {
+    RBQ_CUDA(cudaMemcpyAsync(out_ids, dids, sizeof(int64_t) * nq * k, cudaMemcpyDeviceToHost, s));
+    RBQ_CUDA(cudaMemcpyAsync(out_dist, ddist, sizeof(float) * nq * k, cudaMemcpyDeviceToHost, s));
+  }
+  if (opts.collect_stats) {
+    RBQ_CUDA(cudaEventRecord(t1, s));
+    RBQ_CUDA(cudaEventSynchronize(t1));
+    RBQ_CUDA(cudaEventElapsedTime(&stage[4], t0, t1));
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    for (int i = 0; i < 5; ++i) g_stats[i] = stage[i];
+    g_nstats = 5;
+  }
+  if (!on_dev) RBQ_CUDA(cudaStreamSynchronize(s));
+  return RABITQ_OK;
+}
+
+int rabitq_search(const rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
+                  int32_t nprobe, int32_t bq, float eps0, int64_t* out_ids, float* out_dist,
+                  const rabitq_search_opts* opts) {
+  return search_common(idx, queries, nq, k, nprobe, bq, eps0, out_ids, out_dist, opts, nullptr);
+}
+
+int rabitq_search_trace(const rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
+                        int32_t nprobe, int32_t bq, float eps0, int64_t* out_ids,
+                        float* out_dist, const rabitq_search_opts* opts,
+                        const rabitq_trace* trace) {
+  if (!trace) return fail(RABITQ_EINVAL, "rabitq_search_trace: trace is null");
+  return search_common(idx, queries, nq, k, nprobe, bq, eps0, out_ids, out_dist, opts, trace);
+}
+
+int rabitq_index_info(const rabitq_index* X, int64_t* n, int32_t* d, int32_t* d_pad,
+                      int32_t* n_clusters) {
+  if (!X) return fail(RABITQ_EINVAL, "rabitq_index_info: index is null");
+  if (n) *n = X->n;
+  if (d) *d = X->d;
+  if (d_pad) *d_pad = X->dpad;
+  if (n_clusters) *n_clusters = X->K;
+  return RABITQ_OK;
+}
+
+int rabitq_get_centroids(const rabitq_index* X, float* out) {
+  if (!X || !out) return fail(RABITQ_EINVAL, "rabitq_get_centroids: null pointer");
+  RBQ_CUDA(cudaMemcpy(out, X->centroids, sizeof(float) * X->K * X->d, cudaMemcpyDeviceToHost));
+  return RABITQ_OK;
+}
+
+int rabitq_get_rotation(const rabitq_index* X, double* out) {
+  if (!X || !out) return fail(RABITQ_EINVAL, "rabitq_get_rotation: null pointer");
+  RBQ_CUDA(cudaMemcpy(out, X->P64, sizeof(double) * X->dpad * X->dpad, cudaMemcpyDeviceToHost));
+  return RABITQ_OK;
+}
+
+int rabitq_get_assign(const rabitq_index* X, int32_t* cluster) {
+  if (!X || !cluster) return fail(RABITQ_EINVAL, "rabitq_get_assign: null pointer");
+  RBQ_CUDA(cudaMemcpy(cluster, X->assign, sizeof(int32_t) * X->n, cudaMemcpyDeviceToHost));
+  return RABITQ_OK;
+}
+
+int rabitq_get_buckets(const rabitq_index* X, int32_t* offsets, int32_t* ids) {
+  if (!X) return fail(RABITQ_EINVAL, "rabitq_get_buckets: index is null");
+  if (offsets)
+    RBQ_CUDA(cudaMemcpy(offsets, X->bucket_off, sizeof(int32_t) * (X->K + 1),
+                        cudaMemcpyDeviceToHost));
+  if (ids) RBQ_CUDA(cudaMemcpy(ids, X->perm, sizeof(int32_t) * X->n, cudaMemcpyDeviceToHost));
+  return RABITQ_OK;
+}
+
+int rabitq_get_codes(const rabitq_index* X, uint64_t* out) {
+  if (!X || !out) return fail(RABITQ_EINVAL, "rabitq_get_codes: null pointer");
+  std::vector<uint64_t> b((size_t)X->n * X->W);
+  std::vector<int32_t> perm(X->n);
+  RBQ_CUDA(cudaMemcpy(b.data(), X->codes, sizeof(uint64_t) * b.size(), cudaMemcpyDeviceToHost));
+  RBQ_CUDA(cudaMemcpy(perm.data(), X->perm, sizeof(int32_t) * X->n, cudaMemcpyDeviceToHost));
+  for (int64_t p = 0; p < X->n; ++p)
+    std::memcpy(out + (size_t)perm[p] * X->W, b.data() + (size_t)p * X->W, sizeof(uint64_t) * X->W);
+  return RABITQ_OK;
+}
+
+int rabitq_get_factors(const rabitq_index* X, float* out) {
+  if (!X || !out) return fail(RABITQ_EINVAL, "rabitq_get_factors: null pointer");
+  std::vector<float4> b(X->n);
+  std::vector<int32_t> perm(X->n);
+  RBQ_CUDA(cudaMemcpy(b.data(), X->factors, sizeof(float4) * X->n, cudaMemcpyDeviceToHost));
+  RBQ_CUDA(cudaMemcpy(perm.data(), X->perm, sizeof(int32_t) * X->n, cudaMemcpyDeviceToHost));
+  for (int64_t p = 0; p < X->n; ++p) {
+    float* o = out + (size_t)perm[p] * 4;
+    o[0] = b[p].x;
+    o[1] = b[p].y;
+    o[2] = b[p].z;
+    o[3] = b[p].w;
+  }
+  return RABITQ_OK;
+}
+
+int rabitq_sample_rotation(uint64_t seed, int32_t d_pad, double* out) {
+  g_err.clear();
+  if (!out) return fail(RABITQ_EINVAL, "rabitq_sample_rotation: out is null");
+  if (d_pad < 2 || d_pad > 4096 || d_pad % 2)
+    return fail(RABITQ_EINVAL, "rabitq_sample_rotation: need even 2 <= d_pad <= 4096");
+  double* P = nullptr;
+  float* P32 = nullptr;
+  RBQ_CHECK(dev_alloc(&P, (size_t)d_pad * d_pad));
+  int st = dev_alloc(&P32, (size_t)d_pad * d_pad);
+  if (st == RABITQ_OK) st = sample_rotation_dev(seed, d_pad, P, P32, nullptr);
+  if (st == RABITQ_OK) {
+    cudaError_t e = cudaMemcpy(out, P, sizeof(double) * d_pad * d_pad, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = fail(RABITQ_ECUDA, cudaGetErrorString(e));
+  }
+  cudaFree(P);
+  cudaFree(P32);
+  return st;
+}
+
+int rabitq_index_save(const rabitq_index* X, const char* path) {
+  g_err.clear();
+  if (!X || !path) return fail(RABITQ_EINVAL, "rabitq_index_save: null pointer");
+  struct Part {
+    const void* dev;
+    size_t bytes;
+  };
+  const Part parts[] = {
+      {X->data_b, sizeof(float) * X->n * X->d},     {X->codes, sizeof(uint64_t) * X->n * X->W},
+      {X->factors, sizeof(float4) * X->n},          {X->perm, sizeof(int32_t) * X->n},
+      {X->bucket_off, sizeof(int32_t) * (X->K + 1)}, {X->assign, sizeof(int32_t) * X->n},
+      {X->centroids, sizeof(float) * X->K * X->d},  {X->ptc, sizeof(float) * X->K * X->dpad},
+      {X->P64, sizeof(double) * X->dpad * X->dpad}};
+  std::vector<std::vector<uint8_t>> host;
+  FileHeader h;
+  std::memset(&h, 0, sizeof h);
+  std::memcpy(h.magic, "RABITQ\0\1", 8);
+  h.version = 1;
+  h.n = X->n;
+  h.d = X->d;
+  h.dpad = X->dpad;
+  h.K = X->K;
+  h.W = X->W;
+  uint32_t crc = 0;
+  for (const Part& p : parts) {
+    host.emplace_back(p.bytes);
+    RBQ_CUDA(cudaMemcpy(host.back().data(), p.dev, p.bytes, cudaMemcpyDeviceToHost));
+    crc = crc32_update(crc, host.back().data(), p.bytes);
+    h.payload_bytes += p.bytes;
+  }
+  h.payload_crc = crc;
+  h.header_crc = crc32_update(0, &h, offsetof(FileHeader, header_crc));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(RABITQ_EIO, std::string("cannot open for writing: ") + path);
+  bool ok = std::fwrite(&h, sizeof h, 1, f) == 1;
+  for (auto& b : host) ok = ok && std::fwrite(b.data(), 1, b.size(), f) == b.size();
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(RABITQ_EIO, std::string("write failed: ") + path);
+  return RABITQ_OK;
+}
+
+int rabitq_index_load(const char* path, const rabitq_build_opts* opts, rabitq_index** out) {
+  g_err.clear();
+  (void)opts;
+  if (!path || !out) return fail(RABITQ_EINVAL, "rabitq_index_load: null pointer");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(RABITQ_EIO, std::string("cannot open: ") + path);
+  FileHeader h;
+  if (std::fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, "RABITQ\0\1", 8) != 0 ||
+      h.header_crc != crc32_update(0, &h, offsetof(FileHeader, header_crc)) || h.version != 1 ||
+      h.n < 1 || h.d < 1 || h.K < 1 || h.dpad < h.d || h.dpad % 64 || h.W != h.dpad / 64) {
+    std::fclose(f);
+    return fail(RABITQ_EIO, std::string("not a valid index file (header): ") + path);
+  }
+  auto* X = new rabitq_index();
+  X->n = h.n;
+  X->d = h.d;
+  X->dpad = h.dpad;
+  X->K = h.K;
+  X->W = h.W;
+  cudaGetDevice(&X->device);
+  int st = alloc_index_arrays(X);
+  struct Part {
+    void* dev;
+    size_t bytes;
+  };
+  const Part parts[] = {
+      {X->data_b, sizeof(float) * X->n * X->d},     {X->codes, sizeof(uint64_t) * X->n * X->W},
+      {X->factors, sizeof(float4) * X->n},          {X->perm, sizeof(int32_t) * X->n},
+      {X->bucket_off, sizeof(int32_t) * (X->K + 1)}, {X->assign, sizeof(int32_t) * X->n},
+      {X->centroids, sizeof(float) * X->K * X->d},  {X->ptc, sizeof(float) * X->K * X->dpad},
+      {X->P64, sizeof(double) * X->dpad * X->dpad}};
+  uint32_t crc = 0;
+  uint64_t total = 0;
+  std::vector<uint8_t> buf;
+  for (const Part& p : parts) {
+    if (st != RABITQ_OK) break;
+    buf.resize(p.bytes);
+    if (std::fread(buf.data(), 1, p.bytes, f) != p.bytes) {
+      st = fail(RABITQ_EIO, std::string("truncated index file: ") + path);
+      break;
+    }
+    crc = crc32_update(crc, buf.data(), p.bytes);
+    total += p.bytes;
+    if (cudaMemcpy(p.dev, buf.data(), p.bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+      st = fail(RABITQ_ECUDA, "copy of the index to the device failed");
+  }
+  std::fclose(f);
+  if (st == RABITQ_OK && (crc != h.payload_crc || total != h.payload_bytes))
+    st = fail(RABITQ_EIO, std::string("index file checksum mismatch: ") + path);
+  if (st == RABITQ_OK) st = transpose_f32(X->centroids, X->K, X->d, X->centroids_t, nullptr);
+  if (st == RABITQ_OK) {
+    const int64_t tot = (int64_t)X->dpad * X->dpad;
+    std::vector<double> p64(tot);
+    std::vector<float> p32(tot);
+    cudaMemcpy(p64.data(), X->P64, sizeof(double) * tot, cudaMemcpyDeviceToHost);
+    for (int64_t i = 0; i < tot; ++i) p32[i] = (float)p64[i];
+    if (cudaMemcpy(X->P32, p32.data(), sizeof(float) * tot, cudaMemcpyHostToDevice) != cudaSuccess)
+      st = fail(RABITQ_ECUDA, "copy of P to the device failed");
+  }
+  if (st == RABITQ_OK) st = max_bucket_size(X, nullptr);
+  if (st != RABITQ_OK) {
+    free_index_arrays(X);
+    delete X;
+    return st;
+  }
+  *out = X;
+  return RABITQ_OK;
+}
+
+void rabitq_free(rabitq_index* X) {
+  if (!X) return;
+  cudaDeviceSynchronize();
+  free_index_arrays(X);
+  delete X;
+}
+
+}  // extern "C"

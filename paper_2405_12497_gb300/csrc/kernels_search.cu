@@ -1,0 +1,616 @@
+// kernels_search.cu -- query phase (Alg. 2 of the paper with the IVF probing
+// and error-bound re-ranking of §4).
+//
+// Stages per batch of queries:
+//   1. canonical squared distances to every centroid (kernels_gemm.cu);
+//   2. probe selection: the nprobe nearest centroids by (distance, id);
+//   3. query rotation P^{-1}[q_r; 0] (kernels_gemm.cu, FP32 canonical);
+//   4. one persistent fused kernel, a CTA per query at a time: randomized
+//      B_q-bit quantization of q' per probed cluster (§3.3.1), bucket scan
+//      with the bit-plane popcount form of <x_b, q_u> (§3.3.2), the unbiased
+//      estimator and its error bound (Theorem 3.2), the k-th smallest upper
+//      bound tau, the survivors LB <= tau, their exact distances and the
+//      top-k by (distance, id).
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace rbq {
+namespace {
+
+constexpr int kThreads = 256;
+
+// ------------------------------------------------------------ selection
+// Top-nsel of a row of K non-negative distances by (distance, id): radix
+// select of the nsel-th smallest key, collection of everything below it plus
+// the lowest ids among its ties, then a bitonic sort of the selection.
+__global__ void __launch_bounds__(kThreads) select_kernel(
+    const float* __restrict__ CD, int K, int nprobe, const int32_t* __restrict__ nprobe_q,
+    int sort_n, int32_t* __restrict__ out_ids, float* __restrict__ out_dist) {
+  extern __shared__ unsigned long long sel[];  // sort_n entries
+  __shared__ int hist[256];
+  __shared__ uint32_t s_prefix, s_mask;
+  __shared__ int s_remaining, s_less, s_tie_base;
+  const int q = blockIdx.x;
+  const float* row = CD + (int64_t)q * K;
+  int nsel = nprobe;
+  if (nprobe_q) nsel = min(max(nprobe_q[q], 1), nprobe);
+  if (threadIdx.x == 0) {
+    s_prefix = 0;
+    s_mask = 0;
+    s_remaining = nsel;
+    s_less = 0;
+    s_tie_base = 0;
+  }
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint32_t prefix = s_prefix, mask = s_mask;
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+      const uint32_t key = float_key(row[c]);
+      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int rem = s_remaining, b = 0;
+      while (b < 255 && hist[b] < rem) {
+        rem -= hist[b];
+        ++b;
+      }
+      s_remaining = rem;
+      s_prefix = prefix | ((uint32_t)b << shift);
+      s_mask = mask | (255u << shift);
+    }
+    __syncthreads();
+  }
+  const uint32_t T = s_prefix;
+  const int need_ties = s_remaining;  // ties with key T to take, lowest ids first
+  for (int i = threadIdx.x; i < sort_n; i += blockDim.x) sel[i] = ~0ull;
+  __syncthreads();
+  const int n_less = nsel - need_ties;
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    const uint32_t key = float_key(row[c]);
+    if (key < T) sel[atomicAdd(&s_less, 1)] = ((unsigned long long)key << 32) | (uint32_t)c;
+  }
+  __syncthreads();
+  // ties in ascending id order, chunk by chunk
+  __shared__ int warp_cnt[kThreads / 32];
+  for (int c0 = 0; c0 < K; c0 += blockDim.x) {
+    if (s_tie_base >= need_ties) break;
+    const int c = c0 + threadIdx.x;
+    const bool tie = (c < K) && float_key(row[c]) == T;
+    const unsigned b = __ballot_sync(kFull, tie);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_cnt[wid] = __popc(b);
+    __syncthreads();
+    int before = s_tie_base;
+    for (int w = 0; w < wid; ++w) before += warp_cnt[w];
+    const int rank = before + __popc(b & ((1u << lane) - 1u));
+    if (tie && rank < need_ties)
+      sel[n_less + rank] = ((unsigned long long)T << 32) | (uint32_t)c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_cnt[w];
+      s_tie_base += tot;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  block_bitonic_sort_u64(sel, sort_n);
+  for (int j = threadIdx.x; j < nprobe; j += blockDim.x) {
+    const bool ok = j < nsel;
+    out_ids[(int64_t)q * nprobe + j] = ok ? (int32_t)(sel[j] & 0xffffffffu) : -1;
+    out_dist[(int64_t)q * nprobe + j] = ok ? key_float((uint32_t)(sel[j] >> 32))
+                                           : __int_as_float(0x7f800000);
+  }
+}
+
+// ------------------------------------------------------ fused query kernel
+struct FusedParams {
+  const float* queries;     // nq x d
+  const float* rq;          // nq x dpad
+  const int32_t* probe_ids; // nq x nprobe
+  const float* probe_dist;  // nq x nprobe
+  const int32_t* nprobe_q;  // nq or null
+  const float* ptc;         // K x dpad
+  const uint64_t* codes;    // n x W (bucket order)
+  const float4* factors;    // n (bucket order)
+  const float* data_b;      // n x d (bucket order)
+  const int32_t* perm;      // n
+  const int32_t* bucket_off;
+  int64_t nq, q_offset;
+  int d, dpad, W, bq, k, nprobe, pch, cu, ct;
+  float eps0;
+  uint64_t seed;
+  int cand_cap;
+  int2* cand;               // gridDim.x x cand_cap
+  int64_t* out_ids;
+  float* out_dist;
+  int* err;
+  rabitq_trace tr;
+};
+
+struct FusedSmem {
+  uint64_t* planes;  // pch x bq x W
+  float4* pmeta;     // pch: A, B, E, nq2
+  int* psum;         // pch
+  int* pbeg;         // pch
+  int* pref;         // pch + 1
+  float* qv;         // d
+  uint32_t* ubk;     // cu
+  unsigned long long* topk;  // ct
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline size_t fused_smem_bytes(int pch, int bq, int W, int d, int cu, int ct,
+                                                   size_t* off /* 8 entries or null */) {
+  size_t o = 0, offs[8];
+  offs[0] = o; o = align_up(o + sizeof(uint64_t) * pch * bq * W, 16);
+  offs[1] = o; o = align_up(o + sizeof(float4) * pch, 16);
+  offs[2] = o; o = align_up(o + sizeof(int) * pch, 16);
+  offs[3] = o; o = align_up(o + sizeof(int) * pch, 16);
+  offs[4] = o; o = align_up(o + sizeof(int) * (pch + 1), 16);
+  offs[5] = o; o = align_up(o + sizeof(float) * d, 16);
+  offs[6] = o; o = align_up(o + sizeof(uint32_t) * cu, 16);
+  offs[7] = o; o = align_up(o + sizeof(unsigned long long) * ct, 16);
+  if (off)
+    for (int i = 0; i < 8; ++i) off[i] = offs[i];
+  return o;
+}
+
+// Quantize q' for one probed cluster with one warp (§3.3.1). Lane l holds
+// elements k = 128 i + 4 l + r (r = 0..3), so the four u_k of one Philox call
+// (counter k/4) belong to one lane.
+__device__ __forceinline__ void quantize_probe(const FusedParams& P, const FusedSmem& S, int64_t q,
+                                               int j, int jg, int c, float nq2) {
+  const int lane = threadIdx.x & 31;
+  const int dpad = P.dpad, W = P.W, bq = P.bq;
+  const int nblk = (dpad + 127) >> 7;
+  const float* rq = P.rq + q * dpad;
+  const float* pc = P.ptc + (int64_t)c * dpad;
+  // pass 1: v_l = min qd, v_r = max qd with qd = rq - P^T c
+  float vl = __int_as_float(0x7f800000), vr = __int_as_float(0xff800000);
+  for (int kk = lane; kk < dpad; kk += 32) {
+    const float v = __fsub_rn(rq[kk], pc[kk]);
+    vl = fminf(vl, v);
+    vr = fmaxf(vr, v);
+  }
+  vl = warp_min_f(vl);
+  vr = warp_max_f(vr);
+  const int qmax = (1 << bq) - 1;
+  const float delta = __fdiv_rn(__fsub_rn(vr, vl), (float)qmax);
+  const uint64_t gq = (uint64_t)(P.q_offset + q);
+  int sum = 0;
+  uint64_t* planes = S.planes + (size_t)j * bq * W;
+  for (int i = 0; i < nblk; ++i) {
+    const int k0 = 128 * i + 4 * lane;
+    int qu[4] = {0, 0, 0, 0};
+    if (delta > 0.0f && k0 < dpad) {
+      float qd[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) qd[r] = (k0 + r < dpad) ? __fsub_rn(rq[k0 + r], pc[k0 + r]) : 0.0f;
+      const U4 w = philox4x32_10(P.seed, (uint32_t)(k0 >> 2), (uint32_t)gq, (uint32_t)c, kTagQuant);
+      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (k0 + r < dpad) {
+          const float u = __fmul_rn(__uint2float_rn(ws[r] >> 8), 0x1.0p-24f);
+          const float x = __fdiv_rn(__fsub_rn(qd[r], vl), delta);
+          int v = __float2int_rd(__fadd_rn(x, u));
+          qu[r] = v > qmax ? qmax : v;
+        }
+      }
+    }
+    sum += qu[0] + qu[1] + qu[2] + qu[3];
+    // bit-planes: nibble of lane l sits at bits 4l..4l+3 of the 128-bit block
+    for (int b = 0; b < bq; ++b) {
+      const uint32_t nib = ((qu[0] >> b) & 1) | (((qu[1] >> b) & 1) << 1) |
+                           (((qu[2] >> b) & 1) << 2) | (((qu[3] >> b) & 1) << 3);
+      const uint32_t part = nib << (4 * (lane & 7));
+      const uint32_t q0 = __reduce_or_sync(kFull, lane < 8 ? part : 0u);
+      const uint32_t q1 = __reduce_or_sync(kFull, (lane >= 8 && lane < 16) ? part : 0u);
+      const uint32_t q2 = __reduce_or_sync(kFull, (lane >= 16 && lane < 24) ? part : 0u);
+      const uint32_t q3 = __reduce_or_sync(kFull, lane >= 24 ? part : 0u);
+      if (lane == 0) {
+        const int w0 = 2 * i;
+        if (w0 < W) planes[b * W + w0] = ((uint64_t)q1 << 32) | q0;
+        if (w0 + 1 < W) planes[b * W + w0 + 1] = ((uint64_t)q3 << 32) | q2;
+      }
+    }
+  }
+  sum = warp_sum_i(sum);
+  if (lane == 0) {
+    const float sqd = __fsqrt_rn((float)dpad);
+    const float keps = __fdiv_rn(__fmul_rn(2.0f, P.eps0), __fsqrt_rn((float)(dpad - 1)));
+    const float n_q = __fsqrt_rn(nq2);
+    const float4 m = make_float4(__fdiv_rn(delta, sqd), __fdiv_rn(vl, sqd), __fmul_rn(n_q, keps),
+                                 nq2);
+    S.pmeta[j] = m;
+    S.psum[j] = sum;
+    S.pbeg[j] = P.bucket_off[c];
+    S.pref[j + 1] = P.bucket_off[c + 1] - P.bucket_off[c];  // length; prefix-summed later
+    if (P.tr.sum_qu) P.tr.sum_qu[q * P.nprobe + jg] = sum;
+    if (P.tr.meta) {
+      float* tm = P.tr.meta + (q * P.nprobe + jg) * 4;
+      tm[0] = m.x; tm[1] = m.y; tm[2] = m.z; tm[3] = m.w;
+    }
+  }
+  __syncwarp();
+  if (P.tr.planes) {
+    uint64_t* tp = P.tr.planes + (q * P.nprobe + jg) * (int64_t)bq * W;
+    for (int t = lane; t < bq * W; t += 32) tp[t] = planes[t];
+  }
+}
+
+// Keep the k smallest UB keys: sort the buffer, truncate, return tau'.
+__device__ __forceinline__ void compact_ub(const FusedSmem& S, int cu, int k, int* ub_cnt,
+                                          float* tau) {
+  for (int i = *ub_cnt + threadIdx.x; i < cu; i += blockDim.x) S.ubk[i] = 0xffffffffu;
+  __syncthreads();
+  block_bitonic_sort_u32(S.ubk, cu);
+  if (threadIdx.x == 0) {
+    const int c = *ub_cnt;
+    if (c >= k) {
+      *ub_cnt = k;
+      *tau = key_float(S.ubk[k - 1]);
+    }
+  }
+  __syncthreads();
+}
+
+// Drop candidates whose lower bound exceeds tau' (in place, order kept).
+__device__ __forceinline__ void compact_cand(int2* cand, int* cnt, int cap, float tau,
+                                            int* scratch) {
+  const int n = min(*cnt, cap);
+  int out = 0;
+  __syncthreads();
+  for (int b = 0; b < n; b += blockDim.x) {
+    const int i = b + threadIdx.x;
+    int2 e = make_int2(0, 0);
+    bool keep = false;
+    if (i < n) {
+      e = cand[i];
+      keep = __int_as_float(e.y) <= tau;
+    }
+    const unsigned bal = __ballot_sync(kFull, keep);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) scratch[wid] = __popc(bal);
+    __syncthreads();
+    int before = out;
+    int tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      if (w < wid) before += scratch[w];
+      tot += scratch[w];
+    }
+    if (keep) cand[before + __popc(bal & ((1u << lane) - 1u))] = e;
+    out += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *cnt = out;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_ub_cnt, s_cand_cnt, s_top_cnt, s_overflow;
+  __shared__ float s_tau;
+  __shared__ int s_scratch[kThreads / 32];
+  size_t off[8];
+  fused_smem_bytes(P.pch, P.bq, P.W, P.d, P.cu, P.ct, off);
+  FusedSmem S;
+  S.planes = reinterpret_cast<uint64_t*>(smem + off[0]);
+  S.pmeta = reinterpret_cast<float4*>(smem + off[1]);
+  S.psum = reinterpret_cast<int*>(smem + off[2]);
+  S.pbeg = reinterpret_cast<int*>(smem + off[3]);
+  S.pref = reinterpret_cast<int*>(smem + off[4]);
+  S.qv = reinterpret_cast<float*>(smem + off[5]);
+  S.ubk = reinterpret_cast<uint32_t*>(smem + off[6]);
+  S.topk = reinterpret_cast<unsigned long long*>(smem + off[7]);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+  const int W = P.W, bq = P.bq, k = P.k;
+  int2* cand = P.cand + (int64_t)blockIdx.x * P.cand_cap;
+
+  for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
+    int np = P.nprobe;
+    if (P.nprobe_q) np = min(max(P.nprobe_q[q], 1), P.nprobe);
+    for (int i = tid; i < P.d; i += blockDim.x) S.qv[i] = P.queries[q * P.d + i];
+    if (tid == 0) {
+      s_ub_cnt = 0;
+      s_cand_cnt = 0;
+      s_top_cnt = 0;
+      s_overflow = 0;
+      s_tau = __int_as_float(0x7f800000);
+    }
+    __syncthreads();
+    int pairs_done = 0;
+    for (int pc0 = 0; pc0 < np; pc0 += P.pch) {
+      const int npc = min(P.pch, np - pc0);
+      for (int j = wid; j < npc; j += nwarps) {
+        const int jg = pc0 + j;
+        const int c = P.probe_ids[q * P.nprobe + jg];
+        quantize_probe(P, S, q, j, jg, c, P.probe_dist[q * P.nprobe + jg]);
+      }
+      __syncthreads();
+      if (wid == 0) {  // inclusive prefix of the bucket lengths, 32 at a time
+        int carry = 0;
+        if (lane == 0) S.pref[0] = 0;
+        for (int j0 = 0; j0 < npc; j0 += 32) {
+          const int jj = j0 + lane;
+          int v = (jj < npc) ? S.pref[jj + 1] : 0;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += y;
+          }
+          if (jj < npc) S.pref[jj + 1] = carry + v;
+          carry += __shfl_sync(kFull, v, 31);
+        }
+      }
+      __syncthreads();
+      const int total = S.pref[npc];
+      int j = 0;
+      for (int base = 0; base < total; base += blockDim.x) {
+        const int t = base + tid;
+        if (t < total) {
+          while (S.pref[j + 1] <= t) ++j;
+          const int64_t pos = (int64_t)S.pbeg[j] + (t - S.pref[j]);
+          const uint64_t* code = P.codes + pos * W;
+          const uint64_t* pl = S.planes + (size_t)j * bq * W;
+          int ip = 0;
+          for (int b = 0; b < bq; ++b) {
+            int pb = 0;
+            for (int w = 0; w < W; ++w) pb += __popcll(code[w] & pl[b * W + w]);
+            ip += pb << b;
+          }
+          const float4 f = P.factors[pos];
+          const float4 m = S.pmeta[j];
+          const float t1 = (float)(2 * ip - S.psum[j]);
+          const float xq = __fadd_rn(__fmul_rn(m.x, t1), __fmul_rn(m.y, f.w));
+          const float dist = __fsub_rn(__fadd_rn(f.x, m.w), __fmul_rn(f.y, xq));
+          const float e = __fmul_rn(f.z, m.z);
+          const float lb = __fsub_rn(dist, e), ub = __fadd_rn(dist, e);
+          const float tau = s_tau;
+          if (ub < tau) S.ubk[atomicAdd(&s_ub_cnt, 1)] = float_key(ub);
+          if (lb <= tau) {
+            const int slot = atomicAdd(&s_cand_cnt, 1);
+            if (slot < P.cand_cap)
+              cand[slot] = make_int2((int)pos, __float_as_int(lb));
+            else
+              s_overflow = 1;
+          }
+          if (P.tr.pair_id) {
+            const int64_t tt = pairs_done + t;
+            if (tt < P.tr.pair_cap) {
+              const int64_t o = q * P.tr.pair_cap + tt;
+              P.tr.pair_id[o] = P.perm[pos];
+              P.tr.pair_ip[o] = ip;
+              P.tr.pair_est[3 * o] = dist;
+              P.tr.pair_est[3 * o + 1] = lb;
+              P.tr.pair_est[3 * o + 2] = ub;
+            }
+          }
+        }
+        __syncthreads();
+        if (s_ub_cnt > P.cu - (int)blockDim.x) compact_ub(S, P.cu, k, &s_ub_cnt, &s_tau);
+        if (s_cand_cnt > P.cand_cap - (int)blockDim.x) {
+          compact_cand(cand, &s_cand_cnt, P.cand_cap, s_tau, s_scratch);
+          if (s_cand_cnt > P.cand_cap - (int)blockDim.x && tid == 0) s_overflow = 1;
+          __syncthreads();
+        }
+        if (s_overflow) break;
+      }
+      pairs_done += total;
+      __syncthreads();
+      if (s_overflow) break;
+    }
+    // final tau = k-th smallest upper bound
+    compact_ub(S, P.cu, k, &s_ub_cnt, &s_tau);
+    if (tid == 0 && s_ub_cnt < k) s_tau = __int_as_float(0x7f800000);
+    __syncthreads();
+    const float tau = s_tau;
+    if (tid == 0) {
+      if (s_overflow) atomicExch(P.err, 1);
+      if (P.tr.n_pairs) P.tr.n_pairs[q] = pairs_done;
+      if (P.tr.tau) P.tr.tau[q] = tau;
+    }
+    // survivors: exact distance, top-k by (distance, id)
+    const int nc = min(s_cand_cnt, P.cand_cap);
+    __shared__ int s_surv;
+    if (tid == 0) s_surv = 0;
+    __syncthreads();
+    for (int b = 0; b < nc; b += blockDim.x) {
+      const int i = b + tid;
+      if (i < nc) {
+        const int2 e = cand[i];
+        if (__int_as_float(e.y) <= tau) {
+          const float* x = P.data_b + (int64_t)e.x * P.d;
+          float s = 0.0f;
+          for (int dd = 0; dd < P.d; ++dd) {
+            const float t = __fsub_rn(S.qv[dd], x[dd]);
+            s = __fmaf_rn(t, t, s);
+          }
+          const int id = P.perm[e.x];
+          S.topk[atomicAdd(&s_top_cnt, 1)] =
+              ((unsigned long long)float_key(s) << 32) | (uint32_t)id;
+          const int si = atomicAdd(&s_surv, 1);
+          if (P.tr.surv_ids && si < P.tr.surv_cap) P.tr.surv_ids[q * P.tr.surv_cap + si] = id;
+        }
+      }
+      __syncthreads();
+      if (s_top_cnt > P.ct - (int)blockDim.x) {
+        for (int i2 = s_top_cnt + tid; i2 < P.ct; i2 += blockDim.x) S.topk[i2] = ~0ull;
+        __syncthreads();
+        block_bitonic_sort_u64(S.topk, P.ct);
+        if (tid == 0) s_top_cnt = min(s_top_cnt, k);
+        __syncthreads();
+      }
+    }
+    for (int i2 = s_top_cnt + tid; i2 < P.ct; i2 += blockDim.x) S.topk[i2] = ~0ull;
+    __syncthreads();
+    block_bitonic_sort_u64(S.topk, P.ct);
+    const int got = min(s_top_cnt, k);
+    for (int j2 = tid; j2 < k; j2 += blockDim.x) {
+      const bool ok = j2 < got;
+      P.out_ids[q * k + j2] = ok ? (int64_t)(S.topk[j2] & 0xffffffffu) : -1;
+      P.out_dist[q * k + j2] =
+          ok ? key_float((uint32_t)(S.topk[j2] >> 32)) : __int_as_float(0x7f800000);
+    }
+    if (tid == 0 && P.tr.n_surv) P.tr.n_surv[q] = s_surv;
+    __syncthreads();
+  }
+}
+
+int pow2_at_least(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+int search_dev(const SearchArgs& a, cudaStream_t s) {
+  const rabitq_index* X = a.X;
+  const int K = X->K, d = X->d, dpad = X->dpad, W = X->W;
+  const int nprobe = std::min(a.nprobe, K);
+  if (a.nq == 0) return RABITQ_OK;
+  int dev = 0, sms = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
+  RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+  // fused-kernel shape
+  const int plane_bytes = a.bq * W * 8;
+  int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
+  const int cu = std::max(1024, pow2_at_least(a.k + kThreads));
+  const int ct = std::max(512, pow2_at_least(a.k + kThreads));
+  const size_t smem = fused_smem_bytes(pch, a.bq, W, d, cu, ct, nullptr);
+  RBQ_CUDA(cudaFuncSetAttribute(fused_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  int per_sm = 0;
+  RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_search_kernel, kThreads,
+                                                         smem));
+  per_sm = std::max(per_sm, 1);
+
+  // query chunks bound the centroid-distance scratch (<= 256 Mi floats)
+  const int64_t qchunk = std::max<int64_t>(1, std::min<int64_t>(a.nq, (int64_t(1) << 28) / K));
+  const int64_t grid = std::min<int64_t>(qchunk, (int64_t)sms * per_sm);
+  DevBuf cd, rq, pid, pdist, cand, err;
+  RBQ_CHECK(cd.alloc(sizeof(float) * qchunk * K, s));
+  RBQ_CHECK(rq.alloc(sizeof(float) * qchunk * dpad, s));
+  RBQ_CHECK(pid.alloc(sizeof(int32_t) * qchunk * nprobe, s));
+  RBQ_CHECK(pdist.alloc(sizeof(float) * qchunk * nprobe, s));
+  RBQ_CHECK(cand.alloc(sizeof(int2) * grid * a.cand_cap, s));
+  RBQ_CHECK(err.alloc(sizeof(int), s));
+  RBQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+
+  cudaEvent_t ev[5] = {};
+  const bool timing = a.stage_ms != nullptr;
+  float acc_ms[4] = {0, 0, 0, 0};
+  if (timing)
+    for (auto& e : ev) RBQ_CUDA(cudaEventCreate(&e));
+
+  const int sort_n = pow2_at_least(nprobe);
+  const size_t sel_smem = sizeof(unsigned long long) * sort_n;
+  RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sel_smem));
+  for (int64_t q0 = 0; q0 < a.nq; q0 += qchunk) {
+    const int64_t m = std::min(qchunk, a.nq - q0);
+    const float* Q = a.queries + q0 * d;
+    if (timing) RBQ_CUDA(cudaEventRecord(ev[0], s));
+    RBQ_CHECK(gemm_canon(kSqDist, Q, d, nullptr, nullptr, 0, nullptr, X->centroids_t, K,
+                         cd.as<float>(), K, m, K, d, s));
+    if (timing) RBQ_CUDA(cudaEventRecord(ev[1], s));
+    int32_t* probe_ids = a.trace && a.trace->probe_ids ? a.trace->probe_ids + q0 * nprobe
+                                                       : pid.as<int32_t>();
+    float* probe_dist = a.trace && a.trace->probe_dist ? a.trace->probe_dist + q0 * nprobe
+                                                       : pdist.as<float>();
+    select_kernel<<<(unsigned)m, kThreads, sel_smem, s>>>(
+        cd.as<float>(), K, nprobe, a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr,
+        sort_n, probe_ids, probe_dist);
+    RBQ_CUDA(cudaGetLastError());
+    if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
+    float* rqp = a.trace && a.trace->rq ? a.trace->rq + q0 * dpad : rq.as<float>();
+    RBQ_CHECK(gemm_canon(kDot, Q, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rqp, dpad, m,
+                         dpad, d, s));
+    if (timing) RBQ_CUDA(cudaEventRecord(ev[3], s));
+    FusedParams P;
+    std::memset(&P, 0, sizeof P);
+    P.queries = Q;
+    P.rq = rqp;
+    P.probe_ids = probe_ids;
+    P.probe_dist = probe_dist;
+    P.nprobe_q = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
+    P.ptc = X->ptc;
+    P.codes = X->codes;
+    P.factors = X->factors;
+    P.data_b = X->data_b;
+    P.perm = X->perm;
+    P.bucket_off = X->bucket_off;
+    P.nq = m;
+    P.q_offset = q0;
+    P.d = d;
+    P.dpad = dpad;
+    P.W = W;
+    P.bq = a.bq;
+    P.k = a.k;
+    P.nprobe = nprobe;
+    P.pch = pch;
+    P.cu = cu;
+    P.ct = ct;
+    P.eps0 = a.eps0;
+    P.seed = a.seed;
+    P.cand_cap = a.cand_cap;
+    P.cand = cand.as<int2>();
+    P.out_ids = a.out_ids + q0 * a.k;
+    P.out_dist = a.out_dist + q0 * a.k;
+    P.err = err.as<int>();
+    if (a.trace) {
+      const rabitq_trace& T = *a.trace;
+      P.tr = T;
+      // per-query trace arrays are offset to this chunk
+      P.tr.probe_ids = nullptr;
+      P.tr.probe_dist = nullptr;
+      P.tr.rq = nullptr;
+      if (T.planes) P.tr.planes = T.planes + q0 * nprobe * a.bq * W;
+      if (T.sum_qu) P.tr.sum_qu = T.sum_qu + q0 * nprobe;
+      if (T.meta) P.tr.meta = T.meta + q0 * nprobe * 4;
+      if (T.n_pairs) P.tr.n_pairs = T.n_pairs + q0;
+      if (T.pair_id) {
+        P.tr.pair_id = T.pair_id + q0 * T.pair_cap;
+        P.tr.pair_ip = T.pair_ip + q0 * T.pair_cap;
+        P.tr.pair_est = T.pair_est + q0 * T.pair_cap * 3;
+      }
+      if (T.tau) P.tr.tau = T.tau + q0;
+      if (T.n_surv) P.tr.n_surv = T.n_surv + q0;
+      if (T.surv_ids) P.tr.surv_ids = T.surv_ids + q0 * T.surv_cap;
+    }
+    const unsigned g = (unsigned)std::min<int64_t>(m, grid);
+    fused_search_kernel<<<g, kThreads, smem, s>>>(P);
+    RBQ_CUDA(cudaGetLastError());
+    if (timing) {
+      RBQ_CUDA(cudaEventRecord(ev[4], s));
+      RBQ_CUDA(cudaEventSynchronize(ev[4]));
+      for (int i = 0; i < 4; ++i) {
+        float t = 0;
+        RBQ_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+        acc_ms[i] += t;
+      }
+    }
+  }
+  int h_err = 0;
+  RBQ_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RBQ_CUDA(cudaStreamSynchronize(s));
+  if (timing) {
+    for (int i = 0; i < 4; ++i) a.stage_ms[i] = acc_ms[i];
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  if (h_err)
+    return fail(RABITQ_EOVERFLOW,
+                "a query's candidate list exceeded max_candidates; raise max_candidates");
+  return RABITQ_OK;
+}
+
+}  // namespace rbq

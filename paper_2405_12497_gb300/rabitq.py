@@ -1,0 +1,327 @@
+"""Thin ctypes binding of librabitq.so (include/rabitq.h).
+
+Argument marshalling only: every step of the index build and of the search
+runs in the library's CUDA kernels. Host arrays are numpy; device arrays are
+torch CUDA tensors (torch is used for device memory and streams only). If the
+library cannot be loaded this module raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "librabitq.so")
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EIO, EUNSUPPORTED, EOVERFLOW = 0, -1, -2, -3, -4, -5, -6, -7
+ROT_FP32, ROT_TF32, ROT_BF16 = 0, 1, 2
+SCAN_AUTO, SCAN_POPC, SCAN_TC = 0, 1, 2
+
+# Every symbol include/rabitq.h declares.
+EXPORTS = (
+    "rabitq_build_opts_default", "rabitq_search_opts_default", "rabitq_build", "rabitq_search",
+    "rabitq_search_trace", "rabitq_last_stats", "rabitq_index_info", "rabitq_get_centroids",
+    "rabitq_get_rotation", "rabitq_get_codes", "rabitq_get_factors", "rabitq_get_assign",
+    "rabitq_get_buckets", "rabitq_sample_rotation", "rabitq_index_save", "rabitq_index_load",
+    "rabitq_free", "rabitq_last_error",
+)
+
+
+class RabitqError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rabitq error {code}: {msg}")
+        self.code = code
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("kmeans_iters", C.c_int32), ("kmeans_sample", C.c_int64),
+                ("code_bits", C.c_int32), ("data_on_device", C.c_int32),
+                ("stream", C.c_void_p), ("centroids", C.c_void_p)]
+
+
+class SearchOpts(C.Structure):
+    _fields_ = [("rot_precision", C.c_int32), ("scan_path", C.c_int32),
+                ("quant_seed", C.c_uint64), ("io_on_device", C.c_int32),
+                ("stream", C.c_void_p), ("per_query_nprobe", C.c_void_p),
+                ("max_candidates", C.c_int32), ("collect_stats", C.c_int32)]
+
+
+class Trace(C.Structure):
+    _fields_ = [("probe_ids", C.c_void_p), ("probe_dist", C.c_void_p), ("rq", C.c_void_p),
+                ("planes", C.c_void_p), ("sum_qu", C.c_void_p), ("meta", C.c_void_p),
+                ("pair_cap", C.c_int32), ("n_pairs", C.c_void_p), ("pair_id", C.c_void_p),
+                ("pair_ip", C.c_void_p), ("pair_est", C.c_void_p), ("tau", C.c_void_p),
+                ("surv_cap", C.c_int32), ("n_surv", C.c_void_p), ("surv_ids", C.c_void_p)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load librabitq.so (built in-tree by paper_2405_12497_gb300/build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RabitqError(ECUDA, f"CUDA library not built: {_LIB_PATH} (run build())")
+        L = C.CDLL(_LIB_PATH)
+        vp, i32, i64, u64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_float
+        sig = {
+            "rabitq_build_opts_default": (None, [vp]),
+            "rabitq_search_opts_default": (None, [vp]),
+            "rabitq_build": (C.c_int, [vp, i64, i32, i32, u64, vp, vp]),
+            "rabitq_search": (C.c_int, [vp, vp, i64, i32, i32, i32, f32, vp, vp, vp]),
+            "rabitq_search_trace": (C.c_int, [vp, vp, i64, i32, i32, i32, f32, vp, vp, vp, vp]),
+            "rabitq_last_stats": (C.c_int, [vp, i32]),
+            "rabitq_index_info": (C.c_int, [vp, vp, vp, vp, vp]),
+            "rabitq_get_centroids": (C.c_int, [vp, vp]),
+            "rabitq_get_rotation": (C.c_int, [vp, vp]),
+            "rabitq_get_codes": (C.c_int, [vp, vp]),
+            "rabitq_get_factors": (C.c_int, [vp, vp]),
+            "rabitq_get_assign": (C.c_int, [vp, vp]),
+            "rabitq_get_buckets": (C.c_int, [vp, vp, vp]),
+            "rabitq_sample_rotation": (C.c_int, [u64, i32, vp]),
+            "rabitq_index_save": (C.c_int, [vp, C.c_char_p]),
+            "rabitq_index_load": (C.c_int, [C.c_char_p, vp, vp]),
+            "rabitq_free": (None, [vp]),
+            "rabitq_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != OK:
+        raise RabitqError(code, lib().rabitq_last_error().decode())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _dptr(t):
+    """Device pointer of a contiguous torch CUDA tensor."""
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    return C.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def sample_rotation(seed: int, d_pad: int) -> np.ndarray:
+    """The random orthogonal P (FP64, row-major) generated on the device."""
+    out = np.zeros((d_pad, d_pad), np.float64)
+    _check(lib().rabitq_sample_rotation(seed, d_pad, _np_ptr(out)))
+    return out
+
+
+def last_stats() -> np.ndarray:
+    ms = np.zeros(5, np.float32)
+    n = lib().rabitq_last_stats(_np_ptr(ms), 5)
+    return ms[:max(n, 0)]
+
+
+class Index:
+    """A RaBitQ IVF index owned by the library."""
+
+    def __init__(self, handle):
+        self._h = C.c_void_p(handle) if not isinstance(handle, C.c_void_p) else handle
+        n, d, dp, K = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().rabitq_index_info(self._h, C.byref(n), C.byref(d), C.byref(dp), C.byref(K)))
+        self.n, self.d, self.dpad, self.K = n.value, d.value, dp.value, K.value
+
+    # ---------------------------------------------------------------- build
+    @classmethod
+    def build(cls, data, n_clusters: int, seed: int, code_bits: int = 0, kmeans_iters: int = 10,
+              kmeans_sample: int = 0, centroids=None, stream=None) -> "Index":
+        opts = BuildOpts()
+        lib().rabitq_build_opts_default(C.byref(opts))
+        opts.kmeans_iters = kmeans_iters
+        opts.kmeans_sample = kmeans_sample
+        opts.code_bits = code_bits
+        opts.stream = _stream_handle(stream)
+        keep = []
+        if _is_torch(data):
+            data = data.contiguous()
+            opts.data_on_device = 1
+            ptr = _dptr(data)
+            if centroids is not None:
+                centroids = centroids.contiguous()
+                opts.centroids = _dptr(centroids)
+        else:
+            data = np.ascontiguousarray(data, np.float32)
+            ptr = _np_ptr(data)
+            if centroids is not None:
+                centroids = np.ascontiguousarray(centroids, np.float32)
+                opts.centroids = _np_ptr(centroids)
+        keep += [data, centroids]
+        n, d = data.shape
+        h = C.c_void_p()
+        _check(lib().rabitq_build(ptr, n, d, n_clusters, seed, C.byref(opts), C.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def load(cls, path: str) -> "Index":
+        h = C.c_void_p()
+        _check(lib().rabitq_index_load(path.encode(), None, C.byref(h)))
+        return cls(h)
+
+    def save(self, path: str):
+        _check(lib().rabitq_index_save(self._h, path.encode()))
+
+    def free(self):
+        if self._h:
+            lib().rabitq_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ accessors
+    def centroids(self) -> np.ndarray:
+        out = np.zeros((self.K, self.d), np.float32)
+        _check(lib().rabitq_get_centroids(self._h, _np_ptr(out)))
+        return out
+
+    def rotation(self) -> np.ndarray:
+        out = np.zeros((self.dpad, self.dpad), np.float64)
+        _check(lib().rabitq_get_rotation(self._h, _np_ptr(out)))
+        return out
+
+    def codes(self) -> np.ndarray:
+        out = np.zeros((self.n, self.dpad // 64), np.uint64)
+        _check(lib().rabitq_get_codes(self._h, _np_ptr(out)))
+        return out
+
+    def factors(self) -> np.ndarray:
+        out = np.zeros((self.n, 4), np.float32)
+        _check(lib().rabitq_get_factors(self._h, _np_ptr(out)))
+        return out
+
+    def assign(self) -> np.ndarray:
+        out = np.zeros(self.n, np.int32)
+        _check(lib().rabitq_get_assign(self._h, _np_ptr(out)))
+        return out
+
+    def buckets(self):
+        off = np.zeros(self.K + 1, np.int32)
+        ids = np.zeros(self.n, np.int32)
+        _check(lib().rabitq_get_buckets(self._h, _np_ptr(off), _np_ptr(ids)))
+        return off, ids
+
+    # --------------------------------------------------------------- search
+    def _opts(self, quant_seed, per_query_nprobe, max_candidates, stats, stream, on_device,
+              rot_precision=ROT_FP32, scan_path=SCAN_AUTO):
+        o = SearchOpts()
+        lib().rabitq_search_opts_default(C.byref(o))
+        o.quant_seed = quant_seed
+        o.max_candidates = max_candidates
+        o.collect_stats = 1 if stats else 0
+        o.io_on_device = 1 if on_device else 0
+        o.stream = _stream_handle(stream)
+        o.rot_precision = rot_precision
+        o.scan_path = scan_path
+        return o
+
+    def search(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
+               quant_seed: int = 3, per_query_nprobe=None, max_candidates: int = 16384,
+               stats: bool = False, stream=None, out=None, rot_precision=ROT_FP32,
+               scan_path=SCAN_AUTO):
+        """k-NN search. numpy queries -> numpy (ids int64, dists float32) via
+        host buffers; torch CUDA queries -> torch CUDA outputs."""
+        dev = _is_torch(queries)
+        o = self._opts(quant_seed, per_query_nprobe, max_candidates, stats, stream, dev,
+                       rot_precision, scan_path)
+        if dev:
+            import torch
+            queries = queries.contiguous()
+            nq = queries.shape[0]
+            if out is None:
+                ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+                dist = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+            else:
+                ids, dist = out
+            if per_query_nprobe is not None:
+                per_query_nprobe = per_query_nprobe.to(torch.int32).contiguous()
+                o.per_query_nprobe = _dptr(per_query_nprobe)
+            _check(lib().rabitq_search(self._h, _dptr(queries), nq, k, nprobe, bq, eps0,
+                                       _dptr(ids), _dptr(dist), C.byref(o)))
+            return ids, dist
+        queries = np.ascontiguousarray(queries, np.float32)
+        nq = queries.shape[0]
+        if out is None:
+            ids = np.empty((nq, k), np.int64)
+            dist = np.empty((nq, k), np.float32)
+        else:
+            ids, dist = out
+        if per_query_nprobe is not None:
+            per_query_nprobe = np.ascontiguousarray(per_query_nprobe, np.int32)
+            o.per_query_nprobe = _np_ptr(per_query_nprobe)
+        _check(lib().rabitq_search(self._h, _np_ptr(queries), nq, k, nprobe, bq, eps0,
+                                   _np_ptr(ids), _np_ptr(dist), C.byref(o)))
+        return ids, dist
+
+    def search_trace(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
+                     quant_seed: int = 3, pair_cap: int = 0, surv_cap: int = 0,
+                     max_candidates: int = 16384):
+        """Search of torch CUDA queries that also returns every intermediate
+        (torch CUDA tensors)."""
+        import torch
+        dev = queries.device
+        q = queries.contiguous()
+        nq = q.shape[0]
+        W = self.dpad // 64
+        npb = min(nprobe, self.K)
+        t = {
+            "probe_ids": torch.zeros((nq, npb), dtype=torch.int32, device=dev),
+            "probe_dist": torch.zeros((nq, npb), dtype=torch.float32, device=dev),
+            "rq": torch.zeros((nq, self.dpad), dtype=torch.float32, device=dev),
+            "planes": torch.zeros((nq, npb, bq, W), dtype=torch.int64, device=dev),
+            "sum_qu": torch.zeros((nq, npb), dtype=torch.int32, device=dev),
+            "meta": torch.zeros((nq, npb, 4), dtype=torch.float32, device=dev),
+            "n_pairs": torch.zeros(nq, dtype=torch.int32, device=dev),
+            "pair_id": torch.full((nq, max(pair_cap, 1)), -1, dtype=torch.int32, device=dev),
+            "pair_ip": torch.zeros((nq, max(pair_cap, 1)), dtype=torch.int32, device=dev),
+            "pair_est": torch.zeros((nq, max(pair_cap, 1), 3), dtype=torch.float32, device=dev),
+            "tau": torch.zeros(nq, dtype=torch.float32, device=dev),
+            "n_surv": torch.zeros(nq, dtype=torch.int32, device=dev),
+            "surv_ids": torch.full((nq, max(surv_cap, 1)), -1, dtype=torch.int32, device=dev),
+        }
+        tr = Trace(_dptr(t["probe_ids"]), _dptr(t["probe_dist"]), _dptr(t["rq"]),
+                   _dptr(t["planes"]), _dptr(t["sum_qu"]), _dptr(t["meta"]), pair_cap,
+                   _dptr(t["n_pairs"]),
+                   _dptr(t["pair_id"]) if pair_cap else None,
+                   _dptr(t["pair_ip"]) if pair_cap else None,
+                   _dptr(t["pair_est"]) if pair_cap else None,
+                   _dptr(t["tau"]), surv_cap, _dptr(t["n_surv"]),
+                   _dptr(t["surv_ids"]) if surv_cap else None)
+        ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+        dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        o = self._opts(quant_seed, None, max_candidates, False, None, True)
+        _check(lib().rabitq_search_trace(self._h, _dptr(q), nq, k, nprobe, bq, eps0, _dptr(ids),
+                                         _dptr(dist), C.byref(o), C.byref(tr)))
+        t["ids"], t["dist"] = ids, dist
+        return t

@@ -1,0 +1,64 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol the
+header declares; argument checks answer EINVAL before any device work."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2405_12497_gb300 import build, rabitq
+    build.build()
+    return rabitq
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "rabitq.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rabitq_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    declared = _declared_symbols()
+    assert len(declared) >= 18
+    lib = C.CDLL(L.lib_path())
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(L.EXPORTS) == declared
+
+
+def test_invalid_arguments_fail_before_device_work(L):
+    lib = L.lib()
+    h = C.c_void_p()
+    data = np.zeros((10, 8), np.float32)
+    p = data.ctypes.data_as(C.c_void_p)
+    assert lib.rabitq_build(p, 0, 8, 2, 1, None, C.byref(h)) == L.EINVAL
+    assert lib.rabitq_build(p, 10, 0, 2, 1, None, C.byref(h)) == L.EINVAL
+    assert lib.rabitq_build(p, 10, 8, 11, 1, None, C.byref(h)) == L.EINVAL
+    assert lib.rabitq_build(None, 10, 8, 2, 1, None, C.byref(h)) == L.EINVAL
+    opts = L.BuildOpts()
+    lib.rabitq_build_opts_default(C.byref(opts))
+    assert opts.kmeans_iters == 10
+    opts.code_bits = 65
+    assert lib.rabitq_build(p, 10, 8, 2, 1, C.byref(opts), C.byref(h)) == L.EINVAL
+    assert b"code_bits" in lib.rabitq_last_error()
+    assert lib.rabitq_search(None, p, 1, 1, 1, 4, 1.9, p, p, None) == L.EINVAL
+    assert lib.rabitq_sample_rotation(1, 3, p) == L.EINVAL
+    assert lib.rabitq_index_load(b"/nonexistent/file", None, C.byref(h)) == L.EIO
+    so = L.SearchOpts()
+    lib.rabitq_search_opts_default(C.byref(so))
+    assert so.quant_seed == 3 and so.max_candidates == 16384
+    lib.rabitq_free(None)
+
+
+def test_truncated_index_file_is_rejected(L, tmp_path):
+    lib = L.lib()
+    f = tmp_path / "bad.idx"
+    f.write_bytes(b"RABITQ\x00\x01" + b"\x00" * 20)
+    h = C.c_void_p()
+    assert lib.rabitq_index_load(str(f).encode(), None, C.byref(h)) == L.EIO

@@ -1,0 +1,184 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Bit-exact: the rotation P, k-means centroids and assignment, bucket layout,
+codes and factors, probe lists, rotated queries, quantized bit-planes and
+their constants, integer inner products, estimated distances and bounds, the
+threshold tau, the survivor sets, and the final top-k ids and distances.
+The numerics contract that makes bit-exactness possible (canonical FP32
+summation order, no contraction, Philox draws) is followed independently by
+both sides.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    from paper_2405_12497_gb300 import build, rabitq
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    build.build()
+    return rabitq
+
+
+@pytest.fixture(scope="module")
+def tiny_gpu_index(R, tiny_workload):
+    data, _ = tiny_workload
+    return R.Index.build(data, 16, seed=2, kmeans_iters=10)
+
+
+def _u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+@pytest.mark.parametrize("dpad", [64, 128, 256, 1024])
+def test_rotation_bit_exact(R, oracle_mod, dpad):
+    P = R.sample_rotation(2, dpad)
+    Po = oracle_mod.sample_rotation(2, dpad)
+    assert np.array_equal(P.view(np.uint64), Po.view(np.uint64))
+    assert np.abs(P @ P.T - np.eye(dpad)).max() <= 1e-13
+
+
+def test_build_bit_exact(R, oracle_mod, tiny_gpu_index, tiny_oracle_index):
+    G, O = tiny_gpu_index, tiny_oracle_index
+    assert (G.n, G.d, G.dpad, G.K) == (O.n, O.d, O.dpad, O.K)
+    assert np.array_equal(G.centroids().view(np.uint32), O.centroids.view(np.uint32))
+    assert np.array_equal(G.assign(), O.assign)
+    assert np.array_equal(G.rotation().view(np.uint64), O.P.view(np.uint64))
+    assert np.array_equal(G.codes(), O.codes)
+    assert np.array_equal(G.factors().view(np.uint32), O.factors.view(np.uint32))
+    off, ids = G.buckets()
+    assert np.array_equal(off, O.bucket_off)
+    assert np.array_equal(ids, O.bucket_ids)
+
+
+def _compare_trace(G, O, t, i, q, qid, k, nprobe, bq=4, eps0=1.9, seed=3):
+    o = O.trace(q, qid, k, nprobe, bq=bq, eps0=eps0, seed=seed)
+    npb = min(nprobe, O.K)
+    assert np.array_equal(t["probe_ids"][i].cpu().numpy(), o["probe_ids"])
+    assert np.array_equal(t["probe_dist"][i].cpu().numpy().view(np.uint32),
+                          o["probe_dist"].view(np.uint32))
+    assert np.array_equal(t["rq"][i].cpu().numpy().view(np.uint32), o["rq"].view(np.uint32))
+    assert np.array_equal(_u64(t["planes"][i]), o["planes"])
+    assert np.array_equal(t["sum_qu"][i].cpu().numpy(), o["sum_qu"])
+    assert np.array_equal(t["meta"][i].cpu().numpy().view(np.uint32),
+                          o["meta"][:, :4].view(np.uint32))
+    n = int(t["n_pairs"][i])
+    assert n == len(o["pair_id"])
+    assert np.array_equal(t["pair_id"][i, :n].cpu().numpy(), o["pair_id"])
+    assert np.array_equal(t["pair_ip"][i, :n].cpu().numpy(), o["pair_ip"])
+    assert np.array_equal(t["pair_est"][i, :n].cpu().numpy().view(np.uint32),
+                          o["pair_est"].view(np.uint32))
+    assert np.float32(t["tau"][i].item()).view(np.uint32) == np.float32(o["tau"]).view(np.uint32)
+    ns = int(t["n_surv"][i])
+    assert ns == len(o["surv_ids"])
+    assert np.array_equal(np.sort(t["surv_ids"][i, :ns].cpu().numpy()), o["surv_ids"])
+    assert np.array_equal(t["ids"][i].cpu().numpy(), o["ids"])
+    assert np.array_equal(t["dist"][i].cpu().numpy().view(np.uint32), o["dist"].view(np.uint32))
+
+
+@pytest.mark.parametrize("k,nprobe,bq,eps0", [(10, 4, 4, 1.9), (10, 16, 4, 1.9), (1, 1, 1, 0.0),
+                                               (25, 3, 8, 3.0)])
+def test_search_trace_bit_exact(R, tiny_gpu_index, tiny_oracle_index, tiny_workload, k, nprobe,
+                                bq, eps0):
+    import torch
+    _, Q = tiny_workload
+    sel = np.array([0, 3, 17, 42, 99])
+    qd = torch.from_numpy(Q).cuda()
+    t = R.Index.search_trace(tiny_gpu_index, qd, k, nprobe, bq=bq, eps0=eps0,
+                             pair_cap=12000, surv_cap=12000)
+    for i in sel:
+        _compare_trace(tiny_gpu_index, tiny_oracle_index, t, i, Q[i], int(i), k, nprobe, bq, eps0)
+
+
+def test_search_end_to_end_identical(R, tiny_gpu_index, tiny_oracle_index, tiny_workload):
+    import torch
+    _, Q = tiny_workload
+    ids_o, dist_o = tiny_oracle_index.search(Q, 10, 4)
+    ids_h, dist_h = tiny_gpu_index.search(Q, 10, 4)                  # host buffers
+    ids_d, dist_d = tiny_gpu_index.search(torch.from_numpy(Q).cuda(), 10, 4)  # device
+    assert np.array_equal(ids_h, ids_o)
+    assert np.array_equal(dist_h.view(np.uint32), dist_o.view(np.uint32))
+    assert np.array_equal(ids_d.cpu().numpy(), ids_o)
+    assert np.array_equal(dist_d.cpu().numpy().view(np.uint32), dist_o.view(np.uint32))
+    ids2, dist2 = tiny_gpu_index.search(Q, 10, 4)                    # deterministic
+    assert np.array_equal(ids2, ids_h) and np.array_equal(dist2, dist_h)
+
+
+def test_all_buckets_and_padding(R, tiny_gpu_index, tiny_oracle_index, tiny_workload):
+    _, Q = tiny_workload
+    for k, nprobe in ((10, 16), (1000, 1)):
+        ids_o, dist_o = tiny_oracle_index.search(Q[:20], k, nprobe)
+        ids_g, dist_g = tiny_gpu_index.search(Q[:20], k, nprobe)
+        assert np.array_equal(ids_g, ids_o)
+        assert np.array_equal(dist_g.view(np.uint32), dist_o.view(np.uint32))
+    assert (ids_g == -1).any() and np.isinf(dist_g[ids_g == -1]).all()
+
+
+def _ragged_case(oracle_mod, n, d, K, code_bits, seed, sample=0):
+    rng = np.random.default_rng(seed)
+    data = (rng.standard_normal((n, d)) * rng.uniform(0.1, 3, d)).astype(np.float32)
+    data[5] = data[6]           # duplicate points (distance ties)
+    Q = (rng.standard_normal((7, d)) * 2).astype(np.float32)
+    Q[3] = data[11]             # a query equal to a data point
+    return data, Q
+
+
+@pytest.mark.parametrize("n,d,K,code_bits,sample", [(1037, 100, 7, 0, 0), (777, 960, 5, 1024, 0),
+                                                    (3001, 33, 40, 128, 1500), (300, 8, 300, 0, 0)])
+def test_ragged_shapes_bit_exact(R, oracle_mod, n, d, K, code_bits, sample):
+    data, Q = _ragged_case(oracle_mod, n, d, K, code_bits, n + d)
+    G = R.Index.build(data, K, seed=5, code_bits=code_bits, kmeans_iters=4, kmeans_sample=sample)
+    O = oracle_mod.OracleIndex(data, K=K, seed=5, dpad=G.dpad, iters=4, sample=sample)
+    assert np.array_equal(G.centroids().view(np.uint32), O.centroids.view(np.uint32))
+    assert np.array_equal(G.assign(), O.assign)
+    assert np.array_equal(G.codes(), O.codes)
+    assert np.array_equal(G.factors().view(np.uint32), O.factors.view(np.uint32))
+    nprobe = min(3, K)
+    ids_o, dist_o = O.search(Q, 5, nprobe)
+    ids_g, dist_g = G.search(Q, 5, nprobe)
+    assert np.array_equal(ids_g, ids_o)
+    assert np.array_equal(dist_g.view(np.uint32), dist_o.view(np.uint32))
+
+
+def test_given_centroids_and_zero_residuals(R, oracle_mod, tiny_workload):
+    """Every point its own centroid: zero residuals, a_o := 1, exact estimates."""
+    data = tiny_workload[0][:200]
+    G = R.Index.build(data, 200, seed=3, centroids=data)
+    O = oracle_mod.OracleIndex(data, K=200, seed=3, centroids=data)
+    assert np.array_equal(G.assign(), O.assign)
+    assert np.array_equal(G.factors().view(np.uint32), O.factors.view(np.uint32))
+    assert (G.factors()[:, 0] == 0).all()
+    ids_g, dist_g = G.search(data[:10], 3, 5)
+    ids_o, dist_o = O.search(data[:10], 3, 5)
+    assert np.array_equal(ids_g, ids_o) and (ids_g[:, 0] == np.arange(10)).all()
+
+
+def test_save_load_roundtrip(R, tiny_gpu_index, tiny_workload, tmp_path):
+    _, Q = tiny_workload
+    p = str(tmp_path / "tiny.idx")
+    tiny_gpu_index.save(p)
+    L = R.Index.load(p)
+    assert np.array_equal(L.codes(), tiny_gpu_index.codes())
+    a = tiny_gpu_index.search(Q, 10, 4)
+    b = L.search(Q, 10, 4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    raw = bytearray(open(p, "rb").read())
+    raw[-5] ^= 0xFF
+    open(p, "wb").write(bytes(raw))
+    with pytest.raises(R.RabitqError) as e:
+        R.Index.load(p)
+    assert e.value.code == R.EIO
+
+
+def test_invalid_search_arguments(R, tiny_gpu_index, tiny_workload):
+    _, Q = tiny_workload
+    for kw in (dict(k=0, nprobe=4), dict(k=10, nprobe=17), dict(k=10, nprobe=4, bq=9),
+               dict(k=10, nprobe=4, eps0=float("nan"))):
+        with pytest.raises(R.RabitqError) as e:
+            tiny_gpu_index.search(Q, **kw)
+        assert e.value.code == R.EINVAL
+    ids, dist = tiny_gpu_index.search(Q[:0], 10, 4)
+    assert ids.shape == (0, 10)
