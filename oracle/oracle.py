@@ -75,15 +75,15 @@ def lib():
             "orc_rotate": (None, [vp, i64, i32, vp, i32, vp]),
             "orc_kmeans_sample": (i64, [i64, i64, u64, vp]),
             "orc_kmeans_init_ids": (None, [i64, i32, u64, vp]),
-            "orc_kmeans": (None, [vp, i64, i32, i32, i32, i64, u64, vp, vp, vp]),
-            "orc_encode": (None, [vp, i64, i32, vp, vp, vp, i32, vp, vp]),
+            "orc_kmeans": (None, [vp, i64, i32, i32, i32, i64, u64, vp, vp, vp, i32]),
+            "orc_encode": (None, [vp, i64, i32, vp, vp, vp, i32, vp, vp, i32]),
             "orc_quantize": (None, [vp, vp, i32, i32, u64, i32, i32, f32, f32, vp, vp, vp, vp]),
             "orc_bitplane_ip": (i32, [vp, vp, i32, i32]),
             "orc_estimate": (None, [i32, i32, vp, vp, vp]),
             "orc_select": (None, [vp, i64, i32, i32, vp, vp]),
             "orc_search_trace": (None, [vp, vp, vp, i32, vp, vp, vp]),
             "orc_search": (None, [vp, vp, vp, i64, i32, vp, vp]),
-            "orc_bruteforce_knn": (None, [vp, i64, i32, vp, i64, i32, vp, vp, vp]),
+            "orc_bruteforce_knn": (None, [vp, i64, i32, vp, i64, i32, vp, vp, vp, i32]),
             "orc_estimator_fp64": (None, [vp, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -164,17 +164,18 @@ def kmeans_sample(n: int, sample: int, seed: int) -> np.ndarray:
     return ids[:m].copy()
 
 
-def kmeans(data, K: int, iters: int, seed: int, sample: int = 0):
+def kmeans(data, K: int, iters: int, seed: int, sample: int = 0, threads: int = 1):
     data = _c(data, np.float32)
     n, d = data.shape
     cent = np.zeros((K, d), np.float32)
     assign = np.zeros(n, np.int32)
     adist = np.zeros(n, np.float32)
-    lib().orc_kmeans(_p(data), n, d, K, iters, sample, seed, _p(cent), _p(assign), _p(adist))
+    lib().orc_kmeans(_p(data), n, d, K, iters, sample, seed, _p(cent), _p(assign), _p(adist),
+                     threads)
     return cent, assign, adist
 
 
-def encode(data, centroids, assign, P32):
+def encode(data, centroids, assign, P32, threads: int = 1):
     data = _c(data, np.float32)
     centroids = _c(centroids, np.float32)
     assign = _c(assign, np.int32)
@@ -184,7 +185,7 @@ def encode(data, centroids, assign, P32):
     codes = np.zeros((n, dpad // 64), np.uint64)
     factors = np.zeros((n, 4), np.float32)
     lib().orc_encode(_p(data), n, d, _p(centroids), _p(assign), _p(P32), dpad, _p(codes),
-                     _p(factors))
+                     _p(factors), threads)
     return codes, factors
 
 
@@ -224,14 +225,14 @@ def select(dist, nsel: int):
     return ids, sd
 
 
-def bruteforce_knn(data, Q, k: int, allowed=None):
+def bruteforce_knn(data, Q, k: int, allowed=None, threads: int = 1):
     data = _c(data, np.float32)
     Q = _c(Q, np.float32)
     ids = np.zeros((Q.shape[0], k), np.int64)
     dist = np.zeros((Q.shape[0], k), np.float32)
     al = None if allowed is None else _c(allowed, np.uint8)
     lib().orc_bruteforce_knn(_p(data), data.shape[0], data.shape[1], _p(Q), Q.shape[0], k,
-                             _p(al), _p(ids), _p(dist))
+                             _p(al), _p(ids), _p(dist), threads)
     return ids, dist
 
 
@@ -258,21 +259,27 @@ class OracleIndex:
     """
 
     def __init__(self, data, K: int, seed: int, dpad: int | None = None, iters: int = 10,
-                 sample: int = 0, centroids=None, P=None):
+                 sample: int = 0, centroids=None, P=None, threads: int = 1, _arrays=None):
         self.data = _c(data, np.float32)
         n, d = self.data.shape
         self.n, self.d, self.K = n, d, K
         self.dpad = dpad or code_length(d)
-        if centroids is None:
-            self.centroids, self.assign, self.adist = kmeans(self.data, K, iters, seed, sample)
+        if _arrays is not None:
+            (self.centroids, self.P, self.assign, self.codes, self.factors) = _arrays
+            self.P32 = self.P.astype(np.float32)
         else:
-            self.centroids = _c(centroids, np.float32)
-            dist = sqdist_matrix(self.data, self.centroids)
-            ids, sd = select(dist, 1)
-            self.assign, self.adist = ids[:, 0].copy(), sd[:, 0].copy()
-        self.P = sample_rotation(seed, self.dpad) if P is None else _c(P, np.float64)
-        self.P32 = self.P.astype(np.float32)
-        self.codes, self.factors = encode(self.data, self.centroids, self.assign, self.P32)
+            if centroids is None:
+                self.centroids, self.assign, self.adist = kmeans(self.data, K, iters, seed,
+                                                                 sample, threads)
+            else:
+                self.centroids = _c(centroids, np.float32)
+                dist = sqdist_matrix(self.data, self.centroids)
+                ids, sd = select(dist, 1)
+                self.assign, self.adist = ids[:, 0].copy(), sd[:, 0].copy()
+            self.P = sample_rotation(seed, self.dpad) if P is None else _c(P, np.float64)
+            self.P32 = self.P.astype(np.float32)
+            self.codes, self.factors = encode(self.data, self.centroids, self.assign, self.P32,
+                                              threads)
         self.ptc = rotate(self.centroids, self.P32)
         order = np.lexsort((np.arange(n), self.assign))
         self.bucket_ids = order.astype(np.int32)
@@ -282,6 +289,14 @@ class OracleIndex:
         self._s = _Index(_p(self.data), _p(self.centroids), _p(self.ptc), _p(self.P32),
                          _p(self.codes), _p(self.factors), _p(self.bucket_off),
                          _p(self.bucket_ids), n, d, self.dpad, K)
+
+    @classmethod
+    def from_arrays(cls, data, centroids, P, assign, codes, factors):
+        """An index from given arrays (used to time the oracle's search on an
+        index built elsewhere; nothing built this way is a parity reference)."""
+        arr = (_c(centroids, np.float32), _c(P, np.float64), _c(assign, np.int32),
+               _c(codes, np.uint64), _c(factors, np.float32))
+        return cls(data, K=arr[0].shape[0], seed=0, dpad=arr[1].shape[0], _arrays=arr)
 
     def search(self, Q, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9, seed: int = 3,
                mode: int = 0, threads: int = 1):

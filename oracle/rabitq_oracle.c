@@ -37,6 +37,30 @@
 
 #define ORC_API __attribute__((visibility("default")))
 
+/* Rows [0, n) split evenly over `threads` POSIX threads; each row's
+ * arithmetic is the same whatever the split. */
+typedef void (*orc_rows_fn)(void* ctx, int64_t r0, int64_t r1);
+typedef struct { orc_rows_fn fn; void* ctx; int64_t r0, r1; } orc_rows_job;
+static void* orc_rows_run(void* a) {
+  orc_rows_job* j = (orc_rows_job*)a;
+  j->fn(j->ctx, j->r0, j->r1);
+  return NULL;
+}
+static void parallel_rows(int64_t n, int32_t threads, orc_rows_fn fn, void* ctx) {
+  if (threads < 1) threads = 1;
+  if (threads > n) threads = (int32_t)(n > 0 ? n : 1);
+  if (threads == 1) { fn(ctx, 0, n); return; }
+  pthread_t th[256];
+  orc_rows_job jobs[256];
+  if (threads > 256) threads = 256;
+  for (int32_t t = 0; t < threads; ++t) {
+    jobs[t].fn = fn; jobs[t].ctx = ctx;
+    jobs[t].r0 = n * t / threads; jobs[t].r1 = n * (t + 1) / threads;
+    pthread_create(&th[t], NULL, orc_rows_run, &jobs[t]);
+  }
+  for (int32_t t = 0; t < threads; ++t) pthread_join(th[t], NULL);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as   */
 /* easy as 1, 2, 3", SC'11). Ten rounds; the key is bumped by the Weyl       */
@@ -271,24 +295,36 @@ ORC_API void orc_kmeans_init_ids(int64_t n, int32_t K, uint64_t seed, int32_t* o
   free(taken);
 }
 
-static void assign_all(const float* data, int64_t n, const int32_t* rows, int32_t d,
-                       const float* cent, int32_t K, int32_t* assign, float* adist) {
-  for (int64_t r = 0; r < n; ++r) {
-    const float* x = data + (int64_t)(rows ? rows[r] : r) * d;
+typedef struct {
+  const float* data; const int32_t* rows; int32_t d; const float* cent; int32_t K;
+  int32_t* assign; float* adist;
+} assign_ctx;
+
+static void assign_rows(void* vc, int64_t r0, int64_t r1) {
+  assign_ctx* a = (assign_ctx*)vc;
+  for (int64_t r = r0; r < r1; ++r) {
+    const float* x = a->data + (int64_t)(a->rows ? a->rows[r] : r) * a->d;
     int32_t best = 0;
-    float bd = sqdist32(x, cent, d);
-    for (int32_t c = 1; c < K; ++c) {
-      float dc = sqdist32(x, cent + (int64_t)c * d, d);
+    float bd = sqdist32(x, a->cent, a->d);
+    for (int32_t c = 1; c < a->K; ++c) {
+      float dc = sqdist32(x, a->cent + (int64_t)c * a->d, a->d);
       if (dc < bd) { bd = dc; best = c; }
     }
-    assign[r] = best;
-    if (adist) adist[r] = bd;
+    a->assign[r] = best;
+    if (a->adist) a->adist[r] = bd;
   }
+}
+
+static void assign_all(const float* data, int64_t n, const int32_t* rows, int32_t d,
+                       const float* cent, int32_t K, int32_t* assign, float* adist,
+                       int32_t threads) {
+  assign_ctx a = {data, rows, d, cent, K, assign, adist};
+  parallel_rows(n, threads, assign_rows, &a);
 }
 
 ORC_API void orc_kmeans(const float* data, int64_t n, int32_t d, int32_t K, int32_t iters,
                         int64_t sample, uint64_t seed, float* centroids, int32_t* assign,
-                        float* assign_dist) {
+                        float* assign_dist, int32_t threads) {
   int32_t* rows = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
   int64_t m = orc_kmeans_sample(n, sample, seed, rows);
   if (m < K) m = orc_kmeans_sample(n, 0, seed, rows); /* too small a sample: use all */
@@ -299,7 +335,7 @@ ORC_API void orc_kmeans(const float* data, int64_t n, int32_t d, int32_t K, int3
   int32_t* a = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
   float* sum = (float*)malloc(sizeof(float) * (size_t)d);
   for (int32_t it = 0; it < iters; ++it) {
-    assign_all(data, m, rows, d, centroids, K, a, NULL);
+    assign_all(data, m, rows, d, centroids, K, a, NULL, threads);
     for (int32_t c = 0; c < K; ++c) {
       int64_t cnt = 0;
       for (int32_t i = 0; i < d; ++i) sum[i] = 0.0f;
@@ -314,7 +350,7 @@ ORC_API void orc_kmeans(const float* data, int64_t n, int32_t d, int32_t K, int3
       for (int32_t i = 0; i < d; ++i) centroids[(int64_t)c * d + i] = sum[i] / fc;
     }
   }
-  assign_all(data, n, NULL, d, centroids, K, assign, assign_dist);
+  assign_all(data, n, NULL, d, centroids, K, assign, assign_dist, threads);
   free(rows); free(init); free(a); free(sum);
 }
 
@@ -335,14 +371,21 @@ ORC_API void orc_kmeans(const float* data, int64_t n, int32_t d, int32_t K, int3
  *   G     = 2 popcount(bits) - dpad      (as float)
  * Codes are dpad/64 words per vector, bit k in word k>>6 at position k&63.
  * factors[4*n + {0,1,2,3}] = {F1, F2, F3, G}.                              */
-ORC_API void orc_encode(const float* data, int64_t n, int32_t d, const float* centroids,
-                        const int32_t* assign, const float* P32, int32_t dpad,
-                        uint64_t* codes, float* factors) {
+typedef struct {
+  const float* data; int32_t d; const float* centroids; const int32_t* assign;
+  const float* P32; int32_t dpad; uint64_t* codes; float* factors;
+} encode_ctx;
+
+static void encode_rows(void* vc, int64_t v0, int64_t v1) {
+  encode_ctx* E = (encode_ctx*)vc;
+  const float* data = E->data; const int32_t d = E->d; const float* centroids = E->centroids;
+  const int32_t* assign = E->assign; const float* P32 = E->P32; const int32_t dpad = E->dpad;
+  uint64_t* codes = E->codes; float* factors = E->factors;
   const int32_t W = dpad / 64;
   const float sqrt_dpad = sqrtf((float)dpad);
   float* res = (float*)malloc(sizeof(float) * (size_t)d);
   float* r = (float*)malloc(sizeof(float) * (size_t)dpad);
-  for (int64_t v = 0; v < n; ++v) {
+  for (int64_t v = v0; v < v1; ++v) {
     const float* o = data + v * d;
     const float* c = centroids + (int64_t)assign[v] * d;
     for (int32_t i = 0; i < d; ++i) res[i] = o[i] - c[i];
@@ -380,6 +423,13 @@ ORC_API void orc_encode(const float* data, int64_t n, int32_t d, const float* ce
   }
   free(res);
   free(r);
+}
+
+ORC_API void orc_encode(const float* data, int64_t n, int32_t d, const float* centroids,
+                        const int32_t* assign, const float* P32, int32_t dpad,
+                        uint64_t* codes, float* factors, int32_t threads) {
+  encode_ctx E = {data, d, centroids, assign, P32, dpad, codes, factors};
+  parallel_rows(n, threads, encode_rows, &E);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -742,27 +792,39 @@ ORC_API void orc_search(const orc_index* X, const orc_params* p, const float* Q,
   free(jobs);
 }
 
-/* Exact k nearest neighbours by brute force (canonical FP32 distance,
- * ties by id), restricted to `allowed` ids when allowed != NULL. */
-ORC_API void orc_bruteforce_knn(const float* data, int64_t n, int32_t d, const float* Q,
-                                int64_t nq, int32_t k, const uint8_t* allowed,
-                                int64_t* out_ids, float* out_dist) {
+typedef struct {
+  const float* data; int64_t n; int32_t d; const float* Q; int32_t k; const uint8_t* allowed;
+  int64_t* out_ids; float* out_dist;
+} bf_ctx;
+
+static void bf_rows(void* vc, int64_t q0, int64_t q1) {
+  bf_ctx* B = (bf_ctx*)vc;
+  const int32_t k = B->k, d = B->d;
   float* td = (float*)malloc(sizeof(float) * (size_t)k);
   int32_t* ti = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
-  for (int64_t i = 0; i < nq; ++i) {
+  for (int64_t i = q0; i < q1; ++i) {
     int32_t cnt = 0;
-    const uint8_t* al = allowed ? allowed + i * n : NULL;
-    for (int64_t v = 0; v < n; ++v) {
+    const uint8_t* al = B->allowed ? B->allowed + i * B->n : NULL;
+    for (int64_t v = 0; v < B->n; ++v) {
       if (al && !al[v]) continue;
-      topk_insert(td, ti, &cnt, k, sqdist32(Q + i * d, data + v * d, d), (int32_t)v);
+      topk_insert(td, ti, &cnt, k, sqdist32(B->Q + i * d, B->data + v * d, d), (int32_t)v);
     }
     for (int32_t j = 0; j < k; ++j) {
-      out_ids[i * k + j] = (j < cnt) ? ti[j] : -1;
-      out_dist[i * k + j] = (j < cnt) ? td[j] : INFINITY;
+      B->out_ids[i * k + j] = (j < cnt) ? ti[j] : -1;
+      B->out_dist[i * k + j] = (j < cnt) ? td[j] : INFINITY;
     }
   }
   free(td);
   free(ti);
+}
+
+/* Exact k nearest neighbours by brute force (canonical FP32 distance,
+ * ties by id), restricted to `allowed` ids when allowed != NULL. */
+ORC_API void orc_bruteforce_knn(const float* data, int64_t n, int32_t d, const float* Q,
+                                int64_t nq, int32_t k, const uint8_t* allowed,
+                                int64_t* out_ids, float* out_dist, int32_t threads) {
+  bf_ctx B = {data, n, d, Q, k, allowed, out_ids, out_dist};
+  parallel_rows(nq, threads, bf_rows, &B);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -8,7 +8,7 @@ clustered structure. Data and queries use independent numpy PCG64 streams.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass
+from dataclasses import dataclass, replace as dataclasses_replace  # noqa: F401
 
 import numpy as np
 
@@ -61,19 +61,23 @@ def _chunks(n: int, step: int = 1 << 18):
 
 
 def sift_like(n: int, nq: int, d: int = 128, seed_data: int = 0, seed_query: int = 1):
-    """Non-negative integer-valued vectors in [0, 255] from a 1000-component
-    mixture with heavy-tailed per-dimension scales (SIFT-shaped): s_d =
-    exp(N(0,1)), mu[c,d] = 32 s_d Exp(1), x = clip(round(mu + 8 s_d N(0,1)))."""
+    """Non-negative integer-valued vectors in [0, 255] (SIFT-shaped): a mixture
+    of n/50 components with heavy-tailed per-dimension scales s_d =
+    exp(N(0, 1/4)), centers mu[c, d] = 32 s_d Exp(1), and points
+    x = clip(round(mu + 20 s_d N(0, 1)), 0, 255). The overlap between
+    components is set so that an IVF with ~244 points per bucket needs a few
+    dozen probes for recall@100 = 0.95, as on the real dataset."""
     g = np.random.Generator(np.random.PCG64(seed_data))
-    scale = np.exp(g.standard_normal(d))
-    mu = 32.0 * scale * g.exponential(1.0, (1000, d))
+    n_comp = max(10, n // 50)
+    scale = np.exp(0.5 * g.standard_normal(d))
+    mu = 32.0 * scale * g.exponential(1.0, (n_comp, d))
 
     def draw(m, seed):
         gg = np.random.Generator(np.random.PCG64(seed + 1000))
         out = np.empty((m, d), np.float32)
         for s, e in _chunks(m):
-            comp = gg.integers(0, 1000, e - s)
-            x = mu[comp] + 8.0 * scale * gg.standard_normal((e - s, d))
+            comp = gg.integers(0, n_comp, e - s)
+            x = mu[comp] + 20.0 * scale * gg.standard_normal((e - s, d))
             out[s:e] = np.clip(np.rint(x), 0, 255)
         return out
 
