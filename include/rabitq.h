@@ -69,7 +69,7 @@ typedef struct {
   const int32_t* per_query_nprobe; /* optional nq probe counts (same memory kind
                                as the queries), each clamped to [1, nprobe]      */
   int32_t max_candidates;   /* per-query capacity of the candidate list that
-                               survives the error bound (0 = 16384)              */
+                               survives the error bound (0 = 65536)              */
   int32_t collect_stats;    /* record per-stage device times (rabitq_last_stats) */
 } rabitq_search_opts;
 
@@ -106,8 +106,11 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
  *   eps0      >= 0, confidence parameter of the error bound (Theorem 3.2)
  *   out_ids   nq x k int64 ids, ascending by (distance, id); -1 pads
  *   out_dist  nq x k float32 exact squared distances; +inf pads
- * A candidate is re-ranked iff its distance lower bound is at most the k-th
- * smallest upper bound over all estimated codes of its query.
+ * Re-ranking (§4, order-independent form): the 4k codes with the smallest
+ * estimated distances (the pilot) get exact distances first; tau1 is the
+ * k-th smallest of those, tau_ub the k-th smallest upper bound over all
+ * estimated codes; every other code is re-ranked iff its distance lower
+ * bound is at most min(tau_ub, tau1).
  * Errors: EINVAL; ENOMEM; ECUDA; EOVERFLOW when more than max_candidates
  * codes of one query pass the bound (raise max_candidates).
  */
@@ -131,8 +134,13 @@ int rabitq_search(const rabitq_index* idx, const float* queries, int64_t nq, int
  *   pair_id, pair_ip       nq x pair_cap: id and <x_b, q_u> per pair, in
  *                          probe order then bucket order (ascending id)
  *   pair_est               nq x pair_cap x 3: estimated distance, LB, UB
- *   tau                    nq: k-th smallest UB (+inf if fewer than k)
- *   surv_cap, n_surv, surv_ids  survivors (LB <= tau), in no particular order
+ *   tau_ub                 nq: k-th smallest UB (+inf if fewer than k codes)
+ *   tau1                   nq: k-th smallest exact distance among the pilot,
+ *                          the 4k codes with the smallest estimates (+inf if
+ *                          fewer than k)
+ *   tau                    nq: min(tau_ub, tau1), the drop threshold
+ *   surv_cap, n_surv, surv_ids  the re-rank set (pilot plus every code with
+ *                          LB <= tau), in no particular order
  */
 typedef struct {
   int32_t* probe_ids;
@@ -146,6 +154,8 @@ typedef struct {
   int32_t* pair_id;
   int32_t* pair_ip;
   float* pair_est;
+  float* tau_ub;
+  float* tau1;
   float* tau;
   int32_t surv_cap;
   int32_t* n_surv;

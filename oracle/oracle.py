@@ -56,7 +56,8 @@ class _Trace(C.Structure):
                 ("planes", C.c_void_p), ("sum_qu", C.c_void_p), ("meta", C.c_void_p),
                 ("pair_id", C.c_void_p), ("pair_ip", C.c_void_p), ("pair_est", C.c_void_p),
                 ("cap_pairs", C.c_int32), ("n_pairs", C.c_int32), ("tau", C.c_float),
-                ("surv_ids", C.c_void_p), ("cap_surv", C.c_int32), ("n_surv", C.c_int32)]
+                ("surv_ids", C.c_void_p), ("cap_surv", C.c_int32), ("n_surv", C.c_int32),
+                ("tau_ub", C.c_float), ("tau1", C.c_float)]
 
 
 def lib():
@@ -324,7 +325,7 @@ class OracleIndex:
                  surv_ids=np.zeros(cap, np.int32))
         tr = _Trace(_p(t["probe_ids"]), _p(t["probe_dist"]), _p(t["rq"]), _p(t["planes"]),
                     _p(t["sum_qu"]), _p(t["meta"]), _p(t["pair_id"]), _p(t["pair_ip"]),
-                    _p(t["pair_est"]), cap, 0, 0.0, _p(t["surv_ids"]), cap, 0)
+                    _p(t["pair_est"]), cap, 0, 0.0, _p(t["surv_ids"]), cap, 0, 0.0, 0.0)
         par = _Params(k, nprobe, bq, 0, eps0, seed)
         ids = np.zeros(k, np.int64)
         dist = np.zeros(k, np.float32)
@@ -334,6 +335,6 @@ class OracleIndex:
         for key in ("pair_id", "pair_ip", "pair_est"):
             t[key] = t[key][:n]
         t["surv_ids"] = t["surv_ids"][:tr.n_surv]
-        t["tau"] = tr.tau
+        t["tau"], t["tau_ub"], t["tau1"] = tr.tau, tr.tau_ub, tr.tau1
         t["ids"], t["dist"] = ids, dist
         return t

@@ -558,7 +558,7 @@ typedef struct {
 } orc_index;
 
 typedef struct {
-  int32_t k, nprobe, bq, mode; /* mode 0: error-bound set (tau = k-th UB); 1: sequential */
+  int32_t k, nprobe, bq, mode; /* mode 0: order-independent re-rank set; 1: sequential */
   float eps0;
   uint64_t seed;
 } orc_params;
@@ -577,9 +577,10 @@ typedef struct {
   int32_t cap_pairs;
   int32_t n_pairs;      /* out */
   float tau;            /* out (mode 0)      */
-  int32_t* surv_ids;    /* cap_surv, ascending id */
+  int32_t* surv_ids;    /* cap_surv: the re-rank set, ascending id */
   int32_t cap_surv;
   int32_t n_surv;       /* out */
+  float tau_ub, tau1;   /* out (mode 0) */
 } orc_trace;
 
 static int cmp_pair(float da, int32_t ia, float db, int32_t ib) {
@@ -701,20 +702,57 @@ static void search_one(const orc_index* X, const orc_params* p, const float* q, 
   }
   if (tr) tr->n_pairs = (int32_t)t;
   if (p->mode == 0) {
-    /* error-bound set: tau = k-th smallest upper bound over all estimated
-     * codes; survivors = {LB <= tau} (reading of §4 for k > 1) */
-    float tau = INFINITY;
+    /* Order-independent reading of the re-ranking rule of §4 for k >= 1:
+     *  tau_ub = k-th smallest upper bound over all estimated codes;
+     *  pilot  = the 4k codes with the smallest estimated distance (by
+     *           (estimate, id)), re-ranked first;
+     *  tau1   = k-th smallest exact distance within the pilot;
+     *  tau    = min(tau_ub, tau1) (each is at least the k-th nearest exact
+     *           distance, w.h.p. for tau_ub, always for tau1);
+     *  re-rank set = pilot + every code whose lower bound is <= tau. */
+    float tau_ub = INFINITY, tau1 = INFINITY;
     if (t >= k) {
       float* ubs = (float*)malloc(sizeof(float) * (size_t)t);
       for (int64_t i = 0; i < t; ++i) ubs[i] = pest[3 * i + 2];
       qsort(ubs, (size_t)t, sizeof(float), cmp_float);
-      tau = ubs[k - 1];
+      tau_ub = ubs[k - 1];
       free(ubs);
     }
+    const int64_t m = (4 * (int64_t)k < t) ? 4 * (int64_t)k : t;
+    uint8_t* in_set = (uint8_t*)calloc((size_t)(t + 1), 1);
+    /* pilot: m smallest (estimate, id), by selection into a sorted list */
+    float* pd = (float*)malloc(sizeof(float) * (size_t)(m + 1));
+    int32_t* pi = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int32_t* pix = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int32_t pc = 0;
+    for (int64_t i = 0; i < t; ++i) {
+      float e = pest[3 * i + 0];
+      int32_t id = pid[i];
+      if (pc == m && cmp_pair(e, id, pd[m - 1], pi[m - 1]) >= 0) continue;
+      int32_t pos = (pc < m) ? pc : (int32_t)m - 1;
+      while (pos > 0 && cmp_pair(e, id, pd[pos - 1], pi[pos - 1]) < 0) {
+        pd[pos] = pd[pos - 1]; pi[pos] = pi[pos - 1]; pix[pos] = pix[pos - 1];
+        --pos;
+      }
+      pd[pos] = e; pi[pos] = id; pix[pos] = (int32_t)i;
+      if (pc < m) ++pc;
+    }
+    float* pex = (float*)malloc(sizeof(float) * (size_t)(m + 1));
+    for (int32_t j = 0; j < pc; ++j) {
+      in_set[pix[j]] = 1;
+      pex[j] = sqdist32(q, X->data + (int64_t)pi[j] * d, d);
+    }
+    if (pc >= k) {
+      qsort(pex, (size_t)pc, sizeof(float), cmp_float);
+      tau1 = pex[k - 1];
+    }
+    float tau = tau_ub < tau1 ? tau_ub : tau1;
+    for (int64_t i = 0; i < t; ++i)
+      if (pest[3 * i + 1] <= tau) in_set[i] = 1;
     int32_t ns = 0;
     int32_t* surv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(t + 1));
     for (int64_t i = 0; i < t; ++i)
-      if (pest[3 * i + 1] <= tau) surv[ns++] = pid[i];
+      if (in_set[i]) surv[ns++] = pid[i];
     qsort(surv, (size_t)ns, sizeof(int32_t), cmp_int);
     for (int32_t i = 0; i < ns; ++i) {
       float ex = sqdist32(q, X->data + (int64_t)surv[i] * d, d);
@@ -722,13 +760,15 @@ static void search_one(const orc_index* X, const orc_params* p, const float* q, 
     }
     if (tr) {
       tr->tau = tau;
+      tr->tau_ub = tau_ub;
+      tr->tau1 = tau1;
       tr->n_surv = ns;
       if (tr->surv_ids) {
-        int32_t m = ns < tr->cap_surv ? ns : tr->cap_surv;
-        memcpy(tr->surv_ids, surv, sizeof(int32_t) * (size_t)m);
+        int32_t mm = ns < tr->cap_surv ? ns : tr->cap_surv;
+        memcpy(tr->surv_ids, surv, sizeof(int32_t) * (size_t)mm);
       }
     }
-    free(surv);
+    free(surv); free(in_set); free(pd); free(pi); free(pix); free(pex);
   }
   for (int32_t j = 0; j < k; ++j) {
     out_ids[j] = (j < cnt) ? ti[j] : -1;

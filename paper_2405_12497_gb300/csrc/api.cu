@@ -43,6 +43,7 @@ void free_index_arrays(rabitq_index* X) {
   cudaFree(X->codes);
   cudaFree(X->factors);
   cudaFree(X->perm);
+  cudaFree(X->inv_perm);
   cudaFree(X->bucket_off);
   cudaFree(X->assign);
   cudaFree(X->centroids);
@@ -58,6 +59,7 @@ int alloc_index_arrays(rabitq_index* X) {
   RBQ_CHECK(dev_alloc(&X->codes, (size_t)n * X->W));
   RBQ_CHECK(dev_alloc(&X->factors, (size_t)n));
   RBQ_CHECK(dev_alloc(&X->perm, (size_t)n));
+  RBQ_CHECK(dev_alloc(&X->inv_perm, (size_t)n));
   RBQ_CHECK(dev_alloc(&X->bucket_off, (size_t)X->K + 1));
   RBQ_CHECK(dev_alloc(&X->assign, (size_t)n));
   RBQ_CHECK(dev_alloc(&X->centroids, (size_t)X->K * X->d));
@@ -134,7 +136,7 @@ void rabitq_search_opts_default(rabitq_search_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof *o);
   o->quant_seed = 3;
-  o->max_candidates = 16384;
+  o->max_candidates = 65536;
 }
 
 const char* rabitq_last_error(void) { return g_err.c_str(); }
@@ -207,6 +209,7 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
     RBQ_CHECK(argmin_sqdist(ddata, d, X->centroids_t, n_clusters, n, n_clusters, d, X->assign,
                             adist.as<float>(), s));
     RBQ_CHECK(counting_sort(X->assign, n, n_clusters, X->perm, X->bucket_off, s));
+    RBQ_CHECK(invert_perm(X->perm, n, X->inv_perm, s));
     RBQ_CHECK(gather_rows_f32(ddata, d, X->perm, n, d, X->data_b, s));
     RBQ_CHECK(adist_b.alloc(sizeof(float) * n, s));
     RBQ_CHECK(gather_rows_f32(adist.as<float>(), 1, X->perm, n, 1, adist_b.as<float>(), s));
@@ -239,7 +242,7 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   rabitq_search_opts opts;
   rabitq_search_opts_default(&opts);
   if (opts_in) opts = *opts_in;
-  if (opts.max_candidates == 0) opts.max_candidates = 16384;
+  if (opts.max_candidates == 0) opts.max_candidates = 65536;
   if (nq < 0) return fail(RABITQ_EINVAL, "rabitq_search: nq < 0");
   if (nq == 0) return RABITQ_OK;
   if (!queries || !out_ids || !out_dist) return fail(RABITQ_EINVAL, "rabitq_search: null pointer");
@@ -515,6 +518,7 @@ int rabitq_index_load(const char* path, const rabitq_build_opts* opts, rabitq_in
   if (st == RABITQ_OK && (crc != h.payload_crc || total != h.payload_bytes))
     st = fail(RABITQ_EIO, std::string("index file checksum mismatch: ") + path);
   if (st == RABITQ_OK) st = transpose_f32(X->centroids, X->K, X->d, X->centroids_t, nullptr);
+  if (st == RABITQ_OK) st = invert_perm(X->perm, X->n, X->inv_perm, nullptr);
   if (st == RABITQ_OK) {
     const int64_t tot = (int64_t)X->dpad * X->dpad;
     std::vector<double> p64(tot);

@@ -19,6 +19,7 @@ struct rabitq_index {
   uint64_t* codes = nullptr;      // n x W, bucket order
   float4* factors = nullptr;      // n: {F1, F2, F3, G}, bucket order
   int32_t* perm = nullptr;        // n: bucket position -> id
+  int32_t* inv_perm = nullptr;    // n: id -> bucket position
   int32_t* bucket_off = nullptr;  // K + 1
   int32_t* assign = nullptr;      // n: cluster of id
   float* centroids = nullptr;     // K x d
@@ -86,6 +87,7 @@ int kmeans_dev(const float* data, int64_t n, int32_t d, int32_t K, int32_t iters
 int encode_dev(rabitq_index* X, const float* adist_b, cudaStream_t s);
 int gather_rows_f32(const float* in, int64_t ld, const int32_t* rows, int64_t m, int32_t d,
                     float* out, cudaStream_t s);
+int invert_perm(const int32_t* perm, int64_t n, int32_t* inv, cudaStream_t s);
 int transpose_f32(const float* in, int64_t rows, int64_t cols, float* out, cudaStream_t s);
 int check_finite(const float* x, int64_t count, cudaStream_t s, bool* finite);
 

@@ -146,6 +146,12 @@ __global__ void gather_rows_kernel(const float* __restrict__ in, int64_t ld,
   for (int i = lane; i < d; i += 32) dst[i] = src[i];
 }
 
+__global__ void invert_perm_kernel(const int32_t* __restrict__ perm, int64_t n,
+                                   int32_t* __restrict__ inv) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < n) inv[perm[p]] = (int32_t)p;
+}
+
 __global__ void transpose_kernel(const float* __restrict__ in, int64_t rows, int64_t cols,
                                  float* __restrict__ out) {
   __shared__ float t[32][33];
@@ -416,6 +422,13 @@ int gather_rows_f32(const float* in, int64_t ld, const int32_t* rows, int64_t m,
                     float* out, cudaStream_t s) {
   if (m <= 0) return RABITQ_OK;
   gather_rows_kernel<<<blocks_for(m * 32, 256), 256, 0, s>>>(in, ld, rows, m, d, out);
+  RBQ_CUDA(cudaGetLastError());
+  return RABITQ_OK;
+}
+
+int invert_perm(const int32_t* perm, int64_t n, int32_t* inv, cudaStream_t s) {
+  if (n <= 0) return RABITQ_OK;
+  invert_perm_kernel<<<blocks_for(n, 256), 256, 0, s>>>(perm, n, inv);
   RBQ_CUDA(cudaGetLastError());
   return RABITQ_OK;
 }

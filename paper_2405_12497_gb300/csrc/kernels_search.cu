@@ -119,14 +119,15 @@ struct FusedParams {
   const uint64_t* codes;    // n x W (bucket order)
   const float4* factors;    // n (bucket order)
   const float* data_b;      // n x d (bucket order)
-  const int32_t* perm;      // n
+  const int32_t* perm;      // n: position -> id
+  const int32_t* inv_perm;  // n: id -> position
   const int32_t* bucket_off;
   int64_t nq, q_offset;
-  int d, dpad, W, bq, k, nprobe, pch, cu, ct;
+  int d, dpad, W, bq, k, m, nprobe, pch, cu, ce, ct;
   float eps0;
   uint64_t seed;
   int cand_cap;
-  int2* cand;               // gridDim.x x cand_cap
+  int4* cand;               // gridDim.x x cand_cap: {pos, LB, estimate, -}
   int64_t* out_ids;
   float* out_dist;
   int* err;
@@ -134,31 +135,37 @@ struct FusedParams {
 };
 
 struct FusedSmem {
-  uint64_t* planes;  // pch x bq x W
+  uint64_t* planes;  // pch x bq x W   (re-used as re-rank tiles after the scan)
+  float* tiles;      // nwarps x 32 x 33
   float4* pmeta;     // pch: A, B, E, nq2
   int* psum;         // pch
   int* pbeg;         // pch
   int* pref;         // pch + 1
   float* qv;         // d
-  uint32_t* ubk;     // cu
-  unsigned long long* topk;  // ct
+  uint32_t* ubk;     // cu: upper-bound keys
+  unsigned long long* estk;  // ce: (estimate key << 32) | id
+  unsigned long long* topk;  // ct: (exact distance key << 32) | id
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline size_t fused_smem_bytes(int pch, int bq, int W, int d, int cu, int ct,
-                                                   size_t* off /* 8 entries or null */) {
-  size_t o = 0, offs[8];
-  offs[0] = o; o = align_up(o + sizeof(uint64_t) * pch * bq * W, 16);
+__host__ __device__ inline size_t fused_smem_bytes(int pch, int bq, int W, int d, int cu, int ce,
+                                                   int ct, int nwarps,
+                                                   size_t* off /* 9 entries or null */) {
+  size_t o = 0, offs[9];
+  const size_t planes = sizeof(uint64_t) * pch * bq * W;
+  const size_t tiles = sizeof(float) * nwarps * 32 * 33;
+  offs[0] = o; o = align_up(o + (planes > tiles ? planes : tiles), 16);
   offs[1] = o; o = align_up(o + sizeof(float4) * pch, 16);
   offs[2] = o; o = align_up(o + sizeof(int) * pch, 16);
   offs[3] = o; o = align_up(o + sizeof(int) * pch, 16);
   offs[4] = o; o = align_up(o + sizeof(int) * (pch + 1), 16);
   offs[5] = o; o = align_up(o + sizeof(float) * d, 16);
   offs[6] = o; o = align_up(o + sizeof(uint32_t) * cu, 16);
-  offs[7] = o; o = align_up(o + sizeof(unsigned long long) * ct, 16);
+  offs[7] = o; o = align_up(o + sizeof(unsigned long long) * ce, 16);
+  offs[8] = o; o = align_up(o + sizeof(unsigned long long) * ct, 16);
   if (off)
-    for (int i = 0; i < 8; ++i) off[i] = offs[i];
+    for (int i = 0; i < 9; ++i) off[i] = offs[i];
   return o;
 }
 
@@ -200,13 +207,13 @@ __device__ __forceinline__ void quantize_probe(const FusedParams& P, const Fused
         if (k0 + r < dpad) {
           const float u = __fmul_rn(__uint2float_rn(ws[r] >> 8), 0x1.0p-24f);
           const float x = __fdiv_rn(__fsub_rn(qd[r], vl), delta);
-          int v = __float2int_rd(__fadd_rn(x, u));
+          const int v = __float2int_rd(__fadd_rn(x, u));
           qu[r] = v > qmax ? qmax : v;
         }
       }
     }
     sum += qu[0] + qu[1] + qu[2] + qu[3];
-    // bit-planes: nibble of lane l sits at bits 4l..4l+3 of the 128-bit block
+    // bit-planes: the nibble of lane l sits at bits 4l..4l+3 of the 128-bit block
     for (int b = 0; b < bq; ++b) {
       const uint32_t nib = ((qu[0] >> b) & 1) | (((qu[1] >> b) & 1) << 1) |
                            (((qu[2] >> b) & 1) << 2) | (((qu[3] >> b) & 1) << 3);
@@ -246,42 +253,43 @@ __device__ __forceinline__ void quantize_probe(const FusedParams& P, const Fused
   }
 }
 
-// Keep the k smallest UB keys: sort the buffer, truncate, return tau'.
-__device__ __forceinline__ void compact_ub(const FusedSmem& S, int cu, int k, int* ub_cnt,
-                                          float* tau) {
-  for (int i = *ub_cnt + threadIdx.x; i < cu; i += blockDim.x) S.ubk[i] = 0xffffffffu;
+// Sort a shared key buffer (padded with the maximum key), keep the `keep`
+// smallest; returns the count kept. Whole block; synchronized on return.
+__device__ __forceinline__ void sort_keep_u32(uint32_t* a, int cap, int* cnt, int keep) {
+  for (int i = *cnt + threadIdx.x; i < cap; i += blockDim.x) a[i] = 0xffffffffu;
   __syncthreads();
-  block_bitonic_sort_u32(S.ubk, cu);
-  if (threadIdx.x == 0) {
-    const int c = *ub_cnt;
-    if (c >= k) {
-      *ub_cnt = k;
-      *tau = key_float(S.ubk[k - 1]);
-    }
-  }
+  block_bitonic_sort_u32(a, cap);
+  if (threadIdx.x == 0 && *cnt > keep) *cnt = keep;
   __syncthreads();
 }
 
-// Drop candidates whose lower bound exceeds tau' (in place, order kept).
-__device__ __forceinline__ void compact_cand(int2* cand, int* cnt, int cap, float tau,
-                                            int* scratch) {
+__device__ __forceinline__ void sort_keep_u64(unsigned long long* a, int cap, int* cnt, int keep) {
+  for (int i = *cnt + threadIdx.x; i < cap; i += blockDim.x) a[i] = ~0ull;
+  __syncthreads();
+  block_bitonic_sort_u64(a, cap);
+  if (threadIdx.x == 0 && *cnt > keep) *cnt = keep;
+  __syncthreads();
+}
+
+// In-place, order-keeping compaction of the candidate list with predicate f.
+template <class F>
+__device__ __forceinline__ void compact_cand(int4* cand, int* cnt, int cap, int* scratch, F keep_f) {
   const int n = min(*cnt, cap);
   int out = 0;
   __syncthreads();
   for (int b = 0; b < n; b += blockDim.x) {
     const int i = b + threadIdx.x;
-    int2 e = make_int2(0, 0);
+    int4 e = make_int4(0, 0, 0, 0);
     bool keep = false;
     if (i < n) {
       e = cand[i];
-      keep = __int_as_float(e.y) <= tau;
+      keep = keep_f(e);
     }
     const unsigned bal = __ballot_sync(kFull, keep);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) scratch[wid] = __popc(bal);
     __syncthreads();
-    int before = out;
-    int tot = 0;
+    int before = out, tot = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       if (w < wid) before += scratch[w];
       tot += scratch[w];
@@ -294,25 +302,82 @@ __device__ __forceinline__ void compact_cand(int2* cand, int* cnt, int cap, floa
   __syncthreads();
 }
 
+// Exact squared distances of a list of rows, a warp per 32 rows: the warp
+// stages 32 rows x 32 dims of the raw vectors in shared memory with coalesced
+// loads, then every lane folds its own row in ascending dimension order
+// (canonical squared distance). Keys (distance, id) go to the top-k buffer.
+// SRC 0: the pilot (ids in S.estk); SRC 1: the candidate list (positions).
+template <int SRC>
+__device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q, int count,
+                            const int4* cand, int* top_cnt, int* surv_cnt) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  float* tile = S.tiles + wid * 32 * 33;
+  const int groups = (count + 31) >> 5;
+  for (int g0 = 0; g0 < groups; g0 += nwarps) {
+    const int g = g0 + wid;
+    const int i = g * 32 + lane;
+    const bool valid = (g < groups) && (i < count);
+    int pos = 0, id = 0;
+    if (valid) {
+      if (SRC == 0) {
+        id = (int)(S.estk[i] & 0xffffffffu);
+        pos = P.inv_perm[id];
+      } else {
+        pos = cand[i].x;
+        id = P.perm[pos];
+      }
+    }
+    if (g < groups) {
+      float acc = 0.0f;
+      for (int d0 = 0; d0 < P.d; d0 += 32) {
+        const int wd = min(32, P.d - d0);
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+          const int pr = __shfl_sync(kFull, pos, r);
+          const bool vr = __shfl_sync(kFull, valid, r);
+          if (vr && lane < wd) tile[r * 33 + lane] = P.data_b[(int64_t)pr * P.d + d0 + lane];
+        }
+        __syncwarp();
+        if (valid)
+          for (int dd = 0; dd < wd; ++dd) {
+            const float t = __fsub_rn(S.qv[d0 + dd], tile[lane * 33 + dd]);
+            acc = __fmaf_rn(t, t, acc);
+          }
+        __syncwarp();
+      }
+      if (valid) {
+        S.topk[atomicAdd(top_cnt, 1)] = ((unsigned long long)float_key(acc) << 32) | (uint32_t)id;
+        const int si = atomicAdd(surv_cnt, 1);
+        if (P.tr.surv_ids && si < P.tr.surv_cap) P.tr.surv_ids[q * P.tr.surv_cap + si] = id;
+      }
+    }
+    __syncthreads();
+    if (*top_cnt > P.ct - (int)blockDim.x) sort_keep_u64(S.topk, P.ct, top_cnt, P.k);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_ub_cnt, s_cand_cnt, s_top_cnt, s_overflow;
+  __shared__ int s_ub_cnt, s_est_cnt, s_cand_cnt, s_top_cnt, s_surv, s_overflow;
   __shared__ float s_tau;
+  __shared__ unsigned long long s_est_thr;
   __shared__ int s_scratch[kThreads / 32];
-  size_t off[8];
-  fused_smem_bytes(P.pch, P.bq, P.W, P.d, P.cu, P.ct, off);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+  size_t off[9];
+  fused_smem_bytes(P.pch, P.bq, P.W, P.d, P.cu, P.ce, P.ct, nwarps, off);
   FusedSmem S;
   S.planes = reinterpret_cast<uint64_t*>(smem + off[0]);
+  S.tiles = reinterpret_cast<float*>(smem + off[0]);
   S.pmeta = reinterpret_cast<float4*>(smem + off[1]);
   S.psum = reinterpret_cast<int*>(smem + off[2]);
   S.pbeg = reinterpret_cast<int*>(smem + off[3]);
   S.pref = reinterpret_cast<int*>(smem + off[4]);
   S.qv = reinterpret_cast<float*>(smem + off[5]);
   S.ubk = reinterpret_cast<uint32_t*>(smem + off[6]);
-  S.topk = reinterpret_cast<unsigned long long*>(smem + off[7]);
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
-  const int W = P.W, bq = P.bq, k = P.k;
-  int2* cand = P.cand + (int64_t)blockIdx.x * P.cand_cap;
+  S.estk = reinterpret_cast<unsigned long long*>(smem + off[7]);
+  S.topk = reinterpret_cast<unsigned long long*>(smem + off[8]);
+  const int W = P.W, bq = P.bq, k = P.k, m = P.m;
+  int4* cand = P.cand + (int64_t)blockIdx.x * P.cand_cap;
 
   for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
     int np = P.nprobe;
@@ -320,10 +385,13 @@ __global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
     for (int i = tid; i < P.d; i += blockDim.x) S.qv[i] = P.queries[q * P.d + i];
     if (tid == 0) {
       s_ub_cnt = 0;
+      s_est_cnt = 0;
       s_cand_cnt = 0;
       s_top_cnt = 0;
+      s_surv = 0;
       s_overflow = 0;
       s_tau = __int_as_float(0x7f800000);
+      s_est_thr = ~0ull;
     }
     __syncthreads();
     int pairs_done = 0;
@@ -367,18 +435,25 @@ __global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
             ip += pb << b;
           }
           const float4 f = P.factors[pos];
-          const float4 m = S.pmeta[j];
+          const float4 mt = S.pmeta[j];
+          // estimator (§3.3.2 + Theorem 3.2) and its bound, fixed FP32 order
           const float t1 = (float)(2 * ip - S.psum[j]);
-          const float xq = __fadd_rn(__fmul_rn(m.x, t1), __fmul_rn(m.y, f.w));
-          const float dist = __fsub_rn(__fadd_rn(f.x, m.w), __fmul_rn(f.y, xq));
-          const float e = __fmul_rn(f.z, m.z);
+          const float xq = __fadd_rn(__fmul_rn(mt.x, t1), __fmul_rn(mt.y, f.w));
+          const float dist = __fsub_rn(__fadd_rn(f.x, mt.w), __fmul_rn(f.y, xq));
+          const float e = __fmul_rn(f.z, mt.z);
           const float lb = __fsub_rn(dist, e), ub = __fadd_rn(dist, e);
           const float tau = s_tau;
           if (ub < tau) S.ubk[atomicAdd(&s_ub_cnt, 1)] = float_key(ub);
+          const uint32_t ek = float_key(dist);
+          const unsigned long long thr = s_est_thr;
+          if (ek <= (uint32_t)(thr >> 32)) {
+            const unsigned long long key = ((unsigned long long)ek << 32) | (uint32_t)P.perm[pos];
+            if (key < thr) S.estk[atomicAdd(&s_est_cnt, 1)] = key;
+          }
           if (lb <= tau) {
             const int slot = atomicAdd(&s_cand_cnt, 1);
             if (slot < P.cand_cap)
-              cand[slot] = make_int2((int)pos, __float_as_int(lb));
+              cand[slot] = make_int4((int)pos, __float_as_int(lb), __float_as_int(dist), 0);
             else
               s_overflow = 1;
           }
@@ -395,9 +470,20 @@ __global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
           }
         }
         __syncthreads();
-        if (s_ub_cnt > P.cu - (int)blockDim.x) compact_ub(S, P.cu, k, &s_ub_cnt, &s_tau);
+        if (s_ub_cnt > P.cu - (int)blockDim.x) {  // keep the k smallest upper bounds
+          sort_keep_u32(S.ubk, P.cu, &s_ub_cnt, k);
+          if (tid == 0 && s_ub_cnt >= k) s_tau = key_float(S.ubk[k - 1]);
+          __syncthreads();
+        }
+        if (s_est_cnt > P.ce - (int)blockDim.x) {  // keep the m smallest estimates
+          sort_keep_u64(S.estk, P.ce, &s_est_cnt, m);
+          if (tid == 0 && s_est_cnt >= m) s_est_thr = S.estk[m - 1];
+          __syncthreads();
+        }
         if (s_cand_cnt > P.cand_cap - (int)blockDim.x) {
-          compact_cand(cand, &s_cand_cnt, P.cand_cap, s_tau, s_scratch);
+          const float tau = s_tau;
+          compact_cand(cand, &s_cand_cnt, P.cand_cap, s_scratch,
+                       [tau](const int4& e) { return __int_as_float(e.y) <= tau; });
           if (s_cand_cnt > P.cand_cap - (int)blockDim.x && tid == 0) s_overflow = 1;
           __syncthreads();
         }
@@ -407,51 +493,31 @@ __global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
       __syncthreads();
       if (s_overflow) break;
     }
-    // final tau = k-th smallest upper bound
-    compact_ub(S, P.cu, k, &s_ub_cnt, &s_tau);
-    if (tid == 0 && s_ub_cnt < k) s_tau = __int_as_float(0x7f800000);
-    __syncthreads();
-    const float tau = s_tau;
-    if (tid == 0) {
-      if (s_overflow) atomicExch(P.err, 1);
-      if (P.tr.n_pairs) P.tr.n_pairs[q] = pairs_done;
-      if (P.tr.tau) P.tr.tau[q] = tau;
-    }
-    // survivors: exact distance, top-k by (distance, id)
-    const int nc = min(s_cand_cnt, P.cand_cap);
-    __shared__ int s_surv;
-    if (tid == 0) s_surv = 0;
-    __syncthreads();
-    for (int b = 0; b < nc; b += blockDim.x) {
-      const int i = b + tid;
-      if (i < nc) {
-        const int2 e = cand[i];
-        if (__int_as_float(e.y) <= tau) {
-          const float* x = P.data_b + (int64_t)e.x * P.d;
-          float s = 0.0f;
-          for (int dd = 0; dd < P.d; ++dd) {
-            const float t = __fsub_rn(S.qv[dd], x[dd]);
-            s = __fmaf_rn(t, t, s);
-          }
-          const int id = P.perm[e.x];
-          S.topk[atomicAdd(&s_top_cnt, 1)] =
-              ((unsigned long long)float_key(s) << 32) | (uint32_t)id;
-          const int si = atomicAdd(&s_surv, 1);
-          if (P.tr.surv_ids && si < P.tr.surv_cap) P.tr.surv_ids[q * P.tr.surv_cap + si] = id;
-        }
-      }
-      __syncthreads();
-      if (s_top_cnt > P.ct - (int)blockDim.x) {
-        for (int i2 = s_top_cnt + tid; i2 < P.ct; i2 += blockDim.x) S.topk[i2] = ~0ull;
-        __syncthreads();
-        block_bitonic_sort_u64(S.topk, P.ct);
-        if (tid == 0) s_top_cnt = min(s_top_cnt, k);
-        __syncthreads();
-      }
-    }
-    for (int i2 = s_top_cnt + tid; i2 < P.ct; i2 += blockDim.x) S.topk[i2] = ~0ull;
-    __syncthreads();
-    block_bitonic_sort_u64(S.topk, P.ct);
+    // tau_ub: k-th smallest upper bound; pilot: the m smallest estimates
+    sort_keep_u32(S.ubk, P.cu, &s_ub_cnt, k);
+    const float tau_ub = (s_ub_cnt >= k) ? key_float(S.ubk[k - 1]) : __int_as_float(0x7f800000);
+    sort_keep_u64(S.estk, P.ce, &s_est_cnt, m);
+    const int pilot = s_est_cnt;
+    const unsigned long long pilot_last = pilot > 0 ? S.estk[pilot - 1] : 0ull;
+    const bool pilot_all = pilot < m;  // fewer than m codes: every code is in the pilot
+    // exact distances of the pilot; tau1 = k-th smallest of them
+    rerank_rows<0>(P, S, q, pilot, cand, &s_top_cnt, &s_surv);
+    sort_keep_u64(S.topk, P.ct, &s_top_cnt, k);
+    const float tau1 = (pilot >= k) ? key_float((uint32_t)(S.topk[k - 1] >> 32))
+                                    : __int_as_float(0x7f800000);
+    const float tau = fminf(tau_ub, tau1);
+    // the rest of the re-rank set: LB <= tau, outside the pilot
+    compact_cand(cand, &s_cand_cnt, P.cand_cap, s_scratch, [&](const int4& e) {
+      if (pilot_all || !(__int_as_float(e.y) <= tau)) return false;
+      const uint32_t ek = float_key(__int_as_float(e.z));
+      const uint32_t lk = (uint32_t)(pilot_last >> 32);
+      if (ek < lk) return false;
+      if (ek > lk) return true;
+      const unsigned long long key = ((unsigned long long)ek << 32) | (uint32_t)P.perm[e.x];
+      return key > pilot_last;
+    });
+    rerank_rows<1>(P, S, q, s_cand_cnt, cand, &s_top_cnt, &s_surv);
+    sort_keep_u64(S.topk, P.ct, &s_top_cnt, k);
     const int got = min(s_top_cnt, k);
     for (int j2 = tid; j2 < k; j2 += blockDim.x) {
       const bool ok = j2 < got;
@@ -459,7 +525,14 @@ __global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
       P.out_dist[q * k + j2] =
           ok ? key_float((uint32_t)(S.topk[j2] >> 32)) : __int_as_float(0x7f800000);
     }
-    if (tid == 0 && P.tr.n_surv) P.tr.n_surv[q] = s_surv;
+    if (tid == 0) {
+      if (s_overflow) atomicExch(P.err, 1);
+      if (P.tr.n_pairs) P.tr.n_pairs[q] = pairs_done;
+      if (P.tr.tau_ub) P.tr.tau_ub[q] = tau_ub;
+      if (P.tr.tau1) P.tr.tau1[q] = tau1;
+      if (P.tr.tau) P.tr.tau[q] = tau;
+      if (P.tr.n_surv) P.tr.n_surv[q] = s_surv;
+    }
     __syncthreads();
   }
 }
@@ -484,9 +557,11 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
   // fused-kernel shape
   const int plane_bytes = a.bq * W * 8;
   int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
+  const int m = 4 * a.k;  // pilot size
   const int cu = std::max(1024, pow2_at_least(a.k + kThreads));
+  const int ce = std::max(1024, pow2_at_least(m + kThreads));
   const int ct = std::max(512, pow2_at_least(a.k + kThreads));
-  const size_t smem = fused_smem_bytes(pch, a.bq, W, d, cu, ct, nullptr);
+  const size_t smem = fused_smem_bytes(pch, a.bq, W, d, cu, ce, ct, kThreads / 32, nullptr);
   RBQ_CUDA(cudaFuncSetAttribute(fused_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   int per_sm = 0;
@@ -502,7 +577,7 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
   RBQ_CHECK(rq.alloc(sizeof(float) * qchunk * dpad, s));
   RBQ_CHECK(pid.alloc(sizeof(int32_t) * qchunk * nprobe, s));
   RBQ_CHECK(pdist.alloc(sizeof(float) * qchunk * nprobe, s));
-  RBQ_CHECK(cand.alloc(sizeof(int2) * grid * a.cand_cap, s));
+  RBQ_CHECK(cand.alloc(sizeof(int4) * grid * a.cand_cap, s));
   RBQ_CHECK(err.alloc(sizeof(int), s));
   RBQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
 
@@ -548,6 +623,7 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
     P.factors = X->factors;
     P.data_b = X->data_b;
     P.perm = X->perm;
+    P.inv_perm = X->inv_perm;
     P.bucket_off = X->bucket_off;
     P.nq = m;
     P.q_offset = q0;
@@ -558,12 +634,14 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
     P.k = a.k;
     P.nprobe = nprobe;
     P.pch = pch;
+    P.m = m;
     P.cu = cu;
+    P.ce = ce;
     P.ct = ct;
     P.eps0 = a.eps0;
     P.seed = a.seed;
     P.cand_cap = a.cand_cap;
-    P.cand = cand.as<int2>();
+    P.cand = cand.as<int4>();
     P.out_ids = a.out_ids + q0 * a.k;
     P.out_dist = a.out_dist + q0 * a.k;
     P.err = err.as<int>();
@@ -583,6 +661,8 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
         P.tr.pair_ip = T.pair_ip + q0 * T.pair_cap;
         P.tr.pair_est = T.pair_est + q0 * T.pair_cap * 3;
       }
+      if (T.tau_ub) P.tr.tau_ub = T.tau_ub + q0;
+      if (T.tau1) P.tr.tau1 = T.tau1 + q0;
       if (T.tau) P.tr.tau = T.tau + q0;
       if (T.n_surv) P.tr.n_surv = T.n_surv + q0;
       if (T.surv_ids) P.tr.surv_ids = T.surv_ids + q0 * T.surv_cap;

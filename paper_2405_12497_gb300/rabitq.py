@@ -53,7 +53,8 @@ class Trace(C.Structure):
     _fields_ = [("probe_ids", C.c_void_p), ("probe_dist", C.c_void_p), ("rq", C.c_void_p),
                 ("planes", C.c_void_p), ("sum_qu", C.c_void_p), ("meta", C.c_void_p),
                 ("pair_cap", C.c_int32), ("n_pairs", C.c_void_p), ("pair_id", C.c_void_p),
-                ("pair_ip", C.c_void_p), ("pair_est", C.c_void_p), ("tau", C.c_void_p),
+                ("pair_ip", C.c_void_p), ("pair_est", C.c_void_p), ("tau_ub", C.c_void_p),
+                ("tau1", C.c_void_p), ("tau", C.c_void_p),
                 ("surv_cap", C.c_int32), ("n_surv", C.c_void_p), ("surv_ids", C.c_void_p)]
 
 
@@ -247,7 +248,7 @@ class Index:
         return o
 
     def search(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
-               quant_seed: int = 3, per_query_nprobe=None, max_candidates: int = 16384,
+               quant_seed: int = 3, per_query_nprobe=None, max_candidates: int = 65536,
                stats: bool = False, stream=None, out=None, rot_precision=ROT_FP32,
                scan_path=SCAN_AUTO):
         """k-NN search. numpy queries -> numpy (ids int64, dists float32) via
@@ -286,7 +287,7 @@ class Index:
 
     def search_trace(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
                      quant_seed: int = 3, pair_cap: int = 0, surv_cap: int = 0,
-                     max_candidates: int = 16384):
+                     max_candidates: int = 65536):
         """Search of torch CUDA queries that also returns every intermediate
         (torch CUDA tensors)."""
         import torch
@@ -306,6 +307,8 @@ class Index:
             "pair_id": torch.full((nq, max(pair_cap, 1)), -1, dtype=torch.int32, device=dev),
             "pair_ip": torch.zeros((nq, max(pair_cap, 1)), dtype=torch.int32, device=dev),
             "pair_est": torch.zeros((nq, max(pair_cap, 1), 3), dtype=torch.float32, device=dev),
+            "tau_ub": torch.zeros(nq, dtype=torch.float32, device=dev),
+            "tau1": torch.zeros(nq, dtype=torch.float32, device=dev),
             "tau": torch.zeros(nq, dtype=torch.float32, device=dev),
             "n_surv": torch.zeros(nq, dtype=torch.int32, device=dev),
             "surv_ids": torch.full((nq, max(surv_cap, 1)), -1, dtype=torch.int32, device=dev),
@@ -316,7 +319,8 @@ class Index:
                    _dptr(t["pair_id"]) if pair_cap else None,
                    _dptr(t["pair_ip"]) if pair_cap else None,
                    _dptr(t["pair_est"]) if pair_cap else None,
-                   _dptr(t["tau"]), surv_cap, _dptr(t["n_surv"]),
+                   _dptr(t["tau_ub"]), _dptr(t["tau1"]), _dptr(t["tau"]), surv_cap,
+                   _dptr(t["n_surv"]),
                    _dptr(t["surv_ids"]) if surv_cap else None)
         ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
         dist = torch.empty((nq, k), dtype=torch.float32, device=dev)

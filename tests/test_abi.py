@@ -52,7 +52,7 @@ def test_invalid_arguments_fail_before_device_work(L):
     assert lib.rabitq_index_load(b"/nonexistent/file", None, C.byref(h)) == L.EIO
     so = L.SearchOpts()
     lib.rabitq_search_opts_default(C.byref(so))
-    assert so.quant_seed == 3 and so.max_candidates == 16384
+    assert so.quant_seed == 3 and so.max_candidates == 65536
     lib.rabitq_free(None)
 
 

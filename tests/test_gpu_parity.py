@@ -71,7 +71,8 @@ def _compare_trace(G, O, t, i, q, qid, k, nprobe, bq=4, eps0=1.9, seed=3):
     assert np.array_equal(t["pair_ip"][i, :n].cpu().numpy(), o["pair_ip"])
     assert np.array_equal(t["pair_est"][i, :n].cpu().numpy().view(np.uint32),
                           o["pair_est"].view(np.uint32))
-    assert np.float32(t["tau"][i].item()).view(np.uint32) == np.float32(o["tau"]).view(np.uint32)
+    for key in ("tau", "tau_ub", "tau1"):
+        assert np.float32(t[key][i].item()).view(np.uint32) == np.float32(o[key]).view(np.uint32), key
     ns = int(t["n_surv"][i])
     assert ns == len(o["surv_ids"])
     assert np.array_equal(np.sort(t["surv_ids"][i, :ns].cpu().numpy()), o["surv_ids"])

@@ -371,18 +371,28 @@ def test_search_equals_exact_knn_over_probed_buckets(oracle_mod, tiny_oracle_ind
     assert (ids1 == ids).all(1).mean() >= 0.97
 
 
-def test_trace_survivors_are_exactly_the_bound_set(oracle_mod, tiny_oracle_index, tiny_workload):
+def test_trace_rerank_set_definition(oracle_mod, tiny_oracle_index, tiny_workload):
+    """Re-rank set = pilot (4k smallest estimates by (estimate, id)) plus
+    every code with LB <= min(k-th smallest UB, k-th smallest exact distance
+    in the pilot); recomputed here from the per-pair estimates."""
     X = tiny_oracle_index
     _, Q = tiny_workload
-    t = X.trace(Q[3], 3, 10, 4)
-    ub = np.sort(t["pair_est"][:, 2])
-    assert t["tau"] == ub[9]
-    surv = np.sort(t["pair_id"][t["pair_est"][:, 1] <= t["tau"]])
-    assert np.array_equal(surv, t["surv_ids"])
-    # the true 10-NN of the probed buckets survive and are returned
-    ex = ((X.data[t["pair_id"]] - Q[3]) ** 2).sum(1)
-    top = t["pair_id"][np.lexsort((t["pair_id"], ex))[:10]]
-    assert set(top.tolist()) <= set(t["surv_ids"].tolist())
+    for qi, k, nprobe in ((3, 10, 4), (7, 1, 2), (11, 50, 16)):
+        t = X.trace(Q[qi], qi, k, nprobe)
+        ids, est = t["pair_id"], t["pair_est"]
+        assert t["tau_ub"] == np.sort(est[:, 2])[k - 1]
+        pilot = np.lexsort((ids, est[:, 0]))[:4 * k]
+        ex = oracle_mod.sqdist_matrix(Q[qi:qi + 1], X.data[ids[pilot]])[0]
+        assert t["tau1"] == np.sort(ex)[k - 1]
+        tau = min(t["tau_ub"], t["tau1"])
+        assert t["tau"] == tau
+        want = np.union1d(ids[pilot], ids[est[:, 1] <= tau])
+        assert np.array_equal(want, t["surv_ids"])
+        # the exact k-NN of the probed buckets survive and are returned
+        exa = oracle_mod.sqdist_matrix(Q[qi:qi + 1], X.data[ids])[0]
+        top = ids[np.lexsort((ids, exa))[:k]]
+        assert set(top.tolist()) <= set(t["surv_ids"].tolist())
+        assert np.array_equal(np.sort(top), np.sort(t["ids"]))
 
 
 def test_recall_with_all_buckets_at_eps0(oracle_mod, tiny_oracle_index, tiny_workload):
