@@ -557,9 +557,9 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
   // fused-kernel shape
   const int plane_bytes = a.bq * W * 8;
   int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
-  const int m = 4 * a.k;  // pilot size
+  const int pilot_m = 4 * a.k;  // pilot size
   const int cu = std::max(1024, pow2_at_least(a.k + kThreads));
-  const int ce = std::max(1024, pow2_at_least(m + kThreads));
+  const int ce = std::max(1024, pow2_at_least(pilot_m + kThreads));
   const int ct = std::max(512, pow2_at_least(a.k + kThreads));
   const size_t smem = fused_smem_bytes(pch, a.bq, W, d, cu, ce, ct, kThreads / 32, nullptr);
   RBQ_CUDA(cudaFuncSetAttribute(fused_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -592,23 +592,23 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
   RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sel_smem));
   for (int64_t q0 = 0; q0 < a.nq; q0 += qchunk) {
-    const int64_t m = std::min(qchunk, a.nq - q0);
+    const int64_t nqc = std::min(qchunk, a.nq - q0);
     const float* Q = a.queries + q0 * d;
     if (timing) RBQ_CUDA(cudaEventRecord(ev[0], s));
     RBQ_CHECK(gemm_canon(kSqDist, Q, d, nullptr, nullptr, 0, nullptr, X->centroids_t, K,
-                         cd.as<float>(), K, m, K, d, s));
+                         cd.as<float>(), K, nqc, K, d, s));
     if (timing) RBQ_CUDA(cudaEventRecord(ev[1], s));
     int32_t* probe_ids = a.trace && a.trace->probe_ids ? a.trace->probe_ids + q0 * nprobe
                                                        : pid.as<int32_t>();
     float* probe_dist = a.trace && a.trace->probe_dist ? a.trace->probe_dist + q0 * nprobe
                                                        : pdist.as<float>();
-    select_kernel<<<(unsigned)m, kThreads, sel_smem, s>>>(
+    select_kernel<<<(unsigned)nqc, kThreads, sel_smem, s>>>(
         cd.as<float>(), K, nprobe, a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr,
         sort_n, probe_ids, probe_dist);
     RBQ_CUDA(cudaGetLastError());
     if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
     float* rqp = a.trace && a.trace->rq ? a.trace->rq + q0 * dpad : rq.as<float>();
-    RBQ_CHECK(gemm_canon(kDot, Q, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rqp, dpad, m,
+    RBQ_CHECK(gemm_canon(kDot, Q, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rqp, dpad, nqc,
                          dpad, d, s));
     if (timing) RBQ_CUDA(cudaEventRecord(ev[3], s));
     FusedParams P;
@@ -625,7 +625,7 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
     P.perm = X->perm;
     P.inv_perm = X->inv_perm;
     P.bucket_off = X->bucket_off;
-    P.nq = m;
+    P.nq = nqc;
     P.q_offset = q0;
     P.d = d;
     P.dpad = dpad;
@@ -634,7 +634,7 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
     P.k = a.k;
     P.nprobe = nprobe;
     P.pch = pch;
-    P.m = m;
+    P.m = pilot_m;
     P.cu = cu;
     P.ce = ce;
     P.ct = ct;
@@ -667,7 +667,7 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
       if (T.n_surv) P.tr.n_surv = T.n_surv + q0;
       if (T.surv_ids) P.tr.surv_ids = T.surv_ids + q0 * T.surv_cap;
     }
-    const unsigned g = (unsigned)std::min<int64_t>(m, grid);
+    const unsigned g = (unsigned)std::min<int64_t>(nqc, grid);
     fused_search_kernel<<<g, kThreads, smem, s>>>(P);
     RBQ_CUDA(cudaGetLastError());
     if (timing) {
