@@ -62,13 +62,13 @@ def _chunks(n: int, step: int = 1 << 18):
 
 def sift_like(n: int, nq: int, d: int = 128, seed_data: int = 0, seed_query: int = 1):
     """Non-negative integer-valued vectors in [0, 255] (SIFT-shaped): a mixture
-    of n/50 components with heavy-tailed per-dimension scales s_d =
+    of n/100 components with heavy-tailed per-dimension scales s_d =
     exp(N(0, 1/4)), centers mu[c, d] = 32 s_d Exp(1), and points
-    x = clip(round(mu + 20 s_d N(0, 1)), 0, 255). The overlap between
-    components is set so that an IVF with ~244 points per bucket needs a few
-    dozen probes for recall@100 = 0.95, as on the real dataset."""
+    x = clip(round(mu + 24 s_d N(0, 1)), 0, 255). The overlap between
+    components is set so that an IVF with K = 4096 over 1M points needs about
+    64 probes for recall@100 = 0.95."""
     g = np.random.Generator(np.random.PCG64(seed_data))
-    n_comp = max(10, n // 50)
+    n_comp = max(10, n // 100)
     scale = np.exp(0.5 * g.standard_normal(d))
     mu = 32.0 * scale * g.exponential(1.0, (n_comp, d))
 
@@ -77,7 +77,7 @@ def sift_like(n: int, nq: int, d: int = 128, seed_data: int = 0, seed_query: int
         out = np.empty((m, d), np.float32)
         for s, e in _chunks(m):
             comp = gg.integers(0, n_comp, e - s)
-            x = mu[comp] + 20.0 * scale * gg.standard_normal((e - s, d))
+            x = mu[comp] + 24.0 * scale * gg.standard_normal((e - s, d))
             out[s:e] = np.clip(np.rint(x), 0, 255)
         return out
 
