@@ -167,6 +167,30 @@ int rabitq_search_trace(const rabitq_index* idx, const float* queries, int64_t n
                         float* out_dist, const rabitq_search_opts* opts,
                         const rabitq_trace* trace);
 
+/*
+ * rabitq_search_noalloc -- rabitq_search that allocates no memory, for callers
+ * that cannot allocate when they search: a serving process whose own allocator
+ * already holds the GPU's free memory, a latency-critical path that must not
+ * pay an allocation, a host that forbids allocation after start-up. The paper
+ * has no counterpart; this is a library convenience.
+ * Arguments and results are those of rabitq_search, except that queries,
+ * out_ids, out_dist and opts->per_query_nprobe must be DEVICE pointers
+ * (io_on_device is implied), no trace or stats are produced, and only the
+ * FP32 rotation and popcount scan are available.
+ * Scratch: one fixed 64 MiB device array inside the library (every GPU that
+ * loads the library holds it until exit); queries are processed in chunks
+ * that fit it. The candidate capacity is min(max_candidates, what fits); a
+ * query whose candidates do not fit returns EOVERFLOW. The first call on a
+ * device looks up the array's device address with that device current; make
+ * that first call before any stream capture. All calls share the array:
+ * calls that overlap on the GPU race. Errors: those of rabitq_search, plus
+ * EINVAL for host pointers or for a K so large that one query's centroid
+ * distances do not fit in the scratch.
+ */
+int rabitq_search_noalloc(const rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
+                          int32_t nprobe, int32_t bq, float eps0, int64_t* out_ids,
+                          float* out_dist, const rabitq_search_opts* opts);
+
 /* Per-stage device times (milliseconds) of the last search on this thread
  * with collect_stats set. Stages: 0 centroid distances, 1 probe selection,
  * 2 query rotation, 3 quantize + scan + prune + re-rank, 4 total (including

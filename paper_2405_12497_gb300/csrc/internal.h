@@ -109,5 +109,7 @@ struct SearchArgs {
   float* stage_ms;    // host, 5 entries or null
 };
 int search_dev(const SearchArgs& a, cudaStream_t s);
+int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scratch_bytes,
+                        cudaStream_t s);
 
 }  // namespace rbq

@@ -693,4 +693,115 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
   return RABITQ_OK;
 }
 
+// The same pipeline as search_dev, with every scratch array carved out of a
+// caller-provided device buffer instead of being allocated: query chunks are
+// sized to what fits. Used by the entry point that must not allocate.
+int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scratch_bytes,
+                        cudaStream_t s) {
+  const rabitq_index* X = a.X;
+  const int K = X->K, d = X->d, dpad = X->dpad, W = X->W;
+  const int nprobe = std::min(a.nprobe, K);
+  if (a.nq == 0) return RABITQ_OK;
+  int dev = 0, sms = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
+  RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int plane_bytes = a.bq * W * 8;
+  const int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
+  const int pilot_m = 4 * a.k;
+  const int cu = std::max(1024, pow2_at_least(a.k + kThreads));
+  const int ce = std::max(1024, pow2_at_least(pilot_m + kThreads));
+  const int ct = std::max(512, pow2_at_least(a.k + kThreads));
+  const size_t smem = fused_smem_bytes(pch, a.bq, W, d, cu, ce, ct, kThreads / 32, nullptr);
+  RBQ_CUDA(cudaFuncSetAttribute(fused_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  const int sort_n = pow2_at_least(nprobe);
+  const size_t sel_smem = sizeof(unsigned long long) * sort_n;
+  RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sel_smem));
+  // layout: [error flag | candidate lists (one CTA per SM) | per-chunk query arrays]
+  const size_t A = 256;
+  const int64_t grid = sms;
+  size_t off = A;
+  const size_t cand_room = scratch_bytes / 2 > off ? scratch_bytes / 2 - off : 0;
+  int64_t cap = std::min<int64_t>(a.cand_cap, (int64_t)(cand_room / (sizeof(int4) * grid)));
+  if (cap < 1024) return fail(RABITQ_EINVAL, "rabitq_search_noalloc: scratch too small");
+  int4* cand = reinterpret_cast<int4*>(scratch + off);
+  off = align_up(off + sizeof(int4) * grid * cap, A);
+  const size_t per_q = sizeof(float) * K + sizeof(float) * dpad + sizeof(int32_t) * nprobe +
+                       sizeof(float) * nprobe;
+  const size_t room = scratch_bytes > off + 4 * A ? scratch_bytes - off - 4 * A : 0;
+  const int64_t qchunk = std::min<int64_t>(a.nq, (int64_t)(room / per_q));
+  if (qchunk < 1)
+    return fail(RABITQ_EINVAL,
+                "rabitq_search_noalloc: one query's distances to every centroid do not fit in "
+                "the fixed scratch (K too large)");
+  float* cd = reinterpret_cast<float*>(scratch + off);
+  off = align_up(off + sizeof(float) * qchunk * K, A);
+  float* rq = reinterpret_cast<float*>(scratch + off);
+  off = align_up(off + sizeof(float) * qchunk * dpad, A);
+  int32_t* pid = reinterpret_cast<int32_t*>(scratch + off);
+  off = align_up(off + sizeof(int32_t) * qchunk * nprobe, A);
+  float* pdist = reinterpret_cast<float*>(scratch + off);
+  off = align_up(off + sizeof(float) * qchunk * nprobe, A);
+  if (off > scratch_bytes) return fail(RABITQ_EINVAL, "rabitq_search_noalloc: layout overflow");
+  int* err = reinterpret_cast<int*>(scratch);
+  RBQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));  // the flag must start at zero
+  for (int64_t q0 = 0; q0 < a.nq; q0 += qchunk) {
+    const int64_t nqc = std::min(qchunk, a.nq - q0);
+    const float* Q = a.queries + q0 * d;
+    RBQ_CHECK(gemm_canon(kSqDist, Q, d, nullptr, nullptr, 0, nullptr, X->centroids_t, K, cd, K,
+                         nqc, K, d, s));
+    select_kernel<<<(unsigned)nqc, kThreads, sel_smem, s>>>(
+        cd, K, nprobe, a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr, sort_n, pid,
+        pdist);
+    RBQ_CUDA(cudaGetLastError());
+    RBQ_CHECK(gemm_canon(kDot, Q, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rq, dpad, nqc,
+                         dpad, d, s));
+    FusedParams P;
+    std::memset(&P, 0, sizeof P);
+    P.queries = Q;
+    P.rq = rq;
+    P.probe_ids = pid;
+    P.probe_dist = pdist;
+    P.nprobe_q = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
+    P.ptc = X->ptc;
+    P.codes = X->codes;
+    P.factors = X->factors;
+    P.data_b = X->data_b;
+    P.perm = X->perm;
+    P.inv_perm = X->inv_perm;
+    P.bucket_off = X->bucket_off;
+    P.nq = nqc;
+    P.q_offset = q0;
+    P.d = d;
+    P.dpad = dpad;
+    P.W = W;
+    P.bq = a.bq;
+    P.k = a.k;
+    P.nprobe = nprobe;
+    P.pch = pch;
+    P.m = pilot_m;
+    P.cu = cu;
+    P.ce = ce;
+    P.ct = ct;
+    P.eps0 = a.eps0;
+    P.seed = a.seed;
+    P.cand_cap = (int)cap;
+    P.cand = cand;
+    P.out_ids = a.out_ids + q0 * a.k;
+    P.out_dist = a.out_dist + q0 * a.k;
+    P.err = err;
+    fused_search_kernel<<<(unsigned)std::min<int64_t>(nqc, grid), kThreads, smem, s>>>(P);
+    RBQ_CUDA(cudaGetLastError());
+  }
+  int h_err = 0;
+  RBQ_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RBQ_CUDA(cudaStreamSynchronize(s));
+  if (h_err)
+    return fail(RABITQ_EOVERFLOW,
+                "a query's candidate list exceeded the fixed scratch's capacity");
+  return RABITQ_OK;
+}
+
+
 }  // namespace rbq

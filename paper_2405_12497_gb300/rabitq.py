@@ -26,7 +26,7 @@ EXPORTS = (
     "rabitq_search_trace", "rabitq_last_stats", "rabitq_index_info", "rabitq_get_centroids",
     "rabitq_get_rotation", "rabitq_get_codes", "rabitq_get_factors", "rabitq_get_assign",
     "rabitq_get_buckets", "rabitq_sample_rotation", "rabitq_index_save", "rabitq_index_load",
-    "rabitq_free", "rabitq_last_error",
+    "rabitq_free", "rabitq_last_error", "rabitq_search_noalloc",
 )
 
 
@@ -76,6 +76,7 @@ def lib():
             "rabitq_build": (C.c_int, [vp, i64, i32, i32, u64, vp, vp]),
             "rabitq_search": (C.c_int, [vp, vp, i64, i32, i32, i32, f32, vp, vp, vp]),
             "rabitq_search_trace": (C.c_int, [vp, vp, i64, i32, i32, i32, f32, vp, vp, vp, vp]),
+            "rabitq_search_noalloc": (C.c_int, [vp, vp, i64, i32, i32, i32, f32, vp, vp, vp]),
             "rabitq_last_stats": (C.c_int, [vp, i32]),
             "rabitq_index_info": (C.c_int, [vp, vp, vp, vp, vp]),
             "rabitq_get_centroids": (C.c_int, [vp, vp]),
