@@ -705,7 +705,8 @@ static void search_one(const orc_index* X, const orc_params* p, const float* q, 
     /* Order-independent reading of the re-ranking rule of §4 for k >= 1:
      *  tau_ub = k-th smallest upper bound over all estimated codes;
      *  pilot  = the 4k codes with the smallest estimated distance (by
-     *           (estimate, id)), re-ranked first;
+     *           (estimate, id)) among those with LB <= tau_ub, re-ranked
+     *           first;
      *  tau1   = k-th smallest exact distance within the pilot;
      *  tau    = min(tau_ub, tau1) (each is at least the k-th nearest exact
      *           distance, w.h.p. for tau_ub, always for tau1);
@@ -718,14 +719,16 @@ static void search_one(const orc_index* X, const orc_params* p, const float* q, 
       tau_ub = ubs[k - 1];
       free(ubs);
     }
-    const int64_t m = (4 * (int64_t)k < t) ? 4 * (int64_t)k : t;
+    const int64_t m = 4 * (int64_t)k;
     uint8_t* in_set = (uint8_t*)calloc((size_t)(t + 1), 1);
-    /* pilot: m smallest (estimate, id), by selection into a sorted list */
+    /* pilot: m smallest (estimate, id) with LB <= tau_ub, by selection into a
+     * sorted list */
     float* pd = (float*)malloc(sizeof(float) * (size_t)(m + 1));
     int32_t* pi = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
     int32_t* pix = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
     int32_t pc = 0;
     for (int64_t i = 0; i < t; ++i) {
+      if (!(pest[3 * i + 1] <= tau_ub)) continue;
       float e = pest[3 * i + 0];
       int32_t id = pid[i];
       if (pc == m && cmp_pair(e, id, pd[m - 1], pi[m - 1]) >= 0) continue;

@@ -109,6 +109,13 @@ __global__ void __launch_bounds__(kThreads) select_kernel(
 }
 
 // ------------------------------------------------------ fused query kernel
+// Shared state of the block radix select.
+struct SelState {
+  int hist[256];
+  int bin, rem, tie_taken;
+  int warp_cnt[kThreads / 32];
+};
+
 struct FusedParams {
   const float* queries;     // nq x d
   const float* rq;          // nq x dpad
@@ -135,15 +142,15 @@ struct FusedParams {
 };
 
 struct FusedSmem {
-  uint64_t* planes;  // pch x bq x W   (re-used as re-rank tiles after the scan)
-  float* tiles;      // nwarps x 32 x 33
+  uint64_t* planes;  // pch x bq x W
   float4* pmeta;     // pch: A, B, E, nq2
   int* psum;         // pch
   int* pbeg;         // pch
   int* pref;         // pch + 1
   float* qv;         // d
+  SelState* sel;     // radix-select scratch
   uint32_t* ubk;     // cu: upper-bound keys
-  unsigned long long* estk;  // ce: (estimate key << 32) | id
+  unsigned long long* estk;  // ce: the pilot list, (id << 32) | position
   unsigned long long* topk;  // ct: (exact distance key << 32) | id
 };
 
@@ -153,9 +160,8 @@ __host__ __device__ inline size_t fused_smem_bytes(int pch, int bq, int W, int d
                                                    int ct, int nwarps,
                                                    size_t* off /* 9 entries or null */) {
   size_t o = 0, offs[9];
-  const size_t planes = sizeof(uint64_t) * pch * bq * W;
-  const size_t tiles = sizeof(float) * nwarps * 32 * 33;
-  offs[0] = o; o = align_up(o + (planes > tiles ? planes : tiles), 16);
+  (void)nwarps;
+  offs[0] = o; o = align_up(o + sizeof(uint64_t) * pch * bq * W, 16);
   offs[1] = o; o = align_up(o + sizeof(float4) * pch, 16);
   offs[2] = o; o = align_up(o + sizeof(int) * pch, 16);
   offs[3] = o; o = align_up(o + sizeof(int) * pch, 16);
@@ -253,6 +259,135 @@ __device__ __forceinline__ void quantize_probe(const FusedParams& P, const Fused
   }
 }
 
+// Warp-aggregated slot reservation: lanes with `want` get consecutive slots
+// from one atomicAdd per warp (shared-memory counters are hot).
+__device__ __forceinline__ int warp_reserve(bool want, int* counter) {
+  const unsigned m = __ballot_sync(kFull, want);
+  if (m == 0) return -1;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(kFull, base, leader);
+  return want ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
+
+// ---------------------------------------------------------- block select
+// The want-th smallest (1-based, want <= n) of the n keys a[0..n) by an
+// MSD radix select, 8 bits per pass; histogram updates are aggregated per
+// warp by digit. On return st.rem = how many keys equal to the result are
+// among the `want` smallest. Whole block; synchronized on return.
+template <class K, class F>
+__device__ K block_select_f(int n, int want, SelState& st, F keyf) {
+  constexpr int NB = (int)sizeof(K) * 8;
+  const int tid = threadIdx.x, lane = tid & 31;
+  K prefix = 0, mask = 0;
+  int rem = want;
+  for (int shift = NB - 8; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += blockDim.x) st.hist[i] = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < n; b0 += blockDim.x) {
+      const int i = b0 + tid;
+      K key = 0;
+      bool v = false;
+      if (i < n) {
+        key = keyf(i);
+        v = (key & mask) == prefix;
+      }
+      const int dig = v ? (int)((key >> shift) & 255) : 256 + lane;
+      const unsigned grp = __match_any_sync(kFull, dig);
+      if (v && lane == __ffs(grp) - 1) atomicAdd(&st.hist[dig], __popc(grp));
+    }
+    __syncthreads();
+    if (tid < 32) {
+      int c[8], sum = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        c[u] = st.hist[lane * 8 + u];
+        sum += c[u];
+      }
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned hit = __ballot_sync(kFull, incl >= rem);
+      if (lane == __ffs(hit) - 1) {
+        int cum = incl - sum;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (cum + c[u] >= rem) {
+            st.bin = lane * 8 + u;
+            st.rem = rem - cum;
+            break;
+          }
+          cum += c[u];
+        }
+      }
+    }
+    __syncthreads();
+    prefix |= (K)st.bin << shift;
+    mask |= (K)255 << shift;
+    rem = st.rem;
+    __syncthreads();
+  }
+  return prefix;
+}
+
+template <class K>
+__device__ K block_select(const K* a, int n, int want, SelState& st) {
+  return block_select_f<K>(n, want, st, [a](int i) { return a[i]; });
+}
+
+// In place, keep the keys below T and `ties` of the keys equal to T; returns
+// the new count (whole block; synchronized on return).
+template <class K>
+__device__ int block_keep_below(K* a, int n, K T, int ties, SelState& st) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) st.tie_taken = 0;
+  __syncthreads();
+  int out = 0;
+  for (int b0 = 0; b0 < n; b0 += blockDim.x) {
+    const int i = b0 + tid;
+    K key = 0;
+    bool keep = false;
+    if (i < n) {
+      key = a[i];
+      keep = key < T || (key == T && atomicAdd(&st.tie_taken, 1) < ties);
+    }
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (lane == 0) st.warp_cnt[wid] = __popc(bal);
+    __syncthreads();
+    int before = out, tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      if (w < wid) before += st.warp_cnt[w];
+      tot += st.warp_cnt[w];
+    }
+    if (keep) a[before + __popc(bal & ((1u << lane) - 1u))] = key;
+    out += tot;
+    __syncthreads();
+  }
+  return out;
+}
+
+// Keep the `keep` smallest of the *cnt keys (no order); returns the
+// keep-th smallest key (or ~0 if there are fewer than keep keys).
+template <class K>
+__device__ K select_keep(K* a, int* cnt, int keep, SelState& st) {
+  const int n = *cnt;
+  if (n < keep) {
+    __syncthreads();
+    return ~(K)0;
+  }
+  const K T = block_select<K>(a, n, keep, st);
+  const int kept = block_keep_below<K>(a, n, T, st.rem, st);
+  if (threadIdx.x == 0) *cnt = kept;
+  __syncthreads();
+  return T;
+}
+
 // Sort a shared key buffer (padded with the maximum key), keep the `keep`
 // smallest; returns the count kept. Whole block; synchronized on return.
 __device__ __forceinline__ void sort_keep_u32(uint32_t* a, int cap, int* cnt, int keep) {
@@ -302,77 +437,167 @@ __device__ __forceinline__ void compact_cand(int4* cand, int* cnt, int cap, int*
   __syncthreads();
 }
 
-// Exact squared distances of a list of rows, a warp per 32 rows: the warp
-// stages 32 rows x 32 dims of the raw vectors in shared memory with coalesced
-// loads, then every lane folds its own row in ascending dimension order
-// (canonical squared distance). Keys (distance, id) go to the top-k buffer.
+// Exact squared distances of a list of rows: each lane streams its own row
+// with 16-byte loads (eight in flight per lane, a warp has 256 rows' worth of
+// loads outstanding) and folds it in ascending dimension order (canonical
+// squared distance). Keys (distance, id) go to the top-k buffer.
 // SRC 0: the pilot (ids in S.estk); SRC 1: the candidate list (positions).
 template <int SRC>
 __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q, int count,
                             const int4* cand, int* top_cnt, int* surv_cnt) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  float* tile = S.tiles + wid * 32 * 33;
-  const int groups = (count + 31) >> 5;
-  for (int g0 = 0; g0 < groups; g0 += nwarps) {
-    const int g = g0 + wid;
-    const int i = g * 32 + lane;
-    const bool valid = (g < groups) && (i < count);
+  const int d = P.d;
+  const bool vec = (d & 3) == 0;
+  for (int r0 = 0; r0 < count; r0 += blockDim.x) {
+    const int i = r0 + threadIdx.x;
+    const bool valid = i < count;
     int pos = 0, id = 0;
     if (valid) {
       if (SRC == 0) {
-        id = (int)(S.estk[i] & 0xffffffffu);
-        pos = P.inv_perm[id];
+        const unsigned long long e = S.estk[i];
+        id = (int)(e >> 32);
+        pos = (int)(e & 0xffffffffu);
       } else {
         pos = cand[i].x;
         id = P.perm[pos];
       }
     }
-    if (g < groups) {
-      float acc = 0.0f;
-      for (int d0 = 0; d0 < P.d; d0 += 32) {
-        const int wd = min(32, P.d - d0);
-#pragma unroll 8
-        for (int r = 0; r < 32; ++r) {
-          const int pr = __shfl_sync(kFull, pos, r);
-          const bool vr = __shfl_sync(kFull, valid, r);
-          if (vr && lane < wd) tile[r * 33 + lane] = P.data_b[(int64_t)pr * P.d + d0 + lane];
-        }
-        __syncwarp();
-        if (valid)
-          for (int dd = 0; dd < wd; ++dd) {
-            const float t = __fsub_rn(S.qv[d0 + dd], tile[lane * 33 + dd]);
-            acc = __fmaf_rn(t, t, acc);
+    float acc = 0.0f;
+    if (valid) {
+      const float* x = P.data_b + (int64_t)pos * d;
+      if (vec) {
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        const float4* q4 = reinterpret_cast<const float4*>(S.qv);
+        int c = 0;
+        for (; c + 8 <= (d >> 2); c += 8) {
+          float4 v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = __ldg(x4 + c + u);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float4 qq = q4[c + u];
+            float t = __fsub_rn(qq.x, v[u].x); acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(qq.y, v[u].y); acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(qq.z, v[u].z); acc = __fmaf_rn(t, t, acc);
+            t = __fsub_rn(qq.w, v[u].w); acc = __fmaf_rn(t, t, acc);
           }
-        __syncwarp();
-      }
-      if (valid) {
-        S.topk[atomicAdd(top_cnt, 1)] = ((unsigned long long)float_key(acc) << 32) | (uint32_t)id;
-        const int si = atomicAdd(surv_cnt, 1);
-        if (P.tr.surv_ids && si < P.tr.surv_cap) P.tr.surv_ids[q * P.tr.surv_cap + si] = id;
+        }
+        for (; c < (d >> 2); ++c) {
+          const float4 vv = __ldg(x4 + c), qq = q4[c];
+          float t = __fsub_rn(qq.x, vv.x); acc = __fmaf_rn(t, t, acc);
+          t = __fsub_rn(qq.y, vv.y); acc = __fmaf_rn(t, t, acc);
+          t = __fsub_rn(qq.z, vv.z); acc = __fmaf_rn(t, t, acc);
+          t = __fsub_rn(qq.w, vv.w); acc = __fmaf_rn(t, t, acc);
+        }
+      } else {
+        for (int dd = 0; dd < d; ++dd) {
+          const float t = __fsub_rn(S.qv[dd], __ldg(x + dd));
+          acc = __fmaf_rn(t, t, acc);
+        }
       }
     }
+    const int slot = warp_reserve(valid, top_cnt);
+    if (valid) {
+      S.topk[slot] = ((unsigned long long)float_key(acc) << 32) | (uint32_t)id;
+      const int si = i + (SRC == 0 ? 0 : *surv_cnt);
+      if (P.tr.surv_ids && si < P.tr.surv_cap) P.tr.surv_ids[q * P.tr.surv_cap + si] = id;
+    }
     __syncthreads();
-    if (*top_cnt > P.ct - (int)blockDim.x) sort_keep_u64(S.topk, P.ct, top_cnt, P.k);
+    if (*top_cnt > P.ct - (int)blockDim.x) select_keep<unsigned long long>(S.topk, top_cnt, P.k, *S.sel);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *surv_cnt += count;
+  __syncthreads();
+}
+
+// Code words of one code held in registers (WT > 0: compile-time length,
+// loaded as 16-byte vectors; WT = 0: generic length, read in place).
+template <int WT>
+struct CodeRegs {
+  uint64_t c[WT > 0 ? WT : 1];
+};
+
+template <int WT>
+__device__ __forceinline__ void load_code(CodeRegs<WT>& r, const uint64_t* __restrict__ code) {
+  if constexpr (WT > 0) {
+    if constexpr (WT % 2 == 0) {
+#pragma unroll
+      for (int w = 0; w < WT; w += 2) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(code) + w / 2);
+        r.c[w] = ((uint64_t)v.y << 32) | v.x;
+        r.c[w + 1] = ((uint64_t)v.w << 32) | v.z;
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < WT; ++w) r.c[w] = __ldg(code + w);
+    }
   }
 }
 
-__global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
+// <x_b, q_u> of one code against the bit-planes of its probe (§3.3.2):
+// sum_j 2^j popcount(x_b AND q_u^(j)), unrolled for a compile-time code length
+// (WT words) and B_q (BQT planes); WT = 0 / BQT = 0 use the runtime values.
+template <int WT, int BQT>
+__device__ __forceinline__ int code_ip(const CodeRegs<WT>& r, const uint64_t* __restrict__ code,
+                                       const uint64_t* pl, int W, int bq) {
+  if constexpr (WT > 0 && BQT > 0) {
+    int ip = 0;
+#pragma unroll
+    for (int b = 0; b < BQT; ++b) {
+      uint64_t pw[WT];
+      if constexpr (WT % 2 == 0) {
+#pragma unroll
+        for (int w = 0; w < WT; w += 2) {
+          const uint4 v = *reinterpret_cast<const uint4*>(pl + b * WT + w);
+          pw[w] = ((uint64_t)v.y << 32) | v.x;
+          pw[w + 1] = ((uint64_t)v.w << 32) | v.z;
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < WT; ++w) pw[w] = pl[b * WT + w];
+      }
+      int pb = 0;
+#pragma unroll
+      for (int w = 0; w < WT; ++w) pb += __popcll(r.c[w] & pw[w]);
+      ip += pb << b;
+    }
+    return ip;
+  } else {
+    int ip = 0;
+    for (int b = 0; b < bq; ++b) {
+      int pb = 0;
+      for (int w = 0; w < W; ++w) pb += __popcll(code[w] & pl[b * W + w]);
+      ip += pb << b;
+    }
+    return ip;
+  }
+}
+
+constexpr int kPPT = 4;  // most pairs per thread per scan round (buffer sizing)
+
+// Pairs per thread per round: as many as the code registers allow.
+template <int WT>
+__host__ __device__ constexpr int pairs_per_thread() {
+  return WT == 0 ? 2 : (WT <= 4 ? 4 : (WT <= 8 ? 2 : 1));
+}
+
+template <int WT, int BQT>
+__global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_ub_cnt, s_est_cnt, s_cand_cnt, s_top_cnt, s_surv, s_overflow;
+  __shared__ int s_ub_cnt, s_cand_cnt, s_top_cnt, s_surv, s_overflow;
   __shared__ float s_tau;
-  __shared__ unsigned long long s_est_thr;
   __shared__ int s_scratch[kThreads / 32];
+  __shared__ SelState s_sel;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
   size_t off[9];
   fused_smem_bytes(P.pch, P.bq, P.W, P.d, P.cu, P.ce, P.ct, nwarps, off);
   FusedSmem S;
   S.planes = reinterpret_cast<uint64_t*>(smem + off[0]);
-  S.tiles = reinterpret_cast<float*>(smem + off[0]);
   S.pmeta = reinterpret_cast<float4*>(smem + off[1]);
   S.psum = reinterpret_cast<int*>(smem + off[2]);
   S.pbeg = reinterpret_cast<int*>(smem + off[3]);
   S.pref = reinterpret_cast<int*>(smem + off[4]);
   S.qv = reinterpret_cast<float*>(smem + off[5]);
+  S.sel = &s_sel;
   S.ubk = reinterpret_cast<uint32_t*>(smem + off[6]);
   S.estk = reinterpret_cast<unsigned long long*>(smem + off[7]);
   S.topk = reinterpret_cast<unsigned long long*>(smem + off[8]);
@@ -385,13 +610,11 @@ __global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
     for (int i = tid; i < P.d; i += blockDim.x) S.qv[i] = P.queries[q * P.d + i];
     if (tid == 0) {
       s_ub_cnt = 0;
-      s_est_cnt = 0;
       s_cand_cnt = 0;
       s_top_cnt = 0;
       s_surv = 0;
       s_overflow = 0;
       s_tau = __int_as_float(0x7f800000);
-      s_est_thr = ~0ull;
     }
     __syncthreads();
     int pairs_done = 0;
@@ -421,70 +644,114 @@ __global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
       __syncthreads();
       const int total = S.pref[npc];
       int j = 0;
-      for (int base = 0; base < total; base += blockDim.x) {
-        const int t = base + tid;
-        if (t < total) {
-          while (S.pref[j + 1] <= t) ++j;
-          const int64_t pos = (int64_t)S.pbeg[j] + (t - S.pref[j]);
-          const uint64_t* code = P.codes + pos * W;
-          const uint64_t* pl = S.planes + (size_t)j * bq * W;
-          int ip = 0;
-          for (int b = 0; b < bq; ++b) {
-            int pb = 0;
-            for (int w = 0; w < W; ++w) pb += __popcll(code[w] & pl[b * W + w]);
-            ip += pb << b;
+      constexpr int PPT = pairs_per_thread<WT>();
+      const int step = PPT * blockDim.x;
+      for (int base = 0; base < total; base += step) {
+        // issue every load of this thread's PPT pairs first (they are
+        // independent), then evaluate; keeps PPT code/factor loads in flight
+        int64_t posv[PPT];
+        int jv[PPT];
+        CodeRegs<WT> cr[PPT];
+        float4 fv[PPT];
+#pragma unroll
+        for (int pp = 0; pp < PPT; ++pp) {
+          const int t = base + pp * blockDim.x + tid;
+          posv[pp] = -1;
+          jv[pp] = 0;
+          if (t < total) {
+            while (S.pref[j + 1] <= t) ++j;
+            posv[pp] = (int64_t)S.pbeg[j] + (t - S.pref[j]);
+            jv[pp] = j;
+            load_code<WT>(cr[pp], P.codes + posv[pp] * W);
+            fv[pp] = __ldg(P.factors + posv[pp]);
           }
-          const float4 f = P.factors[pos];
-          const float4 mt = S.pmeta[j];
-          // estimator (§3.3.2 + Theorem 3.2) and its bound, fixed FP32 order
-          const float t1 = (float)(2 * ip - S.psum[j]);
-          const float xq = __fadd_rn(__fmul_rn(mt.x, t1), __fmul_rn(mt.y, f.w));
-          const float dist = __fsub_rn(__fadd_rn(f.x, mt.w), __fmul_rn(f.y, xq));
-          const float e = __fmul_rn(f.z, mt.z);
-          const float lb = __fsub_rn(dist, e), ub = __fadd_rn(dist, e);
-          const float tau = s_tau;
-          if (ub < tau) S.ubk[atomicAdd(&s_ub_cnt, 1)] = float_key(ub);
-          const uint32_t ek = float_key(dist);
-          const unsigned long long thr = s_est_thr;
-          if (ek <= (uint32_t)(thr >> 32)) {
-            const unsigned long long key = ((unsigned long long)ek << 32) | (uint32_t)P.perm[pos];
-            if (key < thr) S.estk[atomicAdd(&s_est_cnt, 1)] = key;
+        }
+        // evaluate the estimator and its bounds for every pair of the round
+        float distv[PPT], lbv[PPT], ubv[PPT];
+        int ipv[PPT];
+        const float tau = s_tau;
+#pragma unroll
+        for (int pp = 0; pp < PPT; ++pp) {
+          distv[pp] = 0.0f;
+          lbv[pp] = __int_as_float(0x7f800000);
+          ubv[pp] = __int_as_float(0x7f800000);
+          ipv[pp] = 0;
+          if (posv[pp] >= 0) {
+            const int jj = jv[pp];
+            const int ip = code_ip<WT, BQT>(cr[pp], P.codes + posv[pp] * W,
+                                            S.planes + (size_t)jj * bq * W, W, bq);
+            const float4 f = fv[pp];
+            const float4 mt = S.pmeta[jj];
+            // estimator (§3.3.2 + Theorem 3.2) and its bound, fixed FP32 order
+            const float t1 = (float)(2 * ip - S.psum[jj]);
+            const float xq = __fadd_rn(__fmul_rn(mt.x, t1), __fmul_rn(mt.y, f.w));
+            const float dist = __fsub_rn(__fadd_rn(f.x, mt.w), __fmul_rn(f.y, xq));
+            const float e = __fmul_rn(f.z, mt.z);
+            distv[pp] = dist;
+            lbv[pp] = __fsub_rn(dist, e);
+            ubv[pp] = __fadd_rn(dist, e);
+            ipv[pp] = ip;
           }
-          if (lb <= tau) {
-            const int slot = atomicAdd(&s_cand_cnt, 1);
-            if (slot < P.cand_cap)
-              cand[slot] = make_int4((int)pos, __float_as_int(lb), __float_as_int(dist), 0);
+        }
+        // one packed warp scan reserves the slots of both buffers
+        int nu = 0, nc = 0;
+#pragma unroll
+        for (int pp = 0; pp < PPT; ++pp) {
+          if (posv[pp] < 0) continue;
+          nu += ubv[pp] < tau;
+          nc += lbv[pp] <= tau;
+        }
+        const int packed = nu | (nc << 16);
+        int incl = packed;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - packed;
+        int bu = 0, bc = 0;
+        if (lane == 0) {
+          if (tot & 0xffff) bu = atomicAdd(&s_ub_cnt, tot & 0xffff);
+          if (tot >> 16) bc = atomicAdd(&s_cand_cnt, tot >> 16);
+        }
+        bu = __shfl_sync(kFull, bu, 0) + (excl & 0xffff);
+        bc = __shfl_sync(kFull, bc, 0) + (excl >> 16);
+#pragma unroll
+        for (int pp = 0; pp < PPT; ++pp) {
+          if (posv[pp] < 0) continue;
+          if (ubv[pp] < tau) S.ubk[bu++] = float_key(ubv[pp]);
+          if (lbv[pp] <= tau) {
+            if (bc < P.cand_cap)
+              cand[bc] = make_int4((int)posv[pp], __float_as_int(lbv[pp]),
+                                   __float_as_int(distv[pp]), 0);
             else
               s_overflow = 1;
+            ++bc;
           }
           if (P.tr.pair_id) {
-            const int64_t tt = pairs_done + t;
+            const int64_t tt = pairs_done + base + pp * blockDim.x + tid;
             if (tt < P.tr.pair_cap) {
               const int64_t o = q * P.tr.pair_cap + tt;
-              P.tr.pair_id[o] = P.perm[pos];
-              P.tr.pair_ip[o] = ip;
-              P.tr.pair_est[3 * o] = dist;
-              P.tr.pair_est[3 * o + 1] = lb;
-              P.tr.pair_est[3 * o + 2] = ub;
+              P.tr.pair_id[o] = __ldg(P.perm + posv[pp]);
+              P.tr.pair_ip[o] = ipv[pp];
+              P.tr.pair_est[3 * o] = distv[pp];
+              P.tr.pair_est[3 * o + 1] = lbv[pp];
+              P.tr.pair_est[3 * o + 2] = ubv[pp];
             }
           }
         }
         __syncthreads();
-        if (s_ub_cnt > P.cu - (int)blockDim.x) {  // keep the k smallest upper bounds
-          sort_keep_u32(S.ubk, P.cu, &s_ub_cnt, k);
-          if (tid == 0 && s_ub_cnt >= k) s_tau = key_float(S.ubk[k - 1]);
+        if (s_ub_cnt > P.cu - step) {  // keep the k smallest upper bounds
+          const uint32_t T = select_keep<uint32_t>(S.ubk, &s_ub_cnt, k, *S.sel);
+          if (tid == 0) s_tau = key_float(T);
           __syncthreads();
         }
-        if (s_est_cnt > P.ce - (int)blockDim.x) {  // keep the m smallest estimates
-          sort_keep_u64(S.estk, P.ce, &s_est_cnt, m);
-          if (tid == 0 && s_est_cnt >= m) s_est_thr = S.estk[m - 1];
-          __syncthreads();
-        }
-        if (s_cand_cnt > P.cand_cap - (int)blockDim.x) {
+        if (s_cand_cnt > P.cand_cap - step) {
           const float tau = s_tau;
           compact_cand(cand, &s_cand_cnt, P.cand_cap, s_scratch,
                        [tau](const int4& e) { return __int_as_float(e.y) <= tau; });
-          if (s_cand_cnt > P.cand_cap - (int)blockDim.x && tid == 0) s_overflow = 1;
+          if (s_cand_cnt > P.cand_cap - step && tid == 0) s_overflow = 1;
           __syncthreads();
         }
         if (s_overflow) break;
@@ -494,27 +761,58 @@ __global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
       if (s_overflow) break;
     }
     // tau_ub: k-th smallest upper bound; pilot: the m smallest estimates
-    sort_keep_u32(S.ubk, P.cu, &s_ub_cnt, k);
-    const float tau_ub = (s_ub_cnt >= k) ? key_float(S.ubk[k - 1]) : __int_as_float(0x7f800000);
-    sort_keep_u64(S.estk, P.ce, &s_est_cnt, m);
-    const int pilot = s_est_cnt;
-    const unsigned long long pilot_last = pilot > 0 ? S.estk[pilot - 1] : 0ull;
-    const bool pilot_all = pilot < m;  // fewer than m codes: every code is in the pilot
+    const int n_ub = s_ub_cnt;
+    const uint32_t T_ub = (n_ub >= k) ? block_select<uint32_t>(S.ubk, n_ub, k, *S.sel) : 0u;
+    const float tau_ub = (n_ub >= k) ? key_float(T_ub) : __int_as_float(0x7f800000);
+    // the candidate list (LB <= running tau') shrinks to LB <= tau_ub
+    compact_cand(cand, &s_cand_cnt, P.cand_cap, s_scratch,
+                 [tau_ub](const int4& e) { return __int_as_float(e.y) <= tau_ub; });
+    // pilot: the m smallest (estimate, id) of the list
+    const int nl = s_cand_cnt;
+    const bool pilot_all = nl <= m;
+    uint32_t T_e = 0xffffffffu, T_id = 0xffffffffu;
+    if (!pilot_all) {
+      T_e = block_select_f<uint32_t>(nl, m, *S.sel,
+                                     [cand](int i) { return float_key(__int_as_float(cand[i].z)); });
+      const int ties = S.sel->rem;
+      // among the list entries whose estimate equals the m-th one, the
+      // `ties` smallest ids belong to the pilot
+      T_id = block_select_f<uint32_t>(nl, ties, *S.sel, [cand, T_e, &P](int i) {
+        const int4 e = cand[i];
+        return float_key(__int_as_float(e.z)) == T_e ? (uint32_t)__ldg(P.perm + e.x) : 0xffffffffu;
+      });
+    }
+    // write the pilot's (id, position) pairs to the pilot list
+    __shared__ int s_pilot;
+    if (tid == 0) s_pilot = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nl; b0 += blockDim.x) {
+      const int i = b0 + tid;
+      bool in = false;
+      int4 e = make_int4(0, 0, 0, 0);
+      if (i < nl) {
+        e = cand[i];
+        const uint32_t ek = float_key(__int_as_float(e.z));
+        in = pilot_all || ek < T_e ||
+             (ek == T_e && (uint32_t)__ldg(P.perm + e.x) <= T_id);
+      }
+      const int slot = warp_reserve(in, &s_pilot);
+      if (in) {
+        S.estk[slot] = ((unsigned long long)(uint32_t)__ldg(P.perm + e.x) << 32) | (uint32_t)e.x;
+        cand[i].w = 1;
+      }
+    }
+    __syncthreads();
+    const int pilot = s_pilot;
     // exact distances of the pilot; tau1 = k-th smallest of them
     rerank_rows<0>(P, S, q, pilot, cand, &s_top_cnt, &s_surv);
-    sort_keep_u64(S.topk, P.ct, &s_top_cnt, k);
-    const float tau1 = (pilot >= k) ? key_float((uint32_t)(S.topk[k - 1] >> 32))
-                                    : __int_as_float(0x7f800000);
+    const unsigned long long T1 =
+        (pilot >= k) ? block_select<unsigned long long>(S.topk, s_top_cnt, k, *S.sel) : 0ull;
+    const float tau1 = (pilot >= k) ? key_float((uint32_t)(T1 >> 32)) : __int_as_float(0x7f800000);
     const float tau = fminf(tau_ub, tau1);
     // the rest of the re-rank set: LB <= tau, outside the pilot
-    compact_cand(cand, &s_cand_cnt, P.cand_cap, s_scratch, [&](const int4& e) {
-      if (pilot_all || !(__int_as_float(e.y) <= tau)) return false;
-      const uint32_t ek = float_key(__int_as_float(e.z));
-      const uint32_t lk = (uint32_t)(pilot_last >> 32);
-      if (ek < lk) return false;
-      if (ek > lk) return true;
-      const unsigned long long key = ((unsigned long long)ek << 32) | (uint32_t)P.perm[e.x];
-      return key > pilot_last;
+    compact_cand(cand, &s_cand_cnt, P.cand_cap, s_scratch, [tau](const int4& e) {
+      return e.w == 0 && __int_as_float(e.y) <= tau;
     });
     rerank_rows<1>(P, S, q, s_cand_cnt, cand, &s_top_cnt, &s_surv);
     sort_keep_u64(S.topk, P.ct, &s_top_cnt, k);
@@ -535,6 +833,19 @@ __global__ void __launch_bounds__(kThreads) fused_search_kernel(FusedParams P) {
     }
     __syncthreads();
   }
+}
+
+typedef void (*FusedFn)(FusedParams);
+
+// Compile-time code lengths of the common shapes (D' = 128, 256, 1024 with
+// B_q = 4); everything else runs the generic instance.
+FusedFn pick_fused(int W, int bq) {
+  if (bq == 4) {
+    if (W == 2) return fused_search_kernel<2, 4>;
+    if (W == 4) return fused_search_kernel<4, 4>;
+    if (W == 16) return fused_search_kernel<16, 4>;
+  }
+  return fused_search_kernel<0, 0>;
 }
 
 int pow2_at_least(int x) {
@@ -558,15 +869,14 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
   const int plane_bytes = a.bq * W * 8;
   int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
   const int pilot_m = 4 * a.k;  // pilot size
-  const int cu = std::max(1024, pow2_at_least(a.k + kThreads));
-  const int ce = std::max(1024, pow2_at_least(pilot_m + kThreads));
+  const int cu = std::max(1024, pow2_at_least(a.k + kPPT * kThreads));
+  const int ce = pow2_at_least(pilot_m);  // the pilot list
   const int ct = std::max(512, pow2_at_least(a.k + kThreads));
   const size_t smem = fused_smem_bytes(pch, a.bq, W, d, cu, ce, ct, kThreads / 32, nullptr);
-  RBQ_CUDA(cudaFuncSetAttribute(fused_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  const FusedFn fn = pick_fused(W, a.bq);
+  RBQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_search_kernel, kThreads,
-                                                         smem));
+  RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
   per_sm = std::max(per_sm, 1);
 
   // query chunks bound the centroid-distance scratch (<= 256 Mi floats)
@@ -668,7 +978,7 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
       if (T.surv_ids) P.tr.surv_ids = T.surv_ids + q0 * T.surv_cap;
     }
     const unsigned g = (unsigned)std::min<int64_t>(nqc, grid);
-    fused_search_kernel<<<g, kThreads, smem, s>>>(P);
+    fn<<<g, kThreads, smem, s>>>(P);
     RBQ_CUDA(cudaGetLastError());
     if (timing) {
       RBQ_CUDA(cudaEventRecord(ev[4], s));
@@ -708,12 +1018,12 @@ int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scra
   const int plane_bytes = a.bq * W * 8;
   const int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
   const int pilot_m = 4 * a.k;
-  const int cu = std::max(1024, pow2_at_least(a.k + kThreads));
-  const int ce = std::max(1024, pow2_at_least(pilot_m + kThreads));
+  const int cu = std::max(1024, pow2_at_least(a.k + kPPT * kThreads));
+  const int ce = pow2_at_least(pilot_m);  // the pilot list
   const int ct = std::max(512, pow2_at_least(a.k + kThreads));
   const size_t smem = fused_smem_bytes(pch, a.bq, W, d, cu, ce, ct, kThreads / 32, nullptr);
-  RBQ_CUDA(cudaFuncSetAttribute(fused_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  const FusedFn fn = pick_fused(W, a.bq);
+  RBQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int sort_n = pow2_at_least(nprobe);
   const size_t sel_smem = sizeof(unsigned long long) * sort_n;
   RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -791,7 +1101,7 @@ int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scra
     P.out_ids = a.out_ids + q0 * a.k;
     P.out_dist = a.out_dist + q0 * a.k;
     P.err = err;
-    fused_search_kernel<<<(unsigned)std::min<int64_t>(nqc, grid), kThreads, smem, s>>>(P);
+    fn<<<(unsigned)std::min<int64_t>(nqc, grid), kThreads, smem, s>>>(P);
     RBQ_CUDA(cudaGetLastError());
   }
   int h_err = 0;

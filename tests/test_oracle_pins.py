@@ -372,16 +372,18 @@ def test_search_equals_exact_knn_over_probed_buckets(oracle_mod, tiny_oracle_ind
 
 
 def test_trace_rerank_set_definition(oracle_mod, tiny_oracle_index, tiny_workload):
-    """Re-rank set = pilot (4k smallest estimates by (estimate, id)) plus
-    every code with LB <= min(k-th smallest UB, k-th smallest exact distance
-    in the pilot); recomputed here from the per-pair estimates."""
+    """Re-rank set = pilot (4k smallest estimates by (estimate, id) among the
+    codes with LB <= k-th smallest UB) plus every code with LB <= min(k-th
+    smallest UB, k-th smallest exact distance in the pilot); recomputed here
+    from the per-pair estimates."""
     X = tiny_oracle_index
     _, Q = tiny_workload
     for qi, k, nprobe in ((3, 10, 4), (7, 1, 2), (11, 50, 16)):
         t = X.trace(Q[qi], qi, k, nprobe)
         ids, est = t["pair_id"], t["pair_est"]
         assert t["tau_ub"] == np.sort(est[:, 2])[k - 1]
-        pilot = np.lexsort((ids, est[:, 0]))[:4 * k]
+        order = np.lexsort((ids, est[:, 0]))
+        pilot = order[est[order, 1] <= t["tau_ub"]][:4 * k]
         ex = oracle_mod.sqdist_matrix(Q[qi:qi + 1], X.data[ids[pilot]])[0]
         assert t["tau1"] == np.sort(ex)[k - 1]
         tau = min(t["tau_ub"], t["tau1"])
