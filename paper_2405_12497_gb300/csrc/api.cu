@@ -51,6 +51,8 @@ void free_index_arrays(rabitq_index* X) {
   cudaFree(X->ptc);
   cudaFree(X->P64);
   cudaFree(X->P32);
+  cudaFree(X->ptb);
+  cudaFree(X->ptf);
 }
 
 int alloc_index_arrays(rabitq_index* X) {
@@ -67,6 +69,9 @@ int alloc_index_arrays(rabitq_index* X) {
   RBQ_CHECK(dev_alloc(&X->ptc, (size_t)X->K * X->dpad));
   RBQ_CHECK(dev_alloc(&X->P64, (size_t)X->dpad * X->dpad));
   RBQ_CHECK(dev_alloc(&X->P32, (size_t)X->dpad * X->dpad));
+  X->kp = (X->d + 63) / 64 * 64;
+  RBQ_CHECK(dev_alloc(reinterpret_cast<uint16_t**>(&X->ptb), (size_t)X->dpad * X->kp));
+  RBQ_CHECK(dev_alloc(&X->ptf, (size_t)X->dpad * X->kp));
   return RABITQ_OK;
 }
 
@@ -214,6 +219,7 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
     RBQ_CHECK(adist_b.alloc(sizeof(float) * n, s));
     RBQ_CHECK(gather_rows_f32(adist.as<float>(), 1, X->perm, n, 1, adist_b.as<float>(), s));
     RBQ_CHECK(sample_rotation_dev(seed, dpad, X->P64, X->P32, s));
+    RBQ_CHECK(pack_pt(X, s));
     RBQ_CHECK(gemm_canon(kDot, X->centroids, d, nullptr, nullptr, 0, nullptr, X->P32, dpad,
                          X->ptc, dpad, n_clusters, dpad, d, s));
     RBQ_CHECK(encode_dev(X, adist_b.as<float>(), s));
@@ -254,8 +260,9 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
     return fail(RABITQ_EINVAL, "rabitq_search: eps0 must be finite and >= 0");
   if (opts.max_candidates < 1024 || opts.max_candidates > (1 << 26))
     return fail(RABITQ_EINVAL, "rabitq_search: max_candidates must be in [1024, 2^26]");
-  if (opts.rot_precision != RABITQ_ROT_FP32)
-    return fail(RABITQ_EUNSUPPORTED, "rabitq_search: only FP32 rotation in this build");
+  if (opts.rot_precision != RABITQ_ROT_FP32 && opts.rot_precision != RABITQ_ROT_TF32 &&
+      opts.rot_precision != RABITQ_ROT_BF16)
+    return fail(RABITQ_EINVAL, "rabitq_search: unknown rot_precision");
   if (opts.scan_path != RABITQ_SCAN_AUTO && opts.scan_path != RABITQ_SCAN_POPC)
     return fail(RABITQ_EUNSUPPORTED, "rabitq_search: only the popcount scan in this build");
   if (trace && (trace->pair_id || trace->pair_ip || trace->pair_est) &&
@@ -527,6 +534,7 @@ int rabitq_index_load(const char* path, const rabitq_build_opts* opts, rabitq_in
     for (int64_t i = 0; i < tot; ++i) p32[i] = (float)p64[i];
     if (cudaMemcpy(X->P32, p32.data(), sizeof(float) * tot, cudaMemcpyHostToDevice) != cudaSuccess)
       st = fail(RABITQ_ECUDA, "copy of P to the device failed");
+    if (st == RABITQ_OK) st = pack_pt(X, nullptr);
   }
   if (st == RABITQ_OK) st = max_bucket_size(X, nullptr);
   if (st != RABITQ_OK) {

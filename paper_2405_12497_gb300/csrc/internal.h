@@ -27,6 +27,11 @@ struct rabitq_index {
   float* ptc = nullptr;           // K x dpad: P^T [c; 0]
   double* P64 = nullptr;          // dpad x dpad
   float* P32 = nullptr;           // dpad x dpad
+  // P^T rows (one per code coordinate), K = d padded to kp, rounded to the
+  // tensor-core operand types of the BF16 / TF32 query rotation
+  int32_t kp = 0;
+  void* ptb = nullptr;            // dpad x kp BF16
+  float* ptf = nullptr;           // dpad x kp TF32-rounded FP32
 };
 
 namespace rbq {
@@ -90,6 +95,13 @@ int gather_rows_f32(const float* in, int64_t ld, const int32_t* rows, int64_t m,
 int invert_perm(const int32_t* perm, int64_t n, int32_t* inv, cudaStream_t s);
 int transpose_f32(const float* in, int64_t rows, int64_t cols, float* out, cudaStream_t s);
 int check_finite(const float* x, int64_t count, cudaStream_t s, bool* finite);
+
+// ---- tensor-core query rotation (kernels_tc.cu) --------------------------
+int pack_pt(rabitq_index* X, cudaStream_t s);
+// out[M x dpad] = Q[M x d] P (mode RABITQ_ROT_BF16 or RABITQ_ROT_TF32);
+// a bounded wait that expires sets *err = 2
+int rotate_tc(const rabitq_index* X, const float* Q, int64_t M, int mode, float* out, int* err,
+              cudaStream_t s);
 
 // ---- search (kernels_search.cu) -----------------------------------------
 struct SearchArgs {

@@ -390,14 +390,6 @@ __device__ K select_keep(K* a, int* cnt, int keep, SelState& st) {
 
 // Sort a shared key buffer (padded with the maximum key), keep the `keep`
 // smallest; returns the count kept. Whole block; synchronized on return.
-__device__ __forceinline__ void sort_keep_u32(uint32_t* a, int cap, int* cnt, int keep) {
-  for (int i = *cnt + threadIdx.x; i < cap; i += blockDim.x) a[i] = 0xffffffffu;
-  __syncthreads();
-  block_bitonic_sort_u32(a, cap);
-  if (threadIdx.x == 0 && *cnt > keep) *cnt = keep;
-  __syncthreads();
-}
-
 __device__ __forceinline__ void sort_keep_u64(unsigned long long* a, int cap, int* cnt, int keep) {
   for (int i = *cnt + threadIdx.x; i < cap; i += blockDim.x) a[i] = ~0ull;
   __syncthreads();
@@ -918,8 +910,11 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
     RBQ_CUDA(cudaGetLastError());
     if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
     float* rqp = a.trace && a.trace->rq ? a.trace->rq + q0 * dpad : rq.as<float>();
-    RBQ_CHECK(gemm_canon(kDot, Q, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rqp, dpad, nqc,
-                         dpad, d, s));
+    if (a.rot_precision == RABITQ_ROT_FP32)
+      RBQ_CHECK(gemm_canon(kDot, Q, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rqp, dpad, nqc,
+                           dpad, d, s));
+    else
+      RBQ_CHECK(rotate_tc(X, Q, nqc, a.rot_precision, rqp, err.as<int>(), s));
     if (timing) RBQ_CUDA(cudaEventRecord(ev[3], s));
     FusedParams P;
     std::memset(&P, 0, sizeof P);
@@ -997,6 +992,8 @@ int search_dev(const SearchArgs& a, cudaStream_t s) {
     for (int i = 0; i < 4; ++i) a.stage_ms[i] = acc_ms[i];
     for (auto& e : ev) cudaEventDestroy(e);
   }
+  if (h_err == 2)
+    return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired in the query rotation");
   if (h_err)
     return fail(RABITQ_EOVERFLOW,
                 "a query's candidate list exceeded max_candidates; raise max_candidates");

@@ -183,3 +183,37 @@ def test_invalid_search_arguments(R, tiny_gpu_index, tiny_workload):
         assert e.value.code == R.EINVAL
     ids, dist = tiny_gpu_index.search(Q[:0], 10, 4)
     assert ids.shape == (0, 10)
+
+
+# ------------------------------------------------- tensor-core rotation modes
+@pytest.mark.parametrize("n,d,code_bits,nq", [(3000, 128, 0, 100), (2000, 960, 1024, 300),
+                                              (1500, 200, 256, 129)])
+def test_tensor_core_rotation_error(R, n, d, code_bits, nq):
+    """BF16 / TF32 query rotation on tensor cores (FP32 accumulation) against
+    the FP64 rotation P^{-1}[q; 0]: normwise relative error per query below
+    a few operand ulps (2^-8 BF16, 2^-11 TF32)."""
+    import torch
+    rng = np.random.default_rng(d)
+    data = rng.standard_normal((n, d)).astype(np.float32)
+    Q = (rng.standard_normal((nq, d)) * 3).astype(np.float32)
+    G = R.Index.build(data, 8, seed=4, code_bits=code_bits, kmeans_iters=2)
+    P = G.rotation()
+    ref = Q.astype(np.float64) @ P[:d]
+    qd = torch.from_numpy(Q).cuda()
+    fp32 = G.search_trace(qd, 5, 2)["rq"].cpu().numpy().astype(np.float64)
+    assert np.abs(fp32 - ref).max() <= 1e-5 * np.abs(ref).max()
+    for mode, tol in ((R.ROT_BF16, 8e-3), (R.ROT_TF32, 1.2e-3)):
+        rq = G.search_trace(qd, 5, 2, rot_precision=mode)["rq"].cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(rq - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert err.max() <= tol, (mode, err.max())
+        assert err.mean() >= 1e-7  # the reduced precision is really in effect
+
+
+def test_tensor_core_rotation_search(R, tiny_gpu_index, tiny_workload):
+    _, Q = tiny_workload
+    ids32, _ = tiny_gpu_index.search(Q, 10, 4)
+    for mode in (R.ROT_BF16, R.ROT_TF32):
+        ids, dist = tiny_gpu_index.search(Q, 10, 4, rot_precision=mode)
+        agree = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids.tolist(), ids32.tolist())])
+        assert agree >= 0.98, (mode, agree)
+        assert (np.diff(dist, axis=1) >= 0).all()
