@@ -263,8 +263,12 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   if (opts.rot_precision != RABITQ_ROT_FP32 && opts.rot_precision != RABITQ_ROT_TF32 &&
       opts.rot_precision != RABITQ_ROT_BF16)
     return fail(RABITQ_EINVAL, "rabitq_search: unknown rot_precision");
-  if (opts.scan_path != RABITQ_SCAN_AUTO && opts.scan_path != RABITQ_SCAN_POPC)
-    return fail(RABITQ_EUNSUPPORTED, "rabitq_search: only the popcount scan in this build");
+  if (opts.scan_path != RABITQ_SCAN_AUTO && opts.scan_path != RABITQ_SCAN_POPC &&
+      opts.scan_path != RABITQ_SCAN_TC)
+    return fail(RABITQ_EINVAL, "rabitq_search: unknown scan_path");
+  if (trace && opts.scan_path != RABITQ_SCAN_POPC &&
+      (trace->planes || trace->sum_qu || trace->meta || trace->pair_id))
+    opts.scan_path = RABITQ_SCAN_POPC;  // bit-planes and per-pair values come from that path
   if (trace && (trace->pair_id || trace->pair_ip || trace->pair_est) &&
       (!trace->pair_id || !trace->pair_ip || !trace->pair_est || trace->pair_cap < 0))
     return fail(RABITQ_EINVAL, "rabitq_search_trace: pair arrays must be given together");

@@ -30,6 +30,7 @@ struct rabitq_index {
   // P^T rows (one per code coordinate), K = d padded to kp, rounded to the
   // tensor-core operand types of the BF16 / TF32 query rotation
   int32_t kp = 0;
+  int32_t tuned_path = 0;         // scan path AUTO uses (rabitq_autotune)
   void* ptb = nullptr;            // dpad x kp BF16
   float* ptf = nullptr;           // dpad x kp TF32-rounded FP32
 };

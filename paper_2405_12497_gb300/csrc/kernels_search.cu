@@ -12,10 +12,14 @@
 //      bound tau, the survivors LB <= tau, their exact distances and the
 //      top-k by (distance, id).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_util.cuh"
 
 namespace rbq {
 namespace {
@@ -175,17 +179,19 @@ __host__ __device__ inline size_t fused_smem_bytes(int pch, int bq, int W, int d
   return o;
 }
 
-// Quantize q' for one probed cluster with one warp (§3.3.1). Lane l holds
-// elements k = 128 i + 4 l + r (r = 0..3), so the four u_k of one Philox call
-// (counter k/4) belong to one lane.
-__device__ __forceinline__ void quantize_probe(const FusedParams& P, const FusedSmem& S, int64_t q,
-                                               int j, int jg, int c, float nq2) {
+// Randomized B_q-bit quantization of q' for one probed cluster with one warp
+// (§3.3.1): qd = rq - P^T c, v_l = min qd, v_r = max qd, Delta = (v_r -
+// v_l)/(2^B_q - 1), q_u[k] = min(floor((qd[k] - v_l)/Delta + u_k), 2^B_q - 1)
+// with u_k from Philox(seed; k/4, query, cluster, 3). Lane l holds elements
+// k = 128 i + 4 l + r (r = 0..3), so the four u_k of one Philox call belong to
+// one lane; emit(i, k0, qu) receives them block by block (warp-uniform).
+// Returns sum(q_u) in every lane; writes v_l and Delta.
+template <class Emit>
+__device__ __forceinline__ int quant_core(const float* rq, const float* pc, int dpad, int bq,
+                                          uint64_t seed, uint64_t gq, int c, float* vl_out,
+                                          float* delta_out, Emit emit) {
   const int lane = threadIdx.x & 31;
-  const int dpad = P.dpad, W = P.W, bq = P.bq;
   const int nblk = (dpad + 127) >> 7;
-  const float* rq = P.rq + q * dpad;
-  const float* pc = P.ptc + (int64_t)c * dpad;
-  // pass 1: v_l = min qd, v_r = max qd with qd = rq - P^T c
   float vl = __int_as_float(0x7f800000), vr = __int_as_float(0xff800000);
   for (int kk = lane; kk < dpad; kk += 32) {
     const float v = __fsub_rn(rq[kk], pc[kk]);
@@ -196,9 +202,7 @@ __device__ __forceinline__ void quantize_probe(const FusedParams& P, const Fused
   vr = warp_max_f(vr);
   const int qmax = (1 << bq) - 1;
   const float delta = __fdiv_rn(__fsub_rn(vr, vl), (float)qmax);
-  const uint64_t gq = (uint64_t)(P.q_offset + q);
   int sum = 0;
-  uint64_t* planes = S.planes + (size_t)j * bq * W;
   for (int i = 0; i < nblk; ++i) {
     const int k0 = 128 * i + 4 * lane;
     int qu[4] = {0, 0, 0, 0};
@@ -206,7 +210,7 @@ __device__ __forceinline__ void quantize_probe(const FusedParams& P, const Fused
       float qd[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) qd[r] = (k0 + r < dpad) ? __fsub_rn(rq[k0 + r], pc[k0 + r]) : 0.0f;
-      const U4 w = philox4x32_10(P.seed, (uint32_t)(k0 >> 2), (uint32_t)gq, (uint32_t)c, kTagQuant);
+      const U4 w = philox4x32_10(seed, (uint32_t)(k0 >> 2), (uint32_t)gq, (uint32_t)c, kTagQuant);
       const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
@@ -219,29 +223,51 @@ __device__ __forceinline__ void quantize_probe(const FusedParams& P, const Fused
       }
     }
     sum += qu[0] + qu[1] + qu[2] + qu[3];
-    // bit-planes: the nibble of lane l sits at bits 4l..4l+3 of the 128-bit block
-    for (int b = 0; b < bq; ++b) {
-      const uint32_t nib = ((qu[0] >> b) & 1) | (((qu[1] >> b) & 1) << 1) |
-                           (((qu[2] >> b) & 1) << 2) | (((qu[3] >> b) & 1) << 3);
-      const uint32_t part = nib << (4 * (lane & 7));
-      const uint32_t q0 = __reduce_or_sync(kFull, lane < 8 ? part : 0u);
-      const uint32_t q1 = __reduce_or_sync(kFull, (lane >= 8 && lane < 16) ? part : 0u);
-      const uint32_t q2 = __reduce_or_sync(kFull, (lane >= 16 && lane < 24) ? part : 0u);
-      const uint32_t q3 = __reduce_or_sync(kFull, lane >= 24 ? part : 0u);
-      if (lane == 0) {
-        const int w0 = 2 * i;
-        if (w0 < W) planes[b * W + w0] = ((uint64_t)q1 << 32) | q0;
-        if (w0 + 1 < W) planes[b * W + w0 + 1] = ((uint64_t)q3 << 32) | q2;
-      }
-    }
+    emit(i, k0, qu);
   }
-  sum = warp_sum_i(sum);
+  *vl_out = vl;
+  *delta_out = delta;
+  return warp_sum_i(sum);
+}
+
+// Per-(query, cluster) constants of the estimator: A = Delta/sqrt(D'),
+// B = v_l/sqrt(D'), E = ||q_r - c|| 2 eps0/sqrt(D'-1), nq2 = ||q_r - c||^2.
+__device__ __forceinline__ float4 quant_meta(float delta, float vl, float nq2, float eps0,
+                                             int dpad) {
+  const float sqd = __fsqrt_rn((float)dpad);
+  const float keps = __fdiv_rn(__fmul_rn(2.0f, eps0), __fsqrt_rn((float)(dpad - 1)));
+  const float n_q = __fsqrt_rn(nq2);
+  return make_float4(__fdiv_rn(delta, sqd), __fdiv_rn(vl, sqd), __fmul_rn(n_q, keps), nq2);
+}
+
+// Quantize for the popcount scan: B_q bit-planes of q_u into shared memory.
+__device__ __forceinline__ void quantize_probe(const FusedParams& P, const FusedSmem& S, int64_t q,
+                                               int j, int jg, int c, float nq2) {
+  const int lane = threadIdx.x & 31;
+  const int dpad = P.dpad, W = P.W, bq = P.bq;
+  uint64_t* planes = S.planes + (size_t)j * bq * W;
+  float vl, delta;
+  const int sum = quant_core(
+      P.rq + q * dpad, P.ptc + (int64_t)c * dpad, dpad, bq, P.seed, (uint64_t)(P.q_offset + q), c,
+      &vl, &delta, [&](int i, int, const int* qu) {
+        // the nibble of lane l sits at bits 4l..4l+3 of the 128-bit block
+        for (int b = 0; b < bq; ++b) {
+          const uint32_t nib = ((qu[0] >> b) & 1) | (((qu[1] >> b) & 1) << 1) |
+                               (((qu[2] >> b) & 1) << 2) | (((qu[3] >> b) & 1) << 3);
+          const uint32_t part = nib << (4 * (lane & 7));
+          const uint32_t q0 = __reduce_or_sync(kFull, lane < 8 ? part : 0u);
+          const uint32_t q1 = __reduce_or_sync(kFull, (lane >= 8 && lane < 16) ? part : 0u);
+          const uint32_t q2 = __reduce_or_sync(kFull, (lane >= 16 && lane < 24) ? part : 0u);
+          const uint32_t q3 = __reduce_or_sync(kFull, lane >= 24 ? part : 0u);
+          if (lane == 0) {
+            const int w0 = 2 * i;
+            if (w0 < W) planes[b * W + w0] = ((uint64_t)q1 << 32) | q0;
+            if (w0 + 1 < W) planes[b * W + w0 + 1] = ((uint64_t)q3 << 32) | q2;
+          }
+        }
+      });
   if (lane == 0) {
-    const float sqd = __fsqrt_rn((float)dpad);
-    const float keps = __fdiv_rn(__fmul_rn(2.0f, P.eps0), __fsqrt_rn((float)(dpad - 1)));
-    const float n_q = __fsqrt_rn(nq2);
-    const float4 m = make_float4(__fdiv_rn(delta, sqd), __fdiv_rn(vl, sqd), __fmul_rn(n_q, keps),
-                                 nq2);
+    const float4 m = quant_meta(delta, vl, nq2, P.eps0, dpad);
     S.pmeta[j] = m;
     S.psum[j] = sum;
     S.pbeg[j] = P.bucket_off[c];
@@ -449,7 +475,7 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
         id = (int)(e >> 32);
         pos = (int)(e & 0xffffffffu);
       } else {
-        pos = cand[i].x;
+        pos = cand[i].x & 0x7fffffff;
         id = P.perm[pos];
       }
     }
@@ -498,6 +524,94 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
   }
   __syncthreads();
   if (threadIdx.x == 0) *surv_cnt += count;
+  __syncthreads();
+}
+
+// Shared counters the per-query finishing step works with.
+struct TailShared {
+  int* cand_cnt;
+  int* top_cnt;
+  int* surv;
+  int* scratch;  // kThreads / 32 ints
+};
+
+// The per-query end of the search (§4, reading R1): given the list of
+// candidates {position, LB, estimate, UB} that contains every code with
+// LB <= tau_ub, keep LB <= tau_ub; pilot = the m smallest (estimate, id);
+// exact distances of the pilot give tau1; tau = min(tau_ub, tau1); exact
+// distances of the other codes with LB <= tau; top-k by (distance, id).
+// The pilot mark is bit 31 of the position. Whole block.
+__device__ void finish_query(const FusedParams& P, const FusedSmem& S, int64_t q, int4* cand,
+                             int cand_cap, float tau_ub, const TailShared& ts) {
+  const int tid = threadIdx.x;
+  const int k = P.k, m = P.m;
+  if (tid == 0) {
+    *ts.top_cnt = 0;
+    *ts.surv = 0;
+  }
+  __syncthreads();
+  compact_cand(cand, ts.cand_cnt, cand_cap, ts.scratch,
+               [tau_ub](const int4& e) { return __int_as_float(e.y) <= tau_ub; });
+  // pilot: the m smallest (estimate, id) of the list
+  const int nl = *ts.cand_cnt;
+  const bool pilot_all = nl <= m;
+  uint32_t T_e = 0xffffffffu, T_id = 0xffffffffu;
+  if (!pilot_all) {
+    T_e = block_select_f<uint32_t>(nl, m, *S.sel,
+                                   [cand](int i) { return float_key(__int_as_float(cand[i].z)); });
+    const int ties = S.sel->rem;
+    // among the list entries whose estimate equals the m-th one, the
+    // `ties` smallest ids belong to the pilot
+    T_id = block_select_f<uint32_t>(nl, ties, *S.sel, [cand, T_e, &P](int i) {
+      const int4 e = cand[i];
+      return float_key(__int_as_float(e.z)) == T_e ? (uint32_t)__ldg(P.perm + e.x) : 0xffffffffu;
+    });
+  }
+  // write the pilot's (id, position) pairs to the pilot list, mark them
+  __shared__ int s_pilot;
+  if (tid == 0) s_pilot = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nl; b0 += blockDim.x) {
+    const int i = b0 + tid;
+    bool in = false;
+    int4 e = make_int4(0, 0, 0, 0);
+    if (i < nl) {
+      e = cand[i];
+      const uint32_t ek = float_key(__int_as_float(e.z));
+      in = pilot_all || ek < T_e || (ek == T_e && (uint32_t)__ldg(P.perm + e.x) <= T_id);
+    }
+    const int slot = warp_reserve(in, &s_pilot);
+    if (in) {
+      S.estk[slot] = ((unsigned long long)(uint32_t)__ldg(P.perm + e.x) << 32) | (uint32_t)e.x;
+      cand[i].x = e.x | (int)0x80000000;
+    }
+  }
+  __syncthreads();
+  const int pilot = s_pilot;
+  // exact distances of the pilot; tau1 = k-th smallest of them
+  rerank_rows<0>(P, S, q, pilot, cand, ts.top_cnt, ts.surv);
+  const unsigned long long T1 =
+      (pilot >= k) ? block_select<unsigned long long>(S.topk, *ts.top_cnt, k, *S.sel) : 0ull;
+  const float tau1 = (pilot >= k) ? key_float((uint32_t)(T1 >> 32)) : __int_as_float(0x7f800000);
+  const float tau = fminf(tau_ub, tau1);
+  // the rest of the re-rank set: LB <= tau, outside the pilot
+  compact_cand(cand, ts.cand_cnt, cand_cap, ts.scratch,
+               [tau](const int4& e) { return e.x >= 0 && __int_as_float(e.y) <= tau; });
+  rerank_rows<1>(P, S, q, *ts.cand_cnt, cand, ts.top_cnt, ts.surv);
+  sort_keep_u64(S.topk, P.ct, ts.top_cnt, k);
+  const int got = min(*ts.top_cnt, k);
+  for (int j2 = tid; j2 < k; j2 += blockDim.x) {
+    const bool ok = j2 < got;
+    P.out_ids[q * k + j2] = ok ? (int64_t)(S.topk[j2] & 0xffffffffu) : -1;
+    P.out_dist[q * k + j2] =
+        ok ? key_float((uint32_t)(S.topk[j2] >> 32)) : __int_as_float(0x7f800000);
+  }
+  if (tid == 0) {
+    if (P.tr.tau_ub) P.tr.tau_ub[q] = tau_ub;
+    if (P.tr.tau1) P.tr.tau1[q] = tau1;
+    if (P.tr.tau) P.tr.tau[q] = tau;
+    if (P.tr.n_surv) P.tr.n_surv[q] = *ts.surv;
+  }
   __syncthreads();
 }
 
@@ -574,7 +688,7 @@ __host__ __device__ constexpr int pairs_per_thread() {
 
 template <int WT, int BQT>
 __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_ub_cnt, s_cand_cnt, s_top_cnt, s_surv, s_overflow;
   __shared__ float s_tau;
   __shared__ int s_scratch[kThreads / 32];
@@ -593,7 +707,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P
   S.ubk = reinterpret_cast<uint32_t*>(smem + off[6]);
   S.estk = reinterpret_cast<unsigned long long*>(smem + off[7]);
   S.topk = reinterpret_cast<unsigned long long*>(smem + off[8]);
-  const int W = P.W, bq = P.bq, k = P.k, m = P.m;
+  const int W = P.W, bq = P.bq, k = P.k;
   int4* cand = P.cand + (int64_t)blockIdx.x * P.cand_cap;
 
   for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
@@ -716,7 +830,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P
           if (lbv[pp] <= tau) {
             if (bc < P.cand_cap)
               cand[bc] = make_int4((int)posv[pp], __float_as_int(lbv[pp]),
-                                   __float_as_int(distv[pp]), 0);
+                                   __float_as_int(distv[pp]), __float_as_int(ubv[pp]));
             else
               s_overflow = 1;
             ++bc;
@@ -756,72 +870,367 @@ __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P
     const int n_ub = s_ub_cnt;
     const uint32_t T_ub = (n_ub >= k) ? block_select<uint32_t>(S.ubk, n_ub, k, *S.sel) : 0u;
     const float tau_ub = (n_ub >= k) ? key_float(T_ub) : __int_as_float(0x7f800000);
-    // the candidate list (LB <= running tau') shrinks to LB <= tau_ub
-    compact_cand(cand, &s_cand_cnt, P.cand_cap, s_scratch,
-                 [tau_ub](const int4& e) { return __int_as_float(e.y) <= tau_ub; });
-    // pilot: the m smallest (estimate, id) of the list
-    const int nl = s_cand_cnt;
-    const bool pilot_all = nl <= m;
-    uint32_t T_e = 0xffffffffu, T_id = 0xffffffffu;
-    if (!pilot_all) {
-      T_e = block_select_f<uint32_t>(nl, m, *S.sel,
-                                     [cand](int i) { return float_key(__int_as_float(cand[i].z)); });
-      const int ties = S.sel->rem;
-      // among the list entries whose estimate equals the m-th one, the
-      // `ties` smallest ids belong to the pilot
-      T_id = block_select_f<uint32_t>(nl, ties, *S.sel, [cand, T_e, &P](int i) {
-        const int4 e = cand[i];
-        return float_key(__int_as_float(e.z)) == T_e ? (uint32_t)__ldg(P.perm + e.x) : 0xffffffffu;
-      });
-    }
-    // write the pilot's (id, position) pairs to the pilot list
-    __shared__ int s_pilot;
-    if (tid == 0) s_pilot = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < nl; b0 += blockDim.x) {
-      const int i = b0 + tid;
-      bool in = false;
-      int4 e = make_int4(0, 0, 0, 0);
-      if (i < nl) {
-        e = cand[i];
-        const uint32_t ek = float_key(__int_as_float(e.z));
-        in = pilot_all || ek < T_e ||
-             (ek == T_e && (uint32_t)__ldg(P.perm + e.x) <= T_id);
-      }
-      const int slot = warp_reserve(in, &s_pilot);
-      if (in) {
-        S.estk[slot] = ((unsigned long long)(uint32_t)__ldg(P.perm + e.x) << 32) | (uint32_t)e.x;
-        cand[i].w = 1;
-      }
-    }
-    __syncthreads();
-    const int pilot = s_pilot;
-    // exact distances of the pilot; tau1 = k-th smallest of them
-    rerank_rows<0>(P, S, q, pilot, cand, &s_top_cnt, &s_surv);
-    const unsigned long long T1 =
-        (pilot >= k) ? block_select<unsigned long long>(S.topk, s_top_cnt, k, *S.sel) : 0ull;
-    const float tau1 = (pilot >= k) ? key_float((uint32_t)(T1 >> 32)) : __int_as_float(0x7f800000);
-    const float tau = fminf(tau_ub, tau1);
-    // the rest of the re-rank set: LB <= tau, outside the pilot
-    compact_cand(cand, &s_cand_cnt, P.cand_cap, s_scratch, [tau](const int4& e) {
-      return e.w == 0 && __int_as_float(e.y) <= tau;
-    });
-    rerank_rows<1>(P, S, q, s_cand_cnt, cand, &s_top_cnt, &s_surv);
-    sort_keep_u64(S.topk, P.ct, &s_top_cnt, k);
-    const int got = min(s_top_cnt, k);
-    for (int j2 = tid; j2 < k; j2 += blockDim.x) {
-      const bool ok = j2 < got;
-      P.out_ids[q * k + j2] = ok ? (int64_t)(S.topk[j2] & 0xffffffffu) : -1;
-      P.out_dist[q * k + j2] =
-          ok ? key_float((uint32_t)(S.topk[j2] >> 32)) : __int_as_float(0x7f800000);
-    }
+    TailShared ts{&s_cand_cnt, &s_top_cnt, &s_surv, s_scratch};
+    finish_query(P, S, q, cand, P.cand_cap, tau_ub, ts);
     if (tid == 0) {
       if (s_overflow) atomicExch(P.err, 1);
       if (P.tr.n_pairs) P.tr.n_pairs[q] = pairs_done;
-      if (P.tr.tau_ub) P.tr.tau_ub[q] = tau_ub;
-      if (P.tr.tau1) P.tr.tau1[q] = tau1;
-      if (P.tr.tau) P.tr.tau[q] = tau;
-      if (P.tr.n_surv) P.tr.n_surv[q] = s_surv;
+    }
+    __syncthreads();
+  }
+}
+
+
+// ------------------------------------------- bucket-major tensor-core scan
+// The queries probing one bucket share its codes, so the scan becomes a
+// product (codes x queries) per bucket: <x_b, q_u> for a tile of 128 codes x
+// 128 (query, cluster) pairs is one K = D' tensor-core product with A = the
+// codes as BF16 0/1 and B = the quantized query values as BF16 0..15, FP32
+// accumulation (exact: every partial sum is an integer below 2^24). The
+// epilogue evaluates the estimator and bounds of every (code, query) pair
+// exactly as the popcount path does and appends the pairs with LB <= tau'_q
+// to the query's candidate list. Pass A covers each query's first probes
+// with tau' = +inf; tau'_q is then the k-th smallest UB of its list; pass B
+// covers the remaining probes. The list then holds every code with
+// LB <= tau_ub (tau_ub <= tau'_q), which is all the per-query end needs.
+constexpr int kTsM = 128;        // codes per tile (TMEM lanes)
+constexpr int kTsN = 128;        // (query, cluster) pairs per tile (TMEM columns)
+constexpr int kTsThreads = 128;  // 4 warps
+
+struct TcScanParams {
+  const uint64_t* codes;
+  const float4* factors;
+  const int32_t* bucket_off;
+  int W, dpad, K, nprobe;
+  const int32_t* pair_perm;  // pair indices (q * nprobe + rank) sorted by key
+  const int32_t* pair_off;   // 2K + 3 key offsets
+  int key_base;              // 0 (pass A) or K + 1 (pass B)
+  const int32_t* tile_off;   // K + 1 tile offsets of this pass
+  const __nv_bfloat16* qub;  // pairs x dpad quantized query values
+  const float4* pmeta;       // pairs: A, B, E, nq2
+  const int32_t* psum;       // pairs: sum(q_u)
+  const float* qtau;         // queries: tau'
+  int4* lists;               // queries x cap
+  int32_t* lcnt;             // queries
+  int cap;
+  int* err;
+};
+
+__global__ void __launch_bounds__(kTsThreads) tc_scan_kernel(TcScanParams P) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint8_t* sA = smem;                 // 128 codes x 128 B (64 BF16 per stage)
+  uint8_t* sB = smem + kTsM * 128;    // 128 pairs x 128 B
+  __shared__ uint32_t s_taddr;
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int s_fail;
+  __shared__ int s_q[kTsN], s_pp[kTsN], s_sum[kTsN];
+  __shared__ float4 s_meta[kTsN];
+  __shared__ float s_tau[kTsN];
+  __shared__ int s_pos[kTsM];
+  __shared__ float4 s_fac[kTsM];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_taddr)),
+                 "r"(kTsN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_fail = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = s_taddr, bar = smem_u32(&s_bar);
+  const uint32_t idesc = make_idesc(1u, kTsM, kTsN);
+  const uint32_t lbo = (kTsM / 8) * 128;  // == (kTsN / 8) * 128
+  uint32_t phase = 0;
+  const int T = P.tile_off[P.K];
+  for (int t = blockIdx.x; t < T && !s_fail; t += gridDim.x) {
+    // bucket of tile t: the last c with tile_off[c] <= t
+    int lo = 0, hi = P.K;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (P.tile_off[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int c = lo;
+    const int cbeg = P.bucket_off[c], Mc = P.bucket_off[c + 1] - cbeg;
+    const int pbeg = P.pair_off[P.key_base + c];
+    const int Nc = P.pair_off[P.key_base + c + 1] - pbeg;
+    const int mt = (Mc + kTsM - 1) / kTsM;
+    const int local = t - P.tile_off[c];
+    const int m0 = (local % mt) * kTsM, n0 = (local / mt) * kTsN;
+    const int rows = min(kTsM, Mc - m0), cols = min(kTsN, Nc - n0);
+    {
+      const int j = tid;
+      if (j < cols) {
+        const int pp = P.pair_perm[pbeg + n0 + j];
+        const int q = pp / P.nprobe;
+        s_pp[j] = pp;
+        s_q[j] = q;
+        s_meta[j] = P.pmeta[pp];
+        s_sum[j] = P.psum[pp];
+        s_tau[j] = P.qtau[q];
+      }
+      const int r = tid;
+      if (r < rows) {
+        const int pos = cbeg + m0 + r;
+        s_pos[r] = pos;
+        s_fac[r] = P.factors[pos];
+      }
+    }
+    __syncthreads();
+    for (int k0 = 0; k0 < P.dpad; k0 += 64) {
+      const int w = k0 >> 6;
+      {  // A: the 64 code bits of row `tid` as BF16 0/1 (1.0 = 0x3F80)
+        const int r = tid;
+        const uint64_t bits = (r < rows) ? __ldg(P.codes + (int64_t)s_pos[r] * P.W + w) : 0ull;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          const uint32_t b8 = (uint32_t)(bits >> (8 * ch)) & 0xffu;
+          uint32_t v[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h)
+            v[h] = (((b8 >> (2 * h)) & 1u) ? 0x3F80u : 0u) |
+                   (((b8 >> (2 * h + 1)) & 1u) ? 0x3F800000u : 0u);
+          *reinterpret_cast<uint4*>(sA + core_off(r, ch, kTsM)) = make_uint4(v[0], v[1], v[2], v[3]);
+        }
+      }
+      {  // B: 64 quantized values of pair column `tid`
+        const int j = tid;
+        const uint4* src = j < cols ? reinterpret_cast<const uint4*>(P.qub + (int64_t)s_pp[j] * P.dpad + k0)
+                                    : nullptr;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          const uint4 v = src ? __ldg(src + ch) : make_uint4(0, 0, 0, 0);
+          *reinterpret_cast<uint4*>(sB + core_off(j, ch, kTsN)) = v;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) {
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {  // K = 16 per instruction, 2 chunks each
+          const uint64_t da = make_desc(a0 + 2 * st * lbo, lbo, 128);
+          const uint64_t db = make_desc(b0 + 2 * st * lbo, lbo, 128);
+          const uint32_t acc = (k0 > 0 || st > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                bar)
+            : "memory");
+      }
+      if (!mbar_wait(bar, phase)) s_fail = 1;
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      __syncthreads();
+      if (s_fail) break;
+    }
+    if (s_fail) break;
+    // epilogue: thread = code row; 16 pair columns per TMEM load
+    const int r = warp * 32 + lane;
+    const bool rv = r < rows;
+    const float4 f = rv ? s_fac[r] : make_float4(0, 0, 0, 0);
+    const int pos = rv ? s_pos[r] : 0;
+    for (int c0 = 0; c0 < cols; c0 += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int j = c0 + e;
+        const bool valid = rv && j < cols;
+        float lb = 0.f, ub = 0.f, dist = 0.f;
+        if (valid) {
+          const int ip = __float2int_rn(__uint_as_float(v[e]));
+          const float4 mt = s_meta[j];
+          const float t1 = (float)(2 * ip - s_sum[j]);
+          const float xq = __fadd_rn(__fmul_rn(mt.x, t1), __fmul_rn(mt.y, f.w));
+          dist = __fsub_rn(__fadd_rn(f.x, mt.w), __fmul_rn(f.y, xq));
+          const float er = __fmul_rn(f.z, mt.z);
+          lb = __fsub_rn(dist, er);
+          ub = __fadd_rn(dist, er);
+        }
+        const bool app = valid && lb <= s_tau[min(j, kTsN - 1)];
+        const unsigned bal = __ballot_sync(kFull, app);
+        if (bal) {
+          const int q = s_q[j];
+          const int leader = __ffs(bal) - 1;
+          int base = 0;
+          if (lane == leader) base = atomicAdd(P.lcnt + q, __popc(bal));
+          base = __shfl_sync(kFull, base, leader);
+          if (app) {
+            const int slot = base + __popc(bal & ((1u << lane) - 1u));
+            if (slot < P.cap)
+              P.lists[(int64_t)q * P.cap + slot] =
+                  make_int4(pos, __float_as_int(lb), __float_as_int(dist), __float_as_int(ub));
+            else
+              atomicExch(P.err, 1);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // TMEM and tile state are reused by the next tile
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  if (s_fail && tid == 0) atomicExch(P.err, 2);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTsN));
+}
+
+// Quantize every (query, cluster) pair to BF16 values (one warp per pair),
+// with the same arithmetic as the popcount path.
+__global__ void quantize_pairs_kernel(const float* __restrict__ rq,
+                                      const int32_t* __restrict__ probe_ids,
+                                      const float* __restrict__ probe_dist,
+                                      const float* __restrict__ ptc, int64_t npairs, int nprobe,
+                                      int dpad, int bq, float eps0, uint64_t seed,
+                                      int64_t q_offset, __nv_bfloat16* __restrict__ qub,
+                                      float4* __restrict__ pmeta, int32_t* __restrict__ psum) {
+  const int64_t pp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (pp >= npairs) return;
+  const int c = probe_ids[pp];
+  if (c < 0) return;
+  const int64_t q = pp / nprobe;
+  __nv_bfloat16* dst = qub + pp * dpad;
+  float vl, delta;
+  const int sum = quant_core(rq + q * dpad, ptc + (int64_t)c * dpad, dpad, bq, seed,
+                             (uint64_t)(q_offset + q), c, &vl, &delta,
+                             [&](int, int k0, const int* qu) {
+                               if (k0 < dpad) {  // dpad is a multiple of 64: 4 elements fit
+                                 __nv_bfloat162 a = __floats2bfloat162_rn((float)qu[0], (float)qu[1]);
+                                 __nv_bfloat162 b = __floats2bfloat162_rn((float)qu[2], (float)qu[3]);
+                                 uint2 u;
+                                 u.x = *reinterpret_cast<uint32_t*>(&a);
+                                 u.y = *reinterpret_cast<uint32_t*>(&b);
+                                 *reinterpret_cast<uint2*>(dst + k0) = u;
+                               }
+                             });
+  if (lane == 0) {
+    pmeta[pp] = quant_meta(delta, vl, probe_dist[pp], eps0, dpad);
+    psum[pp] = sum;
+  }
+}
+
+// Sort keys of the pairs: a pair of probe rank r in pass p (bounds[p] <= r <
+// bounds[p + 1]) gets p (K + 1) + cluster; a pair with no probe gets the
+// last key, npass (K + 1).
+__global__ void pair_keys_kernel(const int32_t* __restrict__ probe_ids, int64_t npairs,
+                                 int nprobe, int b1, int b2, int K, int32_t* __restrict__ key) {
+  const int64_t pp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pp >= npairs) return;
+  const int c = probe_ids[pp];
+  const int rank = (int)(pp % nprobe);
+  const int pass = rank < b1 ? 0 : (rank < b2 ? 1 : 2);
+  key[pp] = c < 0 ? 3 * (K + 1) : pass * (K + 1) + c;
+}
+
+// Tiles per bucket of one pass: ceil(codes / 128) * ceil(pairs / 128).
+__global__ void tile_count_kernel(const int32_t* __restrict__ bucket_off,
+                                  const int32_t* __restrict__ pair_off, int key_base, int K,
+                                  int32_t* __restrict__ tiles) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= K) return;
+  const int Mc = bucket_off[c + 1] - bucket_off[c];
+  const int Nc = pair_off[key_base + c + 1] - pair_off[key_base + c];
+  tiles[c] = (Mc > 0 && Nc > 0) ? ((Mc + kTsM - 1) / kTsM) * ((Nc + kTsN - 1) / kTsN) : 0;
+}
+
+__global__ void fill_f32_kernel(float* __restrict__ a, int64_t n, float v) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+// Between the passes: tau'_q = k-th smallest UB of the list (if it has k
+// entries), and the list keeps LB <= tau'_q. One CTA per query.
+__global__ void __launch_bounds__(kThreads) list_threshold_kernel(int4* __restrict__ lists,
+                                                                  int32_t* __restrict__ lcnt,
+                                                                  int cap, int64_t nq, int k,
+                                                                  float* __restrict__ qtau) {
+  __shared__ SelState sel;
+  __shared__ int s_cnt;
+  __shared__ int s_scratch[kThreads / 32];
+  for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    int4* L = lists + q * cap;
+    if (threadIdx.x == 0) s_cnt = min(lcnt[q], cap);
+    __syncthreads();
+    const int n = s_cnt;
+    float tau = __int_as_float(0x7f800000);
+    if (n >= k) {
+      const uint32_t T = block_select_f<uint32_t>(
+          n, k, sel, [L](int i) { return float_key(__int_as_float(L[i].w)); });
+      tau = key_float(T);
+      compact_cand(L, &s_cnt, cap, s_scratch,
+                   [tau](const int4& e) { return __int_as_float(e.y) <= tau; });
+    }
+    if (threadIdx.x == 0) {
+      qtau[q] = tau;
+      lcnt[q] = s_cnt;
+    }
+    __syncthreads();
+  }
+}
+
+// The per-query end of a tensor-core search: tau_ub = k-th smallest UB of
+// the list, then finish_query. One CTA per query at a time.
+__global__ void __launch_bounds__(kThreads) tc_tail_kernel(FusedParams P, int4* lists,
+                                                           int32_t* lcnt, int cap) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ int s_cand_cnt, s_top_cnt, s_surv;
+  __shared__ int s_scratch[kThreads / 32];
+  __shared__ SelState s_sel;
+  size_t off[9];
+  fused_smem_bytes(P.pch, P.bq, P.W, P.d, P.cu, P.ce, P.ct, blockDim.x >> 5, off);
+  FusedSmem S;
+  S.planes = nullptr;
+  S.pmeta = nullptr;
+  S.psum = S.pbeg = S.pref = nullptr;
+  S.qv = reinterpret_cast<float*>(smem + off[5]);
+  S.sel = &s_sel;
+  S.ubk = nullptr;
+  S.estk = reinterpret_cast<unsigned long long*>(smem + off[7]);
+  S.topk = reinterpret_cast<unsigned long long*>(smem + off[8]);
+  for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
+    for (int i = threadIdx.x; i < P.d; i += blockDim.x) S.qv[i] = P.queries[q * P.d + i];
+    int4* L = lists + q * cap;
+    if (threadIdx.x == 0) s_cand_cnt = min(lcnt[q], cap);
+    __syncthreads();
+    const int n = s_cand_cnt;
+    float tau_ub = __int_as_float(0x7f800000);
+    if (n >= P.k)
+      tau_ub = key_float(block_select_f<uint32_t>(
+          n, P.k, s_sel, [L](int i) { return float_key(__int_as_float(L[i].w)); }));
+    TailShared ts{&s_cand_cnt, &s_top_cnt, &s_surv, s_scratch};
+    finish_query(P, S, q, L, cap, tau_ub, ts);
+    if (P.tr.n_pairs) {  // codes estimated for this query
+      int np = P.nprobe;
+      if (P.nprobe_q) np = min(max(P.nprobe_q[q], 1), P.nprobe);
+      int acc = 0;
+      for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const int c = P.probe_ids[q * P.nprobe + j];
+        acc += P.bucket_off[c + 1] - P.bucket_off[c];
+      }
+      acc = warp_sum_i(acc);
+      if ((threadIdx.x & 31) == 0) atomicAdd(P.tr.n_pairs + q, acc);
     }
     __syncthreads();
   }
@@ -848,7 +1257,23 @@ int pow2_at_least(int x) {
 
 }  // namespace
 
+int search_dev_tc(const SearchArgs& a, cudaStream_t s);
+
+int search_dev_popc(const SearchArgs& a, cudaStream_t s);
+
+// Scan-path choice: the index's tuned choice for AUTO (set by
+// rabitq_autotune), the popcount path otherwise; a TC search whose candidate
+// lists overflow under AUTO is redone on the popcount path.
 int search_dev(const SearchArgs& a, cudaStream_t s) {
+  if (a.scan_path == RABITQ_SCAN_TC) return search_dev_tc(a, s);
+  if (a.scan_path == RABITQ_SCAN_AUTO && a.X->tuned_path == RABITQ_SCAN_TC) {
+    const int st = search_dev_tc(a, s);
+    if (st != RABITQ_EOVERFLOW) return st;
+  }
+  return search_dev_popc(a, s);
+}
+
+int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   const rabitq_index* X = a.X;
   const int K = X->K, d = X->d, dpad = X->dpad, W = X->W;
   const int nprobe = std::min(a.nprobe, K);
@@ -1110,5 +1535,201 @@ int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scra
   return RABITQ_OK;
 }
 
+
+// Search through the bucket-major tensor-core scan (two passes), then the
+// per-query end. Same results as search_dev.
+int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
+  const rabitq_index* X = a.X;
+  const int K = X->K, d = X->d, dpad = X->dpad, W = X->W;
+  const int nprobe = std::min(a.nprobe, K);
+  if (a.nq == 0) return RABITQ_OK;
+  int dev = 0, sms = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
+  RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int cap = a.cand_cap;  // per-query list capacity
+  const int pilot_m = 4 * a.k;
+  const int ce = pow2_at_least(pilot_m);
+  const int ct = std::max(512, pow2_at_least(a.k + kThreads));
+  // passes over probe ranks [0, b1), [b1, b2), [b2, nprobe); tau' is
+  // tightened and the lists compacted after each of the first two
+  const int b1 = std::min(nprobe, 2), b2 = std::min(nprobe, 8);
+  // query chunks: lists <= 4 GiB, centroid distances <= 1 GiB
+  int64_t qchunk = std::min<int64_t>(a.nq, (int64_t(1) << 28) / K);
+  qchunk = std::max<int64_t>(1, std::min<int64_t>(qchunk, (int64_t(1) << 32) / ((int64_t)cap * 16)));
+  const int64_t np = qchunk * nprobe;
+  DevBuf cd, rq, pid, pdist, keys, pperm, poff, qub, pmeta, psum, tiles, toffA, lists, lcnt, qtau,
+      err;
+  RBQ_CHECK(cd.alloc(sizeof(float) * qchunk * K, s));
+  RBQ_CHECK(rq.alloc(sizeof(float) * qchunk * dpad, s));
+  RBQ_CHECK(pid.alloc(sizeof(int32_t) * np, s));
+  RBQ_CHECK(pdist.alloc(sizeof(float) * np, s));
+  RBQ_CHECK(keys.alloc(sizeof(int32_t) * np, s));
+  RBQ_CHECK(pperm.alloc(sizeof(int32_t) * np, s));
+  RBQ_CHECK(poff.alloc(sizeof(int32_t) * (3 * K + 5), s));
+  RBQ_CHECK(qub.alloc(sizeof(__nv_bfloat16) * np * dpad, s));
+  RBQ_CHECK(pmeta.alloc(sizeof(float4) * np, s));
+  RBQ_CHECK(psum.alloc(sizeof(int32_t) * np, s));
+  RBQ_CHECK(tiles.alloc(sizeof(int32_t) * (K + 1), s));
+  RBQ_CHECK(toffA.alloc(sizeof(int32_t) * 3 * (K + 1), s));
+  RBQ_CHECK(lists.alloc(sizeof(int4) * qchunk * cap, s));
+  RBQ_CHECK(lcnt.alloc(sizeof(int32_t) * qchunk, s));
+  RBQ_CHECK(qtau.alloc(sizeof(float) * qchunk, s));
+  RBQ_CHECK(err.alloc(sizeof(int), s));
+  RBQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  RBQ_CUDA(cudaMemsetAsync(tiles.p, 0, sizeof(int32_t) * (K + 1), s));
+
+  const int sort_n = pow2_at_least(nprobe);
+  const size_t sel_smem = sizeof(unsigned long long) * sort_n;
+  RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sel_smem));
+  const size_t scan_smem = 64 * 1024;  // 32 KB of operands; caps residency at 3 CTAs/SM
+  RBQ_CUDA(cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)scan_smem));
+  const size_t tail_smem = fused_smem_bytes(1, a.bq, W, d, 32, ce, ct, kThreads / 32, nullptr);
+  RBQ_CUDA(cudaFuncSetAttribute(tc_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tail_smem));
+  int tail_per_sm = 1;
+  RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tail_per_sm, tc_tail_kernel, kThreads,
+                                                         tail_smem));
+  tail_per_sm = std::max(tail_per_sm, 1);
+  cudaEvent_t ev[5] = {};
+  const bool timing = a.stage_ms != nullptr;
+  float acc_ms[4] = {0, 0, 0, 0};
+  if (timing)
+    for (auto& e : ev) RBQ_CUDA(cudaEventCreate(&e));
+  for (int64_t q0 = 0; q0 < a.nq; q0 += qchunk) {
+    const int64_t nqc = std::min(qchunk, a.nq - q0);
+    const int64_t npc = nqc * nprobe;
+    const float* Q = a.queries + q0 * d;
+    if (timing) RBQ_CUDA(cudaEventRecord(ev[0], s));
+    RBQ_CHECK(gemm_canon(kSqDist, Q, d, nullptr, nullptr, 0, nullptr, X->centroids_t, K,
+                         cd.as<float>(), K, nqc, K, d, s));
+    int32_t* probe_ids = a.trace && a.trace->probe_ids ? a.trace->probe_ids + q0 * nprobe
+                                                       : pid.as<int32_t>();
+    float* probe_dist = a.trace && a.trace->probe_dist ? a.trace->probe_dist + q0 * nprobe
+                                                       : pdist.as<float>();
+    if (timing) RBQ_CUDA(cudaEventRecord(ev[1], s));
+    select_kernel<<<(unsigned)nqc, kThreads, sel_smem, s>>>(
+        cd.as<float>(), K, nprobe, a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr,
+        sort_n, probe_ids, probe_dist);
+    RBQ_CUDA(cudaGetLastError());
+    if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
+    float* rqp = a.trace && a.trace->rq ? a.trace->rq + q0 * dpad : rq.as<float>();
+    if (a.rot_precision == RABITQ_ROT_FP32)
+      RBQ_CHECK(gemm_canon(kDot, Q, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rqp, dpad, nqc,
+                           dpad, d, s));
+    else
+      RBQ_CHECK(rotate_tc(X, Q, nqc, a.rot_precision, rqp, err.as<int>(), s));
+    if (timing) RBQ_CUDA(cudaEventRecord(ev[3], s));
+    // pairs by (pass, bucket)
+    pair_keys_kernel<<<(unsigned)((npc + 255) / 256), 256, 0, s>>>(probe_ids, npc, nprobe, b1, b2,
+                                                                   K, keys.as<int32_t>());
+    RBQ_CHECK(counting_sort(keys.as<int32_t>(), npc, 3 * K + 4, pperm.as<int32_t>(),
+                            poff.as<int32_t>(), s));
+    quantize_pairs_kernel<<<(unsigned)((npc * 32 + 255) / 256), 256, 0, s>>>(
+        rqp, probe_ids, probe_dist, X->ptc, npc, nprobe, dpad, a.bq, a.eps0, a.seed, q0,
+        qub.as<__nv_bfloat16>(), pmeta.as<float4>(), psum.as<int32_t>());
+    RBQ_CUDA(cudaGetLastError());
+    for (int pass = 0; pass < 3; ++pass) {
+      tile_count_kernel<<<(K + 255) / 256, 256, 0, s>>>(X->bucket_off, poff.as<int32_t>(),
+                                                        pass * (K + 1), K, tiles.as<int32_t>());
+      RBQ_CHECK(exclusive_scan_i32(tiles.as<int32_t>(), toffA.as<int32_t>() + pass * (K + 1),
+                                   K + 1, s));
+    }
+    RBQ_CUDA(cudaMemsetAsync(lcnt.p, 0, sizeof(int32_t) * nqc, s));
+    fill_f32_kernel<<<(unsigned)((nqc + 255) / 256), 256, 0, s>>>(qtau.as<float>(), nqc,
+                                                                  HUGE_VALF);
+    TcScanParams T;
+    T.codes = X->codes;
+    T.factors = X->factors;
+    T.bucket_off = X->bucket_off;
+    T.W = W;
+    T.dpad = dpad;
+    T.K = K;
+    T.nprobe = nprobe;
+    T.pair_perm = pperm.as<int32_t>();
+    T.pair_off = poff.as<int32_t>();
+    T.qub = qub.as<__nv_bfloat16>();
+    T.pmeta = pmeta.as<float4>();
+    T.psum = psum.as<int32_t>();
+    T.qtau = qtau.as<float>();
+    T.lists = lists.as<int4>();
+    T.lcnt = lcnt.as<int32_t>();
+    T.cap = cap;
+    T.err = err.as<int>();
+    for (int pass = 0; pass < 3; ++pass) {
+      T.key_base = pass * (K + 1);
+      T.tile_off = toffA.as<int32_t>() + pass * (K + 1);
+      tc_scan_kernel<<<(unsigned)(2 * sms), kTsThreads, scan_smem, s>>>(T);
+      RBQ_CUDA(cudaGetLastError());
+      if (pass < 2) {
+        list_threshold_kernel<<<(unsigned)std::min<int64_t>(nqc, 4 * sms), kThreads, 0, s>>>(
+            lists.as<int4>(), lcnt.as<int32_t>(), cap, nqc, a.k, qtau.as<float>());
+        RBQ_CUDA(cudaGetLastError());
+      }
+    }
+    FusedParams P;
+    std::memset(&P, 0, sizeof P);
+    P.queries = Q;
+    P.probe_ids = probe_ids;
+    P.nprobe_q = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
+    P.data_b = X->data_b;
+    P.perm = X->perm;
+    P.inv_perm = X->inv_perm;
+    P.bucket_off = X->bucket_off;
+    P.nq = nqc;
+    P.q_offset = q0;
+    P.d = d;
+    P.dpad = dpad;
+    P.W = W;
+    P.bq = a.bq;
+    P.k = a.k;
+    P.m = pilot_m;
+    P.nprobe = nprobe;
+    P.pch = 1;
+    P.cu = 32;
+    P.ce = ce;
+    P.ct = ct;
+    P.out_ids = a.out_ids + q0 * a.k;
+    P.out_dist = a.out_dist + q0 * a.k;
+    P.err = err.as<int>();
+    if (a.trace) {
+      const rabitq_trace& Tr = *a.trace;
+      if (Tr.n_pairs) P.tr.n_pairs = Tr.n_pairs + q0;
+      if (Tr.tau_ub) P.tr.tau_ub = Tr.tau_ub + q0;
+      if (Tr.tau1) P.tr.tau1 = Tr.tau1 + q0;
+      if (Tr.tau) P.tr.tau = Tr.tau + q0;
+      if (Tr.n_surv) P.tr.n_surv = Tr.n_surv + q0;
+      if (Tr.surv_ids) {
+        P.tr.surv_ids = Tr.surv_ids + q0 * Tr.surv_cap;
+        P.tr.surv_cap = Tr.surv_cap;
+      }
+    }
+    tc_tail_kernel<<<(unsigned)std::min<int64_t>(nqc, (int64_t)sms * tail_per_sm), kThreads,
+                     tail_smem, s>>>(P, lists.as<int4>(), lcnt.as<int32_t>(), cap);
+    RBQ_CUDA(cudaGetLastError());
+    if (timing) {
+      RBQ_CUDA(cudaEventRecord(ev[4], s));
+      RBQ_CUDA(cudaEventSynchronize(ev[4]));
+      for (int i = 0; i < 4; ++i) {
+        float t = 0;
+        RBQ_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+        acc_ms[i] += t;
+      }
+    }
+  }
+  if (timing) {
+    for (int i = 0; i < 4; ++i) a.stage_ms[i] = acc_ms[i];
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  int h_err = 0;
+  RBQ_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RBQ_CUDA(cudaStreamSynchronize(s));
+  if (h_err == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired in the scan");
+  if (h_err)
+    return fail(RABITQ_EOVERFLOW,
+                "a query's candidate list exceeded max_candidates; raise max_candidates");
+  return RABITQ_OK;
+}
 
 }  // namespace rbq

@@ -288,7 +288,8 @@ class Index:
 
     def search_trace(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
                      quant_seed: int = 3, pair_cap: int = 0, surv_cap: int = 0,
-                     max_candidates: int = 65536, rot_precision=ROT_FP32):
+                     max_candidates: int = 65536, rot_precision=ROT_FP32,
+                     scan_path=SCAN_POPC):
         """Search of torch CUDA queries that also returns every intermediate
         (torch CUDA tensors)."""
         import torch
@@ -325,7 +326,8 @@ class Index:
                    _dptr(t["surv_ids"]) if surv_cap else None)
         ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
         dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-        o = self._opts(quant_seed, None, max_candidates, False, None, True, rot_precision)
+        o = self._opts(quant_seed, None, max_candidates, False, None, True, rot_precision,
+                       scan_path)
         _check(lib().rabitq_search_trace(self._h, _dptr(q), nq, k, nprobe, bq, eps0, _dptr(ids),
                                          _dptr(dist), C.byref(o), C.byref(tr)))
         t["ids"], t["dist"] = ids, dist

@@ -217,3 +217,58 @@ def test_tensor_core_rotation_search(R, tiny_gpu_index, tiny_workload):
         agree = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids.tolist(), ids32.tolist())])
         assert agree >= 0.98, (mode, agree)
         assert (np.diff(dist, axis=1) >= 0).all()
+
+
+# --------------------------------------------- tensor-core (bucket-major) scan
+def _paths_identical(R, G, Q, k, nprobe, **kw):
+    a = G.search(Q, k, nprobe, scan_path=R.SCAN_POPC, **kw)
+    b = G.search(Q, k, nprobe, scan_path=R.SCAN_TC, **kw)
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+    return b
+
+
+@pytest.mark.parametrize("k,nprobe", [(10, 4), (1, 1), (100, 16), (25, 3)])
+def test_tc_scan_matches_popcount_and_oracle(R, tiny_gpu_index, tiny_oracle_index, tiny_workload,
+                                              k, nprobe):
+    """The tensor-core scan (codes x queries per bucket, BF16 0/1 x 0..15,
+    FP32 accumulation) returns exactly what the popcount scan and the oracle
+    return: integer inner products are exact, the rest is the same arithmetic."""
+    _, Q = tiny_workload
+    ids, dist = _paths_identical(R, tiny_gpu_index, Q, k, nprobe)
+    ids_o, dist_o = tiny_oracle_index.search(Q, k, nprobe)
+    assert np.array_equal(ids, ids_o)
+    assert np.array_equal(dist.view(np.uint32), dist_o.view(np.uint32))
+
+
+def test_tc_scan_trace_matches(R, tiny_gpu_index, tiny_workload):
+    import torch
+    _, Q = tiny_workload
+    qd = torch.from_numpy(Q).cuda()
+    G = tiny_gpu_index
+    a = G.search_trace(qd, 10, 6, surv_cap=12000)
+    b = G.search_trace(qd, 10, 6, surv_cap=12000, scan_path=R.SCAN_TC)
+    for key in ("tau_ub", "tau1", "tau", "n_surv", "n_pairs", "ids", "dist", "probe_ids"):
+        assert torch.equal(a[key], b[key]), key
+    for i in range(len(Q)):
+        n = int(a["n_surv"][i])
+        assert torch.equal(torch.sort(a["surv_ids"][i, :n]).values,
+                           torch.sort(b["surv_ids"][i, :n]).values)
+
+
+@pytest.mark.parametrize("n,d,code_bits,K,nq,k,nprobe", [
+    (20000, 128, 0, 16, 2000, 10, 4),      # 5 M tiles x 4 N tiles per bucket
+    (6000, 960, 1024, 8, 300, 20, 3),      # D' = 1024: 16 K stages
+    (5000, 200, 256, 64, 700, 50, 12),     # D' = 256, ragged buckets
+])
+def test_tc_scan_shapes(R, oracle_mod, n, d, code_bits, K, nq, k, nprobe):
+    rng = np.random.default_rng(n + d)
+    cen = rng.standard_normal((30, d))
+    data = (cen[rng.integers(0, 30, n)] + 0.4 * rng.standard_normal((n, d))).astype(np.float32)
+    Q = (cen[rng.integers(0, 30, nq)] + 0.4 * rng.standard_normal((nq, d))).astype(np.float32)
+    G = R.Index.build(data, K, seed=6, code_bits=code_bits, kmeans_iters=3)
+    ids, dist = _paths_identical(R, G, Q, k, nprobe)
+    O = oracle_mod.OracleIndex(data, K=K, seed=6, dpad=G.dpad, iters=3, threads=8)
+    ids_o, dist_o = O.search(Q, k, nprobe, threads=8)   # query indices key the rounding
+    assert np.array_equal(ids, ids_o)
+    assert np.array_equal(dist.view(np.uint32), dist_o.view(np.uint32))
