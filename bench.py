@@ -260,12 +260,87 @@ def run_ours(args, rank, world):
         "clocks": clocks.summary(),
         "wall_s_timed_region": round(wall, 3),
     }
+    if not args.no_learned:
+        res["learned"] = learned_leg(args, G, qd, gt, w, chosen, flush, stream, out, dist)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(G, data, queries, w, chosen, budget_s=args.cpu_budget)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, out, dist):
+    """Learned probe counts: train the predictor on separately drawn training
+    queries (labels from the library's own search over nprobe_max buckets),
+    raise its multiplier on the benchmark queries until recall@100 >= 0.95
+    (the same rule that picks the fixed nprobe), then time the learned search
+    exactly like the fixed one."""
+    import torch
+    from paper_2405_12497_gb300 import rabitq
+    dev = qd.device
+    _, tq = synth.make(w, nq=args.train_nq, seed_query=7, with_data=False)
+    tqd = torch.from_numpy(tq).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    pr = rabitq.Predictor.train(G, tqd, k=w.k, target_recall=TARGET, nprobe_max=args.nprobe_max,
+                                epochs=args.epochs)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    info = pr.info()
+    mult = info["mult"]
+    rec = 0.0
+    for _ in range(48):
+        pr.set_mult(mult)
+        ids, _ = G.search_learned(pr, qd, w.k, bq=w.bq, eps0=w.eps0)
+        rec = recall_at(ids.cpu().numpy(), gt)
+        if rec >= TARGET:
+            break
+        mult *= 2.0 ** 0.125
+    npq = G.predict_nprobe(pr, qd).double()
+
+    def step():
+        G.search_learned(pr, qd, w.k, bq=w.bq, eps0=w.eps0, out=out, stats=True)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms, stages = [], np.zeros(5)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        stages += rabitq.last_stats()
+    total_ms = float(np.sum(ms))
+    world = 1
+    if dist:
+        world = dist.get_world_size()
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    qps = world * w.nq * args.steps / (total_ms / 1e3)
+    return {"value": round(qps, 1), "unit": "queries/s", "recall_at_100": round(rec, 4),
+            "ms_per_step": round(total_ms / args.steps, 4),
+            "mean_nprobe": round(float(npq.mean()), 2),
+            "nprobe_p50_p90_p99": [float(np.percentile(npq.cpu().numpy(), p)) for p in (50, 90, 99)],
+            "fixed_nprobe_same_recall": fixed_nprobe, "mult": round(mult, 5),
+            "calibrated_mult": round(info["mult"], 5), "val_recall": round(info["val_recall"], 4),
+            "val_mean_nprobe": round(info["val_mean_nprobe"], 2),
+            "train_loss": round(info["train_loss"], 4), "val_loss": round(info["val_loss"], 4),
+            "train_queries": args.train_nq, "epochs": args.epochs,
+            "nprobe_max": args.nprobe_max, "train_s": round(train_s, 2),
+            "stage_ms": {"centroid_dist": round(stages[0] / args.steps, 4),
+                         "probe_select_and_mlp": round(stages[1] / args.steps, 4),
+                         "rotation": round(stages[2] / args.steps, 4),
+                         "quantize_scan_prune_rerank": round(stages[3] / args.steps, 4)}}
 
 
 def cpu_baseline(G, data, queries, w, nprobe, budget_s=15.0):
@@ -351,6 +426,10 @@ def main():
     ap.add_argument("--nq", type=int, default=None, help="fewer queries (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-nprobe leg")
+    ap.add_argument("--train-nq", type=int, default=100_000)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--nprobe-max", type=int, default=256)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

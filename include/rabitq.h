@@ -29,6 +29,7 @@ extern "C" {
 #endif
 
 typedef struct rabitq_index rabitq_index;
+typedef struct rabitq_predictor rabitq_predictor;
 
 typedef enum {
   RABITQ_OK = 0,
@@ -190,6 +191,144 @@ int rabitq_search_trace(const rabitq_index* idx, const float* queries, int64_t n
 int rabitq_search_noalloc(const rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
                           int32_t nprobe, int32_t bq, float eps0, int64_t* out_ids,
                           float* out_dist, const rabitq_search_opts* opts);
+
+/*
+ * ---- Learned probe count (an extension; the paper uses one fixed nprobe) --
+ *
+ * A small MLP predicts, per query, how many of the nearest buckets to probe
+ * (§4 probes a fixed number). Input: 64 features of the query's 64 smallest
+ * query-centroid squared distances d_0 <= ... <= d_63 (ties by bucket id;
+ * when K < 64 the last one repeats):
+ *     x_0 = d_0 / (d_0 + s0)        (s0 = mean d_0 over the training queries)
+ *     x_j = d_0 / d_j  (j >= 1)     (1 when d_j = 0)
+ * Network: 64 -> 256 -> ReLU -> 256 -> ReLU -> 1 (y = predicted log2 of the
+ * probe count). Weights and biases hold BF16 values; products accumulate in
+ * FP32. Probe count of a query: clamp(ceil(mult * 2^y), 1, nprobe_max).
+ * Parameters are packed into one vector of RABITQ_MLP_PARAMS floats:
+ *   W1 (64 x 256, row-major: z1[n] = sum_j x_j W1[j][n] + b1[n]), b1 (256),
+ *   W2 (256 x 256), b2 (256), w3 (256), b3 (1).
+ *
+ * Labels (the exact method decides them): for a training query with true
+ * neighbours g_1..g_k, let r_j be the rank (0-based, buckets ordered by
+ * (distance, id)) of the bucket holding g_j, censored at nprobe_max; the
+ * label is the probe count R = 1 + the need-th smallest r_j (need =
+ * ceil(target_recall * k)), at most nprobe_max, so probing R buckets covers
+ * at least `need` of the k neighbours; the regression target is log2 R.
+ * Training minimises the mean squared error with Adam (beta1 0.9, beta2
+ * 0.999, eps 1e-8, all as FP32 values) on an FP32 master copy that is
+ * rounded to BF16 values after every step; mult is then the smallest value on the grid
+ * 2^((i - 128)/32), i = 0..511, whose mean coverage over the validation
+ * queries (fraction of their k neighbours inside the predicted buckets) is
+ * at least target_recall.
+ */
+enum {
+  RABITQ_MLP_IN = 64,
+  RABITQ_MLP_HIDDEN = 256,
+  RABITQ_MLP_PARAMS = 64 * 256 + 256 + 256 * 256 + 256 + 256 + 1
+};
+
+typedef struct {
+  int32_t k;              /* neighbours per training query (default 100)       */
+  float target_recall;    /* mean recall the multiplier is calibrated for
+                             (default 0.95)                                     */
+  int32_t nprobe_max;     /* largest predicted probe count; also the probe count
+                             of the label search when gt_ids is NULL
+                             (0 = min(K, 512))                                   */
+  int32_t epochs;         /* passes over the training split (default 30)       */
+  int32_t batch;          /* rows per Adam step (default 1024)                 */
+  float lr;               /* Adam step size (default 1e-3)                     */
+  float val_fraction;     /* the last fraction of the queries is the validation
+                             split (default 0.1; at least one query each side)  */
+  uint64_t seed;          /* weight initialisation and batch order (default 5) */
+  const int64_t* gt_ids;  /* optional nt x k true neighbour ids (-1 = none);
+                             NULL = rabitq_search with nprobe_max buckets, Bq 4,
+                             eps0 1.9 finds them                               */
+  int32_t io_on_device;   /* train_q and gt_ids are device pointers            */
+  void* stream;           /* cudaStream_t; NULL = the legacy default stream    */
+} rabitq_predictor_opts;
+
+typedef struct {
+  int32_t n_clusters, k, nprobe_max;
+  float target_recall, s0, mult;
+  float train_loss, val_loss;   /* mean squared error of log2 R               */
+  float val_recall;             /* mean coverage of the validation split at mult */
+  float val_mean_nprobe;        /* mean predicted probe count there            */
+  int64_t n_train, n_val;
+} rabitq_predictor_info;
+
+void rabitq_predictor_opts_default(rabitq_predictor_opts* opts);
+
+/*
+ * rabitq_predictor_train -- labels, training and calibration on the GPU.
+ *   idx        the index the predictor serves (its K and centroids)
+ *   train_q    nt x d training queries (nt >= 2)
+ *   out        receives the new predictor (library-owned until
+ *              rabitq_predictor_free)
+ * Errors: EINVAL (sizes, k > 1024, target outside (0, 1], non-finite
+ * queries); ENOMEM; ECUDA; EOVERFLOW from the label search.
+ */
+int rabitq_predictor_train(const rabitq_index* idx, const float* train_q, int64_t nt,
+                           const rabitq_predictor_opts* opts, rabitq_predictor** out);
+
+/* A predictor from given parameters (host, RABITQ_MLP_PARAMS floats, each
+ * rounded to BF16), feature scale s0 > 0, multiplier mult > 0, for an index
+ * of n_clusters buckets. */
+int rabitq_predictor_create(const float* params, float s0, float mult, int32_t nprobe_max,
+                            int32_t n_clusters, rabitq_predictor** out);
+int rabitq_predictor_get_info(const rabitq_predictor* pr, rabitq_predictor_info* out);
+/* Copy the parameters (BF16 values as float) to a HOST buffer. */
+int rabitq_predictor_get_params(const rabitq_predictor* pr, float* out /* RABITQ_MLP_PARAMS */);
+/* Replace the multiplier (e.g. for a recall/speed sweep), mult > 0. */
+int rabitq_predictor_set_mult(rabitq_predictor* pr, float mult);
+void rabitq_predictor_free(rabitq_predictor* pr);
+
+/*
+ * rabitq_predict_nprobe -- per-query probe counts (and optionally the
+ * features, nq x 64, and the network outputs y, nq) of nq queries. Memory
+ * kind of queries and outputs per opts->io_on_device; opts->stream used.
+ */
+int rabitq_predict_nprobe(const rabitq_index* idx, const rabitq_predictor* pr,
+                          const float* queries, int64_t nq, int32_t* out_nprobe,
+                          float* out_features, float* out_y, const rabitq_search_opts* opts);
+
+/*
+ * rabitq_search_learned -- rabitq_search with each query's probe count from
+ * the predictor (computed inside the search from the same query-centroid
+ * distances). The result equals rabitq_search with nprobe = nprobe_max and
+ * per_query_nprobe = rabitq_predict_nprobe's output. opts->per_query_nprobe
+ * must be NULL. Errors: those of rabitq_search; EINVAL when the predictor
+ * was made for another K.
+ */
+int rabitq_search_learned(const rabitq_index* idx, const rabitq_predictor* pr,
+                          const float* queries, int64_t nq, int32_t k, int32_t bq, float eps0,
+                          int64_t* out_ids, float* out_dist, const rabitq_search_opts* opts);
+
+/*
+ * rabitq_compute_labels -- the labels above for nq queries with given true
+ * neighbours (host buffers): ranks (nq x k, r_j censored at nprobe_max, in
+ * the order of gt_ids) and label_r (nq, the probe count R).
+ */
+int rabitq_compute_labels(const rabitq_index* idx, const float* queries, int64_t nq,
+                          const int64_t* gt_ids, int32_t k, float target_recall,
+                          int32_t nprobe_max, int32_t* ranks, int32_t* label_r);
+
+/*
+ * rabitq_mlp_grad -- one forward and backward pass of the network on the
+ * GPU, host buffers: params (RABITQ_MLP_PARAMS), X (B x 64), t (B). Writes
+ * y (B, may be NULL), the gradient of mean((y - t)^2) with respect to every
+ * parameter (grads, packed like params, may be NULL) and that loss (may be
+ * NULL). For gradient checks and for inspecting a trained network.
+ */
+int rabitq_mlp_grad(const float* params, const float* X, const float* t, int64_t B, float* y,
+                    float* grads, float* loss);
+
+/*
+ * rabitq_mlp_adam -- one Adam step (step >= 1) of the training update on the
+ * GPU, host buffers of RABITQ_MLP_PARAMS floats: master, m1, m2 are updated
+ * in place; work receives the master rounded to BF16 values.
+ */
+int rabitq_mlp_adam(float* master, float* m1, float* m2, const float* grads, int32_t step,
+                    float lr, float* work);
 
 /* Per-stage device times (milliseconds) of the last search on this thread
  * with collect_stats set. Stages: 0 centroid distances, 1 probe selection,

@@ -15,7 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librabitq.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "kernels_gemm.cu", "kernels_build.cu", "kernels_search.cu", "kernels_tc.cu", "noalloc.cu"]
+SOURCES = [
+    "api.cu", "api_predictor.cu", "kernels_gemm.cu", "kernels_build.cu", "kernels_search.cu",
+    "kernels_tc.cu", "kernels_mlp.cu", "noalloc.cu",
+]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-Wshadow", "--expt-relaxed-constexpr"]
 

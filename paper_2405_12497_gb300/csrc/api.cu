@@ -241,7 +241,7 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
 static int search_common(const rabitq_index* X, const float* queries, int64_t nq, int32_t k,
                          int32_t nprobe, int32_t bq, float eps0, int64_t* out_ids,
                          float* out_dist, const rabitq_search_opts* opts_in,
-                         const rabitq_trace* trace) {
+                         const rabitq_trace* trace, const rabitq_predictor* pr = nullptr) {
   g_err.clear();
   g_nstats = 0;
   if (!X) return fail(RABITQ_EINVAL, "rabitq_search: index is null");
@@ -283,7 +283,7 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
     RBQ_CUDA(cudaEventCreate(&t1));
     RBQ_CUDA(cudaEventRecord(t0, s));
   }
-  DevBuf qb, ib, db, nb;
+  DevBuf qb, ib, db, nb, pb;
   const float* dq = queries;
   int64_t* dids = out_ids;
   float* ddist = out_dist;
@@ -320,6 +320,11 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   a.trace = trace;
   a.rot_precision = opts.rot_precision;
   a.scan_path = opts.scan_path;
+  if (pr) {
+    RBQ_CHECK(pb.alloc(sizeof(int32_t) * nq, s));
+    a.pred = pr;
+    a.pred_nprobe = pb.as<int32_t>();
+  }
   float stage[5] = {0, 0, 0, 0, 0};
   a.stage_ms = opts.collect_stats ? stage : nullptr;
   RBQ_CHECK(search_dev(a, s));
@@ -352,6 +357,18 @@ int rabitq_search_trace(const rabitq_index* idx, const float* queries, int64_t n
                         const rabitq_trace* trace) {
   if (!trace) return fail(RABITQ_EINVAL, "rabitq_search_trace: trace is null");
   return search_common(idx, queries, nq, k, nprobe, bq, eps0, out_ids, out_dist, opts, trace);
+}
+
+int rabitq_search_learned(const rabitq_index* idx, const rabitq_predictor* pr,
+                          const float* queries, int64_t nq, int32_t k, int32_t bq, float eps0,
+                          int64_t* out_ids, float* out_dist, const rabitq_search_opts* opts) {
+  if (!idx || !pr) return fail(RABITQ_EINVAL, "rabitq_search_learned: null index or predictor");
+  if (pr->K != idx->K)
+    return fail(RABITQ_EINVAL, "rabitq_search_learned: predictor made for another bucket count");
+  if (opts && opts->per_query_nprobe)
+    return fail(RABITQ_EINVAL, "rabitq_search_learned: per_query_nprobe must be NULL");
+  return search_common(idx, queries, nq, k, pr->nprobe_max, bq, eps0, out_ids, out_dist, opts,
+                       nullptr, pr);
 }
 
 int rabitq_index_info(const rabitq_index* X, int64_t* n, int32_t* d, int32_t* d_pad,

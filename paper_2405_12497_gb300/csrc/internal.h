@@ -35,6 +35,20 @@ struct rabitq_index {
   float* ptf = nullptr;           // dpad x kp TF32-rounded FP32
 };
 
+// Learned probe-count predictor (kernels_mlp.cu): MLP weights with BF16
+// values, the feature scale s0 and the calibrated multiplier.
+struct rabitq_predictor {
+  int device = 0;
+  int32_t K = 0;           // bucket count of the index it was trained on
+  int32_t k = 0;           // neighbours per query its labels cover
+  int32_t nprobe_max = 0;  // largest probe count it predicts
+  float target_recall = 0, s0 = 0, mult = 1;
+  float train_loss = 0, val_loss = 0, val_recall = 0, val_mean_nprobe = 0;
+  int64_t n_train = 0, n_val = 0;
+  float* params = nullptr;  // RABITQ_MLP_PARAMS, BF16 values stored as FP32
+  void* params_bf16 = nullptr;  // the same values packed as BF16 (inference)
+};
+
 namespace rbq {
 
 // error plumbing (thread-local message)
@@ -120,9 +134,61 @@ struct SearchArgs {
   int32_t rot_precision;
   int32_t scan_path;
   float* stage_ms;    // host, 5 entries or null
+  // learned probe counts: the predictor sets each query's probe count (at
+  // most nprobe) from its centroid distances; pred_nprobe (device, nq) keeps
+  // them. Null for a fixed or caller-given probe count.
+  const rabitq_predictor* pred = nullptr;
+  int32_t* pred_nprobe = nullptr;
 };
 int search_dev(const SearchArgs& a, cudaStream_t s);
+// Probe counts of nq queries from a predictor: query-centroid distances, the
+// 64 smallest, features, MLP, multiplier. feat (nq x 64) and y (nq) optional.
+int predict_dev(const rabitq_index* X, const rabitq_predictor* pr, const float* Q, int64_t nq,
+                int32_t* nprobe_out, float* feat, float* y, cudaStream_t s);
+// Top-nsel buckets of each query (ascending (distance, id)), for nq queries.
+int select_buckets(const rabitq_index* X, const float* Q, int64_t nq, int nsel, int32_t* ids,
+                   float* dist, cudaStream_t s);
 int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scratch_bytes,
                         cudaStream_t s);
+
+// ---- learned probe count (kernels_mlp.cu) ---------------------------------
+constexpr int kMlpIn = RABITQ_MLP_IN, kMlpHidden = RABITQ_MLP_HIDDEN;
+constexpr int kMlpParams = RABITQ_MLP_PARAMS;
+struct MlpWork {  // activations and gradients of one batch
+  DevBuf buf;
+  float *Z1, *H1, *Z2, *H2, *dH2, *dH1, *y, *dy, *se, *T, *W2T;
+  int alloc(int64_t B, cudaStream_t s);
+};
+int mlp_forward(const float* params, const float* X, int64_t B, float* Z1, float* H1, float* Z2,
+                float* H2, float* y, cudaStream_t s);
+int mlp_backward(const float* params, const float* X, const float* t, int64_t B, float* grads,
+                 MlpWork& w, cudaStream_t s);
+int mlp_adam(float* master, float* work, const float* g, float* m1, float* m2, float lr, int step,
+             cudaStream_t s);
+// features from each query's ascending centroid distances (row stride ld,
+// navail = min(64, K) valid entries)
+int mlp_features(const float* sel_dist, int64_t ld, int64_t nq, int navail, float s0, float* X,
+                 cudaStream_t s);
+// fused inference: features, MLP and probe counts in one kernel
+int mlp_infer(const rabitq_predictor* pr, const float* sel_dist, int64_t ld, int64_t nq,
+              int navail, int32_t* nprobe_out, float* feat, float* y, cudaStream_t s);
+// in = out allowed; packed (BF16) may be null
+int mlp_round(const float* in, float* out, void* packed, int n, cudaStream_t s);
+// neighbours a label must cover: ceil(target k), with a tolerance of 1e-6 k
+// for the float target (0.95f * 100 is 94.9999988...)
+inline int mlp_need(float target, int k) {
+  const double v = (double)target * k - 1e-6 * k;
+  int need = (int)v;
+  if ((double)need < v) ++need;
+  return need < 1 ? 1 : (need > k ? k : need);
+}
+int predictor_train_dev(const rabitq_index* X, const float* Q, int64_t nt,
+                        const int64_t* gt, const rabitq_predictor_opts& o, rabitq_predictor* pr,
+                        cudaStream_t s);
+int mlp_labels_dev(const rabitq_index* X, const float* Q, int64_t nq, const int64_t* gt, int k,
+                   int need, int nmax, int32_t* ranks, int32_t* label_r, cudaStream_t s);
+int mlp_pack_bf16(rabitq_predictor* pr, cudaStream_t s);
+// sum of (y - t)^2 over n rows in FP64, fixed order (one value at out, device)
+int mlp_sum_sq_err(const float* y, const float* t, int64_t n, double* out, cudaStream_t s);
 
 }  // namespace rbq

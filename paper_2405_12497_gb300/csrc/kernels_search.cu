@@ -25,6 +25,10 @@ namespace rbq {
 namespace {
 
 constexpr int kThreads = 256;
+// select_kernel's shared-memory limit: every caller sets the same value (the
+// largest selection, 16384 entries), so concurrent searches never lower it
+// under one another's launch
+constexpr int kSelMaxSmem = 8 * 16384;
 
 // ------------------------------------------------------------ selection
 // Top-nsel of a row of K non-negative distances by (distance, id): radix
@@ -1255,6 +1259,19 @@ int pow2_at_least(int x) {
   return p;
 }
 
+// Learned probe counts of one query chunk from its centroid distances cd
+// (nqc x K): the min(64, K) nearest buckets, then the fused MLP kernel.
+int predict_chunk(const SearchArgs& a, const float* cd, int64_t nqc, int64_t q0, int32_t* fid,
+                  float* fdist, cudaStream_t s) {
+  const int K = a.X->K;
+  const int navail = std::min(kMlpIn, K);
+  const int sn = pow2_at_least(navail);
+  select_kernel<<<(unsigned)nqc, kThreads, sizeof(unsigned long long) * sn, s>>>(
+      cd, K, navail, nullptr, sn, fid, fdist);
+  RBQ_CUDA(cudaGetLastError());
+  return mlp_infer(a.pred, fdist, navail, nqc, navail, a.pred_nprobe + q0, nullptr, nullptr, s);
+}
+
 }  // namespace
 
 int search_dev_tc(const SearchArgs& a, cudaStream_t s);
@@ -1306,6 +1323,11 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   RBQ_CHECK(pdist.alloc(sizeof(float) * qchunk * nprobe, s));
   RBQ_CHECK(cand.alloc(sizeof(int4) * grid * a.cand_cap, s));
   RBQ_CHECK(err.alloc(sizeof(int), s));
+  DevBuf fid, fdist;  // learned probe counts: the 64 nearest buckets per query
+  if (a.pred) {
+    RBQ_CHECK(fid.alloc(sizeof(int32_t) * qchunk * kMlpIn, s));
+    RBQ_CHECK(fdist.alloc(sizeof(float) * qchunk * kMlpIn, s));
+  }
   RBQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
 
   cudaEvent_t ev[5] = {};
@@ -1317,7 +1339,7 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   const int sort_n = pow2_at_least(nprobe);
   const size_t sel_smem = sizeof(unsigned long long) * sort_n;
   RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sel_smem));
+                                kSelMaxSmem));
   for (int64_t q0 = 0; q0 < a.nq; q0 += qchunk) {
     const int64_t nqc = std::min(qchunk, a.nq - q0);
     const float* Q = a.queries + q0 * d;
@@ -1329,8 +1351,13 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
                                                        : pid.as<int32_t>();
     float* probe_dist = a.trace && a.trace->probe_dist ? a.trace->probe_dist + q0 * nprobe
                                                        : pdist.as<float>();
+    const int32_t* npq = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
+    if (a.pred) {
+      RBQ_CHECK(predict_chunk(a, cd.as<float>(), nqc, q0, fid.as<int32_t>(), fdist.as<float>(), s));
+      npq = a.pred_nprobe + q0;
+    }
     select_kernel<<<(unsigned)nqc, kThreads, sel_smem, s>>>(
-        cd.as<float>(), K, nprobe, a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr,
+        cd.as<float>(), K, nprobe, npq,
         sort_n, probe_ids, probe_dist);
     RBQ_CUDA(cudaGetLastError());
     if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
@@ -1347,7 +1374,7 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
     P.rq = rqp;
     P.probe_ids = probe_ids;
     P.probe_dist = probe_dist;
-    P.nprobe_q = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
+    P.nprobe_q = npq;
     P.ptc = X->ptc;
     P.codes = X->codes;
     P.factors = X->factors;
@@ -1449,7 +1476,7 @@ int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scra
   const int sort_n = pow2_at_least(nprobe);
   const size_t sel_smem = sizeof(unsigned long long) * sort_n;
   RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sel_smem));
+                                kSelMaxSmem));
   // layout: [error flag | candidate lists (one CTA per SM) | per-chunk query arrays]
   const size_t A = 256;
   const int64_t grid = sms;
@@ -1575,13 +1602,18 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
   RBQ_CHECK(lcnt.alloc(sizeof(int32_t) * qchunk, s));
   RBQ_CHECK(qtau.alloc(sizeof(float) * qchunk, s));
   RBQ_CHECK(err.alloc(sizeof(int), s));
+  DevBuf fid, fdist;  // learned probe counts: the 64 nearest buckets per query
+  if (a.pred) {
+    RBQ_CHECK(fid.alloc(sizeof(int32_t) * qchunk * kMlpIn, s));
+    RBQ_CHECK(fdist.alloc(sizeof(float) * qchunk * kMlpIn, s));
+  }
   RBQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
   RBQ_CUDA(cudaMemsetAsync(tiles.p, 0, sizeof(int32_t) * (K + 1), s));
 
   const int sort_n = pow2_at_least(nprobe);
   const size_t sel_smem = sizeof(unsigned long long) * sort_n;
   RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sel_smem));
+                                kSelMaxSmem));
   const size_t scan_smem = 64 * 1024;  // 32 KB of operands; caps residency at 3 CTAs/SM
   RBQ_CUDA(cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)scan_smem));
@@ -1609,8 +1641,13 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
     float* probe_dist = a.trace && a.trace->probe_dist ? a.trace->probe_dist + q0 * nprobe
                                                        : pdist.as<float>();
     if (timing) RBQ_CUDA(cudaEventRecord(ev[1], s));
+    const int32_t* npq = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
+    if (a.pred) {
+      RBQ_CHECK(predict_chunk(a, cd.as<float>(), nqc, q0, fid.as<int32_t>(), fdist.as<float>(), s));
+      npq = a.pred_nprobe + q0;
+    }
     select_kernel<<<(unsigned)nqc, kThreads, sel_smem, s>>>(
-        cd.as<float>(), K, nprobe, a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr,
+        cd.as<float>(), K, nprobe, npq,
         sort_n, probe_ids, probe_dist);
     RBQ_CUDA(cudaGetLastError());
     if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
@@ -1672,7 +1709,7 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
     std::memset(&P, 0, sizeof P);
     P.queries = Q;
     P.probe_ids = probe_ids;
-    P.nprobe_q = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
+    P.nprobe_q = npq;
     P.data_b = X->data_b;
     P.perm = X->perm;
     P.inv_perm = X->inv_perm;
@@ -1729,6 +1766,49 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
   if (h_err)
     return fail(RABITQ_EOVERFLOW,
                 "a query's candidate list exceeded max_candidates; raise max_candidates");
+  return RABITQ_OK;
+}
+
+// Top-nsel buckets of each query, ascending (distance, id): the canonical
+// query-centroid distances of the IVF probe (§4), then the block select.
+int select_buckets(const rabitq_index* X, const float* Q, int64_t nq, int nsel, int32_t* ids,
+                   float* dist, cudaStream_t s) {
+  if (nq <= 0) return RABITQ_OK;
+  const int K = X->K, d = X->d;
+  nsel = std::min(nsel, K);
+  const int64_t qchunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t(1) << 28) / K));
+  DevBuf cd;
+  RBQ_CHECK(cd.alloc(sizeof(float) * qchunk * K, s));
+  const int sn = pow2_at_least(nsel);
+  const size_t smem = sizeof(unsigned long long) * sn;
+  RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSelMaxSmem));
+  for (int64_t q0 = 0; q0 < nq; q0 += qchunk) {
+    const int64_t m = std::min(qchunk, nq - q0);
+    RBQ_CHECK(gemm_canon(kSqDist, Q + q0 * d, d, nullptr, nullptr, 0, nullptr, X->centroids_t, K,
+                         cd.as<float>(), K, m, K, d, s));
+    select_kernel<<<(unsigned)m, kThreads, smem, s>>>(cd.as<float>(), K, nsel, nullptr, sn,
+                                                       ids + q0 * nsel, dist + q0 * nsel);
+    RBQ_CUDA(cudaGetLastError());
+  }
+  return RABITQ_OK;
+}
+
+// Learned probe counts (and optionally features and network outputs).
+int predict_dev(const rabitq_index* X, const rabitq_predictor* pr, const float* Q, int64_t nq,
+                int32_t* nprobe_out, float* feat, float* y, cudaStream_t s) {
+  if (nq <= 0) return RABITQ_OK;
+  const int navail = std::min(kMlpIn, X->K);
+  const int64_t chunk = std::min<int64_t>(nq, int64_t(1) << 20);
+  DevBuf ids, dist;
+  RBQ_CHECK(ids.alloc(sizeof(int32_t) * chunk * navail, s));
+  RBQ_CHECK(dist.alloc(sizeof(float) * chunk * navail, s));
+  for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+    const int64_t m = std::min(chunk, nq - q0);
+    RBQ_CHECK(select_buckets(X, Q + q0 * X->d, m, navail, ids.as<int32_t>(), dist.as<float>(), s));
+    RBQ_CHECK(mlp_infer(pr, dist.as<float>(), navail, m, navail, nprobe_out + q0,
+                        feat ? feat + q0 * kMlpIn : nullptr, y ? y + q0 : nullptr, s));
+  }
   return RABITQ_OK;
 }
 

@@ -27,7 +27,14 @@ EXPORTS = (
     "rabitq_get_rotation", "rabitq_get_codes", "rabitq_get_factors", "rabitq_get_assign",
     "rabitq_get_buckets", "rabitq_sample_rotation", "rabitq_index_save", "rabitq_index_load",
     "rabitq_free", "rabitq_last_error", "rabitq_search_noalloc",
+    "rabitq_predictor_opts_default", "rabitq_predictor_train", "rabitq_predictor_create",
+    "rabitq_predictor_get_info", "rabitq_predictor_get_params", "rabitq_predictor_set_mult",
+    "rabitq_predictor_free", "rabitq_predict_nprobe", "rabitq_search_learned",
+    "rabitq_compute_labels", "rabitq_mlp_grad", "rabitq_mlp_adam",
 )
+
+MLP_IN, MLP_HIDDEN = 64, 256
+MLP_PARAMS = 64 * 256 + 256 + 256 * 256 + 256 + 256 + 1
 
 
 class RabitqError(RuntimeError):
@@ -56,6 +63,20 @@ class Trace(C.Structure):
                 ("pair_ip", C.c_void_p), ("pair_est", C.c_void_p), ("tau_ub", C.c_void_p),
                 ("tau1", C.c_void_p), ("tau", C.c_void_p),
                 ("surv_cap", C.c_int32), ("n_surv", C.c_void_p), ("surv_ids", C.c_void_p)]
+
+
+class PredictorOpts(C.Structure):
+    _fields_ = [("k", C.c_int32), ("target_recall", C.c_float), ("nprobe_max", C.c_int32),
+                ("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float),
+                ("val_fraction", C.c_float), ("seed", C.c_uint64), ("gt_ids", C.c_void_p),
+                ("io_on_device", C.c_int32), ("stream", C.c_void_p)]
+
+
+class PredictorInfo(C.Structure):
+    _fields_ = [("n_clusters", C.c_int32), ("k", C.c_int32), ("nprobe_max", C.c_int32),
+                ("target_recall", C.c_float), ("s0", C.c_float), ("mult", C.c_float),
+                ("train_loss", C.c_float), ("val_loss", C.c_float), ("val_recall", C.c_float),
+                ("val_mean_nprobe", C.c_float), ("n_train", C.c_int64), ("n_val", C.c_int64)]
 
 
 def lib_path() -> str:
@@ -90,6 +111,18 @@ def lib():
             "rabitq_index_load": (C.c_int, [C.c_char_p, vp, vp]),
             "rabitq_free": (None, [vp]),
             "rabitq_last_error": (C.c_char_p, []),
+            "rabitq_predictor_opts_default": (None, [vp]),
+            "rabitq_predictor_train": (C.c_int, [vp, vp, i64, vp, vp]),
+            "rabitq_predictor_create": (C.c_int, [vp, f32, f32, i32, i32, vp]),
+            "rabitq_predictor_get_info": (C.c_int, [vp, vp]),
+            "rabitq_predictor_get_params": (C.c_int, [vp, vp]),
+            "rabitq_predictor_set_mult": (C.c_int, [vp, f32]),
+            "rabitq_predictor_free": (None, [vp]),
+            "rabitq_predict_nprobe": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp]),
+            "rabitq_search_learned": (C.c_int, [vp, vp, vp, i64, i32, i32, f32, vp, vp, vp]),
+            "rabitq_compute_labels": (C.c_int, [vp, vp, i64, vp, i32, f32, i32, vp, vp]),
+            "rabitq_mlp_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp]),
+            "rabitq_mlp_adam": (C.c_int, [vp, vp, vp, vp, i32, f32, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -332,3 +365,165 @@ class Index:
                                          _dptr(dist), C.byref(o), C.byref(tr)))
         t["ids"], t["dist"] = ids, dist
         return t
+
+
+    # ------------------------------------------------------ learned nprobe
+    def search_learned(self, predictor: "Predictor", queries, k: int, bq: int = 4,
+                       eps0: float = 1.9, quant_seed: int = 3, max_candidates: int = 65536,
+                       stats: bool = False, stream=None, out=None, rot_precision=ROT_FP32,
+                       scan_path=SCAN_AUTO):
+        """Search with each query's probe count from the predictor."""
+        dev = _is_torch(queries)
+        o = self._opts(quant_seed, None, max_candidates, stats, stream, dev, rot_precision,
+                       scan_path)
+        if dev:
+            import torch
+            queries = queries.contiguous()
+            nq = queries.shape[0]
+            if out is None:
+                ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+                dist = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+            else:
+                ids, dist = out
+            _check(lib().rabitq_search_learned(self._h, predictor._h, _dptr(queries), nq, k, bq,
+                                               eps0, _dptr(ids), _dptr(dist), C.byref(o)))
+            return ids, dist
+        queries = np.ascontiguousarray(queries, np.float32)
+        nq = queries.shape[0]
+        ids = np.empty((nq, k), np.int64)
+        dist = np.empty((nq, k), np.float32)
+        _check(lib().rabitq_search_learned(self._h, predictor._h, _np_ptr(queries), nq, k, bq,
+                                           eps0, _np_ptr(ids), _np_ptr(dist), C.byref(o)))
+        return ids, dist
+
+    def predict_nprobe(self, predictor: "Predictor", queries, features: bool = False):
+        """Per-query probe counts; with features=True also (features nq x 64,
+        network outputs y). numpy in -> numpy out; torch CUDA in -> torch out."""
+        o = self._opts(3, None, 65536, False, None, _is_torch(queries))
+        if _is_torch(queries):
+            import torch
+            q = queries.contiguous()
+            nq = q.shape[0]
+            npb = torch.empty(nq, dtype=torch.int32, device=q.device)
+            f = torch.empty((nq, MLP_IN), dtype=torch.float32, device=q.device) if features else None
+            y = torch.empty(nq, dtype=torch.float32, device=q.device) if features else None
+            _check(lib().rabitq_predict_nprobe(self._h, predictor._h, _dptr(q), nq, _dptr(npb),
+                                               _dptr(f) if features else None,
+                                               _dptr(y) if features else None, C.byref(o)))
+            return (npb, f, y) if features else npb
+        q = np.ascontiguousarray(queries, np.float32)
+        nq = q.shape[0]
+        npb = np.empty(nq, np.int32)
+        f = np.empty((nq, MLP_IN), np.float32) if features else None
+        y = np.empty(nq, np.float32) if features else None
+        _check(lib().rabitq_predict_nprobe(self._h, predictor._h, _np_ptr(q), nq, _np_ptr(npb),
+                                           _np_ptr(f) if features else None,
+                                           _np_ptr(y) if features else None, C.byref(o)))
+        return (npb, f, y) if features else npb
+
+    def compute_labels(self, queries, gt_ids, k: int, target_recall: float, nprobe_max: int):
+        """(ranks nq x k, label probe counts nq) of queries with true neighbours gt_ids."""
+        q = np.ascontiguousarray(queries, np.float32)
+        g = np.ascontiguousarray(gt_ids, np.int64)
+        nq = q.shape[0]
+        ranks = np.empty((nq, k), np.int32)
+        lab = np.empty(nq, np.int32)
+        _check(lib().rabitq_compute_labels(self._h, _np_ptr(q), nq, _np_ptr(g), k, target_recall,
+                                           nprobe_max, _np_ptr(ranks), _np_ptr(lab)))
+        return ranks, lab
+
+
+class Predictor:
+    """The learned probe-count MLP (owned by the library)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @classmethod
+    def train(cls, index: Index, train_q, k: int = 100, target_recall: float = 0.95,
+              nprobe_max: int = 0, epochs: int = 30, batch: int = 1024, lr: float = 1e-3,
+              val_fraction: float = 0.1, seed: int = 5, gt_ids=None, stream=None) -> "Predictor":
+        o = PredictorOpts()
+        lib().rabitq_predictor_opts_default(C.byref(o))
+        o.k, o.target_recall, o.nprobe_max = k, target_recall, nprobe_max
+        o.epochs, o.batch, o.lr, o.val_fraction, o.seed = epochs, batch, lr, val_fraction, seed
+        o.stream = _stream_handle(stream)
+        keep = []
+        if _is_torch(train_q):
+            q = train_q.contiguous()
+            o.io_on_device = 1
+            qp = _dptr(q)
+            if gt_ids is not None:
+                import torch
+                g = gt_ids.to(torch.int64).contiguous()
+                keep.append(g)
+                o.gt_ids = _dptr(g)
+        else:
+            q = np.ascontiguousarray(train_q, np.float32)
+            qp = _np_ptr(q)
+            if gt_ids is not None:
+                g = np.ascontiguousarray(gt_ids, np.int64)
+                keep.append(g)
+                o.gt_ids = _np_ptr(g)
+        h = C.c_void_p()
+        _check(lib().rabitq_predictor_train(index._h, qp, q.shape[0], C.byref(o), C.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def create(cls, params, s0: float, mult: float, nprobe_max: int, n_clusters: int):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == MLP_PARAMS
+        h = C.c_void_p()
+        _check(lib().rabitq_predictor_create(_np_ptr(p), s0, mult, nprobe_max, n_clusters,
+                                             C.byref(h)))
+        return cls(h)
+
+    def info(self) -> dict:
+        i = PredictorInfo()
+        _check(lib().rabitq_predictor_get_info(self._h, C.byref(i)))
+        return {name: getattr(i, name) for name, _ in PredictorInfo._fields_}
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        _check(lib().rabitq_predictor_get_params(self._h, _np_ptr(out)))
+        return out
+
+    def set_mult(self, mult: float):
+        _check(lib().rabitq_predictor_set_mult(self._h, mult))
+
+    def free(self):
+        if self._h:
+            lib().rabitq_predictor_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mlp_grad(params, X, t):
+    """One forward/backward pass on the GPU: (y, grads, loss)."""
+    p = np.ascontiguousarray(params, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    B = X.shape[0]
+    y = np.empty(B, np.float32)
+    g = np.empty(MLP_PARAMS, np.float32)
+    loss = C.c_float()
+    _check(lib().rabitq_mlp_grad(_np_ptr(p), _np_ptr(X), _np_ptr(t), B, _np_ptr(y), _np_ptr(g),
+                                 C.byref(loss)))
+    return y, g, loss.value
+
+
+def mlp_adam(master, m1, m2, grads, step: int, lr: float):
+    """One Adam step on the GPU: (master, m1, m2, work) after the step."""
+    ms = np.array(master, np.float32, copy=True)
+    a = np.array(m1, np.float32, copy=True)
+    b = np.array(m2, np.float32, copy=True)
+    g = np.ascontiguousarray(grads, np.float32)
+    w = np.empty(MLP_PARAMS, np.float32)
+    _check(lib().rabitq_mlp_adam(_np_ptr(ms), _np_ptr(a), _np_ptr(b), _np_ptr(g), step, lr,
+                                 _np_ptr(w)))
+    return ms, a, b, w

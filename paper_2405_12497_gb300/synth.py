@@ -60,7 +60,8 @@ def _chunks(n: int, step: int = 1 << 18):
         yield s, min(n, s + step)
 
 
-def sift_like(n: int, nq: int, d: int = 128, seed_data: int = 0, seed_query: int = 1):
+def sift_like(n: int, nq: int, d: int = 128, seed_data: int = 0, seed_query: int = 1,
+              with_data: bool = True):
     """Non-negative integer-valued vectors in [0, 255] (SIFT-shaped): a mixture
     of n/100 components with heavy-tailed per-dimension scales s_d =
     exp(N(0, 1/4)), centers mu[c, d] = 32 s_d Exp(1), and points
@@ -81,10 +82,11 @@ def sift_like(n: int, nq: int, d: int = 128, seed_data: int = 0, seed_query: int
             out[s:e] = np.clip(np.rint(x), 0, 255)
         return out
 
-    return draw(n, seed_data), draw(nq, seed_query)
+    return (draw(n, seed_data) if with_data else None), draw(nq, seed_query)
 
 
-def gist_like(n: int, nq: int, d: int = 960, seed_data: int = 0, seed_query: int = 1):
+def gist_like(n: int, nq: int, d: int = 960, seed_data: int = 0, seed_query: int = 1,
+              with_data: bool = True):
     """Vectors in [0, 1] from a 500-component mixture, mu ~ Beta(2, 5) per
     dimension, x = clip(mu + 0.05 N(0, 1), 0, 1) (GIST-shaped)."""
     g = np.random.Generator(np.random.PCG64(seed_data))
@@ -98,11 +100,11 @@ def gist_like(n: int, nq: int, d: int = 960, seed_data: int = 0, seed_query: int
             out[s:e] = np.clip(mu[comp] + 0.05 * gg.standard_normal((e - s, d)), 0.0, 1.0)
         return out
 
-    return draw(n, seed_data), draw(nq, seed_query)
+    return (draw(n, seed_data) if with_data else None), draw(nq, seed_query)
 
 
 def deep_like(n: int, nq: int, d: int = 256, n_comp: int = 10_000, seed_data: int = 0,
-              seed_query: int = 1):
+              seed_query: int = 1, with_data: bool = True):
     """Unit-norm vectors from a 10k-component mixture: mu ~ N(0, I/d),
     x = normalize(mu + 0.5 N(0, I/d)) (DEEP-shaped)."""
     g = np.random.Generator(np.random.PCG64(seed_data))
@@ -118,19 +120,22 @@ def deep_like(n: int, nq: int, d: int = 256, n_comp: int = 10_000, seed_data: in
             out[s:e] = x
         return out
 
-    return draw(n, seed_data), draw(nq, seed_query)
+    return (draw(n, seed_data) if with_data else None), draw(nq, seed_query)
 
 
-def make(w: Workload, n: int | None = None, nq: int | None = None):
-    """Data and queries of a workload (optionally with fewer points/queries)."""
+def make(w: Workload, n: int | None = None, nq: int | None = None, seed_query: int = 1,
+         with_data: bool = True):
+    """Data and queries of a workload (optionally with fewer points/queries;
+    another seed_query draws another query set from the same mixture, e.g.
+    training queries; with_data=False skips drawing the data, returning None)."""
     n = w.n if n is None else n
     nq = w.nq if nq is None else nq
     if w is TINY or w.name.startswith("tiny"):
-        return tiny(n=n, nq=nq, d=w.d)
+        return tiny(n=n, nq=nq, d=w.d, seed_query=seed_query)
     if w.name.startswith("sift"):
-        return sift_like(n, nq, w.d)
+        return sift_like(n, nq, w.d, seed_query=seed_query, with_data=with_data)
     if w.name.startswith("gist"):
-        return gist_like(n, nq, w.d)
+        return gist_like(n, nq, w.d, seed_query=seed_query, with_data=with_data)
     if w.name.startswith("deep"):
-        return deep_like(n, nq, w.d)
+        return deep_like(n, nq, w.d, seed_query=seed_query, with_data=with_data)
     raise ValueError(w.name)
