@@ -330,6 +330,21 @@ int rabitq_mlp_grad(const float* params, const float* X, const float* t, int64_t
 int rabitq_mlp_adam(float* master, float* m1, float* m2, const float* grads, int32_t step,
                     float lr, float* work);
 
+/*
+ * rabitq_autotune -- time the popcount scan (RABITQ_SCAN_POPC) and the
+ * tensor-core scan (RABITQ_SCAN_TC) on a sample of queries at the given
+ * search parameters, best of `reps` (>= 1) runs each after one warm-up run,
+ * and make the faster one the path RABITQ_SCAN_AUTO takes on this index from
+ * then on (both give identical results). A tensor-core run that overflows
+ * its candidate lists counts as infinitely slow. opts as for rabitq_search
+ * (scan_path is ignored). chosen (may be NULL) receives the path; times_ms
+ * (may be NULL, 2 entries) the best times {popcount, tensor-core}, -1 for a
+ * path that failed. Not thread-safe against searches on the same index.
+ */
+int rabitq_autotune(rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
+                    int32_t nprobe, int32_t bq, float eps0, int32_t reps,
+                    const rabitq_search_opts* opts, int32_t* chosen, float* times_ms);
+
 /* Per-stage device times (milliseconds) of the last search on this thread
  * with collect_stats set. Stages: 0 centroid distances, 1 probe selection,
  * 2 query rotation, 3 quantize + scan + prune + re-rank, 4 total (including

@@ -371,6 +371,78 @@ int rabitq_search_learned(const rabitq_index* idx, const rabitq_predictor* pr,
                        nullptr, pr);
 }
 
+int rabitq_autotune(rabitq_index* X, const float* queries, int64_t nq, int32_t k,
+                    int32_t nprobe, int32_t bq, float eps0, int32_t reps,
+                    const rabitq_search_opts* opts_in, int32_t* chosen, float* times_ms) {
+  g_err.clear();
+  if (!X) return fail(RABITQ_EINVAL, "rabitq_autotune: index is null");
+  if (nq < 1 || !queries) return fail(RABITQ_EINVAL, "rabitq_autotune: need queries (nq >= 1)");
+  if (reps < 1 || reps > 1000) return fail(RABITQ_EINVAL, "rabitq_autotune: need 1 <= reps <= 1000");
+  rabitq_search_opts opts;
+  rabitq_search_opts_default(&opts);
+  if (opts_in) opts = *opts_in;
+  opts.collect_stats = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(opts.stream);
+  // device copies of the inputs and outputs, so that every timed run is the
+  // same device-resident search
+  DevBuf qb, ib, db, nb;
+  const float* dq = queries;
+  const int32_t* dnp = opts.per_query_nprobe;
+  if (!opts.io_on_device) {
+    RBQ_CHECK(qb.alloc(sizeof(float) * nq * X->d, s));
+    RBQ_CUDA(cudaMemcpyAsync(qb.p, queries, sizeof(float) * nq * X->d, cudaMemcpyHostToDevice, s));
+    dq = qb.as<float>();
+    if (dnp) {
+      RBQ_CHECK(nb.alloc(sizeof(int32_t) * nq, s));
+      RBQ_CUDA(cudaMemcpyAsync(nb.p, dnp, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, s));
+      dnp = nb.as<int32_t>();
+    }
+  }
+  RBQ_CHECK(ib.alloc(sizeof(int64_t) * nq * k, s));
+  RBQ_CHECK(db.alloc(sizeof(float) * nq * k, s));
+  opts.io_on_device = 1;
+  opts.per_query_nprobe = dnp;
+  cudaEvent_t e0, e1;
+  RBQ_CUDA(cudaEventCreate(&e0));
+  RBQ_CUDA(cudaEventCreate(&e1));
+  float best[2] = {-1.0f, -1.0f};
+  const int paths[2] = {RABITQ_SCAN_POPC, RABITQ_SCAN_TC};
+  int st_all = RABITQ_OK;
+  for (int p = 0; p < 2 && st_all == RABITQ_OK; ++p) {
+    opts.scan_path = paths[p];
+    for (int r = 0; r <= reps; ++r) {  // run 0 warms up
+      RBQ_CUDA(cudaEventRecord(e0, s));
+      const int st = search_common(X, dq, nq, k, nprobe, bq, eps0, ib.as<int64_t>(),
+                                   db.as<float>(), &opts, nullptr);
+      if (st == RABITQ_EOVERFLOW && paths[p] == RABITQ_SCAN_TC) {
+        best[p] = -1.0f;
+        break;
+      }
+      if (st != RABITQ_OK) {
+        st_all = st;
+        break;
+      }
+      RBQ_CUDA(cudaEventRecord(e1, s));
+      RBQ_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      RBQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (r > 0 && (best[p] < 0.0f || ms < best[p])) best[p] = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st_all != RABITQ_OK) return st_all;
+  const int pick = (best[1] >= 0.0f && best[1] < best[0]) ? RABITQ_SCAN_TC : RABITQ_SCAN_POPC;
+  X->tuned_path = pick;
+  if (chosen) *chosen = pick;
+  if (times_ms) {
+    times_ms[0] = best[0];
+    times_ms[1] = best[1];
+  }
+  g_err.clear();
+  return RABITQ_OK;
+}
+
 int rabitq_index_info(const rabitq_index* X, int64_t* n, int32_t* d, int32_t* d_pad,
                       int32_t* n_clusters) {
   if (!X) return fail(RABITQ_EINVAL, "rabitq_index_info: index is null");

@@ -147,6 +147,11 @@ struct FusedParams {
   float* out_dist;
   int* err;
   rabitq_trace tr;
+  // query scheduling: CTAs take the next query from *next (zeroed before the
+  // launch) in the order `order` (null = ascending); next == null = static
+  // striding by gridDim.x
+  const int32_t* order;
+  int* next;
 };
 
 struct FusedSmem {
@@ -714,7 +719,18 @@ __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P
   const int W = P.W, bq = P.bq, k = P.k;
   int4* cand = P.cand + (int64_t)blockIdx.x * P.cand_cap;
 
-  for (int64_t q = blockIdx.x; q < P.nq; q += gridDim.x) {
+  __shared__ int s_next;
+  // next work item: dynamic (one atomic per query, taken by thread 0 and
+  // broadcast) or static striding
+  auto fetch = [&](int64_t cur) -> int64_t {
+    if (!P.next) return cur + gridDim.x;
+    __syncthreads();
+    if (tid == 0) s_next = atomicAdd(P.next, 1);
+    __syncthreads();
+    return s_next;
+  };
+  for (int64_t it = P.next ? fetch(0) : (int64_t)blockIdx.x; it < P.nq; it = fetch(it)) {
+    const int64_t q = P.order ? (int64_t)P.order[it] : it;
     int np = P.nprobe;
     if (P.nprobe_q) np = min(max(P.nprobe_q[q], 1), P.nprobe);
     for (int i = tid; i < P.d; i += blockDim.x) S.qv[i] = P.queries[q * P.d + i];
@@ -1253,6 +1269,14 @@ FusedFn pick_fused(int W, int bq) {
   return fused_search_kernel<0, 0>;
 }
 
+// Longest-first order of queries with per-query probe counts: key =
+// nprobe - (clamped count), sorted stably (ties keep ascending query id).
+__global__ void order_key_kernel(const int32_t* __restrict__ npq, int64_t n, int nprobe,
+                                 int32_t* __restrict__ key) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) key[i] = nprobe - min(max(npq[i], 1), nprobe);
+}
+
 int pow2_at_least(int x) {
   int p = 1;
   while (p < x) p <<= 1;
@@ -1323,8 +1347,16 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   RBQ_CHECK(pdist.alloc(sizeof(float) * qchunk * nprobe, s));
   RBQ_CHECK(cand.alloc(sizeof(int4) * grid * a.cand_cap, s));
   RBQ_CHECK(err.alloc(sizeof(int), s));
+  // dynamic query scheduling; with per-query probe counts, longest first
+  DevBuf nextc, okey, order, ooff;
+  RBQ_CHECK(nextc.alloc(sizeof(int), s));
+  if (a.pred || a.per_query_nprobe) {
+    RBQ_CHECK(okey.alloc(sizeof(int32_t) * qchunk, s));
+    RBQ_CHECK(order.alloc(sizeof(int32_t) * qchunk, s));
+    RBQ_CHECK(ooff.alloc(sizeof(int32_t) * (nprobe + 2), s));
+  }
   DevBuf fid, fdist;  // learned probe counts: the 64 nearest buckets per query
-  if (a.pred) {
+  if (a.pred && nprobe < std::min(kMlpIn, K)) {
     RBQ_CHECK(fid.alloc(sizeof(int32_t) * qchunk * kMlpIn, s));
     RBQ_CHECK(fdist.alloc(sizeof(float) * qchunk * kMlpIn, s));
   }
@@ -1352,14 +1384,24 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
     float* probe_dist = a.trace && a.trace->probe_dist ? a.trace->probe_dist + q0 * nprobe
                                                        : pdist.as<float>();
     const int32_t* npq = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
-    if (a.pred) {
+    // learned counts: when the probe list holds the 64 nearest buckets, the
+    // features come from it (one selection); otherwise from a selection of
+    // their own. The scan reads only the first nprobe_q entries either way.
+    const int navail = std::min(kMlpIn, K);
+    const bool pred_from_list = a.pred && nprobe >= navail;
+    if (a.pred && !pred_from_list) {
       RBQ_CHECK(predict_chunk(a, cd.as<float>(), nqc, q0, fid.as<int32_t>(), fdist.as<float>(), s));
       npq = a.pred_nprobe + q0;
     }
     select_kernel<<<(unsigned)nqc, kThreads, sel_smem, s>>>(
-        cd.as<float>(), K, nprobe, npq,
+        cd.as<float>(), K, nprobe, pred_from_list ? nullptr : npq,
         sort_n, probe_ids, probe_dist);
     RBQ_CUDA(cudaGetLastError());
+    if (pred_from_list) {
+      RBQ_CHECK(mlp_infer(a.pred, probe_dist, nprobe, nqc, navail, a.pred_nprobe + q0, nullptr,
+                          nullptr, s));
+      npq = a.pred_nprobe + q0;
+    }
     if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
     float* rqp = a.trace && a.trace->rq ? a.trace->rq + q0 * dpad : rq.as<float>();
     if (a.rot_precision == RABITQ_ROT_FP32)
@@ -1402,6 +1444,15 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
     P.out_ids = a.out_ids + q0 * a.k;
     P.out_dist = a.out_dist + q0 * a.k;
     P.err = err.as<int>();
+    P.next = nextc.as<int>();
+    RBQ_CUDA(cudaMemsetAsync(nextc.p, 0, sizeof(int), s));
+    if (npq) {
+      order_key_kernel<<<(unsigned)((nqc + 255) / 256), 256, 0, s>>>(npq, nqc, nprobe,
+                                                                    okey.as<int32_t>());
+      RBQ_CHECK(counting_sort(okey.as<int32_t>(), nqc, nprobe + 1, order.as<int32_t>(),
+                              ooff.as<int32_t>(), s));
+      P.order = order.as<int32_t>();
+    }
     if (a.trace) {
       const rabitq_trace& T = *a.trace;
       P.tr = T;
@@ -1550,6 +1601,8 @@ int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scra
     P.out_ids = a.out_ids + q0 * a.k;
     P.out_dist = a.out_dist + q0 * a.k;
     P.err = err;
+    P.next = reinterpret_cast<int*>(scratch + 64);  // in the flag's 256-byte block
+    RBQ_CUDA(cudaMemsetAsync(P.next, 0, sizeof(int), s));
     fn<<<(unsigned)std::min<int64_t>(nqc, grid), kThreads, smem, s>>>(P);
     RBQ_CUDA(cudaGetLastError());
   }

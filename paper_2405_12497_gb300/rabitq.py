@@ -30,7 +30,7 @@ EXPORTS = (
     "rabitq_predictor_opts_default", "rabitq_predictor_train", "rabitq_predictor_create",
     "rabitq_predictor_get_info", "rabitq_predictor_get_params", "rabitq_predictor_set_mult",
     "rabitq_predictor_free", "rabitq_predict_nprobe", "rabitq_search_learned",
-    "rabitq_compute_labels", "rabitq_mlp_grad", "rabitq_mlp_adam",
+    "rabitq_compute_labels", "rabitq_mlp_grad", "rabitq_mlp_adam", "rabitq_autotune",
 )
 
 MLP_IN, MLP_HIDDEN = 64, 256
@@ -123,6 +123,7 @@ def lib():
             "rabitq_compute_labels": (C.c_int, [vp, vp, i64, vp, i32, f32, i32, vp, vp]),
             "rabitq_mlp_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp]),
             "rabitq_mlp_adam": (C.c_int, [vp, vp, vp, vp, i32, f32, vp]),
+            "rabitq_autotune": (C.c_int, [vp, vp, i64, i32, i32, i32, f32, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -366,6 +367,24 @@ class Index:
         t["ids"], t["dist"] = ids, dist
         return t
 
+
+    def autotune(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
+                 reps: int = 3, max_candidates: int = 65536, rot_precision=ROT_FP32):
+        """Time both scan paths on these queries; AUTO takes the faster one from
+        now on. Returns (chosen path, {"popc": ms, "tc": ms})."""
+        dev = _is_torch(queries)
+        o = self._opts(3, None, max_candidates, False, None, dev, rot_precision)
+        if dev:
+            q = queries.contiguous()
+            qp = _dptr(q)
+        else:
+            q = np.ascontiguousarray(queries, np.float32)
+            qp = _np_ptr(q)
+        chosen = C.c_int32()
+        t = np.zeros(2, np.float32)
+        _check(lib().rabitq_autotune(self._h, qp, q.shape[0], k, nprobe, bq, eps0, reps,
+                                     C.byref(o), C.byref(chosen), _np_ptr(t)))
+        return chosen.value, {"popc": float(t[0]), "tc": float(t[1])}
 
     # ------------------------------------------------------ learned nprobe
     def search_learned(self, predictor: "Predictor", queries, k: int, bq: int = 4,

@@ -169,16 +169,17 @@ def test_inference_equals_training_forward(R, tiny_workload, tiny_gpu_index):
 
 
 @pytest.mark.parametrize("scan", ["popc", "tc"])
-def test_search_learned_equals_per_query_search(R, tiny_workload, tiny_gpu_index, scan):
+@pytest.mark.parametrize("nmax", [12, 16])  # 16 = K: features read from the probe list
+def test_search_learned_equals_per_query_search(R, tiny_workload, tiny_gpu_index, scan, nmax):
     import torch
     _, queries = tiny_workload
-    p = rand_params(8, scale=0.3)
-    pr = R.Predictor.create(p, 30.0, 1.0, 12, 16)
+    p = rand_params(8, scale=1.0)
+    pr = R.Predictor.create(p, 30.0, 1.0, nmax, 16)
     path = R.SCAN_POPC if scan == "popc" else R.SCAN_TC
     npb = tiny_gpu_index.predict_nprobe(pr, queries)
-    assert npb.min() >= 1 and npb.max() <= 12
+    assert npb.min() >= 1 and npb.max() <= nmax and len(np.unique(npb)) > 1
     ids, dist = tiny_gpu_index.search_learned(pr, queries, 10, scan_path=path)
-    ids2, dist2 = tiny_gpu_index.search(queries, 10, 12, per_query_nprobe=npb, scan_path=path)
+    ids2, dist2 = tiny_gpu_index.search(queries, 10, nmax, per_query_nprobe=npb, scan_path=path)
     assert np.array_equal(ids, ids2)
     assert np.array_equal(dist.view(np.uint32), dist2.view(np.uint32))
     # device queries give the same
