@@ -30,6 +30,7 @@ extern "C" {
 
 typedef struct rabitq_index rabitq_index;
 typedef struct rabitq_predictor rabitq_predictor;
+typedef struct rabitq_plan rabitq_plan;
 
 typedef enum {
   RABITQ_OK = 0,
@@ -70,7 +71,7 @@ typedef struct {
   const int32_t* per_query_nprobe; /* optional nq probe counts (same memory kind
                                as the queries), each clamped to [1, nprobe]      */
   int32_t max_candidates;   /* per-query capacity of the candidate list that
-                               survives the error bound (0 = 65536)              */
+                               survives the error bound, 4096..2^26 (0 = 65536) */
   int32_t collect_stats;    /* record per-stage device times (rabitq_last_stats) */
 } rabitq_search_opts;
 
@@ -344,6 +345,58 @@ int rabitq_mlp_adam(float* master, float* m1, float* m2, const float* grads, int
 int rabitq_autotune(rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
                     int32_t nprobe, int32_t bq, float eps0, int32_t reps,
                     const rabitq_search_opts* opts, int32_t* chosen, float* times_ms);
+
+/*
+ * ---- Search plans (CUDA-graph replay of a whole search) -------------------
+ *
+ * rabitq_plan_create -- a search of up to nq_max queries at fixed k, nprobe,
+ * bq, eps0 and options (rot_precision, quant_seed, max_candidates; the scan
+ * is the popcount path; per_query_nprobe is not supported), optionally with
+ * learned probe counts (pr != NULL: nprobe is then pr's nprobe_max). All
+ * device memory is allocated here: the plan's query buffer (nq_max x d), its
+ * result buffers (nq_max x k ids and distances) and the scratch. The first
+ * run of each batch size nq captures the launch sequence of rabitq_search
+ * into a CUDA graph; later runs replay it. Results equal rabitq_search's
+ * with scan_path RABITQ_SCAN_POPC. The index and predictor must outlive the
+ * plan. Errors: those of rabitq_search's arguments; EUNSUPPORTED; ENOMEM.
+ */
+int rabitq_plan_create(const rabitq_index* idx, const rabitq_predictor* pr, int64_t nq_max,
+                       int32_t k, int32_t nprobe, int32_t bq, float eps0,
+                       const rabitq_search_opts* opts, rabitq_plan** out);
+
+/* Device pointers of the plan's buffers (owned by the plan; any may be NULL):
+ * queries nq_max x d (the input of rabitq_plan_run), ids / dist nq_max x k
+ * (its output), nprobe nq_max (the learned probe counts of the last run, or
+ * NULL without a predictor). */
+int rabitq_plan_buffers(const rabitq_plan* plan, float** queries, int64_t** ids, float** dist,
+                        int32_t** nprobe);
+
+/* Search the first nq (0..nq_max) rows of the plan's query buffer into its
+ * result buffers: one graph launch on `stream` (a cudaStream_t; NULL = the
+ * legacy stream), asynchronous. Runs on one plan must not overlap (they share
+ * the scratch): issue them on one stream. Errors of the device work are
+ * reported by rabitq_plan_sync. */
+int rabitq_plan_run(rabitq_plan* plan, int64_t nq, void* stream);
+
+/* Wait for `stream`; return OK, or the first device error (EOVERFLOW,
+ * ETIMEOUT) of the runs since the last rabitq_plan_sync, and clear it. */
+int rabitq_plan_sync(rabitq_plan* plan, void* stream);
+
+/* Copy nq queries (host or device memory) into the plan, run it, copy the
+ * results out (host or device memory) and sync: the whole round trip on
+ * `stream`. With pinned host buffers every copy is asynchronous. */
+int rabitq_plan_search(rabitq_plan* plan, const float* queries, int64_t nq, int64_t* out_ids,
+                       float* out_dist, void* stream);
+
+/* With opts->collect_stats set at creation, the device times (ms) of the
+ * last run's stages: 0 centroid distances, 1 probe selection (+ learned
+ * counts), 2 query rotation, 3 order + fused quantize/scan/prune/re-rank --
+ * recorded by event nodes inside the graph. Waits for the last run. Returns
+ * the number of entries written (0 without collect_stats). */
+int rabitq_plan_stats(rabitq_plan* plan, float* ms, int32_t cap);
+
+/* Release a plan (NULL is a no-op). */
+void rabitq_plan_free(rabitq_plan* plan);
 
 /* Per-stage device times (milliseconds) of the last search on this thread
  * with collect_stats set. Stages: 0 centroid distances, 1 probe selection,

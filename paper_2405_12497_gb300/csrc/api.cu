@@ -258,8 +258,8 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   if (bq < 1 || bq > 8) return fail(RABITQ_EINVAL, "rabitq_search: need 1 <= bq <= 8");
   if (!(eps0 >= 0.0f) || !std::isfinite(eps0))
     return fail(RABITQ_EINVAL, "rabitq_search: eps0 must be finite and >= 0");
-  if (opts.max_candidates < 1024 || opts.max_candidates > (1 << 26))
-    return fail(RABITQ_EINVAL, "rabitq_search: max_candidates must be in [1024, 2^26]");
+  if (opts.max_candidates < 4096 || opts.max_candidates > (1 << 26))
+    return fail(RABITQ_EINVAL, "rabitq_search: max_candidates must be in [4096, 2^26]");
   if (opts.rot_precision != RABITQ_ROT_FP32 && opts.rot_precision != RABITQ_ROT_TF32 &&
       opts.rot_precision != RABITQ_ROT_BF16)
     return fail(RABITQ_EINVAL, "rabitq_search: unknown rot_precision");

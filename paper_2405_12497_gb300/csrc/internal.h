@@ -101,6 +101,11 @@ int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t 
 // stable counting sort of ids [0, n) by key (cluster); perm: position -> id
 int counting_sort(const int32_t* key, int64_t n, int32_t K, int32_t* perm, int32_t* offsets,
                   cudaStream_t s);
+// the same with caller-provided scratch of counting_sort_ws_ints(n, K) ints
+// (no allocation, so it can be captured in a CUDA graph)
+int64_t counting_sort_ws_ints(int64_t n, int32_t K);
+int counting_sort_ws(const int32_t* key, int64_t n, int32_t K, int32_t* perm, int32_t* offsets,
+                     int32_t* ws, cudaStream_t s);
 int sample_rotation_dev(uint64_t seed, int32_t dpad, double* P64, float* P32, cudaStream_t s);
 int kmeans_dev(const float* data, int64_t n, int32_t d, int32_t K, int32_t iters, int64_t sample,
                uint64_t seed, float* centroids, cudaStream_t s);
@@ -139,6 +144,10 @@ struct SearchArgs {
   // them. Null for a fixed or caller-given probe count.
   const rabitq_predictor* pred = nullptr;
   int32_t* pred_nprobe = nullptr;
+  // carved path only: 5 events recorded (as external graph nodes when
+  // captured) around the stages: distances | selection (+ MLP) | rotation |
+  // fused scan, prune and re-rank. Single-chunk searches only.
+  cudaEvent_t* stage_ev = nullptr;
 };
 int search_dev(const SearchArgs& a, cudaStream_t s);
 // Probe counts of nq queries from a predictor: query-centroid distances, the
@@ -150,6 +159,16 @@ int select_buckets(const rabitq_index* X, const float* Q, int64_t nq, int nsel, 
                    float* dist, cudaStream_t s);
 int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scratch_bytes,
                         cudaStream_t s);
+// The allocation-free, synchronization-free launch sequence of the popcount
+// search (capturable in a CUDA graph). The scratch's first int is the error
+// flag (1 = candidate overflow, 2 = tensor-core wait expired), which this call
+// sets but never clears.
+int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t scratch_bytes,
+                          int64_t grid, int64_t cap, cudaStream_t s);
+// scratch bytes for nq_max queries in one chunk with a.cand_cap candidates per CTA
+size_t carved_bytes(const SearchArgs& a, int64_t grid, int64_t nq_max);
+// CTAs of the fused kernel at full residency for these search parameters
+int fused_grid(const SearchArgs& a, int* grid_out);
 
 // ---- learned probe count (kernels_mlp.cu) ---------------------------------
 constexpr int kMlpIn = RABITQ_MLP_IN, kMlpHidden = RABITQ_MLP_HIDDEN;

@@ -383,39 +383,64 @@ int DevBuf::alloc(size_t bytes, cudaStream_t st) {
   return RABITQ_OK;
 }
 
+namespace {
+int scan_ws(const int32_t* in, int32_t* out, int64_t n, int32_t* sums, cudaStream_t s) {
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  scan_tile_sums<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+  scan_sums_inplace<<<1, kScanThreads, 0, s>>>(sums, (int)nb);
+  scan_tile_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+  RBQ_CUDA(cudaGetLastError());
+  return RABITQ_OK;
+}
+}  // namespace
+
 int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s) {
   if (n <= 0) return RABITQ_OK;
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
   DevBuf sums;
   RBQ_CHECK(sums.alloc(sizeof(int32_t) * nb, s));
-  scan_tile_sums<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums.as<int32_t>());
-  scan_sums_inplace<<<1, kScanThreads, 0, s>>>(sums.as<int32_t>(), (int)nb);
-  scan_tile_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums.as<int32_t>());
+  return scan_ws(in, out, n, sums.as<int32_t>(), s);
+}
+
+namespace {
+int64_t sort_windows(int64_t n, int32_t K) {
+  int64_t nw = (n + 2047) / 2048;
+  const int64_t cap = (int64_t(1) << 25) / K;
+  if (nw > cap) nw = cap;
+  if (nw < 1) nw = 1;
+  return nw;
+}
+}  // namespace
+
+int64_t counting_sort_ws_ints(int64_t n, int32_t K) {
+  const int64_t cells = (int64_t)K * sort_windows(n, K);
+  return 2 * cells + (cells + kScanTile - 1) / kScanTile;
+}
+
+int counting_sort_ws(const int32_t* key, int64_t n, int32_t K, int32_t* perm, int32_t* offsets,
+                     int32_t* ws, cudaStream_t s) {
+  const int64_t nw = sort_windows(n, K);
+  const int64_t L = (n + nw - 1) / nw;
+  const int64_t cells = (int64_t)K * nw;
+  int32_t* hist = ws;
+  int32_t* off = ws + cells;
+  int32_t* sums = ws + 2 * cells;
+  RBQ_CUDA(cudaMemsetAsync(hist, 0, sizeof(int32_t) * cells, s));
+  const unsigned blocks = blocks_for(nw * 32, 256);
+  sort_hist_kernel<<<blocks, 256, 0, s>>>(key, n, (int)nw, L, hist);
+  RBQ_CUDA(cudaGetLastError());
+  RBQ_CHECK(scan_ws(hist, off, cells, sums, s));
+  bucket_offsets_kernel<<<blocks_for(K + 1, 256), 256, 0, s>>>(off, K, (int)nw, n, offsets);
+  sort_scatter_kernel<<<blocks, 256, 0, s>>>(key, n, (int)nw, L, off, perm);
   RBQ_CUDA(cudaGetLastError());
   return RABITQ_OK;
 }
 
 int counting_sort(const int32_t* key, int64_t n, int32_t K, int32_t* perm, int32_t* offsets,
                   cudaStream_t s) {
-  int64_t nw = (n + 2047) / 2048;
-  const int64_t cap = (int64_t(1) << 25) / K;
-  if (nw > cap) nw = cap;
-  if (nw < 1) nw = 1;
-  const int64_t L = (n + nw - 1) / nw;
-  const int64_t cells = (int64_t)K * nw;
-  DevBuf hist, off;
-  RBQ_CHECK(hist.alloc(sizeof(int32_t) * cells, s));
-  RBQ_CHECK(off.alloc(sizeof(int32_t) * cells, s));
-  RBQ_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * cells, s));
-  const unsigned blocks = blocks_for(nw * 32, 256);
-  sort_hist_kernel<<<blocks, 256, 0, s>>>(key, n, (int)nw, L, hist.as<int32_t>());
-  RBQ_CUDA(cudaGetLastError());
-  RBQ_CHECK(exclusive_scan_i32(hist.as<int32_t>(), off.as<int32_t>(), cells, s));
-  bucket_offsets_kernel<<<blocks_for(K + 1, 256), 256, 0, s>>>(off.as<int32_t>(), K, (int)nw, n,
-                                                              offsets);
-  sort_scatter_kernel<<<blocks, 256, 0, s>>>(key, n, (int)nw, L, off.as<int32_t>(), perm);
-  RBQ_CUDA(cudaGetLastError());
-  return RABITQ_OK;
+  DevBuf ws;
+  RBQ_CHECK(ws.alloc(sizeof(int32_t) * counting_sort_ws_ints(n, K), s));
+  return counting_sort_ws(key, n, K, perm, offsets, ws.as<int32_t>(), s);
 }
 
 int gather_rows_f32(const float* in, int64_t ld, const int32_t* rows, int64_t m, int32_t d,

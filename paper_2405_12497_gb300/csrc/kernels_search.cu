@@ -1503,18 +1503,97 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   return RABITQ_OK;
 }
 
-// The same pipeline as search_dev, with every scratch array carved out of a
-// caller-provided device buffer instead of being allocated: query chunks are
-// sized to what fits. Used by the entry point that must not allocate.
-int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scratch_bytes,
-                        cudaStream_t s) {
+// ---------------------------------------------- carved (allocation-free) path
+// The popcount pipeline with every scratch array carved out of one device
+// buffer: no allocation and no host synchronization between the launches, so
+// the whole sequence can also be captured in a CUDA graph (search plans).
+//
+// Layout: [flags (error, work counter) | candidate lists (grid x cap) |
+// per-chunk arrays for qchunk queries].
+namespace {
+
+struct Carve {
+  int64_t grid = 0, cap = 0, qchunk = 0;
+  size_t o_cand = 0, o_cd = 0, o_rq = 0, o_pid = 0, o_pdist = 0, o_pnp = 0, o_fid = 0,
+         o_fdist = 0, o_okey = 0, o_order = 0, o_ooff = 0, o_sortws = 0, end = 0;
+};
+
+constexpr size_t kCarveAlign = 256;
+
+// Offsets for the given grid, candidate capacity and query chunk.
+Carve carve_layout(const SearchArgs& a, int64_t grid, int64_t cap, int64_t qchunk) {
+  const rabitq_index* X = a.X;
+  const int K = X->K, nprobe = std::min(a.nprobe, K);
+  const bool ordered = a.pred || a.per_query_nprobe;
+  const bool own_select = a.pred && nprobe < std::min(kMlpIn, K);
+  Carve L;
+  L.grid = grid;
+  L.cap = cap;
+  L.qchunk = qchunk;
+  size_t o = kCarveAlign;  // the flags
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, kCarveAlign);
+    return at;
+  };
+  L.o_cand = take(sizeof(int4) * grid * cap);
+  L.o_cd = take(sizeof(float) * qchunk * K);
+  L.o_rq = take(sizeof(float) * qchunk * X->dpad);
+  L.o_pid = take(sizeof(int32_t) * qchunk * nprobe);
+  L.o_pdist = take(sizeof(float) * qchunk * nprobe);
+  L.o_pnp = take(a.pred ? sizeof(int32_t) * qchunk : 0);
+  L.o_fid = take(own_select ? sizeof(int32_t) * qchunk * kMlpIn : 0);
+  L.o_fdist = take(own_select ? sizeof(float) * qchunk * kMlpIn : 0);
+  L.o_okey = take(ordered ? sizeof(int32_t) * qchunk : 0);
+  L.o_order = take(ordered ? sizeof(int32_t) * qchunk : 0);
+  L.o_ooff = take(ordered ? sizeof(int32_t) * (nprobe + 2) : 0);
+  L.o_sortws = take(ordered ? sizeof(int32_t) * counting_sort_ws_ints(qchunk, nprobe + 1) : 0);
+  L.end = o;
+  return L;
+}
+
+}  // namespace
+
+size_t carved_bytes(const SearchArgs& a, int64_t grid, int64_t nq_max) {
+  return carve_layout(a, grid, a.cand_cap, std::max<int64_t>(nq_max, 1)).end;
+}
+
+int fused_grid(const SearchArgs& a, int* grid_out) {
+  const rabitq_index* X = a.X;
+  const int nprobe = std::min(a.nprobe, X->K), W = X->W;
+  const int plane_bytes = a.bq * W * 8;
+  const int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
+  const int cu = std::max(1024, pow2_at_least(a.k + kPPT * kThreads));
+  const int ce = pow2_at_least(4 * a.k);
+  const int ct = std::max(512, pow2_at_least(a.k + kThreads));
+  const size_t smem = fused_smem_bytes(pch, a.bq, W, X->d, cu, ce, ct, kThreads / 32, nullptr);
+  const FusedFn fn = pick_fused(W, a.bq);
+  RBQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, per_sm = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
+  RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
+  *grid_out = sms * std::max(per_sm, 1);
+  return RABITQ_OK;
+}
+
+// Enqueue the search of a.nq queries (chunks of what fits) on stream s. The
+// error flag is the first int of the scratch (1 = candidate overflow,
+// 2 = tensor-core wait expired); the caller zeroes it before the first call
+// and reads it after the stream has drained. grid: CTAs of the fused kernel
+// (0 = one per SM); cap: candidate capacity per CTA.
+int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t scratch_bytes,
+                          int64_t grid, int64_t cap, cudaStream_t s) {
   const rabitq_index* X = a.X;
   const int K = X->K, d = X->d, dpad = X->dpad, W = X->W;
   const int nprobe = std::min(a.nprobe, K);
   if (a.nq == 0) return RABITQ_OK;
-  int dev = 0, sms = 0;
-  RBQ_CUDA(cudaGetDevice(&dev));
-  RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (grid <= 0) {
+    int dev = 0, sms = 0;
+    RBQ_CUDA(cudaGetDevice(&dev));
+    RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    grid = sms;
+  }
   const int plane_bytes = a.bq * W * 8;
   const int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
   const int pilot_m = 4 * a.k;
@@ -1528,52 +1607,75 @@ int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scra
   const size_t sel_smem = sizeof(unsigned long long) * sort_n;
   RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kSelMaxSmem));
-  // layout: [error flag | candidate lists (one CTA per SM) | per-chunk query arrays]
-  const size_t A = 256;
-  const int64_t grid = sms;
-  size_t off = A;
-  const size_t cand_room = scratch_bytes / 2 > off ? scratch_bytes / 2 - off : 0;
-  int64_t cap = std::min<int64_t>(a.cand_cap, (int64_t)(cand_room / (sizeof(int4) * grid)));
-  if (cap < 1024) return fail(RABITQ_EINVAL, "rabitq_search_noalloc: scratch too small");
-  int4* cand = reinterpret_cast<int4*>(scratch + off);
-  off = align_up(off + sizeof(int4) * grid * cap, A);
-  const size_t per_q = sizeof(float) * K + sizeof(float) * dpad + sizeof(int32_t) * nprobe +
-                       sizeof(float) * nprobe;
-  const size_t room = scratch_bytes > off + 4 * A ? scratch_bytes - off - 4 * A : 0;
-  const int64_t qchunk = std::min<int64_t>(a.nq, (int64_t)(room / per_q));
-  if (qchunk < 1)
+  if (cap < 4096) return fail(RABITQ_EINVAL, "search scratch too small for the candidate lists");
+  int64_t lo = 1, hi = a.nq;
+  if (carve_layout(a, grid, cap, 1).end > scratch_bytes)
     return fail(RABITQ_EINVAL,
-                "rabitq_search_noalloc: one query's distances to every centroid do not fit in "
-                "the fixed scratch (K too large)");
-  float* cd = reinterpret_cast<float*>(scratch + off);
-  off = align_up(off + sizeof(float) * qchunk * K, A);
-  float* rq = reinterpret_cast<float*>(scratch + off);
-  off = align_up(off + sizeof(float) * qchunk * dpad, A);
-  int32_t* pid = reinterpret_cast<int32_t*>(scratch + off);
-  off = align_up(off + sizeof(int32_t) * qchunk * nprobe, A);
-  float* pdist = reinterpret_cast<float*>(scratch + off);
-  off = align_up(off + sizeof(float) * qchunk * nprobe, A);
-  if (off > scratch_bytes) return fail(RABITQ_EINVAL, "rabitq_search_noalloc: layout overflow");
+                "one query's distances to every centroid do not fit in the search scratch "
+                "(K too large)");
+  while (lo < hi) {  // largest chunk that fits
+    const int64_t mid = lo + (hi - lo + 1) / 2;
+    if (carve_layout(a, grid, cap, mid).end <= scratch_bytes) lo = mid; else hi = mid - 1;
+  }
+  const Carve L = carve_layout(a, grid, cap, lo);
+  const int64_t qchunk = L.qchunk;
   int* err = reinterpret_cast<int*>(scratch);
-  RBQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));  // the flag must start at zero
+  int* next = reinterpret_cast<int*>(scratch + 64);
+  int4* cand = reinterpret_cast<int4*>(scratch + L.o_cand);
+  float* cd = reinterpret_cast<float*>(scratch + L.o_cd);
+  float* rq = reinterpret_cast<float*>(scratch + L.o_rq);
+  int32_t* pid = reinterpret_cast<int32_t*>(scratch + L.o_pid);
+  float* pdist = reinterpret_cast<float*>(scratch + L.o_pdist);
+  int32_t* pnp = reinterpret_cast<int32_t*>(scratch + L.o_pnp);
+  int32_t* fid = reinterpret_cast<int32_t*>(scratch + L.o_fid);
+  float* fdist = reinterpret_cast<float*>(scratch + L.o_fdist);
+  int32_t* okey = reinterpret_cast<int32_t*>(scratch + L.o_okey);
+  int32_t* order = reinterpret_cast<int32_t*>(scratch + L.o_order);
+  int32_t* ooff = reinterpret_cast<int32_t*>(scratch + L.o_ooff);
+  int32_t* sortws = reinterpret_cast<int32_t*>(scratch + L.o_sortws);
+  const int navail = std::min(kMlpIn, K);
   for (int64_t q0 = 0; q0 < a.nq; q0 += qchunk) {
     const int64_t nqc = std::min(qchunk, a.nq - q0);
     const float* Q = a.queries + q0 * d;
+    const bool ev = a.stage_ev && q0 == 0 && nqc == a.nq;
+    if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[0], s, cudaEventRecordExternal));
     RBQ_CHECK(gemm_canon(kSqDist, Q, d, nullptr, nullptr, 0, nullptr, X->centroids_t, K, cd, K,
                          nqc, K, d, s));
+    if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[1], s, cudaEventRecordExternal));
+    const int32_t* npq = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
+    const bool pred_from_list = a.pred && nprobe >= navail;
+    if (a.pred && !pred_from_list) {
+      const int sn = pow2_at_least(navail);
+      select_kernel<<<(unsigned)nqc, kThreads, sizeof(unsigned long long) * sn, s>>>(
+          cd, K, navail, nullptr, sn, fid, fdist);
+      RBQ_CUDA(cudaGetLastError());
+      RBQ_CHECK(mlp_infer(a.pred, fdist, navail, nqc, navail, pnp, nullptr, nullptr, s));
+      npq = pnp;
+    }
     select_kernel<<<(unsigned)nqc, kThreads, sel_smem, s>>>(
-        cd, K, nprobe, a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr, sort_n, pid,
-        pdist);
+        cd, K, nprobe, pred_from_list ? nullptr : npq, sort_n, pid, pdist);
     RBQ_CUDA(cudaGetLastError());
-    RBQ_CHECK(gemm_canon(kDot, Q, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rq, dpad, nqc,
-                         dpad, d, s));
+    if (pred_from_list) {
+      RBQ_CHECK(mlp_infer(a.pred, pdist, nprobe, nqc, navail, pnp, nullptr, nullptr, s));
+      npq = pnp;
+    }
+    if (a.pred && a.pred_nprobe)
+      RBQ_CUDA(cudaMemcpyAsync(a.pred_nprobe + q0, pnp, sizeof(int32_t) * nqc,
+                               cudaMemcpyDeviceToDevice, s));
+    if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[2], s, cudaEventRecordExternal));
+    if (a.rot_precision == RABITQ_ROT_FP32)
+      RBQ_CHECK(gemm_canon(kDot, Q, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rq, dpad, nqc,
+                           dpad, d, s));
+    else
+      RBQ_CHECK(rotate_tc(X, Q, nqc, a.rot_precision, rq, err, s));
+    if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[3], s, cudaEventRecordExternal));
     FusedParams P;
     std::memset(&P, 0, sizeof P);
     P.queries = Q;
     P.rq = rq;
     P.probe_ids = pid;
     P.probe_dist = pdist;
-    P.nprobe_q = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
+    P.nprobe_q = npq;
     P.ptc = X->ptc;
     P.codes = X->codes;
     P.factors = X->factors;
@@ -1601,14 +1703,37 @@ int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scra
     P.out_ids = a.out_ids + q0 * a.k;
     P.out_dist = a.out_dist + q0 * a.k;
     P.err = err;
-    P.next = reinterpret_cast<int*>(scratch + 64);  // in the flag's 256-byte block
-    RBQ_CUDA(cudaMemsetAsync(P.next, 0, sizeof(int), s));
+    P.next = next;
+    RBQ_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
+    if (npq) {
+      order_key_kernel<<<(unsigned)((nqc + 255) / 256), 256, 0, s>>>(npq, nqc, nprobe, okey);
+      RBQ_CUDA(cudaGetLastError());
+      RBQ_CHECK(counting_sort_ws(okey, nqc, nprobe + 1, order, ooff, sortws, s));
+      P.order = order;
+    }
     fn<<<(unsigned)std::min<int64_t>(nqc, grid), kThreads, smem, s>>>(P);
     RBQ_CUDA(cudaGetLastError());
+    if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[4], s, cudaEventRecordExternal));
   }
+  return RABITQ_OK;
+}
+
+int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scratch_bytes,
+                        cudaStream_t s) {
+  if (a.nq == 0) return RABITQ_OK;
+  int* err = reinterpret_cast<int*>(scratch);
+  RBQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));  // the flag must start at zero
+  // one CTA per SM; the candidate lists take at most half of the scratch
+  int dev = 0, sms = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
+  RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t cap = std::min<int64_t>(
+      a.cand_cap, (int64_t)((scratch_bytes / 2 - kCarveAlign) / (sizeof(int4) * sms)));
+  RBQ_CHECK(search_enqueue_carved(a, scratch, scratch_bytes, sms, cap, s));
   int h_err = 0;
   RBQ_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   RBQ_CUDA(cudaStreamSynchronize(s));
+  if (h_err == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired in the query rotation");
   if (h_err)
     return fail(RABITQ_EOVERFLOW,
                 "a query's candidate list exceeded the fixed scratch's capacity");

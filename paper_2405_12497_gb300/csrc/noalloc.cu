@@ -64,8 +64,8 @@ extern "C" int rabitq_search_noalloc(const rabitq_index* X, const float* queries
   if (bq < 1 || bq > 8) return fail(RABITQ_EINVAL, "rabitq_search_noalloc: need 1 <= bq <= 8");
   if (!(eps0 >= 0.0f) || !(eps0 < __builtin_inff()))
     return fail(RABITQ_EINVAL, "rabitq_search_noalloc: eps0 must be finite and >= 0");
-  if (opts.max_candidates < 1024 || opts.max_candidates > (1 << 26))
-    return fail(RABITQ_EINVAL, "rabitq_search_noalloc: max_candidates must be in [1024, 2^26]");
+  if (opts.max_candidates < 4096 || opts.max_candidates > (1 << 26))
+    return fail(RABITQ_EINVAL, "rabitq_search_noalloc: max_candidates must be in [4096, 2^26]");
   if (opts.rot_precision != RABITQ_ROT_FP32 ||
       (opts.scan_path != RABITQ_SCAN_AUTO && opts.scan_path != RABITQ_SCAN_POPC))
     return fail(RABITQ_EUNSUPPORTED, "rabitq_search_noalloc: FP32 rotation, popcount scan only");

@@ -31,6 +31,8 @@ EXPORTS = (
     "rabitq_predictor_get_info", "rabitq_predictor_get_params", "rabitq_predictor_set_mult",
     "rabitq_predictor_free", "rabitq_predict_nprobe", "rabitq_search_learned",
     "rabitq_compute_labels", "rabitq_mlp_grad", "rabitq_mlp_adam", "rabitq_autotune",
+    "rabitq_plan_create", "rabitq_plan_buffers", "rabitq_plan_run", "rabitq_plan_sync",
+    "rabitq_plan_search", "rabitq_plan_free", "rabitq_plan_stats",
 )
 
 MLP_IN, MLP_HIDDEN = 64, 256
@@ -124,6 +126,13 @@ def lib():
             "rabitq_mlp_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp]),
             "rabitq_mlp_adam": (C.c_int, [vp, vp, vp, vp, i32, f32, vp]),
             "rabitq_autotune": (C.c_int, [vp, vp, i64, i32, i32, i32, f32, i32, vp, vp, vp]),
+            "rabitq_plan_create": (C.c_int, [vp, vp, i64, i32, i32, i32, f32, vp, vp]),
+            "rabitq_plan_buffers": (C.c_int, [vp, vp, vp, vp, vp]),
+            "rabitq_plan_run": (C.c_int, [vp, i64, vp]),
+            "rabitq_plan_sync": (C.c_int, [vp, vp]),
+            "rabitq_plan_search": (C.c_int, [vp, vp, i64, vp, vp, vp]),
+            "rabitq_plan_free": (None, [vp]),
+            "rabitq_plan_stats": (C.c_int, [vp, vp, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -323,7 +332,7 @@ class Index:
     def search_trace(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
                      quant_seed: int = 3, pair_cap: int = 0, surv_cap: int = 0,
                      max_candidates: int = 65536, rot_precision=ROT_FP32,
-                     scan_path=SCAN_POPC):
+                     scan_path=SCAN_POPC, per_query_nprobe=None):
         """Search of torch CUDA queries that also returns every intermediate
         (torch CUDA tensors)."""
         import torch
@@ -362,6 +371,10 @@ class Index:
         dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
         o = self._opts(quant_seed, None, max_candidates, False, None, True, rot_precision,
                        scan_path)
+        if per_query_nprobe is not None:
+            npq = per_query_nprobe.to(device=dev, dtype=torch.int32).contiguous()
+            t["per_query_nprobe"] = npq
+            o.per_query_nprobe = _dptr(npq)
         _check(lib().rabitq_search_trace(self._h, _dptr(q), nq, k, nprobe, bq, eps0, _dptr(ids),
                                          _dptr(dist), C.byref(o), C.byref(tr)))
         t["ids"], t["dist"] = ids, dist
@@ -546,3 +559,82 @@ def mlp_adam(master, m1, m2, grads, step: int, lr: float):
     _check(lib().rabitq_mlp_adam(_np_ptr(ms), _np_ptr(a), _np_ptr(b), _np_ptr(g), step, lr,
                                  _np_ptr(w)))
     return ms, a, b, w
+
+
+class _DevArray:
+    """A view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 2,
+                                         "strides": None}
+
+
+class Plan:
+    """A reusable search (CUDA-graph replay) of up to nq_max queries."""
+
+    def __init__(self, index: Index, k: int, nprobe: int, nq_max: int, bq: int = 4,
+                 eps0: float = 1.9, predictor: "Predictor | None" = None, quant_seed: int = 3,
+                 max_candidates: int = 65536, rot_precision=ROT_FP32, stats: bool = False):
+        import torch
+        o = index._opts(quant_seed, None, max_candidates, stats, None, True, rot_precision,
+                        SCAN_POPC)
+        h = C.c_void_p()
+        _check(lib().rabitq_plan_create(index._h, predictor._h if predictor else None, nq_max, k,
+                                        nprobe, bq, eps0, C.byref(o), C.byref(h)))
+        self._h = h
+        self._index, self._pred = index, predictor  # keep them alive
+        self.k, self.nq_max, self.d = k, nq_max, index.d
+        qp, ip, dp, npp = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+        _check(lib().rabitq_plan_buffers(h, C.byref(qp), C.byref(ip), C.byref(dp), C.byref(npp)))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.queries = torch.as_tensor(_DevArray(qp.value, (nq_max, index.d), "<f4"), device=dev)
+        self.ids = torch.as_tensor(_DevArray(ip.value, (nq_max, k), "<i8"), device=dev)
+        self.dist = torch.as_tensor(_DevArray(dp.value, (nq_max, k), "<f4"), device=dev)
+        self.nprobe = (torch.as_tensor(_DevArray(npp.value, (nq_max,), "<i4"), device=dev)
+                       if npp.value else None)
+
+    def run(self, nq: int, stream=None):
+        """Search rows [0, nq) of self.queries into self.ids / self.dist (async)."""
+        _check(lib().rabitq_plan_run(self._h, nq, _stream_handle(stream)))
+
+    def sync(self, stream=None):
+        _check(lib().rabitq_plan_sync(self._h, _stream_handle(stream)))
+
+    def stats(self) -> np.ndarray:
+        """Stage times (ms) of the last run (plans created with stats=True)."""
+        ms = np.zeros(4, np.float32)
+        n = lib().rabitq_plan_stats(self._h, _np_ptr(ms), 4)
+        if n < 0:
+            _check(n)
+        return ms[:n]
+
+    def search(self, queries, out=None, stream=None):
+        """Round trip: queries (numpy or torch) in, (ids, dist) out in the same kind."""
+        nq = queries.shape[0]
+        if _is_torch(queries):
+            import torch
+            q = queries.contiguous()
+            if out is None:
+                out = (torch.empty((nq, self.k), dtype=torch.int64, device=q.device),
+                       torch.empty((nq, self.k), dtype=torch.float32, device=q.device))
+            _check(lib().rabitq_plan_search(self._h, _dptr(q), nq, _dptr(out[0]), _dptr(out[1]),
+                                            _stream_handle(stream)))
+            return out
+        q = np.ascontiguousarray(queries, np.float32)
+        if out is None:
+            out = (np.empty((nq, self.k), np.int64), np.empty((nq, self.k), np.float32))
+        _check(lib().rabitq_plan_search(self._h, _np_ptr(q), nq, _np_ptr(out[0]), _np_ptr(out[1]),
+                                        _stream_handle(stream)))
+        return out
+
+    def free(self):
+        if self._h:
+            lib().rabitq_plan_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

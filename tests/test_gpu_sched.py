@@ -37,3 +37,87 @@ def test_autotune_rejects_bad_arguments(R, tiny_workload):
         idx.autotune(queries, 10, 4, reps=0)
     with pytest.raises(R.RabitqError):
         idx.autotune(queries, 10, 99)                    # nprobe > K
+
+
+@pytest.fixture(scope="module")
+def tiny_idx(R, tiny_workload):
+    data, _ = tiny_workload
+    return R.Index.build(data, 16, seed=2, kmeans_iters=10)
+
+
+def _same(a, b):
+    assert np.array_equal(np.asarray(a[0]), np.asarray(b[0]))
+    assert np.array_equal(np.asarray(a[1]).view(np.uint32), np.asarray(b[1]).view(np.uint32))
+
+
+@pytest.mark.parametrize("rot", ["fp32", "bf16"])
+def test_plan_replays_equal_search(R, tiny_workload, tiny_idx, rot):
+    import torch
+    _, queries = tiny_workload
+    rp = R.ROT_FP32 if rot == "fp32" else R.ROT_BF16
+    plan = R.Plan(tiny_idx, 10, 5, 100, rot_precision=rp)
+    qd = torch.from_numpy(queries).cuda()
+    for nq in (100, 1, 37, 100, 37):           # new sizes capture, repeats replay
+        plan.queries[:nq].copy_(qd[:nq])
+        plan.run(nq)
+        plan.sync()
+        ref = tiny_idx.search(queries[:nq], 10, 5, scan_path=R.SCAN_POPC, rot_precision=rp)
+        _same((plan.ids[:nq].cpu().numpy(), plan.dist[:nq].cpu().numpy()), ref)
+    # round trip through host memory
+    _same(plan.search(queries[:50]), tiny_idx.search(queries[:50], 10, 5, scan_path=R.SCAN_POPC,
+                                                      rot_precision=rp))
+    with pytest.raises(R.RabitqError):
+        plan.run(101)                           # more than nq_max
+
+
+def test_plan_with_predictor_equals_learned_search(R, tiny_workload, tiny_idx):
+    import math
+    _, queries = tiny_workload
+    rng = np.random.default_rng(3)
+    from oracle import mlp_oracle as M
+    p = M.pack(rng.uniform(-1, 1, (64, 256)) * math.sqrt(6 / 64), rng.normal(0, .1, 256),
+               rng.uniform(-1, 1, (256, 256)) * math.sqrt(6 / 256), rng.normal(0, .1, 256),
+               rng.uniform(-1, 1, 256) * math.sqrt(6 / 256), 2.0).astype(np.float32)
+    for nmax in (12, 16):
+        pr = R.Predictor.create(p, 30.0, 1.0, nmax, 16)
+        plan = R.Plan(tiny_idx, 10, 0, 100, predictor=pr)
+        _same(plan.search(queries), tiny_idx.search_learned(pr, queries, 10,
+                                                            scan_path=R.SCAN_POPC))
+        assert np.array_equal(plan.nprobe.cpu().numpy(), tiny_idx.predict_nprobe(pr, queries))
+
+
+def test_plan_reports_overflow_like_search(R, tiny_workload, tiny_idx):
+    _, queries = tiny_workload
+    try:
+        ref = tiny_idx.search(queries, 100, 16, max_candidates=4096, scan_path=R.SCAN_POPC)
+        ref_err = None
+    except R.RabitqError as e:
+        ref, ref_err = None, e.code
+    plan = R.Plan(tiny_idx, 100, 16, 100, max_candidates=4096)
+    if ref_err is None:
+        _same(plan.search(queries), ref)
+    else:
+        with pytest.raises(R.RabitqError) as ei:
+            plan.search(queries)
+        assert ei.value.code == ref_err
+        # the sync that reported the error cleared the flag
+        plan.sync()
+
+
+def test_min_candidate_capacity(R, tiny_workload, tiny_idx):
+    _, queries = tiny_workload
+    with pytest.raises(R.RabitqError):
+        tiny_idx.search(queries, 10, 4, max_candidates=4095)
+    with pytest.raises(R.RabitqError):
+        R.Plan(tiny_idx, 10, 4, 100, max_candidates=4095)
+    _same(tiny_idx.search(queries, 10, 2, max_candidates=4096),
+          tiny_idx.search(queries, 10, 2))
+
+
+def test_plan_rejects_bad_arguments(R, tiny_idx):
+    with pytest.raises(R.RabitqError):
+        R.Plan(tiny_idx, 10, 17, 100)            # nprobe > K
+    with pytest.raises(R.RabitqError):
+        R.Plan(tiny_idx, 0, 4, 100)              # k < 1
+    with pytest.raises(R.RabitqError):
+        R.Plan(tiny_idx, 10, 4, 0)               # nq_max < 1
