@@ -152,6 +152,7 @@ struct FusedParams {
   // striding by gridDim.x
   const int32_t* order;
   int* next;
+  int scap;  // shared-memory capacity for the tail's candidate list (0 = none)
 };
 
 struct FusedSmem {
@@ -165,14 +166,16 @@ struct FusedSmem {
   uint32_t* ubk;     // cu: upper-bound keys
   unsigned long long* estk;  // ce: the pilot list, (id << 32) | position
   unsigned long long* topk;  // ct: (exact distance key << 32) | id
+  int4* scand;               // scap: the candidate list staged for the tail
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 __host__ __device__ inline size_t fused_smem_bytes(int pch, int bq, int W, int d, int cu, int ce,
                                                    int ct, int nwarps,
-                                                   size_t* off /* 9 entries or null */) {
-  size_t o = 0, offs[9];
+                                                   size_t* off /* 10 entries or null */,
+                                                   int scap = 0) {
+  size_t o = 0, offs[10];
   (void)nwarps;
   offs[0] = o; o = align_up(o + sizeof(uint64_t) * pch * bq * W, 16);
   offs[1] = o; o = align_up(o + sizeof(float4) * pch, 16);
@@ -183,8 +186,9 @@ __host__ __device__ inline size_t fused_smem_bytes(int pch, int bq, int W, int d
   offs[6] = o; o = align_up(o + sizeof(uint32_t) * cu, 16);
   offs[7] = o; o = align_up(o + sizeof(unsigned long long) * ce, 16);
   offs[8] = o; o = align_up(o + sizeof(unsigned long long) * ct, 16);
+  offs[9] = o; o = align_up(o + sizeof(int4) * scap, 16);
   if (off)
-    for (int i = 0; i < 9; ++i) off[i] = offs[i];
+    for (int i = 0; i < 10; ++i) off[i] = offs[i];
   return o;
 }
 
@@ -423,13 +427,56 @@ __device__ K select_keep(K* a, int* cnt, int keep, SelState& st) {
   return T;
 }
 
-// Sort a shared key buffer (padded with the maximum key), keep the `keep`
-// smallest; returns the count kept. Whole block; synchronized on return.
-__device__ __forceinline__ void sort_keep_u64(unsigned long long* a, int cap, int* cnt, int keep) {
-  for (int i = *cnt + threadIdx.x; i < cap; i += blockDim.x) a[i] = ~0ull;
+// Keep the `keep` smallest of the *cnt distinct (distance key << 32 | id)
+// keys of a: a 32-bit select on the distance half, then -- only when more
+// keys share the boundary distance than are kept -- one on the id half of
+// those. Returns the keep-th smallest key (~0 if there are fewer than keep).
+// Whole block; synchronized on return.
+__device__ unsigned long long select_keep_dk(unsigned long long* a, int* cnt, int keep,
+                                             SelState& st) {
+  const int n = *cnt;
+  if (n < keep) {
+    __syncthreads();
+    return ~0ull;
+  }
+  const uint32_t Td =
+      block_select_f<uint32_t>(n, keep, st, [a](int i) { return (uint32_t)(a[i] >> 32); });
+  const int ties = st.rem;
+  uint32_t Tid = 0xffffffffu;
+  if (st.hist[st.bin] > ties)
+    Tid = block_select_f<uint32_t>(n, ties, st, [a, Td](int i) {
+      return (uint32_t)(a[i] >> 32) == Td ? (uint32_t)(a[i] & 0xffffffffu) : 0xffffffffu;
+    });
+  unsigned long long T = ((unsigned long long)Td << 32) | Tid;
+  if (Tid == 0xffffffffu) {  // every key at the boundary distance is kept
+    T = ((unsigned long long)Td << 32) | 0xffffffffu;
+  }
+  const int kept = block_keep_below<unsigned long long>(a, n, T, 1, st);
+  if (threadIdx.x == 0) *cnt = kept;
   __syncthreads();
-  block_bitonic_sort_u64(a, cap);
-  if (threadIdx.x == 0 && *cnt > keep) *cnt = keep;
+  if (Tid == 0xffffffffu) {
+    // the keep-th smallest key itself: the largest kept key
+    __shared__ unsigned long long s_max;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    unsigned long long mx = 0;
+    for (int i = threadIdx.x; i < kept; i += blockDim.x) mx = a[i] > mx ? a[i] : mx;
+    atomicMax(&s_max, mx);
+    __syncthreads();
+    T = s_max;
+    __syncthreads();
+  }
+  return T;
+}
+
+// Sort the first pow2(keep) slots of a shared key buffer holding *cnt <=
+// keep keys (padded with the maximum key). Whole block; synchronized on return.
+__device__ __forceinline__ void sort_kept_u64(unsigned long long* a, int cnt, int keep) {
+  int n = 1;
+  while (n < keep) n <<= 1;
+  for (int i = cnt + threadIdx.x; i < n; i += blockDim.x) a[i] = ~0ull;
+  __syncthreads();
+  block_bitonic_sort_u64(a, n);
   __syncthreads();
 }
 
@@ -474,6 +521,15 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
                             const int4* cand, int* top_cnt, int* surv_cnt) {
   const int d = P.d;
   const bool vec = (d & 3) == 0;
+  // Ask L2 for every row of the set first (no registers held, no waiting):
+  // the loads below then find most rows in L2 instead of waiting on DRAM
+  // eight loads at a time.
+  const int row_bytes = d * (int)sizeof(float);
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const int pos = SRC == 0 ? (int)(S.estk[i] & 0xffffffffu) : (cand[i].x & 0x7fffffff);
+    const char* x = reinterpret_cast<const char*>(P.data_b + (int64_t)pos * d);
+    for (int o = 0; o < row_bytes; o += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(x + o));
+  }
   for (int r0 = 0; r0 < count; r0 += blockDim.x) {
     const int i = r0 + threadIdx.x;
     const bool valid = i < count;
@@ -529,7 +585,7 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
       if (P.tr.surv_ids && si < P.tr.surv_cap) P.tr.surv_ids[q * P.tr.surv_cap + si] = id;
     }
     __syncthreads();
-    if (*top_cnt > P.ct - (int)blockDim.x) select_keep<unsigned long long>(S.topk, top_cnt, P.k, *S.sel);
+    if (*top_cnt > P.ct - (int)blockDim.x) select_keep_dk(S.topk, top_cnt, P.k, *S.sel);
   }
   __syncthreads();
   if (threadIdx.x == 0) *surv_cnt += count;
@@ -570,11 +626,14 @@ __device__ void finish_query(const FusedParams& P, const FusedSmem& S, int64_t q
                                    [cand](int i) { return float_key(__int_as_float(cand[i].z)); });
     const int ties = S.sel->rem;
     // among the list entries whose estimate equals the m-th one, the
-    // `ties` smallest ids belong to the pilot
-    T_id = block_select_f<uint32_t>(nl, ties, *S.sel, [cand, T_e, &P](int i) {
-      const int4 e = cand[i];
-      return float_key(__int_as_float(e.z)) == T_e ? (uint32_t)__ldg(P.perm + e.x) : 0xffffffffu;
-    });
+    // `ties` smallest ids belong to the pilot; the last pass's histogram
+    // counts those entries, and when all of them belong (the usual case:
+    // one entry) no id selection is needed
+    if (S.sel->hist[S.sel->bin] > ties)
+      T_id = block_select_f<uint32_t>(nl, ties, *S.sel, [cand, T_e, &P](int i) {
+        const int4 e = cand[i];
+        return float_key(__int_as_float(e.z)) == T_e ? (uint32_t)__ldg(P.perm + e.x) : 0xffffffffu;
+      });
   }
   // write the pilot's (id, position) pairs to the pilot list, mark them
   __shared__ int s_pilot;
@@ -599,16 +658,19 @@ __device__ void finish_query(const FusedParams& P, const FusedSmem& S, int64_t q
   const int pilot = s_pilot;
   // exact distances of the pilot; tau1 = k-th smallest of them
   rerank_rows<0>(P, S, q, pilot, cand, ts.top_cnt, ts.surv);
+  // tau1: the k-th smallest exact distance of the pilot; only the k smallest
+  // pilot keys can be in the result, so the rest are dropped here
   const unsigned long long T1 =
-      (pilot >= k) ? block_select<unsigned long long>(S.topk, *ts.top_cnt, k, *S.sel) : 0ull;
+      (pilot >= k) ? select_keep_dk(S.topk, ts.top_cnt, k, *S.sel) : ~0ull;
   const float tau1 = (pilot >= k) ? key_float((uint32_t)(T1 >> 32)) : __int_as_float(0x7f800000);
   const float tau = fminf(tau_ub, tau1);
   // the rest of the re-rank set: LB <= tau, outside the pilot
   compact_cand(cand, ts.cand_cnt, cand_cap, ts.scratch,
                [tau](const int4& e) { return e.x >= 0 && __int_as_float(e.y) <= tau; });
   rerank_rows<1>(P, S, q, *ts.cand_cnt, cand, ts.top_cnt, ts.surv);
-  sort_keep_u64(S.topk, P.ct, ts.top_cnt, k);
+  select_keep_dk(S.topk, ts.top_cnt, k, *S.sel);
   const int got = min(*ts.top_cnt, k);
+  sort_kept_u64(S.topk, got, k);
   for (int j2 = tid; j2 < k; j2 += blockDim.x) {
     const bool ok = j2 < got;
     P.out_ids[q * k + j2] = ok ? (int64_t)(S.topk[j2] & 0xffffffffu) : -1;
@@ -696,15 +758,15 @@ __host__ __device__ constexpr int pairs_per_thread() {
 }
 
 template <int WT, int BQT>
-__global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P) {
+__global__ void __launch_bounds__(kThreads, 3) fused_search_kernel(FusedParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_ub_cnt, s_cand_cnt, s_top_cnt, s_surv, s_overflow;
   __shared__ float s_tau;
   __shared__ int s_scratch[kThreads / 32];
   __shared__ SelState s_sel;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
-  size_t off[9];
-  fused_smem_bytes(P.pch, P.bq, P.W, P.d, P.cu, P.ce, P.ct, nwarps, off);
+  size_t off[10];
+  fused_smem_bytes(P.pch, P.bq, P.W, P.d, P.cu, P.ce, P.ct, nwarps, off, P.scap);
   FusedSmem S;
   S.planes = reinterpret_cast<uint64_t*>(smem + off[0]);
   S.pmeta = reinterpret_cast<float4*>(smem + off[1]);
@@ -716,10 +778,11 @@ __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P
   S.ubk = reinterpret_cast<uint32_t*>(smem + off[6]);
   S.estk = reinterpret_cast<unsigned long long*>(smem + off[7]);
   S.topk = reinterpret_cast<unsigned long long*>(smem + off[8]);
+  S.scand = reinterpret_cast<int4*>(smem + off[9]);
   const int W = P.W, bq = P.bq, k = P.k;
   int4* cand = P.cand + (int64_t)blockIdx.x * P.cand_cap;
 
-  __shared__ int s_next;
+  __shared__ int s_next, s_next_fill;
   // next work item: dynamic (one atomic per query, taken by thread 0 and
   // broadcast) or static striding
   auto fetch = [&](int64_t cur) -> int64_t {
@@ -772,16 +835,24 @@ __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P
       int j = 0;
       constexpr int PPT = pairs_per_thread<WT>();
       const int step = PPT * blockDim.x;
+      // each thread takes PPT consecutive pairs per round (mostly of one
+      // probe), so the probe's bit-planes and constants stay in registers
+      // and are reloaded only when the thread's pairs move to another probe
+      constexpr bool kRegPlanes = WT > 0 && BQT > 0;
+      uint64_t rpl[kRegPlanes ? BQT * WT : 1];
+      float4 rmt = make_float4(0.f, 0.f, 0.f, 0.f);
+      int rsum = 0, rj = -1;
       for (int base = 0; base < total; base += step) {
         // issue every load of this thread's PPT pairs first (they are
         // independent), then evaluate; keeps PPT code/factor loads in flight
+        const int t0 = base + tid * PPT;
         int64_t posv[PPT];
         int jv[PPT];
         CodeRegs<WT> cr[PPT];
         float4 fv[PPT];
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp) {
-          const int t = base + pp * blockDim.x + tid;
+          const int t = t0 + pp;
           posv[pp] = -1;
           jv[pp] = 0;
           if (t < total) {
@@ -804,12 +875,37 @@ __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P
           ipv[pp] = 0;
           if (posv[pp] >= 0) {
             const int jj = jv[pp];
-            const int ip = code_ip<WT, BQT>(cr[pp], P.codes + posv[pp] * W,
-                                            S.planes + (size_t)jj * bq * W, W, bq);
+            int ip;
+            float4 mt;
+            int psum;
+            if constexpr (kRegPlanes) {
+              if (jj != rj) {  // the thread's pairs entered another probe
+                const uint64_t* pl = S.planes + (size_t)jj * BQT * WT;
+#pragma unroll
+                for (int w = 0; w < BQT * WT; ++w) rpl[w] = pl[w];
+                rmt = S.pmeta[jj];
+                rsum = S.psum[jj];
+                rj = jj;
+              }
+              ip = 0;
+#pragma unroll
+              for (int b = 0; b < BQT; ++b) {
+                int pb = 0;
+#pragma unroll
+                for (int w = 0; w < WT; ++w) pb += __popcll(cr[pp].c[w] & rpl[b * WT + w]);
+                ip += pb << b;
+              }
+              mt = rmt;
+              psum = rsum;
+            } else {
+              ip = code_ip<WT, BQT>(cr[pp], P.codes + posv[pp] * W,
+                                    S.planes + (size_t)jj * bq * W, W, bq);
+              mt = S.pmeta[jj];
+              psum = S.psum[jj];
+            }
             const float4 f = fv[pp];
-            const float4 mt = S.pmeta[jj];
             // estimator (§3.3.2 + Theorem 3.2) and its bound, fixed FP32 order
-            const float t1 = (float)(2 * ip - S.psum[jj]);
+            const float t1 = (float)(2 * ip - psum);
             const float xq = __fadd_rn(__fmul_rn(mt.x, t1), __fmul_rn(mt.y, f.w));
             const float dist = __fsub_rn(__fadd_rn(f.x, mt.w), __fmul_rn(f.y, xq));
             const float e = __fmul_rn(f.z, mt.z);
@@ -856,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P
             ++bc;
           }
           if (P.tr.pair_id) {
-            const int64_t tt = pairs_done + base + pp * blockDim.x + tid;
+            const int64_t tt = pairs_done + t0 + pp;
             if (tt < P.tr.pair_cap) {
               const int64_t o = q * P.tr.pair_cap + tt;
               P.tr.pair_id[o] = __ldg(P.perm + posv[pp]);
@@ -868,16 +964,17 @@ __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P
           }
         }
         __syncthreads();
-        if (s_ub_cnt > P.cu - step) {  // keep the k smallest upper bounds
+        const int room = step;
+        if (s_ub_cnt > P.cu - room) {  // keep the k smallest upper bounds
           const uint32_t T = select_keep<uint32_t>(S.ubk, &s_ub_cnt, k, *S.sel);
           if (tid == 0) s_tau = key_float(T);
           __syncthreads();
         }
-        if (s_cand_cnt > P.cand_cap - step) {
+        if (s_cand_cnt > P.cand_cap - room) {
           const float tau = s_tau;
           compact_cand(cand, &s_cand_cnt, P.cand_cap, s_scratch,
                        [tau](const int4& e) { return __int_as_float(e.y) <= tau; });
-          if (s_cand_cnt > P.cand_cap - step && tid == 0) s_overflow = 1;
+          if (s_cand_cnt > P.cand_cap - room && tid == 0) s_overflow = 1;
           __syncthreads();
         }
         if (s_overflow) break;
@@ -891,7 +988,44 @@ __global__ void __launch_bounds__(kThreads, 2) fused_search_kernel(FusedParams P
     const uint32_t T_ub = (n_ub >= k) ? block_select<uint32_t>(S.ubk, n_ub, k, *S.sel) : 0u;
     const float tau_ub = (n_ub >= k) ? key_float(T_ub) : __int_as_float(0x7f800000);
     TailShared ts{&s_cand_cnt, &s_top_cnt, &s_surv, s_scratch};
-    finish_query(P, S, q, cand, P.cand_cap, tau_ub, ts);
+    // Stage the entries with LB <= tau_ub in shared memory (one pass with
+    // four loads in flight per thread) so that the tail's selections and
+    // compactions read shared memory; if they do not fit, the tail works on
+    // the list in global memory, which this pass only reads.
+    int4* tcand = cand;
+    int tcap = P.cand_cap;
+    if (P.scap > 0) {
+      const int n_c = min(s_cand_cnt, P.cand_cap);
+      if (tid == 0) s_next_fill = 0;
+      __syncthreads();
+      for (int b = 0; b < n_c; b += 4 * blockDim.x) {
+        int4 e[4];
+        bool keep[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = b + u * blockDim.x + tid;
+          keep[u] = false;
+          if (i < n_c) {
+            e[u] = cand[i];
+            keep[u] = __int_as_float(e[u].y) <= tau_ub;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int slot = warp_reserve(keep[u], &s_next_fill);
+          if (keep[u] && slot < P.scap) S.scand[slot] = e[u];
+        }
+      }
+      __syncthreads();
+      if (s_next_fill <= P.scap) {
+        tcand = S.scand;
+        tcap = P.scap;
+        __syncthreads();
+        if (tid == 0) s_cand_cnt = s_next_fill;
+      }
+      __syncthreads();
+    }
+    finish_query(P, S, q, tcand, tcap, tau_ub, ts);
     if (tid == 0) {
       if (s_overflow) atomicExch(P.err, 1);
       if (P.tr.n_pairs) P.tr.n_pairs[q] = pairs_done;
@@ -1218,7 +1352,7 @@ __global__ void __launch_bounds__(kThreads) tc_tail_kernel(FusedParams P, int4* 
   __shared__ int s_cand_cnt, s_top_cnt, s_surv;
   __shared__ int s_scratch[kThreads / 32];
   __shared__ SelState s_sel;
-  size_t off[9];
+  size_t off[10];
   fused_smem_bytes(P.pch, P.bq, P.W, P.d, P.cu, P.ce, P.ct, blockDim.x >> 5, off);
   FusedSmem S;
   S.planes = nullptr;
@@ -1283,6 +1417,57 @@ int pow2_at_least(int x) {
   return p;
 }
 
+// Shape of the fused kernel for a search: probes staged per chunk, buffer
+// sizes, and the shared-memory capacity for staging the tail's candidate
+// list -- the largest of 4096, 2048, 1024 entries that keeps the residency
+// the kernel has without it (0 if none does). The kernel's dynamic
+// shared-memory limit is set once to the device maximum, so concurrent
+// searches with different shapes never lower it under each other.
+struct FusedShape {
+  int pch, pilot_m, cu, ce, ct, scap, per_sm;
+  size_t smem;
+  FusedFn fn;
+};
+
+int fused_shape(const SearchArgs& a, FusedShape* f) {
+  const rabitq_index* X = a.X;
+  const int nprobe = std::min(a.nprobe, X->K), W = X->W;
+  const int plane_bytes = a.bq * W * 8;
+  f->pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
+  f->pilot_m = 4 * a.k;
+  f->cu = std::max(1024, pow2_at_least(a.k + kPPT * kThreads));
+  f->ce = pow2_at_least(f->pilot_m);
+  f->ct = std::max(1024, pow2_at_least(a.k + kThreads));
+  f->fn = pick_fused(W, a.bq);
+  int dev = 0, optin = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
+  RBQ_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  RBQ_CUDA(cudaFuncGetAttributes(&fa, f->fn));
+  optin -= (int)fa.sharedSizeBytes;  // the limit counts dynamic shared memory only
+  RBQ_CUDA(cudaFuncSetAttribute(f->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  const size_t base =
+      fused_smem_bytes(f->pch, a.bq, W, X->d, f->cu, f->ce, f->ct, kThreads / 32, nullptr);
+  int per_base = 0;
+  RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_base, f->fn, kThreads, base));
+  f->scap = 0;
+  f->smem = base;
+  f->per_sm = std::max(per_base, 1);
+  for (int scap = 4096; scap >= 1024; scap /= 2) {
+    const size_t sm = fused_smem_bytes(f->pch, a.bq, W, X->d, f->cu, f->ce, f->ct, kThreads / 32,
+                                       nullptr, scap);
+    if (sm > (size_t)optin) continue;
+    int per = 0;
+    RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f->fn, kThreads, sm));
+    if (per >= per_base && per >= 1) {
+      f->scap = scap;
+      f->smem = sm;
+      break;
+    }
+  }
+  return RABITQ_OK;
+}
+
 // Learned probe counts of one query chunk from its centroid distances cd
 // (nqc x K): the min(64, K) nearest buckets, then the fused MLP kernel.
 int predict_chunk(const SearchArgs& a, const float* cd, int64_t nqc, int64_t q0, int32_t* fid,
@@ -1324,18 +1509,12 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
 
   // fused-kernel shape
-  const int plane_bytes = a.bq * W * 8;
-  int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
-  const int pilot_m = 4 * a.k;  // pilot size
-  const int cu = std::max(1024, pow2_at_least(a.k + kPPT * kThreads));
-  const int ce = pow2_at_least(pilot_m);  // the pilot list
-  const int ct = std::max(512, pow2_at_least(a.k + kThreads));
-  const size_t smem = fused_smem_bytes(pch, a.bq, W, d, cu, ce, ct, kThreads / 32, nullptr);
-  const FusedFn fn = pick_fused(W, a.bq);
-  RBQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
-  per_sm = std::max(per_sm, 1);
+  FusedShape fs;
+  RBQ_CHECK(fused_shape(a, &fs));
+  const int pch = fs.pch, pilot_m = fs.pilot_m, cu = fs.cu, ce = fs.ce, ct = fs.ct;
+  const size_t smem = fs.smem;
+  const FusedFn fn = fs.fn;
+  const int per_sm = fs.per_sm;
 
   // query chunks bound the centroid-distance scratch (<= 256 Mi floats)
   const int64_t qchunk = std::max<int64_t>(1, std::min<int64_t>(a.nq, (int64_t(1) << 28) / K));
@@ -1437,6 +1616,7 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
     P.cu = cu;
     P.ce = ce;
     P.ct = ct;
+    P.scap = fs.scap;
     P.eps0 = a.eps0;
     P.seed = a.seed;
     P.cand_cap = a.cand_cap;
@@ -1559,21 +1739,12 @@ size_t carved_bytes(const SearchArgs& a, int64_t grid, int64_t nq_max) {
 }
 
 int fused_grid(const SearchArgs& a, int* grid_out) {
-  const rabitq_index* X = a.X;
-  const int nprobe = std::min(a.nprobe, X->K), W = X->W;
-  const int plane_bytes = a.bq * W * 8;
-  const int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
-  const int cu = std::max(1024, pow2_at_least(a.k + kPPT * kThreads));
-  const int ce = pow2_at_least(4 * a.k);
-  const int ct = std::max(512, pow2_at_least(a.k + kThreads));
-  const size_t smem = fused_smem_bytes(pch, a.bq, W, X->d, cu, ce, ct, kThreads / 32, nullptr);
-  const FusedFn fn = pick_fused(W, a.bq);
-  RBQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int dev = 0, sms = 0, per_sm = 0;
+  FusedShape fs;
+  RBQ_CHECK(fused_shape(a, &fs));
+  int dev = 0, sms = 0;
   RBQ_CUDA(cudaGetDevice(&dev));
   RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
-  *grid_out = sms * std::max(per_sm, 1);
+  *grid_out = sms * fs.per_sm;
   return RABITQ_OK;
 }
 
@@ -1594,15 +1765,11 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
     RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     grid = sms;
   }
-  const int plane_bytes = a.bq * W * 8;
-  const int pch = std::max(1, std::min(nprobe, (32 * 1024) / plane_bytes));
-  const int pilot_m = 4 * a.k;
-  const int cu = std::max(1024, pow2_at_least(a.k + kPPT * kThreads));
-  const int ce = pow2_at_least(pilot_m);  // the pilot list
-  const int ct = std::max(512, pow2_at_least(a.k + kThreads));
-  const size_t smem = fused_smem_bytes(pch, a.bq, W, d, cu, ce, ct, kThreads / 32, nullptr);
-  const FusedFn fn = pick_fused(W, a.bq);
-  RBQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FusedShape fs;
+  RBQ_CHECK(fused_shape(a, &fs));
+  const int pch = fs.pch, pilot_m = fs.pilot_m, cu = fs.cu, ce = fs.ce, ct = fs.ct;
+  const size_t smem = fs.smem;
+  const FusedFn fn = fs.fn;
   const int sort_n = pow2_at_least(nprobe);
   const size_t sel_smem = sizeof(unsigned long long) * sort_n;
   RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1696,6 +1863,7 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
     P.cu = cu;
     P.ce = ce;
     P.ct = ct;
+    P.scap = fs.scap;
     P.eps0 = a.eps0;
     P.seed = a.seed;
     P.cand_cap = (int)cap;
@@ -1754,7 +1922,7 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
   const int cap = a.cand_cap;  // per-query list capacity
   const int pilot_m = 4 * a.k;
   const int ce = pow2_at_least(pilot_m);
-  const int ct = std::max(512, pow2_at_least(a.k + kThreads));
+  const int ct = std::max(1024, pow2_at_least(a.k + kThreads));
   // passes over probe ranks [0, b1), [b1, b2), [b2, nprobe); tau' is
   // tightened and the lists compacted after each of the first two
   const int b1 = std::min(nprobe, 2), b2 = std::min(nprobe, 8);
