@@ -172,9 +172,9 @@ def run_ours(args, rank, world):
 
     # ---- leg 1: fixed nprobe (the paper's method)
     plan = rabitq.Plan(G, w.k, chosen, w.nq, bq=w.bq, eps0=w.eps0, stats=True)
-    fixed = time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=True)
+    fixed = time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=True, name="fixed")
     fixed.update({"nprobe": chosen, "nprobe_sweep": {str(a): round(b, 4) for a, b in sweep.items()}})
-    fixed["roofline"] = roofline(G, qd, w, chosen, None, fixed["fused_ms"], hbm, src)
+    fixed["roofline"] = roofline(G, qd, w, chosen, None, fixed["fused_ms"], hbm, src, "fixed")
     fixed["scan_gbs"] = fixed["roofline"].pop("scan_gbs")
     fixed["ns_per_code"] = fixed["roofline"].pop("ns_per_code")
     fixed["gpu_launches_per_step"] = 4
@@ -242,7 +242,27 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
-def time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=False):
+class _Range:
+    """An NVTX range (for ncu --nvtx-include), a no-op where NVTX is missing."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        try:
+            import torch
+            torch.cuda.nvtx.range_push(self.name)
+            self.on = True
+        except Exception:
+            self.on = False
+
+    def __exit__(self, *exc):
+        if self.on:
+            import torch
+            torch.cuda.nvtx.range_pop()
+
+
+def time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=False, name="leg"):
     """Time K graph replays of a plan (W warm-up replays first), L2 flushed
     before each; per-step device time by CUDA events on the launching stream,
     the fused kernel's time by the event nodes inside the graph."""
@@ -267,7 +287,8 @@ def time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=False):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        plan.run(w.nq)
+        with _Range(f"timed:{name}"):
+            plan.run(w.nq)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -299,7 +320,24 @@ def time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=False):
     return out
 
 
-def roofline(G, qd, w, nprobe, per_query, fused_ms, hbm, src):
+def measured_traffic(leg: str, nq: int):
+    """DRAM bytes of one fused-kernel launch of nq queries from the recorded
+    ncu capture (profiles/fused_search_traffic.json), scaled by queries; None
+    when there is no capture of this leg or the kernel source has changed
+    since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "fused_search_traffic.json")
+    src = os.path.join(ROOT, "paper_2405_12497_gb300", "csrc", "kernels_search.cu")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    if rec.get("kernels_search_sha1") != sha or leg not in rec:
+        return None
+    return int(rec[leg]["dram_bytes_per_query"] * nq)
+
+
+def roofline(G, qd, w, nprobe, per_query, fused_ms, hbm, src, leg):
     """Algorithmic bytes of the fused scan/prune/re-rank kernel (one launch):
     per estimated code D'/8 + 12 bytes, per survivor 4 D bytes -- counted on
     the first 2000 queries by the trace and scaled to the batch."""
@@ -313,7 +351,8 @@ def roofline(G, qd, w, nprobe, per_query, fused_ms, hbm, src):
     achieved = bytes_launch / (fused_ms / 1e3) / 1e9
     scan_bytes = w.nq * pairs_per_q * (G.dpad / 8 + 12)
     return {"kernel": "fused_search_kernel", "bound": "hbm", "achieved": round(achieved, 1),
-            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+            "traffic": measured_traffic(leg, w.nq),
             "peak_source": src, "algorithmic_bytes_per_launch": int(bytes_launch),
             "pairs_per_query": round(pairs_per_q, 1), "survivors_per_query": round(surv_per_q, 1),
             "scan_gbs": round(scan_bytes / (fused_ms / 1e3) / 1e9, 1),
@@ -347,8 +386,9 @@ def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, dist, hbm, src)
         mult *= 2.0 ** 0.125
     npq = G.predict_nprobe(pr, qd)
     plan = rabitq.Plan(G, w.k, 0, w.nq, bq=w.bq, eps0=w.eps0, predictor=pr, stats=True)
-    leg = time_leg(args, plan, qd, gt, w, flush, stream, dist)
-    leg["roofline"] = roofline(G, qd, w, args.nprobe_max, npq, leg["fused_ms"], hbm, src)
+    leg = time_leg(args, plan, qd, gt, w, flush, stream, dist, name="learned")
+    leg["roofline"] = roofline(G, qd, w, args.nprobe_max, npq, leg["fused_ms"], hbm, src,
+                               "learned")
     leg["scan_gbs"] = leg["roofline"].pop("scan_gbs")
     leg["ns_per_code"] = leg["roofline"].pop("ns_per_code")
     leg["gpu_launches_per_step"] = 12
