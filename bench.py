@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 from paper_2405_12497_gb300 import synth  # noqa: E402
 
 NPROBES = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256)
+WORKLOADS = {"sift": synth.SIFT_LIKE, "gist": synth.GIST_LIKE, "deep": synth.DEEP_LIKE}
 TARGET = 0.95
 METRIC = "QPS at recall@100=0.95 on 1 GB300; code-scan GB/s vs HBM peak"
 
@@ -127,28 +128,21 @@ def run_ours(args, rank, world):
     if dist:
         dist.barrier()
     B.build()
-    w = synth.SIFT_LIKE
+    w = WORKLOADS[args.workload]
     if args.nq:
         w = synth.dataclasses_replace(w, nq=args.nq)
+    if args.n:
+        w = synth.dataclasses_replace(w, n=args.n)
     data, queries = synth.make(w)
     dev = torch.device("cuda", local)
     dd = torch.from_numpy(data).to(dev)
     qd = torch.from_numpy(queries).to(dev)
     t0 = time.time()
-    G = rabitq.Index.build(dd, w.n_clusters, seed=2, kmeans_iters=w.kmeans_iters)
+    G = rabitq.Index.build(dd, w.n_clusters, seed=2, kmeans_iters=w.kmeans_iters,
+                           kmeans_sample=w.kmeans_sample, code_bits=w.code_bits)
     torch.cuda.synchronize()
     build_s = time.time() - t0
-
-    # exact ground truth (FP64 on the device; the data are integers so it is exact)
-    gt = []
-    xn = (dd.double() ** 2).sum(1)
-    xt = dd.double().T.contiguous()
-    for s in range(0, w.nq, 500):
-        q = qd[s:s + 500].double()
-        d2 = (q ** 2).sum(1, keepdim=True) + xn[None] - 2.0 * (q @ xt)
-        gt.append(torch.topk(d2, w.k, largest=False).indices)
-    gt = torch.cat(gt).cpu().numpy()
-    del xt, xn
+    gt = exact_knn(dd, qd, w.k)
 
     # nprobe sweep (untimed): smallest nprobe with mean recall@100 >= 0.95
     sweep = {}
@@ -184,6 +178,10 @@ def run_ours(args, rank, world):
     if not args.no_learned:
         legs["learned"] = learned_leg(args, G, qd, gt, w, chosen, flush, stream, dist, hbm, src)
 
+    precision = None
+    if args.workload == "gist" or args.precision:
+        precision = precision_legs(args, G, qd, gt, w, chosen, flush, stream, dist, data)
+
     best_name = max(legs, key=lambda n: legs[n]["value"] if legs[n]["recall_at_100"] >= TARGET
                     else -1.0)
     best = legs[best_name]
@@ -208,12 +206,15 @@ def run_ours(args, rank, world):
         e2e_ms.append((time.perf_counter() - t1) * 1e3)
     e2e_qps = world * w.nq / (np.mean(e2e_ms) / 1e3)
     e2e_rec = recall_at(ih, gt)
+    latency = batch1_latency(G, bplan_args(best_name, legs, chosen), qd, w, flush)
 
+    for lg in legs.values():
+        lg.pop("_pred_obj", None)
     res = {
         "metric": METRIC, "value": round(qps, 1), "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u1+f32",
-        "data": "synthetic (SIFT-shaped, seeded)",
+        "data": f"synthetic ({w.name} shape, seeded)",
         "config": {"workload": w.name, "mode": f"{best_name} nprobe", "n": w.n, "d": w.d,
                    "nq_per_gpu": w.nq, "n_clusters": w.n_clusters, "k": w.k, "bq": w.bq,
                    "eps0": w.eps0, "recall_at_100": round(rec, 4),
@@ -230,10 +231,14 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": int(qh.nbytes), "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes),
                 "recall_at_100": round(e2e_rec, 4),
                 "path": "rabitq_plan_search: pinned host queries -> plan -> pinned host results"},
+        "batch1_latency_us": latency,
+        "popc_roof": popc_roof(best, w, G),
         "gpu_launches": best["gpu_launches_per_step"] * args.steps,
         "clocks": fixed.pop("clocks"),
         "legs": legs,
     }
+    if precision is not None:
+        res["rotation_precision"] = precision
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(G, data, queries, w, chosen, budget_s=args.cpu_budget)
     if rank == 0:
@@ -260,6 +265,124 @@ class _Range:
         if self.on:
             import torch
             torch.cuda.nvtx.range_pop()
+
+
+def exact_knn(dd, qd, k):
+    """Exact k nearest neighbours (the ground truth of recall): FP32 distances
+    by ||q||^2 + ||x||^2 - 2 q.x (TF32 off) pick 2k + 64 candidates per query,
+    whose FP64 distances then decide the top k (ties by id)."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    n, d = dd.shape
+    xn = (dd.double() ** 2).sum(1).float()
+    cand = 2 * k + 64
+    step = max(1, min(1000, int(4e9 // (4 * n))))  # <= 4 GB of distances per chunk
+    out = []
+    for s in range(0, qd.shape[0], step):
+        q = qd[s:s + step]
+        d2 = (q * q).sum(1, keepdim=True) + xn[None] - 2.0 * (q @ dd.T)
+        ci = torch.topk(d2, min(cand, n), largest=False).indices
+        del d2
+        xc = dd[ci].double()                                   # (m, cand, d)
+        ex = ((xc - q.double()[:, None, :]) ** 2).sum(-1)       # exact FP64
+        order = torch.argsort(ci, dim=1)                        # ids ascending, then stable
+        ci, key = torch.gather(ci, 1, order), torch.gather(ex, 1, order)
+        top = torch.sort(key, dim=1, stable=True).indices[:, :k]
+        out.append(torch.gather(ci, 1, top))
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return torch.cat(out).cpu().numpy()
+
+
+def precision_legs(args, G, qd, gt, w, nprobe, flush, stream, dist, data):
+    """The query rotation in FP32 (canonical SIMT), TF32 and BF16 (tensor
+    cores, FP32 accumulation) at the fixed nprobe: throughput, recall@100,
+    the rotation's normwise relative error against the FP64 rotation of the
+    oracle's definition (P^-1 [q; 0] with the index's FP64 P), and the mean
+    relative error of the estimated distances against exact FP64 distances
+    over the estimated pairs of 20 queries."""
+    import torch
+    from paper_2405_12497_gb300 import rabitq
+    P = G.rotation()
+    nt = min(200, w.nq)
+    Q = qd[:nt].cpu().numpy().astype(np.float64)
+    ref = Q @ P[:w.d]
+    X = data.astype(np.float64)
+    out = {}
+    for name, mode in (("fp32", rabitq.ROT_FP32), ("tf32", rabitq.ROT_TF32),
+                       ("bf16", rabitq.ROT_BF16)):
+        plan = rabitq.Plan(G, w.k, nprobe, w.nq, bq=w.bq, eps0=w.eps0, rot_precision=mode,
+                           stats=True)
+        leg = time_leg(args, plan, qd, gt, w, flush, stream, dist, name=f"rot_{name}")
+        leg.pop("_plan")
+        t = G.search_trace(qd[:nt], w.k, nprobe, bq=w.bq, eps0=w.eps0, rot_precision=mode)
+        rq = t["rq"].cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(rq - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        t2 = G.search_trace(qd[:20], w.k, nprobe, bq=w.bq, eps0=w.eps0, rot_precision=mode,
+                            pair_cap=4096, scan_path=rabitq.SCAN_POPC)
+        est_err = []
+        for i in range(20):
+            n = min(int(t2["n_pairs"][i]), 4096)
+            ids = t2["pair_id"][i, :n].cpu().numpy()
+            est = t2["pair_est"][i, :n, 0].cpu().numpy().astype(np.float64)
+            exact = ((X[ids] - Q[i][None, :]) ** 2).sum(1)
+            ok = exact > 0
+            est_err.append(np.abs(est[ok] - exact[ok]) / exact[ok])
+        est_err = np.concatenate(est_err)
+        out[name] = {"value": leg["value"], "unit": "queries/s",
+                     "recall_at_100": leg["recall_at_100"],
+                     "rotation_rel_err": {"mean": float(err.mean()), "max": float(err.max())},
+                     "estimated_dist_rel_err": {"mean": float(est_err.mean()),
+                                                "p99": float(np.percentile(est_err, 99))},
+                     "stage_ms": leg["stage_ms"]}
+    return out
+
+
+def bplan_args(best_name, legs, nprobe):
+    """How to make a one-query plan of the headline leg."""
+    return {"predictor": legs[best_name].get("_pred_obj"), "nprobe": nprobe}
+
+
+def batch1_latency(G, pa, qd, w, flush, n=200):
+    """Search latency of single queries (the paper's per-query protocol):
+    one-query plan replays on the device, each timed with CUDA events, L2 not
+    flushed between them (a serving loop's steady state). p50 / p99 in us."""
+    import torch
+    from paper_2405_12497_gb300 import rabitq
+    plan = rabitq.Plan(G, w.k, pa["nprobe"] if pa["predictor"] is None else 0, 1, bq=w.bq,
+                       eps0=w.eps0, predictor=pa["predictor"])
+    stream = torch.cuda.current_stream()
+    out = []
+    for i in range(n + 10):
+        plan.queries[0].copy_(qd[i % qd.shape[0]])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run(1)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= 10:
+            out.append(e0.elapsed_time(e1) * 1e3)
+    plan.sync()
+    return {"p50": round(float(np.percentile(out, 50)), 1),
+            "p99": round(float(np.percentile(out, 99)), 1), "queries": n,
+            "mode": "learned nprobe" if pa["predictor"] is not None else f"nprobe {pa['nprobe']}"}
+
+
+def popc_roof(best, w, G):
+    """The popcount co-bound of the scan: B_q * D'/32 32-bit POPC per
+    (query, code) at 16 POPC per clock per SM (sm_80+ rate) and the sampled
+    SM clock, against the pairs the headline leg estimated per second."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    mhz = 2070.0
+    popc_per_pair = w.bq * G.dpad // 32
+    roof = sms * 16 * mhz * 1e6 / popc_per_pair
+    pairs = best["roofline"]["pairs_per_query"] * w.nq / (best["fused_ms"] / 1e3)
+    return {"pairs_per_s": round(pairs / 1e9, 2), "roof_pairs_per_s": round(roof / 1e9, 1),
+            "unit": "G pairs/s", "frac": round(pairs / roof, 4),
+            "assumed": f"16 POPC/clk/SM x {sms} SMs x {mhz:.0f} MHz, {popc_per_pair} POPC per pair"}
 
 
 def time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=False, name="leg"):
@@ -392,6 +515,7 @@ def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, dist, hbm, src)
     leg["scan_gbs"] = leg["roofline"].pop("scan_gbs")
     leg["ns_per_code"] = leg["roofline"].pop("ns_per_code")
     leg["gpu_launches_per_step"] = 12
+    leg["_pred_obj"] = pr
     npf = npq.double().cpu().numpy()
     leg.update({
         "mean_nprobe": round(float(npf.mean()), 2),
@@ -421,9 +545,16 @@ def cpu_baseline(G, data, queries, w, nprobe, budget_s=15.0):
     t0 = time.perf_counter()
     X.search(queries[:m2], w.k, nprobe, bq=w.bq, eps0=w.eps0, threads=cores)
     dt = time.perf_counter() - t0
+    # the paper's protocol: one thread, one query at a time (a short sample)
+    m1 = min(len(queries), 200)
+    t1 = time.perf_counter()
+    X.search(queries[:m1], w.k, nprobe, bq=w.bq, eps0=w.eps0, threads=1)
+    d1 = time.perf_counter() - t1
     return {"value": round(m2 / dt, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
             "sample": f"first {m2} of {len(queries)} queries, nprobe {nprobe}, k {w.k}, "
-                      f"{cores} threads, {dt:.1f} s"}
+                      f"{cores} threads, {dt:.1f} s",
+            "single_thread": {"value": round(m1 / d1, 2), "unit": "queries/s",
+                              "sample": f"first {m1} queries, 1 thread, {d1:.1f} s"}}
 
 
 # ------------------------------------------------------------- reference
@@ -463,7 +594,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * sum(times) / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u1+f32",
-        "data": "synthetic (SIFT-shaped, seeded)", "impl": "reference",
+        "data": f"synthetic ({w.name} shape, seeded)", "impl": "reference",
         "config": {"workload": w.name, "n": w.n, "d": w.d, "n_clusters": w.n_clusters, "k": w.k,
                    "bq": w.bq, "eps0": w.eps0, "nprobe": chosen,
                    "recall_at_100_sample200": round(rec, 4), "queries_per_step": m,
@@ -486,6 +617,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nprobe", type=int, default=None)
     ap.add_argument("--nq", type=int, default=None, help="fewer queries (profiling runs)")
+    ap.add_argument("--workload", default="sift", choices=sorted(WORKLOADS),
+                    help="sift: 1M x 128 (the headline); gist: 1M x 960; deep: 10M x 256")
+    ap.add_argument("--n", type=int, default=None, help="fewer points (smaller runs)")
+    ap.add_argument("--precision", action="store_true",
+                    help="also time the TF32 / BF16 query rotation (always for gist)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-nprobe leg")
