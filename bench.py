@@ -443,7 +443,7 @@ def time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=False, name="
     return out
 
 
-def measured_traffic(leg: str, nq: int):
+def measured_traffic(workload: str, leg: str, nq: int):
     """DRAM bytes of one fused-kernel launch of nq queries from the recorded
     ncu capture (profiles/fused_search_traffic.json), scaled by queries; None
     when there is no capture of this leg or the kernel source has changed
@@ -455,9 +455,10 @@ def measured_traffic(leg: str, nq: int):
         return None
     rec = json.load(open(path))
     sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    if rec.get("kernels_search_sha1") != sha or leg not in rec:
+    ent = rec.get(workload, {}).get(leg)
+    if rec.get("kernels_search_sha1") != sha or ent is None:
         return None
-    return int(rec[leg]["dram_bytes_per_query"] * nq)
+    return int(ent["dram_bytes_per_query"] * nq)
 
 
 def roofline(G, qd, w, nprobe, per_query, fused_ms, hbm, src, leg):
@@ -475,7 +476,7 @@ def roofline(G, qd, w, nprobe, per_query, fused_ms, hbm, src, leg):
     scan_bytes = w.nq * pairs_per_q * (G.dpad / 8 + 12)
     return {"kernel": "fused_search_kernel", "bound": "hbm", "achieved": round(achieved, 1),
             "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-            "traffic": measured_traffic(leg, w.nq),
+            "traffic": measured_traffic(w.name, leg, w.nq),
             "peak_source": src, "algorithmic_bytes_per_launch": int(bytes_launch),
             "pairs_per_query": round(pairs_per_q, 1), "survivors_per_query": round(surv_per_q, 1),
             "scan_gbs": round(scan_bytes / (fused_ms / 1e3) / 1e9, 1),

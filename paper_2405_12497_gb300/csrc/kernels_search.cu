@@ -122,6 +122,7 @@ struct SelState {
   int hist[256];
   int bin, rem, tie_taken;
   int warp_cnt[kThreads / 32];
+  unsigned long long wmin[kThreads / 32], wmax[kThreads / 32];
 };
 
 struct FusedParams {
@@ -320,10 +321,49 @@ __device__ __forceinline__ int warp_reserve(bool want, int* counter) {
 template <class K, class F>
 __device__ K block_select_f(int n, int want, SelState& st, F keyf) {
   constexpr int NB = (int)sizeof(K) * 8;
-  const int tid = threadIdx.x, lane = tid & 31;
-  K prefix = 0, mask = 0;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // The leading bits where the smallest and the largest key agree are common
+  // to every key and need no histogram pass: one min/max pass finds them.
+  K kmin = ~(K)0, kmax = 0;
+  for (int i = tid; i < n; i += blockDim.x) {
+    const K key = keyf(i);
+    kmin = key < kmin ? key : kmin;
+    kmax = key > kmax ? key : kmax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const K a = __shfl_xor_sync(kFull, kmin, o), b = __shfl_xor_sync(kFull, kmax, o);
+    kmin = a < kmin ? a : kmin;
+    kmax = b > kmax ? b : kmax;
+  }
+  if (lane == 0) {
+    st.wmin[wid] = kmin;
+    st.wmax[wid] = kmax;
+  }
+  __syncthreads();
+  kmin = ~(K)0;
+  kmax = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    kmin = (K)st.wmin[w] < kmin ? (K)st.wmin[w] : kmin;
+    kmax = (K)st.wmax[w] > kmax ? (K)st.wmax[w] : kmax;
+  }
+  if (kmin == kmax) {  // all keys equal: the answer, with every key a tie
+    __syncthreads();
+    if (tid == 0) {
+      st.bin = (int)(kmin & 255);
+      st.hist[st.bin] = n;
+      st.rem = want;
+    }
+    __syncthreads();
+    return kmin;
+  }
+  const K diff = kmin ^ kmax;
+  const int top = NB - 1 - (sizeof(K) == 8 ? __clzll((long long)diff) : __clz((int)diff));
+  const int start = (top / 8) * 8;  // the byte holding the highest differing bit
+  K mask = start + 8 >= NB ? (K)0 : ~(((K)1 << (start + 8)) - 1);
+  K prefix = kmin & mask;
   int rem = want;
-  for (int shift = NB - 8; shift >= 0; shift -= 8) {
+  for (int shift = start; shift >= 0; shift -= 8) {
     for (int i = tid; i < 256; i += blockDim.x) st.hist[i] = 0;
     __syncthreads();
     for (int b0 = 0; b0 < n; b0 += blockDim.x) {
@@ -585,7 +625,9 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
       if (P.tr.surv_ids && si < P.tr.surv_cap) P.tr.surv_ids[q * P.tr.surv_cap + si] = id;
     }
     __syncthreads();
-    if (*top_cnt > P.ct - (int)blockDim.x) select_keep_dk(S.topk, top_cnt, P.k, *S.sel);
+    const int tc = *top_cnt;  // read between barriers (see the scan's upkeep)
+    __syncthreads();
+    if (tc > P.ct - (int)blockDim.x) select_keep_dk(S.topk, top_cnt, P.k, *S.sel);
   }
   __syncthreads();
   if (threadIdx.x == 0) *surv_cnt += count;
@@ -607,7 +649,8 @@ struct TailShared {
 // distances of the other codes with LB <= tau; top-k by (distance, id).
 // The pilot mark is bit 31 of the position. Whole block.
 __device__ void finish_query(const FusedParams& P, const FusedSmem& S, int64_t q, int4* cand,
-                             int cand_cap, float tau_ub, const TailShared& ts) {
+                             int cand_cap, float tau_ub, const TailShared& ts,
+                             bool filtered = false) {
   const int tid = threadIdx.x;
   const int k = P.k, m = P.m;
   if (tid == 0) {
@@ -615,8 +658,9 @@ __device__ void finish_query(const FusedParams& P, const FusedSmem& S, int64_t q
     *ts.surv = 0;
   }
   __syncthreads();
-  compact_cand(cand, ts.cand_cnt, cand_cap, ts.scratch,
-               [tau_ub](const int4& e) { return __int_as_float(e.y) <= tau_ub; });
+  if (!filtered)  // (a list staged with LB <= tau_ub is already filtered)
+    compact_cand(cand, ts.cand_cnt, cand_cap, ts.scratch,
+                 [tau_ub](const int4& e) { return __int_as_float(e.y) <= tau_ub; });
   // pilot: the m smallest (estimate, id) of the list
   const int nl = *ts.cand_cnt;
   const bool pilot_all = nl <= m;
@@ -850,14 +894,24 @@ __global__ void __launch_bounds__(kThreads, 3) fused_search_kernel(FusedParams P
         int jv[PPT];
         CodeRegs<WT> cr[PPT];
         float4 fv[PPT];
+        // consecutive pairs advance through a bucket: the prefix array is
+        // consulted again only at a bucket boundary
+        int64_t pos = 0;
+        int next_b = 0;
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp) {
           const int t = t0 + pp;
           posv[pp] = -1;
           jv[pp] = 0;
           if (t < total) {
-            while (S.pref[j + 1] <= t) ++j;
-            posv[pp] = (int64_t)S.pbeg[j] + (t - S.pref[j]);
+            if (pp == 0 || t >= next_b) {
+              while (S.pref[j + 1] <= t) ++j;
+              pos = (int64_t)S.pbeg[j] + (t - S.pref[j]);
+              next_b = S.pref[j + 1];
+            } else {
+              ++pos;
+            }
+            posv[pp] = pos;
             jv[pp] = j;
             load_code<WT>(cr[pp], P.codes + posv[pp] * W);
             fv[pp] = __ldg(P.factors + posv[pp]);
@@ -963,21 +1017,29 @@ __global__ void __launch_bounds__(kThreads, 3) fused_search_kernel(FusedParams P
             }
           }
         }
+        // Buffer upkeep. The counters are read between two barriers: after
+        // every append of this round and before any append of the next, so
+        // that every thread takes the same branches (a warp that ran ahead
+        // into the next round must not change what a slower one reads).
         __syncthreads();
         const int room = step;
-        if (s_ub_cnt > P.cu - room) {  // keep the k smallest upper bounds
+        const int ub_cnt = s_ub_cnt, c_cnt = s_cand_cnt;
+        bool ovf = s_overflow != 0;
+        __syncthreads();
+        if (ub_cnt > P.cu - room) {  // keep the k smallest upper bounds
           const uint32_t T = select_keep<uint32_t>(S.ubk, &s_ub_cnt, k, *S.sel);
           if (tid == 0) s_tau = key_float(T);
           __syncthreads();
         }
-        if (s_cand_cnt > P.cand_cap - room) {
+        if (c_cnt > P.cand_cap - room) {
           const float tau = s_tau;
           compact_cand(cand, &s_cand_cnt, P.cand_cap, s_scratch,
                        [tau](const int4& e) { return __int_as_float(e.y) <= tau; });
-          if (s_cand_cnt > P.cand_cap - room && tid == 0) s_overflow = 1;
+          if (s_cand_cnt > P.cand_cap - room) ovf = true;  // same value in every thread
           __syncthreads();
+          if (ovf && tid == 0) s_overflow = 1;
         }
-        if (s_overflow) break;
+        if (ovf) break;
       }
       pairs_done += total;
       __syncthreads();
@@ -1025,7 +1087,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_search_kernel(FusedParams P
       }
       __syncthreads();
     }
-    finish_query(P, S, q, tcand, tcap, tau_ub, ts);
+    finish_query(P, S, q, tcand, tcap, tau_ub, ts, tcand == S.scand);
     if (tid == 0) {
       if (s_overflow) atomicExch(P.err, 1);
       if (P.tr.n_pairs) P.tr.n_pairs[q] = pairs_done;
