@@ -178,6 +178,10 @@ def run_ours(args, rank, world):
     if not args.no_learned:
         legs["learned"] = learned_leg(args, G, qd, gt, w, chosen, flush, stream, dist, hbm, src)
 
+    cold = None
+    if args.cold_scan or args.workload == "deep":
+        cold = cold_scan_leg(args, G, qd, gt, w, flush, stream, dist, hbm, src)
+
     precision = None
     if args.workload == "gist" or args.precision:
         precision = precision_legs(args, G, qd, gt, w, chosen, flush, stream, dist, data)
@@ -239,6 +243,8 @@ def run_ours(args, rank, world):
     }
     if precision is not None:
         res["rotation_precision"] = precision
+    if cold is not None:
+        res["cold_scan"] = cold
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(G, data, queries, w, chosen, budget_s=args.cpu_budget)
     if rank == 0:
@@ -292,6 +298,26 @@ def exact_knn(dd, qd, k):
         out.append(torch.gather(ci, 1, top))
     torch.backends.cuda.matmul.allow_tf32 = prev
     return torch.cat(out).cpu().numpy()
+
+
+def cold_scan_leg(args, G, qd, gt, w, flush, stream, dist, hbm, src):
+    """The scan against HBM: a fixed large nprobe (default 128) whatever the
+    recall, on an index whose codes and factors do not fit in L2, L2 flushed
+    before every step. Reports the fused kernel's algorithmic bytes per second
+    (codes + factors of every estimated pair, plus re-ranked rows) against the
+    HBM peak, and the code-scan part alone."""
+    from paper_2405_12497_gb300 import rabitq
+    npb = args.cold_nprobe
+    plan = rabitq.Plan(G, w.k, npb, w.nq, bq=w.bq, eps0=w.eps0, stats=True,
+                       max_candidates=1 << 18)
+    leg = time_leg(args, plan, qd, gt, w, flush, stream, dist, name="cold_scan")
+    leg.pop("_plan")
+    rl = roofline(G, qd, w, npb, None, leg["fused_ms"], hbm, src, f"cold{npb}")
+    index_mb = G.n * (G.dpad / 8 + 16) / 1e6
+    return {"nprobe": npb, "value": leg["value"], "unit": "queries/s",
+            "recall_at_100": leg["recall_at_100"], "fused_ms": round(leg["fused_ms"], 4),
+            "codes_and_factors_mb": round(index_mb, 1), "roofline": rl,
+            "stage_ms": leg["stage_ms"]}
 
 
 def precision_legs(args, G, qd, gt, w, nprobe, flush, stream, dist, data):
@@ -621,6 +647,9 @@ def main():
     ap.add_argument("--workload", default="sift", choices=sorted(WORKLOADS),
                     help="sift: 1M x 128 (the headline); gist: 1M x 960; deep: 10M x 256")
     ap.add_argument("--n", type=int, default=None, help="fewer points (smaller runs)")
+    ap.add_argument("--cold-scan", action="store_true",
+                    help="also time a fixed large nprobe for the HBM scan (always for deep)")
+    ap.add_argument("--cold-nprobe", type=int, default=128)
     ap.add_argument("--precision", action="store_true",
                     help="also time the TF32 / BF16 query rotation (always for gist)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
