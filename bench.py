@@ -636,6 +636,54 @@ def run_reference(args):
     print(json.dumps(res), flush=True)
 
 
+def run_accuracy_study(args):
+    """Distance-estimation accuracy on the GPU (the paper's error study, §5.2.2
+    style, on synthetic SIFT-shaped data): for code lengths D' = 128, 256, 512
+    (padding) and B_q = 1..8, over every estimated pair of 50 queries (nprobe
+    16): mean / max relative error of the estimated squared distance against
+    the exact FP64 one, its mean signed relative error and least-squares fit
+    (unbiasedness), and the fraction of pairs whose exact distance lies inside
+    the error bound for eps0 = 0.5 .. 4 (the bound is linear in eps0, so one
+    trace at eps0 = 1.9 gives every eps0)."""
+    import torch
+    from paper_2405_12497_gb300 import build as B
+    from paper_2405_12497_gb300 import rabitq
+    B.build()
+    n = args.n or 200_000
+    w = synth.dataclasses_replace(synth.SIFT_LIKE, n=n, nq=50, n_clusters=max(64, n // 244))
+    data, queries = synth.make(w)
+    X = data.astype(np.float64)
+    qd = torch.from_numpy(queries).cuda()
+    eps_grid = (0.5, 1.0, 1.5, 1.9, 2.5, 3.0, 4.0)
+    out = {"study": "distance-estimation accuracy", "workload": f"sift-like n={n} d={w.d}",
+           "n_clusters": w.n_clusters, "queries": 50, "nprobe": 16, "rows": []}
+    for cb in (128, 256, 512):
+        G = rabitq.Index.build(data, w.n_clusters, seed=2, code_bits=cb)
+        for bq in (1, 2, 3, 4, 5, 6, 8):
+            t = G.search_trace(qd, 10, 16, bq=bq, eps0=1.9, pair_cap=16384)
+            est_all, ex_all, half_all = [], [], []
+            for i in range(50):
+                m = min(int(t["n_pairs"][i]), 16384)
+                ids = t["pair_id"][i, :m].cpu().numpy()
+                pe = t["pair_est"][i, :m].cpu().numpy().astype(np.float64)
+                ex = ((X[ids] - queries[i].astype(np.float64)[None, :]) ** 2).sum(1)
+                est_all.append(pe[:, 0])
+                half_all.append((pe[:, 2] - pe[:, 1]) / 2)
+                ex_all.append(ex)
+            est, ex, half = (np.concatenate(v) for v in (est_all, ex_all, half_all))
+            ok = ex > 0
+            rel = np.abs(est[ok] - ex[ok]) / ex[ok]
+            slope, icpt = np.polyfit(ex, est, 1)
+            cover = {str(e): float(np.mean(np.abs(est - ex) <= half * (e / 1.9))) for e in eps_grid}
+            out["rows"].append({"code_bits": cb, "bq": bq, "pairs": int(len(est)),
+                                "rel_err_mean": float(rel.mean()), "rel_err_max": float(rel.max()),
+                                "signed_rel_err_mean": float(((est[ok] - ex[ok]) / ex[ok]).mean()),
+                                "fit_slope": float(slope), "fit_intercept_rel": float(icpt / ex.mean()),
+                                "bound_coverage": cover})
+        G.free()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -658,6 +706,9 @@ def main():
     ap.add_argument("--train-nq", type=int, default=100_000)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--nprobe-max", type=int, default=256)
+    ap.add_argument("--study", default=None, choices=["accuracy"],
+                    help="instead of the benchmark line, print the distance-estimation "
+                         "accuracy study (one JSON line)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -666,6 +717,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args)
+        return
+    if args.study == "accuracy":
+        if rank == 0:
+            run_accuracy_study(args)
         return
     run_ours(args, rank, world)
 

@@ -133,19 +133,20 @@ __device__ __forceinline__ int probe_count(float y, float mult, int nmax) {
   return n < 1 ? 1 : n;
 }
 
-// Fused inference: kQB queries per block, one hidden unit per thread.
+// Fused inference: kQB queries per block, one hidden unit per thread. The
+// activations are stored transposed ([unit][query]) so that each step of a
+// dot product reads the kQB values of one unit with 16-byte broadcast loads.
 constexpr int kQB = 32, kInferThreads = kH;
-constexpr int kHP = kH + 1;  // padded activation rows (the output layer reads rows per lane)
-constexpr size_t kInferSmem = sizeof(float) * (kQB * kF + 2 * kQB * kHP);
+constexpr size_t kInferSmem = sizeof(float) * (kQB * kF + 2 * kQB * kH);
 
 __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(
     const float* __restrict__ sel_dist, int64_t ld, int64_t nq, int navail, float s0,
     const __nv_bfloat16* __restrict__ P, float mult, int nmax, float* __restrict__ feat_out,
     float* __restrict__ y_out, int32_t* __restrict__ np_out) {
   extern __shared__ __align__(1024) float sm[];
-  float* xs = sm;              // kQB x kF
-  float* h1 = xs + kQB * kF;   // kQB x kHP
-  float* h2 = h1 + kQB * kHP;  // kQB x kHP
+  float* xT = sm;               // kF x kQB
+  float* h1T = xT + kQB * kF;   // kH x kQB
+  float* h2T = h1T + kQB * kH;  // kH x kQB
   const int tid = threadIdx.x;
   const int64_t q0 = (int64_t)blockIdx.x * kQB;
   const int nqb = (int)(nq - q0 < kQB ? nq - q0 : kQB);
@@ -156,50 +157,56 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(
       v = feature(sel_dist + (q0 + q) * ld, navail, j, s0);
       if (feat_out) feat_out[(q0 + q) * kF + j] = v;
     }
-    xs[i] = v;
+    xT[j * kQB + q] = v;
   }
   __syncthreads();
   const int n = tid;
   float acc[kQB];
-  // layer 1
+  // one dense layer: acc[q] = fold_j fma(in[j][q], W[j][n], acc[q]), ascending j
+  auto layer = [&](const float* inT, int nin, int woff) {
 #pragma unroll
-  for (int q = 0; q < kQB; ++q) acc[q] = 0.0f;
-  for (int j = 0; j < kF; ++j) {
-    const float w = __bfloat162float(P[oW1 + j * kH + n]);
+    for (int q = 0; q < kQB; ++q) acc[q] = 0.0f;
+    for (int j = 0; j < nin; ++j) {
+      const float w = __bfloat162float(P[woff + j * kH + n]);
+      const float4* a4 = reinterpret_cast<const float4*>(inT + j * kQB);
 #pragma unroll
-    for (int q = 0; q < kQB; ++q) acc[q] = __fmaf_rn(xs[q * kF + j], w, acc[q]);
-  }
-  {
-    const float b = __bfloat162float(P[ob1 + n]);
-#pragma unroll
-    for (int q = 0; q < kQB; ++q) {
-      const float z = __fadd_rn(acc[q], b);
-      h1[q * kHP + n] = z > 0.0f ? z : 0.0f;
+      for (int c = 0; c < kQB / 4; ++c) {
+        const float4 a = a4[c];
+        acc[4 * c] = __fmaf_rn(a.x, w, acc[4 * c]);
+        acc[4 * c + 1] = __fmaf_rn(a.y, w, acc[4 * c + 1]);
+        acc[4 * c + 2] = __fmaf_rn(a.z, w, acc[4 * c + 2]);
+        acc[4 * c + 3] = __fmaf_rn(a.w, w, acc[4 * c + 3]);
+      }
     }
-  }
+  };
+  auto bias_relu_store = [&](int boff, float* outT) {
+    const float bb = __bfloat162float(P[boff + n]);
+    float4* o4 = reinterpret_cast<float4*>(outT + n * kQB);
+#pragma unroll
+    for (int c = 0; c < kQB / 4; ++c) {
+      float4 v;
+      float z = __fadd_rn(acc[4 * c], bb);
+      v.x = z > 0.0f ? z : 0.0f;
+      z = __fadd_rn(acc[4 * c + 1], bb);
+      v.y = z > 0.0f ? z : 0.0f;
+      z = __fadd_rn(acc[4 * c + 2], bb);
+      v.z = z > 0.0f ? z : 0.0f;
+      z = __fadd_rn(acc[4 * c + 3], bb);
+      v.w = z > 0.0f ? z : 0.0f;
+      o4[c] = v;
+    }
+  };
+  layer(xT, kF, oW1);
+  bias_relu_store(ob1, h1T);
   __syncthreads();
-  // layer 2
-#pragma unroll
-  for (int q = 0; q < kQB; ++q) acc[q] = 0.0f;
-  for (int j = 0; j < kH; ++j) {
-    const float w = __bfloat162float(P[oW2 + j * kH + n]);
-#pragma unroll
-    for (int q = 0; q < kQB; ++q) acc[q] = __fmaf_rn(h1[q * kHP + j], w, acc[q]);
-  }
-  {
-    const float b = __bfloat162float(P[ob2 + n]);
-#pragma unroll
-    for (int q = 0; q < kQB; ++q) {
-      const float z = __fadd_rn(acc[q], b);
-      h2[q * kHP + n] = z > 0.0f ? z : 0.0f;
-    }
-  }
+  layer(h1T, kH, oW2);
+  bias_relu_store(ob2, h2T);
   __syncthreads();
   // output layer: one lane per query, ascending hidden index
   if (tid < nqb) {
     float s = 0.0f;
     for (int j = 0; j < kH; ++j)
-      s = __fmaf_rn(h2[tid * kHP + j], __bfloat162float(P[ow3 + j]), s);
+      s = __fmaf_rn(h2T[j * kQB + tid], __bfloat162float(P[ow3 + j]), s);
     const float y = __fadd_rn(s, __bfloat162float(P[ob3]));
     if (y_out) y_out[q0 + tid] = y;
     if (np_out) np_out[q0 + tid] = probe_count(y, mult, nmax);
