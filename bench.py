@@ -684,6 +684,112 @@ def run_accuracy_study(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serving_study(args):
+    """A serving loop on one GPU: three resident indices (1M x 128 SIFT-shaped,
+    1M x 420 and 1M x 960 GIST-shaped recipes, K = 4096), each with a trained
+    probe-count predictor and a search plan per k in {10, 100} (CUDA-graph
+    replay per batch size); a Poisson stream of requests, each a batch of 1..256
+    queries for a random index and k, admitted when the device has room for
+    its buffers, served in arrival order on one stream. Reports p50 / p99
+    latency (arrival to results on the host), QPS and recall@k."""
+    import torch
+    from paper_2405_12497_gb300 import build as B
+    from paper_2405_12497_gb300 import rabitq
+    B.build()
+    rng = np.random.default_rng(11)
+    dev = torch.device("cuda", 0)
+    specs = [("sift-like-1M-d128", synth.SIFT_LIKE),
+             ("gist-like-1M-d420", synth.dataclasses_replace(synth.GIST_LIKE, d=420, code_bits=448,
+                                                               name="gist-like-1M-d420")),
+             ("gist-like-1M-d960", synth.GIST_LIKE)]
+    n = args.n or 1_000_000
+    pool = 2000
+    idx = []
+    for name, w in specs:
+        w = synth.dataclasses_replace(w, n=n, nq=pool)
+        data, queries = synth.make(w)
+        dd = torch.from_numpy(data).to(dev)
+        qd = torch.from_numpy(queries).to(dev)
+        G = rabitq.Index.build(dd, w.n_clusters, seed=2, code_bits=w.code_bits)
+        gt = exact_knn(dd, qd, 100)
+        _, tq = synth.make(w, nq=20_000, seed_query=7, with_data=False)
+        pr = rabitq.Predictor.train(G, torch.from_numpy(tq).to(dev), k=100, target_recall=TARGET,
+                                    nprobe_max=256, epochs=10)
+        # raise the multiplier until the pool reaches the target at k = 100
+        mult = pr.info()["mult"]
+        for _ in range(48):
+            pr.set_mult(mult)
+            ids, _ = G.search_learned(pr, qd, 100)
+            if recall_at(ids.cpu().numpy(), gt) >= TARGET:
+                break
+            mult *= 2.0 ** 0.125
+        plans = {k: rabitq.Plan(G, k, 0, 256, predictor=pr) for k in (10, 100)}
+        idx.append({"name": name, "G": G, "pr": pr, "qd": qd, "gt": gt, "plans": plans,
+                    "mult": mult, "dd": dd})
+        del data
+    # requests
+    n_req = args.steps * 100 if args.steps else 1000
+    reqs = [(int(rng.integers(0, 3)), int(rng.choice([10, 100])), int(rng.integers(1, 257)))
+            for _ in range(n_req)]
+    def serve(i, k, b, off):
+        pl = idx[i]["plans"][k]
+        pl.queries[:b].copy_(idx[i]["qd"][off:off + b])
+        pl.run(b)
+        out = pl.ids[:b, :k].clone()
+        pl.sync()
+        return out
+
+    # capture every graph the stream will use, then time the service path alone
+    t0 = time.perf_counter()
+    for i, k, b in reqs:
+        serve(i, k, b, 0)
+    warm_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for i, k, b in reqs[:300]:
+        serve(i, k, b, 0)
+    sat_s = time.perf_counter() - t0
+    service = sat_s / 300
+    sat_qps = sum(b for _, _, b in reqs[:300]) / sat_s
+    rate = 0.7 / service  # 70% offered load
+    gaps = rng.exponential(1.0 / rate, n_req)
+    arrivals = np.cumsum(gaps)
+    free0, _ = torch.cuda.mem_get_info()
+    lat, results, admitted = [], [], 0
+    start = time.perf_counter()
+    for r, (i, k, b) in enumerate(reqs):
+        now = time.perf_counter() - start
+        if now < arrivals[r]:
+            time.sleep(arrivals[r] - now)
+        if r % 64 == 0:
+            free, _ = torch.cuda.mem_get_info()
+        if b * (idx[i]["G"].d * 4 + k * 12) > free:
+            continue  # not admitted: no room for the request's buffers
+        admitted += 1
+        off = int(rng.integers(0, pool - b + 1))
+        ids = serve(i, k, b, off)
+        lat.append((time.perf_counter() - start - arrivals[r]) * 1e3)
+        results.append((i, k, off, ids))
+    wall = time.perf_counter() - start
+    hits, totq = 0.0, 0
+    for i, k, off, ids in results:  # recall, outside the timed loop
+        got = ids.cpu().numpy()
+        gt = idx[i]["gt"][off:off + got.shape[0], :k]
+        hits += sum(len(np.intersect1d(a, g)) / k for a, g in zip(got, gt))
+        totq += got.shape[0]
+    out = {"study": "serving loop", "indices": [x["name"] for x in idx], "requests": n_req,
+           "admitted": admitted, "batch": "uniform 1..256", "k": [10, 100],
+           "offered_load": 0.7, "arrival_rate_per_s": round(rate, 1),
+           "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                          "p99": round(float(np.percentile(lat, 99)), 3),
+                          "mean": round(float(np.mean(lat)), 3)},
+           "qps": round(totq / wall, 1), "recall_at_k": round(float(hits / totq), 4),
+           "mean_service_ms": round(service * 1e3, 3), "saturated_qps": round(sat_qps, 1),
+           "graph_capture_s": round(warm_s, 2),
+           "free_device_memory_gb": round(free0 / 1e9, 1),
+           "multipliers": {x["name"]: round(x["mult"], 4) for x in idx}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -706,7 +812,7 @@ def main():
     ap.add_argument("--train-nq", type=int, default=100_000)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--nprobe-max", type=int, default=256)
-    ap.add_argument("--study", default=None, choices=["accuracy"],
+    ap.add_argument("--study", default=None, choices=["accuracy", "serving"],
                     help="instead of the benchmark line, print the distance-estimation "
                          "accuracy study (one JSON line)")
     args = ap.parse_args()
@@ -721,6 +827,10 @@ def main():
     if args.study == "accuracy":
         if rank == 0:
             run_accuracy_study(args)
+        return
+    if args.study == "serving":
+        if rank == 0:
+            run_serving_study(args)
         return
     run_ours(args, rank, world)
 
