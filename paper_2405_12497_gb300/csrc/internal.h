@@ -148,6 +148,9 @@ struct SearchArgs {
   // captured) around the stages: distances | selection (+ MLP) | rotation |
   // fused scan, prune and re-rank. Single-chunk searches only.
   cudaEvent_t* stage_ev = nullptr;
+  // a batch too small to fill the GPU may split each query's probes over
+  // several CTAs and merge them (identical results); off where scratch is fixed
+  int allow_split = 1;
 };
 int search_dev(const SearchArgs& a, cudaStream_t s);
 // Probe counts of nq queries from a predictor: query-centroid distances, the

@@ -154,6 +154,16 @@ struct FusedParams {
   const int32_t* order;
   int* next;
   int scap;  // shared-memory capacity for the tail's candidate list (0 = none)
+  // Split mode (split > 1, for batches too small to fill the GPU): work item
+  // i scans probe slice i % split of query i / split into candidate region i
+  // and writes the slice's k smallest upper-bound keys to ub_out[i k ...] and
+  // {keys written, candidates} to slice_cnt[2 i ...]; split_merge_kernel
+  // then finishes each query from its slices. cand2: one merged-list region
+  // of cand_cap entries per query.
+  int split;
+  uint32_t* ub_out;
+  int* slice_cnt;
+  int4* cand2;
 };
 
 struct FusedSmem {
@@ -836,10 +846,17 @@ __global__ void __launch_bounds__(kThreads, 3) fused_search_kernel(FusedParams P
     __syncthreads();
     return s_next;
   };
-  for (int64_t it = P.next ? fetch(0) : (int64_t)blockIdx.x; it < P.nq; it = fetch(it)) {
-    const int64_t q = P.order ? (int64_t)P.order[it] : it;
+  const int split = P.split > 1 ? P.split : 1;
+  const int64_t n_items = P.nq * split;
+  for (int64_t it = P.next ? fetch(0) : (int64_t)blockIdx.x; it < n_items; it = fetch(it)) {
+    const int64_t qi = it / split;
+    const int sl = (int)(it % split);
+    const int64_t q = P.order ? (int64_t)P.order[qi] : qi;
     int np = P.nprobe;
     if (P.nprobe_q) np = min(max(P.nprobe_q[q], 1), P.nprobe);
+    // this item's probes: all of them, or slice sl of `split`
+    const int pb = (int)((int64_t)np * sl / split), pe = (int)((int64_t)np * (sl + 1) / split);
+    if (split > 1) cand = P.cand + it * P.cand_cap;
     for (int i = tid; i < P.d; i += blockDim.x) S.qv[i] = P.queries[q * P.d + i];
     if (tid == 0) {
       s_ub_cnt = 0;
@@ -851,8 +868,8 @@ __global__ void __launch_bounds__(kThreads, 3) fused_search_kernel(FusedParams P
     }
     __syncthreads();
     int pairs_done = 0;
-    for (int pc0 = 0; pc0 < np; pc0 += P.pch) {
-      const int npc = min(P.pch, np - pc0);
+    for (int pc0 = pb; pc0 < pe; pc0 += P.pch) {
+      const int npc = min(P.pch, pe - pc0);
       for (int j = wid; j < npc; j += nwarps) {
         const int jg = pc0 + j;
         const int c = P.probe_ids[q * P.nprobe + jg];
@@ -1045,6 +1062,18 @@ __global__ void __launch_bounds__(kThreads, 3) fused_search_kernel(FusedParams P
       __syncthreads();
       if (s_overflow) break;
     }
+    if (split > 1) {  // a slice: hand its k smallest upper bounds and its list to the merge
+      if (s_ub_cnt > k) select_keep<uint32_t>(S.ubk, &s_ub_cnt, k, *S.sel);
+      const int nk = min(s_ub_cnt, k);
+      for (int i = tid; i < nk; i += blockDim.x) P.ub_out[it * k + i] = S.ubk[i];
+      if (tid == 0) {
+        P.slice_cnt[2 * it] = nk;
+        P.slice_cnt[2 * it + 1] = min(s_cand_cnt, P.cand_cap);
+        if (s_overflow) atomicExch(P.err, 1);
+      }
+      __syncthreads();
+      continue;
+    }
     // tau_ub: k-th smallest upper bound; pilot: the m smallest estimates
     const int n_ub = s_ub_cnt;
     const uint32_t T_ub = (n_ub >= k) ? block_select<uint32_t>(S.ubk, n_ub, k, *S.sel) : 0u;
@@ -1096,6 +1125,84 @@ __global__ void __launch_bounds__(kThreads, 3) fused_search_kernel(FusedParams P
   }
 }
 
+
+// The end of a split search: one CTA per query gathers its slices' upper
+// bounds (the union holds the query's k smallest, so tau_ub is exact),
+// stages the slices' candidates with LB <= tau_ub (shared memory when they
+// fit, else the query's merged-list region), and finishes the query like the
+// fused kernel. Results are identical to an unsplit search.
+__global__ void __launch_bounds__(kThreads) split_merge_kernel(FusedParams P) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ int s_cand_cnt, s_top_cnt, s_surv, s_fill;
+  __shared__ int s_scratch[kThreads / 32];
+  __shared__ SelState s_sel;
+  __shared__ int s_off[33];
+  const int tid = threadIdx.x;
+  size_t off[10];
+  fused_smem_bytes(P.pch, P.bq, P.W, P.d, P.cu, P.ce, P.ct, blockDim.x >> 5, off, P.scap);
+  FusedSmem S;
+  S.planes = nullptr;
+  S.pmeta = nullptr;
+  S.psum = nullptr;
+  S.pbeg = nullptr;
+  S.pref = nullptr;
+  S.qv = reinterpret_cast<float*>(smem + off[5]);
+  S.sel = &s_sel;
+  S.ubk = reinterpret_cast<uint32_t*>(smem + off[6]);
+  S.estk = reinterpret_cast<unsigned long long*>(smem + off[7]);
+  S.topk = reinterpret_cast<unsigned long long*>(smem + off[8]);
+  S.scand = reinterpret_cast<int4*>(smem + off[9]);
+  const int k = P.k, split = P.split;
+  for (int64_t qi = blockIdx.x; qi < P.nq; qi += gridDim.x) {
+    const int64_t q = P.order ? (int64_t)P.order[qi] : qi;
+    for (int i = tid; i < P.d; i += blockDim.x) S.qv[i] = P.queries[q * P.d + i];
+    if (tid == 0) {
+      s_off[0] = 0;
+      for (int sl = 0; sl < split; ++sl) s_off[sl + 1] = s_off[sl] + P.slice_cnt[2 * (qi * split + sl)];
+      s_top_cnt = 0;
+      s_surv = 0;
+      s_fill = 0;
+    }
+    __syncthreads();
+    const int n_ub = s_off[split];
+    for (int sl = 0; sl < split; ++sl)
+      for (int i = tid; i < s_off[sl + 1] - s_off[sl]; i += blockDim.x)
+        S.ubk[s_off[sl] + i] = P.ub_out[(qi * split + sl) * k + i];
+    __syncthreads();
+    const uint32_t T_ub = (n_ub >= k) ? block_select<uint32_t>(S.ubk, n_ub, k, *S.sel) : 0u;
+    const float tau_ub = (n_ub >= k) ? key_float(T_ub) : __int_as_float(0x7f800000);
+    int4* merged = P.cand2 + qi * P.cand_cap;
+    for (int sl = 0; sl < split; ++sl) {
+      const int64_t item = qi * split + sl;
+      const int4* src = P.cand + item * P.cand_cap;
+      const int n_c = P.slice_cnt[2 * item + 1];
+      for (int b = 0; b < n_c; b += blockDim.x) {
+        const int i = b + tid;
+        int4 e = make_int4(0, 0, 0, 0);
+        bool keep = false;
+        if (i < n_c) {
+          e = src[i];
+          keep = __int_as_float(e.y) <= tau_ub;
+        }
+        const int slot = warp_reserve(keep, &s_fill);
+        if (keep) {
+          if (slot < P.scap) S.scand[slot] = e;
+          if (slot < P.cand_cap) merged[slot] = e;
+        }
+      }
+    }
+    __syncthreads();
+    const int nf = s_fill;
+    if (nf > P.cand_cap && tid == 0) atomicExch(P.err, 1);
+    const bool in_smem = nf <= P.scap;
+    if (tid == 0) s_cand_cnt = min(nf, P.cand_cap);
+    __syncthreads();
+    TailShared ts{&s_cand_cnt, &s_top_cnt, &s_surv, s_scratch};
+    finish_query(P, S, q, in_smem ? S.scand : merged, in_smem ? P.scap : P.cand_cap, tau_ub, ts,
+                 true);
+    __syncthreads();
+  }
+}
 
 // ------------------------------------------- bucket-major tensor-core scan
 // The queries probing one bucket share its codes, so the scan becomes a
@@ -1549,6 +1656,30 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s);
 
 int search_dev_popc(const SearchArgs& a, cudaStream_t s);
 
+namespace {
+// Probe slices per query for a chunk of nqc queries: 1 when the queries fill
+// the GPU (full = resident CTAs); otherwise up to 16, no more than the probes,
+// and the slices' k smallest upper bounds must fit the merge's buffer.
+int split_factor(const SearchArgs& a, int64_t nqc, int64_t full, const FusedShape& fs) {
+  if (a.trace || !a.allow_split || nqc * 2 > full) return 1;
+  int sp = (int)std::min<int64_t>(16, full / std::max<int64_t>(nqc, 1));
+  sp = std::min(sp, std::min(a.nprobe, a.X->K));
+  sp = std::min(sp, fs.cu / std::max(a.k, 1));
+  return std::max(1, sp);
+}
+
+int set_merge_attr() {
+  int dev = 0, optin = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
+  RBQ_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  RBQ_CUDA(cudaFuncGetAttributes(&fa, split_merge_kernel));
+  RBQ_CUDA(cudaFuncSetAttribute(split_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes));
+  return RABITQ_OK;
+}
+}  // namespace
+
 // Scan-path choice: the index's tuned choice for AUTO (set by
 // rabitq_autotune), the popcount path otherwise; a TC search whose candidate
 // lists overflow under AUTO is redone on the popcount path.
@@ -1580,14 +1711,23 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
 
   // query chunks bound the centroid-distance scratch (<= 256 Mi floats)
   const int64_t qchunk = std::max<int64_t>(1, std::min<int64_t>(a.nq, (int64_t(1) << 28) / K));
-  const int64_t grid = std::min<int64_t>(qchunk, (int64_t)sms * per_sm);
-  DevBuf cd, rq, pid, pdist, cand, err;
+  const int64_t full = (int64_t)sms * per_sm;
+  const int64_t grid = std::min<int64_t>(qchunk, full);
+  // a batch too small to fill the GPU splits each query's probes over CTAs
+  const int split = split_factor(a, std::min(qchunk, a.nq), full, fs);
+  DevBuf cd, rq, pid, pdist, cand, err, ubout, scnt, cand2;
   RBQ_CHECK(cd.alloc(sizeof(float) * qchunk * K, s));
   RBQ_CHECK(rq.alloc(sizeof(float) * qchunk * dpad, s));
   RBQ_CHECK(pid.alloc(sizeof(int32_t) * qchunk * nprobe, s));
   RBQ_CHECK(pdist.alloc(sizeof(float) * qchunk * nprobe, s));
-  RBQ_CHECK(cand.alloc(sizeof(int4) * grid * a.cand_cap, s));
+  RBQ_CHECK(cand.alloc(sizeof(int4) * std::max<int64_t>(grid, qchunk * split) * a.cand_cap, s));
   RBQ_CHECK(err.alloc(sizeof(int), s));
+  if (split > 1) {
+    RBQ_CHECK(ubout.alloc(sizeof(uint32_t) * qchunk * split * a.k, s));
+    RBQ_CHECK(scnt.alloc(sizeof(int) * qchunk * split * 2, s));
+    RBQ_CHECK(cand2.alloc(sizeof(int4) * qchunk * a.cand_cap, s));
+    RBQ_CHECK(set_merge_attr());
+  }
   // dynamic query scheduling; with per-query probe counts, longest first
   DevBuf nextc, okey, order, ooff;
   RBQ_CHECK(nextc.alloc(sizeof(int), s));
@@ -1717,9 +1857,19 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
       if (T.n_surv) P.tr.n_surv = T.n_surv + q0;
       if (T.surv_ids) P.tr.surv_ids = T.surv_ids + q0 * T.surv_cap;
     }
-    const unsigned g = (unsigned)std::min<int64_t>(nqc, grid);
+    P.split = split;
+    if (split > 1) {
+      P.ub_out = ubout.as<uint32_t>();
+      P.slice_cnt = scnt.as<int>();
+      P.cand2 = cand2.as<int4>();
+    }
+    const unsigned g = (unsigned)std::min<int64_t>(nqc * split, split > 1 ? full : grid);
     fn<<<g, kThreads, smem, s>>>(P);
     RBQ_CUDA(cudaGetLastError());
+    if (split > 1) {
+      split_merge_kernel<<<(unsigned)std::min<int64_t>(nqc, full), kThreads, smem, s>>>(P);
+      RBQ_CUDA(cudaGetLastError());
+    }
     if (timing) {
       RBQ_CUDA(cudaEventRecord(ev[4], s));
       RBQ_CUDA(cudaEventSynchronize(ev[4]));
@@ -1756,6 +1906,7 @@ namespace {
 
 struct Carve {
   int64_t grid = 0, cap = 0, qchunk = 0;
+  size_t o_ubout = 0, o_scnt = 0, o_cand2 = 0;  // split mode (grid-sized)
   size_t o_cand = 0, o_cd = 0, o_rq = 0, o_pid = 0, o_pdist = 0, o_pnp = 0, o_fid = 0,
          o_fdist = 0, o_okey = 0, o_order = 0, o_ooff = 0, o_sortws = 0, end = 0;
 };
@@ -1790,6 +1941,10 @@ Carve carve_layout(const SearchArgs& a, int64_t grid, int64_t cap, int64_t qchun
   L.o_order = take(ordered ? sizeof(int32_t) * qchunk : 0);
   L.o_ooff = take(ordered ? sizeof(int32_t) * (nprobe + 2) : 0);
   L.o_sortws = take(ordered ? sizeof(int32_t) * counting_sort_ws_ints(qchunk, nprobe + 1) : 0);
+  // split mode: at most grid items (slices) and grid / 2 queries
+  L.o_ubout = take(a.allow_split ? sizeof(uint32_t) * grid * a.k : 0);
+  L.o_scnt = take(a.allow_split ? sizeof(int) * grid * 2 : 0);
+  L.o_cand2 = take(a.allow_split ? sizeof(int4) * (grid / 2) * cap : 0);
   L.end = o;
   return L;
 }
@@ -1941,16 +2096,30 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
       RBQ_CHECK(counting_sort_ws(okey, nqc, nprobe + 1, order, ooff, sortws, s));
       P.order = order;
     }
-    fn<<<(unsigned)std::min<int64_t>(nqc, grid), kThreads, smem, s>>>(P);
+    const int split = a.allow_split ? split_factor(a, nqc, grid, fs) : 1;
+    P.split = split;
+    if (split > 1) {
+      P.ub_out = reinterpret_cast<uint32_t*>(scratch + L.o_ubout);
+      P.slice_cnt = reinterpret_cast<int*>(scratch + L.o_scnt);
+      P.cand2 = reinterpret_cast<int4*>(scratch + L.o_cand2);
+    }
+    fn<<<(unsigned)std::min<int64_t>(nqc * split, grid), kThreads, smem, s>>>(P);
     RBQ_CUDA(cudaGetLastError());
+    if (split > 1) {
+      RBQ_CHECK(set_merge_attr());
+      split_merge_kernel<<<(unsigned)std::min<int64_t>(nqc, grid), kThreads, smem, s>>>(P);
+      RBQ_CUDA(cudaGetLastError());
+    }
     if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[4], s, cudaEventRecordExternal));
   }
   return RABITQ_OK;
 }
 
-int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scratch_bytes,
+int search_dev_prealloc(const SearchArgs& a_in, unsigned char* scratch, size_t scratch_bytes,
                         cudaStream_t s) {
-  if (a.nq == 0) return RABITQ_OK;
+  if (a_in.nq == 0) return RABITQ_OK;
+  SearchArgs a = a_in;
+  a.allow_split = 0;  // the fixed scratch has no room for the split buffers
   int* err = reinterpret_cast<int*>(scratch);
   RBQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));  // the flag must start at zero
   // one CTA per SM; the candidate lists take at most half of the scratch

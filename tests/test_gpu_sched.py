@@ -121,3 +121,22 @@ def test_plan_rejects_bad_arguments(R, tiny_idx):
         R.Plan(tiny_idx, 0, 4, 100)              # k < 1
     with pytest.raises(R.RabitqError):
         R.Plan(tiny_idx, 10, 4, 0)               # nq_max < 1
+
+
+def test_split_batches_equal_unsplit(R, tiny_workload, tiny_idx):
+    """Small batches split each query's probes over several CTAs and merge
+    them; the results equal those of a batch large enough not to split."""
+    _, queries = tiny_workload
+    big = np.concatenate([queries] * 6)            # 600 queries: no split
+    ref_ids, ref_dist = tiny_idx.search(big, 10, 8, scan_path=R.SCAN_POPC)
+    for nq in (1, 3, 50):
+        ids, dist = tiny_idx.search(queries[:nq], 10, 8, scan_path=R.SCAN_POPC)
+        assert np.array_equal(ids, ref_ids[:nq])
+        assert np.array_equal(dist.view(np.uint32), ref_dist[:nq].view(np.uint32))
+    # through a plan (CUDA graph) as well, k = 100 and every probe
+    ref_ids, ref_dist = tiny_idx.search(big, 100, 16, scan_path=R.SCAN_POPC)
+    plan = R.Plan(tiny_idx, 100, 16, 64)
+    for nq in (1, 7, 64):
+        ids, dist = plan.search(queries[:nq])
+        assert np.array_equal(ids, ref_ids[:nq])
+        assert np.array_equal(dist.view(np.uint32), ref_dist[:nq].view(np.uint32))
