@@ -808,11 +808,17 @@ constexpr int kPPT = 4;  // most pairs per thread per scan round (buffer sizing)
 // Pairs per thread per round: as many as the code registers allow.
 template <int WT>
 __host__ __device__ constexpr int pairs_per_thread() {
-  return WT == 0 ? 2 : (WT <= 4 ? 4 : (WT <= 8 ? 2 : 1));
+  return WT == 0 ? 2 : (WT <= 4 ? 2 : (WT <= 8 ? 2 : 1));
+}
+
+// Residency: 4 CTAs per SM for the short codes (D' <= 256), 3 otherwise.
+template <int WT>
+constexpr int fused_min_blocks() {
+  return (WT > 0 && WT <= 4) ? 4 : 3;
 }
 
 template <int WT, int BQT>
-__global__ void __launch_bounds__(kThreads, 3) fused_search_kernel(FusedParams P) {
+__global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search_kernel(FusedParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_ub_cnt, s_cand_cnt, s_top_cnt, s_surv, s_overflow;
   __shared__ float s_tau;
@@ -899,7 +905,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_search_kernel(FusedParams P
       // each thread takes PPT consecutive pairs per round (mostly of one
       // probe), so the probe's bit-planes and constants stay in registers
       // and are reloaded only when the thread's pairs move to another probe
-      constexpr bool kRegPlanes = WT > 0 && BQT > 0;
+      constexpr bool kRegPlanes = WT > 0 && WT <= 4 && BQT > 0;
       uint64_t rpl[kRegPlanes ? BQT * WT : 1];
       float4 rmt = make_float4(0.f, 0.f, 0.f, 0.f);
       int rsum = 0, rj = -1;
