@@ -43,7 +43,10 @@ class _Index(C.Structure):
     _fields_ = [("data", C.c_void_p), ("centroids", C.c_void_p), ("ptc", C.c_void_p),
                 ("P32", C.c_void_p), ("codes", C.c_void_p), ("factors", C.c_void_p),
                 ("bucket_off", C.c_void_p), ("bucket_ids", C.c_void_p),
-                ("n", C.c_int64), ("d", C.c_int32), ("dpad", C.c_int32), ("K", C.c_int32)]
+                ("n", C.c_int64), ("d", C.c_int32), ("dpad", C.c_int32), ("K", C.c_int32),
+                ("assign", C.c_void_p), ("metric", C.c_int32)]
+
+METRICS = {"l2": 0, "ip": 1, "cosine": 1}
 
 
 class _Params(C.Structure):
@@ -78,6 +81,10 @@ def lib():
             "orc_kmeans_init_ids": (None, [i64, i32, u64, vp]),
             "orc_kmeans": (None, [vp, i64, i32, i32, i32, i64, u64, vp, vp, vp, i32]),
             "orc_encode": (None, [vp, i64, i32, vp, vp, vp, i32, vp, vp, i32]),
+            "orc_encode_metric": (None, [vp, i64, i32, vp, vp, vp, i32, vp, vp, i32, i32]),
+            "orc_normalize_rows": (None, [vp, i64, i32, vp]),
+            "orc_bruteforce_ip": (None, [vp, i64, i32, vp, i64, i32, vp, vp, i32]),
+            "orc_estimate_codes": (None, [vp, vp, vp, i64, vp, i32, vp, i32]),
             "orc_quantize": (None, [vp, vp, i32, i32, u64, i32, i32, f32, f32, vp, vp, vp, vp]),
             "orc_bitplane_ip": (i32, [vp, vp, i32, i32]),
             "orc_estimate": (None, [i32, i32, vp, vp, vp]),
@@ -176,7 +183,7 @@ def kmeans(data, K: int, iters: int, seed: int, sample: int = 0, threads: int = 
     return cent, assign, adist
 
 
-def encode(data, centroids, assign, P32, threads: int = 1):
+def encode(data, centroids, assign, P32, threads: int = 1, metric: str = "l2"):
     data = _c(data, np.float32)
     centroids = _c(centroids, np.float32)
     assign = _c(assign, np.int32)
@@ -185,9 +192,17 @@ def encode(data, centroids, assign, P32, threads: int = 1):
     dpad = P32.shape[0]
     codes = np.zeros((n, dpad // 64), np.uint64)
     factors = np.zeros((n, 4), np.float32)
-    lib().orc_encode(_p(data), n, d, _p(centroids), _p(assign), _p(P32), dpad, _p(codes),
-                     _p(factors), threads)
+    lib().orc_encode_metric(_p(data), n, d, _p(centroids), _p(assign), _p(P32), dpad,
+                            _p(codes), _p(factors), METRICS[metric], threads)
     return codes, factors
+
+
+def normalize_rows(x) -> np.ndarray:
+    """Unit rows (canonical FP32 norm; zero rows stay zero): footnote of §6."""
+    x = _c(x, np.float32)
+    out = np.zeros_like(x)
+    lib().orc_normalize_rows(_p(x), x.shape[0], x.shape[1], _p(out))
+    return out
 
 
 def quantize(rq, ptc, bq: int, seed: int, qid: int, cid: int, nq2: float, eps0: float):
@@ -237,6 +252,17 @@ def bruteforce_knn(data, Q, k: int, allowed=None, threads: int = 1):
     return ids, dist
 
 
+def bruteforce_ip(data, Q, k: int, threads: int = 1):
+    """Exact k largest inner products (canonical FP32 dot, ties by id)."""
+    data = _c(data, np.float32)
+    Q = _c(Q, np.float32)
+    ids = np.zeros((Q.shape[0], k), np.int64)
+    ip = np.zeros((Q.shape[0], k), np.float32)
+    lib().orc_bruteforce_ip(_p(data), data.shape[0], data.shape[1], _p(Q), Q.shape[0], k,
+                            _p(ids), _p(ip), threads)
+    return ids, ip
+
+
 def estimator_fp64(P, o, q):
     P = _c(P, np.float64)
     o = _c(o, np.float64)
@@ -260,8 +286,13 @@ class OracleIndex:
     """
 
     def __init__(self, data, K: int, seed: int, dpad: int | None = None, iters: int = 10,
-                 sample: int = 0, centroids=None, P=None, threads: int = 1, _arrays=None):
-        self.data = _c(data, np.float32)
+                 sample: int = 0, centroids=None, P=None, threads: int = 1, _arrays=None,
+                 metric: str = "l2"):
+        if metric not in METRICS:
+            raise ValueError(f"metric must be one of {sorted(METRICS)}")
+        self.metric = metric
+        # cosine: the index holds unit vectors and queries are made unit (§6 footnote)
+        self.data = normalize_rows(data) if metric == "cosine" else _c(data, np.float32)
         n, d = self.data.shape
         self.n, self.d, self.K = n, d, K
         self.dpad = dpad or code_length(d)
@@ -280,16 +311,18 @@ class OracleIndex:
             self.P = sample_rotation(seed, self.dpad) if P is None else _c(P, np.float64)
             self.P32 = self.P.astype(np.float32)
             self.codes, self.factors = encode(self.data, self.centroids, self.assign, self.P32,
-                                              threads)
+                                              threads, metric)
         self.ptc = rotate(self.centroids, self.P32)
         order = np.lexsort((np.arange(n), self.assign))
         self.bucket_ids = order.astype(np.int32)
         counts = np.bincount(self.assign, minlength=K)
         self.bucket_off = np.zeros(K + 1, np.int32)
         self.bucket_off[1:] = np.cumsum(counts)
+        self.assign = _c(self.assign, np.int32)
         self._s = _Index(_p(self.data), _p(self.centroids), _p(self.ptc), _p(self.P32),
                          _p(self.codes), _p(self.factors), _p(self.bucket_off),
-                         _p(self.bucket_ids), n, d, self.dpad, K)
+                         _p(self.bucket_ids), n, d, self.dpad, K, _p(self.assign),
+                         METRICS[metric])
 
     @classmethod
     def from_arrays(cls, data, centroids, P, assign, codes, factors):
@@ -299,9 +332,15 @@ class OracleIndex:
                _c(codes, np.uint64), _c(factors, np.float32))
         return cls(data, K=arr[0].shape[0], seed=0, dpad=arr[1].shape[0], _arrays=arr)
 
+    def _queries(self, Q):
+        Q = _c(Q, np.float32)
+        return normalize_rows(Q) if self.metric == "cosine" else Q
+
     def search(self, Q, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9, seed: int = 3,
                mode: int = 0, threads: int = 1):
-        Q = _c(Q, np.float32)
+        """Top-k ids and exact values: squared distances ascending (l2), or
+        inner products / cosines descending (ip, cosine)."""
+        Q = self._queries(Q)
         nq = Q.shape[0]
         par = _Params(k, nprobe, bq, mode, eps0, seed)
         ids = np.zeros((nq, k), np.int64)
@@ -312,7 +351,7 @@ class OracleIndex:
     def trace(self, q, qid: int, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
               seed: int = 3):
         """Every intermediate of one query's search (mode 0)."""
-        q = _c(q, np.float32)
+        q = self._queries(np.atleast_2d(q))[0]
         nprobe = min(nprobe, self.K)
         W = self.dpad // 64
         sizes = np.diff(self.bucket_off)
@@ -338,3 +377,23 @@ class OracleIndex:
         t["tau"], t["tau_ub"], t["tau1"] = tr.tau, tr.tau_ub, tr.tau1
         t["ids"], t["dist"] = ids, dist
         return t
+
+    def estimate(self, Q, ids, bq: int = 4, eps0: float = 1.9, seed: int = 3,
+                 threads: int = 1):
+        """Single-code estimates (§3.3.2, first case): for query i and code
+        ids[i, j] the estimate and its lower / upper bound, shape (nq, m, 3);
+        the query is quantized against the code's own cluster with stream
+        qid = i. Squared distances (l2) or inner products (ip, cosine); -1
+        ids give NaNs."""
+        Q = self._queries(Q)
+        ids = _c(ids, np.int64)
+        if ids.ndim != 2 or ids.shape[0] != Q.shape[0]:
+            raise ValueError("ids must be nq x m")
+        if ((ids < -1) | (ids >= self.n)).any():
+            raise ValueError("ids out of range")
+        m = ids.shape[1]
+        out = np.zeros((Q.shape[0], m, 3), np.float32)
+        par = _Params(0, 0, bq, 0, eps0, seed)
+        lib().orc_estimate_codes(C.byref(self._s), C.byref(par), _p(Q), Q.shape[0], _p(ids), m,
+                                 _p(out), threads)
+        return out

@@ -27,7 +27,14 @@
  * Parity status: k-means (orc_kmeans) has no external pin -- parity
  * unpinned; its invariants (argmin assignment, mean update, non-increasing
  * objective) are tested instead. Every other function is pinned by the
- * tests in tests/test_oracle_pins.py.
+ * tests in tests/test_oracle_pins.py (the inner-product / cosine metric and
+ * the single-code estimator in tests/test_oracle_ip_pins.py).
+ *
+ * Metrics: squared Euclidean distance (the paper's setting) and the inner
+ * product of the paper's closing footnote (§6), which also gives the cosine
+ * similarity on unit vectors. Internally an inner-product search ranks by
+ * the score -<o_r, q_r> (smaller is better), so the bounds, thresholds and
+ * re-ranking rule are those of the distance search.
  */
 #include <math.h>
 #include <pthread.h>
@@ -221,6 +228,8 @@ ORC_API void orc_sample_rotation(uint64_t seed, int32_t dpad, double* P) {
 /* ------------------------------------------------------------------------ */
 /* Canonical FP32 kernels of the numerics contract.                          */
 /* ------------------------------------------------------------------------ */
+enum { ORC_METRIC_L2 = 0, ORC_METRIC_IP = 1 };
+
 static float sqdist32(const float* a, const float* b, int32_t d) {
   float s = 0.0f;
   for (int32_t i = 0; i < d; ++i) {
@@ -228,6 +237,24 @@ static float sqdist32(const float* a, const float* b, int32_t d) {
     s = fmaf(t, t, s);
   }
   return s;
+}
+
+static float dot32(const float* a, const float* b, int32_t d) {
+  float s = 0.0f;
+  for (int32_t i = 0; i < d; ++i) s = fmaf(a[i], b[i], s);
+  return s;
+}
+
+/* Unit vectors for the cosine similarity (footnote of §6: the cosine of two
+ * vectors equals the inner product of their unit vectors):
+ * out_r = x_r / ||x_r||, ||x_r|| = sqrt(canonical dot(x_r, x_r)); a zero row
+ * stays zero. */
+ORC_API void orc_normalize_rows(const float* x, int64_t n, int32_t d, float* out) {
+  for (int64_t r = 0; r < n; ++r) {
+    const float* xr = x + r * d;
+    float nrm = sqrtf(dot32(xr, xr, d));
+    for (int32_t i = 0; i < d; ++i) out[r * d + i] = (nrm > 0.0f) ? xr[i] / nrm : xr[i];
+  }
 }
 
 /* out[r*nb + c] = canonical squared distance between a_r and b_c. */
@@ -370,10 +397,19 @@ ORC_API void orc_kmeans(const float* data, int64_t n, int32_t d, int32_t K, int3
  *   F3    = n_o sqrt(1 - a_o^2) / a_o    (coefficient of the error bound)
  *   G     = 2 popcount(bits) - dpad      (as float)
  * Codes are dpad/64 words per vector, bit k in word k>>6 at position k&63.
- * factors[4*n + {0,1,2,3}] = {F1, F2, F3, G}.                              */
+ * factors[4*n + {0,1,2,3}] = {F1, F2, F3, G}.
+ *
+ * Inner-product metric (footnote of §6): <o_r, q_r> = ||o_r - c|| ||q_r - c||
+ * <o, q> + <o_r - c, c> + <q_r, c>, so the score -<o_r, q_r> takes the form
+ * (F1 + add) - F2 xq of the distance estimator with
+ *   F1 = -<o_r - c, c>  (canonical dot of the FP32 residual and c)
+ *   F2 = n_o / a_o      (half the distance coefficient: exact scaling)
+ *   F3 = n_o sqrt(1 - a_o^2) / (2 a_o)   (half: the score's bound is half
+ *                                          the distance's)
+ * and add = -<q_r, c> per (query, cluster).                                */
 typedef struct {
   const float* data; int32_t d; const float* centroids; const int32_t* assign;
-  const float* P32; int32_t dpad; uint64_t* codes; float* factors;
+  const float* P32; int32_t dpad; uint64_t* codes; float* factors; int32_t metric;
 } encode_ctx;
 
 static void encode_rows(void* vc, int64_t v0, int64_t v1) {
@@ -416,6 +452,12 @@ static void encode_rows(void* vc, int64_t v0, int64_t v1) {
     float sq = sqrtf(om);
     float num = n_o * sq;
     float F3 = num / a_o;
+    if (E->metric == ORC_METRIC_IP) {
+      float oc = dot32(res, c, d);
+      F1 = -oc;
+      F2 = 0.5f * F2;
+      F3 = 0.5f * F3;
+    }
     factors[4 * v + 0] = F1;
     factors[4 * v + 1] = F2;
     factors[4 * v + 2] = F3;
@@ -425,11 +467,19 @@ static void encode_rows(void* vc, int64_t v0, int64_t v1) {
   free(r);
 }
 
+ORC_API void orc_encode_metric(const float* data, int64_t n, int32_t d, const float* centroids,
+                               const int32_t* assign, const float* P32, int32_t dpad,
+                               uint64_t* codes, float* factors, int32_t metric,
+                               int32_t threads) {
+  encode_ctx E = {data, d, centroids, assign, P32, dpad, codes, factors, metric};
+  parallel_rows(n, threads, encode_rows, &E);
+}
+
 ORC_API void orc_encode(const float* data, int64_t n, int32_t d, const float* centroids,
                         const int32_t* assign, const float* P32, int32_t dpad,
                         uint64_t* codes, float* factors, int32_t threads) {
-  encode_ctx E = {data, d, centroids, assign, P32, dpad, codes, factors};
-  parallel_rows(n, threads, encode_rows, &E);
+  orc_encode_metric(data, n, d, centroids, assign, P32, dpad, codes, factors, ORC_METRIC_L2,
+                    threads);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -555,6 +605,8 @@ typedef struct {
   const int32_t* bucket_ids;/* n: ids of bucket c in ascending order */
   int64_t n;
   int32_t d, dpad, K;
+  const int32_t* assign;    /* n: cluster of each id                 */
+  int32_t metric;           /* ORC_METRIC_L2 or ORC_METRIC_IP        */
 } orc_index;
 
 typedef struct {
@@ -631,13 +683,26 @@ ORC_API void orc_select(const float* dist, int64_t nrows, int32_t K, int32_t nse
   free(ti);
 }
 
+/* Exact score of (q, id): the canonical squared distance, or -<q, o> for
+ * the inner-product metric. */
+static float exact_score(const orc_index* X, const float* q, int32_t id) {
+  const float* o = X->data + (int64_t)id * X->d;
+  return X->metric == ORC_METRIC_IP ? -dot32(q, o, X->d) : sqdist32(q, o, X->d);
+}
+
+/* Centroid score: ||q - c||^2, or -<q, c> (probe the largest inner products). */
+static float centroid_score(const orc_index* X, const float* q, int32_t c) {
+  const float* cc = X->centroids + (int64_t)c * X->d;
+  return X->metric == ORC_METRIC_IP ? -dot32(q, cc, X->d) : sqdist32(q, cc, X->d);
+}
+
 static void search_one(const orc_index* X, const orc_params* p, const float* q, int32_t qid,
                        int64_t* out_ids, float* out_dist, orc_trace* tr, float* scratch_cd,
                        int32_t* scratch_ids, float* scratch_pd) {
   const int32_t d = X->d, dpad = X->dpad, K = X->K, W = dpad / 64;
   const int32_t nprobe = p->nprobe < K ? p->nprobe : K;
   /* centroid distances and the nprobe nearest (paper §4) */
-  for (int32_t c = 0; c < K; ++c) scratch_cd[c] = sqdist32(q, X->centroids + (int64_t)c * d, d);
+  for (int32_t c = 0; c < K; ++c) scratch_cd[c] = centroid_score(X, q, c);
   orc_select(scratch_cd, 1, K, nprobe, scratch_ids, scratch_pd);
   /* inverse rotation of the raw query (Alg. 2 step 1, by linearity) */
   float* rq = (float*)malloc(sizeof(float) * (size_t)dpad);
@@ -665,8 +730,13 @@ static void search_one(const orc_index* X, const orc_params* p, const float* q, 
   for (int32_t j = 0; j < nprobe; ++j) {
     int32_t c = scratch_ids[j];
     int32_t sq;
-    orc_quantize(rq, X->ptc + (int64_t)c * dpad, dpad, p->bq, p->seed, qid, c, scratch_pd[j],
+    /* ||q_r - c||^2 scales the bound; the estimator's additive constant
+     * (meta[3]) is the centroid score: ||q_r - c||^2, or -<q_r, c> */
+    float nq2 = (X->metric == ORC_METRIC_IP)
+                    ? sqdist32(q, X->centroids + (int64_t)c * d, d) : scratch_pd[j];
+    orc_quantize(rq, X->ptc + (int64_t)c * dpad, dpad, p->bq, p->seed, qid, c, nq2,
                  p->eps0, NULL, planes, &sq, meta);
+    meta[3] = scratch_pd[j];
     if (tr) {
       memcpy(tr->planes + (int64_t)j * p->bq * W, planes, sizeof(uint64_t) * (size_t)p->bq * W);
       tr->sum_qu[j] = sq;
@@ -693,7 +763,7 @@ static void search_one(const orc_index* X, const orc_params* p, const float* q, 
          * distance of the current k-th nearest neighbour (§4) */
         float kth = (cnt == k) ? td[k - 1] : INFINITY;
         if (!(est[1] > kth)) {
-          float ex = sqdist32(q, X->data + (int64_t)id * d, d);
+          float ex = exact_score(X, q, id);
           topk_insert(td, ti, &cnt, k, ex, id);
         }
       }
@@ -743,7 +813,7 @@ static void search_one(const orc_index* X, const orc_params* p, const float* q, 
     float* pex = (float*)malloc(sizeof(float) * (size_t)(m + 1));
     for (int32_t j = 0; j < pc; ++j) {
       in_set[pix[j]] = 1;
-      pex[j] = sqdist32(q, X->data + (int64_t)pi[j] * d, d);
+      pex[j] = exact_score(X, q, pi[j]);
     }
     if (pc >= k) {
       qsort(pex, (size_t)pc, sizeof(float), cmp_float);
@@ -758,7 +828,7 @@ static void search_one(const orc_index* X, const orc_params* p, const float* q, 
       if (in_set[i]) surv[ns++] = pid[i];
     qsort(surv, (size_t)ns, sizeof(int32_t), cmp_int);
     for (int32_t i = 0; i < ns; ++i) {
-      float ex = sqdist32(q, X->data + (int64_t)surv[i] * d, d);
+      float ex = exact_score(X, q, surv[i]);
       topk_insert(td, ti, &cnt, k, ex, surv[i]);
     }
     if (tr) {
@@ -773,9 +843,12 @@ static void search_one(const orc_index* X, const orc_params* p, const float* q, 
     }
     free(surv); free(in_set); free(pd); free(pi); free(pix); free(pex);
   }
+  /* inner products are returned as <o_r, q_r> (descending), -inf pads */
+  const int neg = X->metric == ORC_METRIC_IP;
   for (int32_t j = 0; j < k; ++j) {
     out_ids[j] = (j < cnt) ? ti[j] : -1;
-    out_dist[j] = (j < cnt) ? td[j] : INFINITY;
+    float v = (j < cnt) ? td[j] : INFINITY;
+    out_dist[j] = neg ? -v : v;
   }
   free(rq); free(pid); free(pest); free(planes); free(td); free(ti);
 }
@@ -837,7 +910,7 @@ ORC_API void orc_search(const orc_index* X, const orc_params* p, const float* Q,
 
 typedef struct {
   const float* data; int64_t n; int32_t d; const float* Q; int32_t k; const uint8_t* allowed;
-  int64_t* out_ids; float* out_dist;
+  int64_t* out_ids; float* out_dist; int32_t metric;
 } bf_ctx;
 
 static void bf_rows(void* vc, int64_t q0, int64_t q1) {
@@ -850,11 +923,14 @@ static void bf_rows(void* vc, int64_t q0, int64_t q1) {
     const uint8_t* al = B->allowed ? B->allowed + i * B->n : NULL;
     for (int64_t v = 0; v < B->n; ++v) {
       if (al && !al[v]) continue;
-      topk_insert(td, ti, &cnt, k, sqdist32(B->Q + i * d, B->data + v * d, d), (int32_t)v);
+      float sc = (B->metric == ORC_METRIC_IP) ? -dot32(B->Q + i * d, B->data + v * d, d)
+                                              : sqdist32(B->Q + i * d, B->data + v * d, d);
+      topk_insert(td, ti, &cnt, k, sc, (int32_t)v);
     }
     for (int32_t j = 0; j < k; ++j) {
       B->out_ids[i * k + j] = (j < cnt) ? ti[j] : -1;
-      B->out_dist[i * k + j] = (j < cnt) ? td[j] : INFINITY;
+      float v = (j < cnt) ? td[j] : INFINITY;
+      B->out_dist[i * k + j] = (B->metric == ORC_METRIC_IP) ? -v : v;
     }
   }
   free(td);
@@ -866,8 +942,80 @@ static void bf_rows(void* vc, int64_t q0, int64_t q1) {
 ORC_API void orc_bruteforce_knn(const float* data, int64_t n, int32_t d, const float* Q,
                                 int64_t nq, int32_t k, const uint8_t* allowed,
                                 int64_t* out_ids, float* out_dist, int32_t threads) {
-  bf_ctx B = {data, n, d, Q, k, allowed, out_ids, out_dist};
+  bf_ctx B = {data, n, d, Q, k, allowed, out_ids, out_dist, ORC_METRIC_L2};
   parallel_rows(nq, threads, bf_rows, &B);
+}
+
+/* Exact k largest inner products (canonical FP32 dot, ranked by the score
+ * -<q, o> with ties by id); out_ip holds <q, o>, -inf pads. */
+ORC_API void orc_bruteforce_ip(const float* data, int64_t n, int32_t d, const float* Q,
+                               int64_t nq, int32_t k, int64_t* out_ids, float* out_ip,
+                               int32_t threads) {
+  bf_ctx B = {data, n, d, Q, k, NULL, out_ids, out_ip, ORC_METRIC_IP};
+  parallel_rows(nq, threads, bf_rows, &B);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Single-code estimator (§3.3.2, the first case: one query and one code at */
+/* a time, as a graph index would visit them).                              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const orc_index* X; const orc_params* p; const float* Q; const int64_t* ids; int32_t m;
+  float* out;
+} est_ctx;
+
+static void est_rows(void* vc, int64_t i0, int64_t i1) {
+  est_ctx* E = (est_ctx*)vc;
+  const orc_index* X = E->X;
+  const orc_params* p = E->p;
+  const int32_t d = X->d, dpad = X->dpad, W = dpad / 64;
+  float* rq = (float*)malloc(sizeof(float) * (size_t)dpad);
+  uint64_t* planes = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)p->bq * W);
+  for (int64_t i = i0; i < i1; ++i) {
+    const float* q = E->Q + i * d;
+    orc_rotate(q, 1, d, X->P32, dpad, rq);
+    for (int32_t j = 0; j < E->m; ++j) {
+      float* o = E->out + 3 * (i * E->m + j);
+      int64_t id = E->ids[i * E->m + j];
+      if (id < 0) {
+        o[0] = o[1] = o[2] = NAN;
+        continue;
+      }
+      int32_t c = X->assign[id];
+      float nq2 = sqdist32(q, X->centroids + (int64_t)c * d, d);
+      float meta[6];
+      int32_t sq;
+      orc_quantize(rq, X->ptc + (int64_t)c * dpad, dpad, p->bq, p->seed, (int32_t)i, c, nq2,
+                   p->eps0, NULL, planes, &sq, meta);
+      meta[3] = centroid_score(X, q, c);
+      int32_t ip = orc_bitplane_ip(X->codes + id * W, planes, W, p->bq);
+      float est[3];
+      orc_estimate(ip, sq, X->factors + 4 * id, meta, est);
+      if (X->metric == ORC_METRIC_IP) {
+        o[0] = -est[0];
+        o[1] = -est[2];
+        o[2] = -est[1];
+      } else {
+        o[0] = est[0];
+        o[1] = est[1];
+        o[2] = est[2];
+      }
+    }
+  }
+  free(rq);
+  free(planes);
+}
+
+/* For query i (quantization stream qid = i) and code ids[i m + j]: quantize
+ * the rotated query against the code's own cluster c (cid = c) and evaluate
+ * the estimator with its bound. out[3 (i m + j) + {0, 1, 2}] = {estimate,
+ * lower bound, upper bound} of the squared distance, or of <o_r, q_r> for the
+ * inner-product metric; an id of -1 gives three NaNs. */
+ORC_API void orc_estimate_codes(const orc_index* X, const orc_params* p, const float* Q,
+                                int64_t nq, const int64_t* ids, int32_t m, float* out,
+                                int32_t threads) {
+  est_ctx E = {X, p, Q, ids, m, out};
+  parallel_rows(nq, threads, est_rows, &E);
 }
 
 /* ------------------------------------------------------------------------ */
