@@ -14,6 +14,12 @@ scan, error-bound prune, exact re-rank, top-k), replayed as one CUDA graph
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+--metric ip|cosine runs the same line on an inner-product / cosine index
+(the closing footnote of the paper, §6) with exact maximum-inner-product
+ground truth (no learned leg: the predictor's features are distances).
+--study estimate times the single-code estimator (§3.3.2, first case) on
+scattered ids.
+
 --impl reference times the CPU oracle on the host cores (the only other
 place this script runs oracle/ code besides the cpu_baseline leg).
 """
@@ -35,6 +41,7 @@ sys.path.insert(0, ROOT)
 from paper_2405_12497_gb300 import synth  # noqa: E402
 
 NPROBES = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256)
+NPROBES_WIDE = NPROBES + (384, 512, 768, 1024)  # inner products need more probes
 WORKLOADS = {"sift": synth.SIFT_LIKE, "gist": synth.GIST_LIKE, "deep": synth.DEEP_LIKE}
 TARGET = 0.95
 METRIC = "QPS at recall@100=0.95 on 1 GB300; code-scan GB/s vs HBM peak"
@@ -55,7 +62,11 @@ def recall_at(ids: np.ndarray, gt: np.ndarray) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling during the timed region: samples
+    every 25 ms, stamped on arrival; the sampler is running (first sample in)
+    before the region starts, and the summary keeps the samples that arrived
+    between mark_start() and mark_end() (the nearest later one if the region
+    was shorter than a sampling period)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -65,22 +76,36 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            limit = time.perf_counter() + 5.0
+            while not self.lines and time.perf_counter() < limit:
+                time.sleep(0.01)
         except OSError:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
+        limit = self.t1 + 1.0
+        while self.proc and time.perf_counter() < limit and \
+                not any(t >= self.t1 for t, _ in self.lines):
+            time.sleep(0.005)
 
     def __exit__(self, *exc):
         if self.proc:
@@ -93,7 +118,12 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        lines = self.lines
+        if self.t0 is not None and self.t1 is not None:
+            inside = [(t, ln) for t, ln in lines if self.t0 <= t <= self.t1]
+            after = [(t, ln) for t, ln in lines if t > self.t1][:1]
+            lines = inside or after
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -108,7 +138,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": 25}
 
 
 # ------------------------------------------------------------------ ours
@@ -139,23 +169,30 @@ def run_ours(args, rank, world):
     qd = torch.from_numpy(queries).to(dev)
     t0 = time.time()
     G = rabitq.Index.build(dd, w.n_clusters, seed=2, kmeans_iters=w.kmeans_iters,
-                           kmeans_sample=w.kmeans_sample, code_bits=w.code_bits)
+                           kmeans_sample=w.kmeans_sample, code_bits=w.code_bits,
+                           metric=args.metric)
     torch.cuda.synchronize()
     build_s = time.time() - t0
-    gt = exact_knn(dd, qd, w.k)
+    if args.metric == "l2":
+        gt = exact_knn(dd, qd, w.k)
+    else:
+        args.no_learned = True  # learned probe counts need distances
+        gt = exact_mips(dd, qd, w.k, cosine=args.metric == "cosine")
+    tag = "" if args.metric == "l2" else "-" + args.metric  # traffic records are per metric
 
     # nprobe sweep (untimed): smallest nprobe with mean recall@100 >= 0.95
     sweep = {}
     chosen = args.nprobe
     if chosen is None:
-        for npb in NPROBES:
+        grid = NPROBES if args.metric == "l2" else NPROBES_WIDE
+        for npb in grid:
             ids, _ = G.search(qd, w.k, npb, bq=w.bq, eps0=w.eps0)
             sweep[npb] = recall_at(ids.cpu().numpy(), gt)
             if sweep[npb] >= TARGET:
                 chosen = npb
                 break
         if chosen is None:
-            chosen = NPROBES[-1]
+            chosen = grid[-1]
     ids, _ = G.search(qd, w.k, chosen, bq=w.bq, eps0=w.eps0)
     rec = recall_at(ids.cpu().numpy(), gt)
     sweep[chosen] = rec
@@ -168,7 +205,8 @@ def run_ours(args, rank, world):
     plan = rabitq.Plan(G, w.k, chosen, w.nq, bq=w.bq, eps0=w.eps0, stats=True)
     fixed = time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=True, name="fixed")
     fixed.update({"nprobe": chosen, "nprobe_sweep": {str(a): round(b, 4) for a, b in sweep.items()}})
-    fixed["roofline"] = roofline(G, qd, w, chosen, None, fixed["fused_ms"], hbm, src, "fixed")
+    fixed["roofline"] = roofline(G, qd, w, chosen, None, fixed["fused_ms"], hbm, src,
+                                 "fixed" + tag)
     fixed["scan_gbs"] = fixed["roofline"].pop("scan_gbs")
     fixed["ns_per_code"] = fixed["roofline"].pop("ns_per_code")
     fixed["gpu_launches_per_step"] = 4
@@ -221,7 +259,7 @@ def run_ours(args, rank, world):
         "data": f"synthetic ({w.name} shape, seeded)",
         "config": {"workload": w.name, "mode": f"{best_name} nprobe", "n": w.n, "d": w.d,
                    "nq_per_gpu": w.nq, "n_clusters": w.n_clusters, "k": w.k, "bq": w.bq,
-                   "eps0": w.eps0, "recall_at_100": round(rec, 4),
+                   "eps0": w.eps0, "recall_at_100": round(rec, 4), "similarity": args.metric,
                    "rotation": "fp32", "scan": "popcount",
                    "launch": "CUDA graph replay of the whole search (rabitq_plan_run)",
                    "l2": "flushed before each step",
@@ -245,7 +283,7 @@ def run_ours(args, rank, world):
         res["rotation_precision"] = precision
     if cold is not None:
         res["cold_scan"] = cold
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.metric == "l2":
         res["cpu_baseline"] = cpu_baseline(G, data, queries, w, chosen, budget_s=args.cpu_budget)
     if rank == 0:
         print(json.dumps(res), flush=True)
@@ -294,6 +332,33 @@ def exact_knn(dd, qd, k):
         ex = ((xc - q.double()[:, None, :]) ** 2).sum(-1)       # exact FP64
         order = torch.argsort(ci, dim=1)                        # ids ascending, then stable
         ci, key = torch.gather(ci, 1, order), torch.gather(ex, 1, order)
+        top = torch.sort(key, dim=1, stable=True).indices[:, :k]
+        out.append(torch.gather(ci, 1, top))
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return torch.cat(out).cpu().numpy()
+
+
+def exact_mips(dd, qd, k, cosine=False):
+    """Exact k largest inner products (the ground truth of recall for the
+    inner-product metric; cosine: of the unit vectors): FP32 products (TF32
+    off) pick 2k + 64 candidates per query, whose FP64 products decide the
+    top k (ties by id)."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    if cosine:
+        dd = dd / dd.double().norm(dim=1, keepdim=True).clamp_min(1e-30).float()
+        qd = qd / qd.double().norm(dim=1, keepdim=True).clamp_min(1e-30).float()
+    n, d = dd.shape
+    cand = 2 * k + 64
+    step = max(1, min(1000, int(4e9 // (4 * n))))
+    out = []
+    for s in range(0, qd.shape[0], step):
+        q = qd[s:s + step]
+        ci = torch.topk(q @ dd.T, min(cand, n), largest=True).indices
+        ex = (dd[ci].double() * q.double()[:, None, :]).sum(-1)      # exact FP64
+        order = torch.argsort(ci, dim=1)
+        ci, key = torch.gather(ci, 1, order), torch.gather(-ex, 1, order)
         top = torch.sort(key, dim=1, stable=True).indices[:, :k]
         out.append(torch.gather(ci, 1, top))
     torch.backends.cuda.matmul.allow_tf32 = prev
@@ -431,6 +496,8 @@ def time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=False, name="
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    if sampler:
+        sampler.mark_start()
     for _ in range(args.steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -443,6 +510,8 @@ def time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=False, name="
         ms.append(e0.elapsed_time(e1))
         stages.append(plan.stats())
     torch.cuda.synchronize()
+    if sampler:
+        sampler.mark_end()
     if dist:
         dist.barrier()
     if sampler:
@@ -684,6 +753,68 @@ def run_accuracy_study(args):
     print(json.dumps(out), flush=True)
 
 
+def run_estimate_study(args):
+    """The single-code estimator (§3.3.2, first case: one query against one
+    code, as a graph index visits neighbours) on the SIFT-shaped 1M index:
+    nq queries x m ids each, drawn uniformly (scattered codes, every one in
+    its own cluster), through rabitq_estimate with device buffers, L2
+    flushed before each timed call, CUDA events on the stream. Per estimate
+    the kernel quantizes the query against the code's cluster (D' Philox
+    draws and roundings), reads one code (D'/8 bytes) and its factors (16
+    bytes) and evaluates the estimator; the batched bucket scan amortizes the
+    quantization over a whole bucket instead."""
+    import torch
+    from paper_2405_12497_gb300 import build as B
+    from paper_2405_12497_gb300 import rabitq
+    B.build()
+    w = WORKLOADS[args.workload]
+    n = args.n or w.n
+    nq = args.nq or 10_000
+    data, queries = synth.make(w, n=n, nq=nq)
+    dev = torch.device("cuda", 0)
+    dd = torch.from_numpy(data).to(dev)
+    qd = torch.from_numpy(queries).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {"study": "single-code estimator", "workload": w.name, "n": n, "d": w.d,
+           "n_clusters": w.n_clusters, "nq": nq, "bq": w.bq, "eps0": w.eps0,
+           "l2": "flushed before each call", "rows": []}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    for metric in ("l2", "ip"):
+        G = rabitq.Index.build(dd, w.n_clusters, seed=2, kmeans_iters=w.kmeans_iters,
+                               kmeans_sample=w.kmeans_sample, code_bits=w.code_bits,
+                               metric=metric)
+        for m in (32, 128):
+            ids = torch.randint(0, n, (nq, m), generator=gen, device=dev, dtype=torch.int64)
+            for _ in range(args.warmup):
+                out = G.estimate(qd, ids, bq=w.bq, eps0=w.eps0)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                out = G.estimate(qd, ids, bq=w.bq, eps0=w.eps0)
+                b.record()
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            t = float(np.median(ms))
+            o = out[..., 0].double()
+            x = dd[ids].double()
+            true = ((x - qd.double()[:, None, :]) ** 2).sum(-1) if metric == "l2" else \
+                (x * qd.double()[:, None, :]).sum(-1)
+            inside = ((out[..., 1].double() <= true) & (true <= out[..., 2].double())).float()
+            res["rows"].append({
+                "metric": metric, "m": m, "estimates": nq * m, "ms": round(t, 4),
+                "estimates_per_s": round(nq * m / (t / 1e3), 1),
+                "ns_per_estimate": round(t * 1e6 / (nq * m), 3),
+                "bound_coverage": round(float(inside.mean()), 4),
+                "mean_abs_err": round(float((o - true).abs().mean()), 4)})
+            del x, true
+        G.free()
+    print(json.dumps(res), flush=True)
+
+
 def run_serving_study(args):
     """A serving loop on one GPU: three resident indices (1M x 128 SIFT-shaped,
     1M x 420 and 1M x 960 GIST-shaped recipes, K = 4096), each with a trained
@@ -812,7 +943,9 @@ def main():
     ap.add_argument("--train-nq", type=int, default=100_000)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--nprobe-max", type=int, default=256)
-    ap.add_argument("--study", default=None, choices=["accuracy", "serving"],
+    ap.add_argument("--metric", default="l2", choices=["l2", "ip", "cosine"],
+                    help="similarity of the index (l2: the paper's squared distance)")
+    ap.add_argument("--study", default=None, choices=["accuracy", "serving", "estimate"],
                     help="instead of the benchmark line, print the distance-estimation "
                          "accuracy study (one JSON line)")
     args = ap.parse_args()
@@ -831,6 +964,10 @@ def main():
     if args.study == "serving":
         if rank == 0:
             run_serving_study(args)
+        return
+    if args.study == "estimate":
+        if rank == 0:
+            run_estimate_study(args)
         return
     run_ours(args, rank, world)
 

@@ -48,6 +48,15 @@ typedef enum {
  * FP32 accumulation. */
 enum { RABITQ_ROT_FP32 = 0, RABITQ_ROT_TF32 = 1, RABITQ_ROT_BF16 = 2 };
 
+/* Similarity of an index (fixed at build). L2: squared Euclidean distance,
+ * the paper's setting. IP: inner product, by the decomposition of the
+ * paper's closing footnote (§6): <o_r, q_r> = ||o_r - c|| ||q_r - c|| <o, q>
+ * + <o_r - c, c> + <q_r, c>, where <o, q> of the unit residuals is estimated
+ * exactly as for distances (same code, same bound, halved). COSINE: the
+ * inner product of unit vectors (data normalized at build, queries at
+ * search). IP and COSINE probe the clusters with the largest <q_r, c>. */
+enum { RABITQ_METRIC_L2 = 0, RABITQ_METRIC_IP = 1, RABITQ_METRIC_COSINE = 2 };
+
 /* Bucket-scan implementation of <x_b, q_u> (§3.3.2): bit-plane popcount or
  * an exact integer product on tensor cores; AUTO picks per shape. */
 enum { RABITQ_SCAN_AUTO = 0, RABITQ_SCAN_POPC = 1, RABITQ_SCAN_TC = 2 };
@@ -60,6 +69,7 @@ typedef struct {
   void* stream;             /* cudaStream_t to run on; NULL = the legacy stream */
   const float* centroids;   /* optional K x d centroids (host or device, as
                                `data`); when given, k-means is skipped          */
+  int32_t metric;           /* RABITQ_METRIC_* (default L2)                     */
 } rabitq_build_opts;
 
 typedef struct {
@@ -107,7 +117,11 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
  *   bq        1..8 bits of the randomized query quantization (§3.3.1)
  *   eps0      >= 0, confidence parameter of the error bound (Theorem 3.2)
  *   out_ids   nq x k int64 ids, ascending by (distance, id); -1 pads
- *   out_dist  nq x k float32 exact squared distances; +inf pads
+ *   out_dist  nq x k float32 exact squared distances; +inf pads. For the
+ *             IP / COSINE metrics: exact inner products (cosines), ids
+ *             descending by (value, then ascending id); -inf pads. The
+ *             search ranks by the score -<o_r, q_r> with the same bounds
+ *             and re-ranking rule.
  * Re-ranking (§4, order-independent form): the 4k codes with the smallest
  * estimated distances (the pilot) get exact distances first; tau1 is the
  * k-th smallest of those, tau_ub the k-th smallest upper bound over all
@@ -124,18 +138,21 @@ int rabitq_search(const rabitq_index* idx, const float* queries, int64_t nq, int
  * rabitq_search_trace -- rabitq_search that also writes the intermediates of
  * every stage, for staged verification. All pointers are DEVICE memory (the
  * queries and outputs too); any trace pointer may be NULL to skip it.
- *   probe_ids, probe_dist  nq x nprobe: probed clusters by (distance, id)
- *                          and ||q_r - c||^2
+ *   probe_ids, probe_dist  nq x nprobe: probed clusters by (score, id)
+ *                          and the score ||q_r - c||^2 (IP / COSINE:
+ *                          -<q_r, c>)
  *   rq                     nq x D': P^{-1} [q_r; 0]
  *   planes                 nq x nprobe x bq x (D'/64) bit-planes of q_u
  *   sum_qu                 nq x nprobe: sum of q_u
  *   meta                   nq x nprobe x 4: Delta/sqrt(D'), v_l/sqrt(D'),
- *                          ||q_r-c|| 2 eps0/sqrt(D'-1), ||q_r-c||^2
+ *                          ||q_r-c|| 2 eps0/sqrt(D'-1), and the estimator's
+ *                          additive term ||q_r-c||^2 (IP / COSINE: -<q_r, c>)
  *   pair_cap               per-query capacity of the pair arrays
  *   n_pairs                nq: codes estimated per query
  *   pair_id, pair_ip       nq x pair_cap: id and <x_b, q_u> per pair, in
  *                          probe order then bucket order (ascending id)
  *   pair_est               nq x pair_cap x 3: estimated distance, LB, UB
+ *                          (IP / COSINE: of the score -<o_r, q_r>)
  *   tau_ub                 nq: k-th smallest UB (+inf if fewer than k codes)
  *   tau1                   nq: k-th smallest exact distance among the pilot,
  *                          the 4k codes with the smallest estimates (+inf if
@@ -266,7 +283,10 @@ void rabitq_predictor_opts_default(rabitq_predictor_opts* opts);
  *   out        receives the new predictor (library-owned until
  *              rabitq_predictor_free)
  * Errors: EINVAL (sizes, k > 1024, target outside (0, 1], non-finite
- * queries); ENOMEM; ECUDA; EOVERFLOW from the label search.
+ * queries); ENOMEM; ECUDA; EOVERFLOW from the label search; EUNSUPPORTED
+ * for an IP / COSINE index (the features are sorted centroid distances:
+ * learned probe counts, labels, learned searches and plans with a
+ * predictor need a RABITQ_METRIC_L2 index).
  */
 int rabitq_predictor_train(const rabitq_index* idx, const float* train_q, int64_t nt,
                            const rabitq_predictor_opts* opts, rabitq_predictor** out);
@@ -404,6 +424,30 @@ void rabitq_plan_free(rabitq_plan* plan);
  * host<->device copies). Returns the number of stages written (<= cap). */
 int rabitq_last_stats(float* ms, int32_t cap);
 
+/* The index's RABITQ_METRIC_*. */
+int rabitq_index_metric(const rabitq_index* idx, int32_t* metric);
+
+/*
+ * rabitq_estimate -- the single-code estimator (§3.3.2, the first case: one
+ * query against one code at a time, as a graph index visits its
+ * neighbours). For query i and code ids[i m + j] the query is quantized
+ * against the code's own cluster c (random stream of query i and cluster c,
+ * as in the bucket scan, so the values equal the scan's for the same batch)
+ * and the estimator of Theorem 3.2 is evaluated with its bound.
+ *   queries  nq x d float32
+ *   ids      nq x m int64 data ids; -1 marks an empty slot
+ *   bq, eps0 as for rabitq_search; opts: rot_precision, quant_seed,
+ *            io_on_device, stream (other fields ignored)
+ *   out      nq x m x 3 float32: {estimate, lower bound, upper bound} of the
+ *            squared distance, or of <o_r, q_r> for IP / COSINE; an empty
+ *            slot gets three NaNs
+ * Errors: EINVAL (sizes; an id outside [-1, n) is reported after the call
+ * and its slot gets NaNs); ENOMEM; ECUDA.
+ */
+int rabitq_estimate(const rabitq_index* idx, const float* queries, int64_t nq,
+                    const int64_t* ids, int32_t m, int32_t bq, float eps0, float* out,
+                    const rabitq_search_opts* opts);
+
 /* Sizes of an index: n, d, D' (code bits), K. Any pointer may be NULL. */
 int rabitq_index_info(const rabitq_index* idx, int64_t* n, int32_t* d, int32_t* d_pad,
                       int32_t* n_clusters);
@@ -414,7 +458,9 @@ int rabitq_get_rotation(const rabitq_index* idx, double* out /* D' x D', P row-m
 int rabitq_get_codes(const rabitq_index* idx, uint64_t* out /* n x D'/64; bit i of the
                      code is word i>>6, bit i&63 */);
 /* factors: n x 4 = {||o_r-c||^2, 2||o_r-c||/<o_bar,o>,
- * ||o_r-c|| sqrt(1-<o_bar,o>^2)/<o_bar,o>, 2 popcount(code) - D'} */
+ * ||o_r-c|| sqrt(1-<o_bar,o>^2)/<o_bar,o>, 2 popcount(code) - D'}; for the
+ * IP / COSINE metrics {-<o_r-c, c>, ||o_r-c||/<o_bar,o>,
+ * ||o_r-c|| sqrt(1-<o_bar,o>^2)/(2<o_bar,o>), 2 popcount(code) - D'} */
 int rabitq_get_factors(const rabitq_index* idx, float* out /* n x 4 */);
 int rabitq_get_assign(const rabitq_index* idx, int32_t* cluster /* n */);
 /* Bucket layout: offsets (K+1) and the ids of each bucket, ascending. */

@@ -116,7 +116,7 @@ uint32_t crc32_update(uint32_t crc, const void* data, size_t len) {
 struct FileHeader {
   char magic[8];  // "RABITQ\0\1"
   uint32_t version;
-  uint32_t reserved;
+  uint32_t metric;  // RABITQ_METRIC_* (0, the squared distance, in older files)
   int64_t n;
   int32_t d, dpad, K, W;
   uint64_t payload_bytes;
@@ -167,6 +167,9 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
   if (n_clusters < 1 || n_clusters > n || n_clusters > 65536)
     return fail(RABITQ_EINVAL, "rabitq_build: need 1 <= n_clusters <= min(n, 65536)");
   if (opts.kmeans_iters < 0) return fail(RABITQ_EINVAL, "rabitq_build: kmeans_iters < 0");
+  if (opts.metric != RABITQ_METRIC_L2 && opts.metric != RABITQ_METRIC_IP &&
+      opts.metric != RABITQ_METRIC_COSINE)
+    return fail(RABITQ_EINVAL, "rabitq_build: unknown metric");
   int32_t dpad = opts.code_bits ? opts.code_bits : (d + 63) / 64 * 64;
   if (dpad % 64 != 0 || dpad < d || dpad > 4096)
     return fail(RABITQ_EINVAL, "rabitq_build: code_bits must be a multiple of 64, >= d, <= 4096");
@@ -180,6 +183,7 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
   X->dpad = dpad;
   X->K = n_clusters;
   X->W = dpad / 64;
+  X->metric = opts.metric;
   RBQ_CUDA(cudaGetDevice(&X->device));
   int st = alloc_index_arrays(X);
   if (st != RABITQ_OK) {
@@ -188,7 +192,7 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
     return st;
   }
   auto body = [&]() -> int {
-    DevBuf dbuf, adist, adist_b;
+    DevBuf dbuf, adist, adist_b, unit;
     const float* ddata = data;
     if (!opts.data_on_device) {
       RBQ_CHECK(dbuf.alloc(sizeof(float) * n * d, s));
@@ -198,6 +202,11 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
     bool finite = true;
     RBQ_CHECK(check_finite(ddata, n * d, s, &finite));
     if (!finite) return fail(RABITQ_EINVAL, "rabitq_build: data has a non-finite value");
+    if (opts.metric == RABITQ_METRIC_COSINE) {  // the index holds unit vectors
+      RBQ_CHECK(unit.alloc(sizeof(float) * n * d, s));
+      RBQ_CHECK(normalize_rows(ddata, n, d, unit.as<float>(), s));
+      ddata = unit.as<float>();
+    }
     if (opts.centroids) {
       RBQ_CUDA(cudaMemcpyAsync(X->centroids, opts.centroids, sizeof(float) * n_clusters * d,
                                opts.data_on_device ? cudaMemcpyDeviceToDevice
@@ -365,6 +374,8 @@ int rabitq_search_learned(const rabitq_index* idx, const rabitq_predictor* pr,
   if (!idx || !pr) return fail(RABITQ_EINVAL, "rabitq_search_learned: null index or predictor");
   if (pr->K != idx->K)
     return fail(RABITQ_EINVAL, "rabitq_search_learned: predictor made for another bucket count");
+  if (idx->metric != RABITQ_METRIC_L2)
+    return fail(RABITQ_EUNSUPPORTED, "rabitq_search_learned: learned probe counts need a squared-distance (L2) index");
   if (opts && opts->per_query_nprobe)
     return fail(RABITQ_EINVAL, "rabitq_search_learned: per_query_nprobe must be NULL");
   return search_common(idx, queries, nq, k, pr->nprobe_max, bq, eps0, out_ids, out_dist, opts,
@@ -440,6 +451,63 @@ int rabitq_autotune(rabitq_index* X, const float* queries, int64_t nq, int32_t k
     times_ms[1] = best[1];
   }
   g_err.clear();
+  return RABITQ_OK;
+}
+
+int rabitq_index_metric(const rabitq_index* X, int32_t* metric) {
+  if (!X || !metric) return fail(RABITQ_EINVAL, "rabitq_index_metric: null pointer");
+  *metric = X->metric;
+  return RABITQ_OK;
+}
+
+int rabitq_estimate(const rabitq_index* X, const float* queries, int64_t nq, const int64_t* ids,
+                    int32_t m, int32_t bq, float eps0, float* out,
+                    const rabitq_search_opts* opts_in) {
+  g_err.clear();
+  if (!X) return fail(RABITQ_EINVAL, "rabitq_estimate: index is null");
+  rabitq_search_opts opts;
+  rabitq_search_opts_default(&opts);
+  if (opts_in) opts = *opts_in;
+  if (nq < 0 || m < 0) return fail(RABITQ_EINVAL, "rabitq_estimate: nq < 0 or m < 0");
+  if (nq == 0 || m == 0) return RABITQ_OK;
+  if (!queries || !ids || !out) return fail(RABITQ_EINVAL, "rabitq_estimate: null pointer");
+  if (m > (1 << 20) || nq > (int64_t(1) << 40) / m)
+    return fail(RABITQ_EINVAL, "rabitq_estimate: nq x m too large");
+  if (bq < 1 || bq > 8) return fail(RABITQ_EINVAL, "rabitq_estimate: need 1 <= bq <= 8");
+  if (!(eps0 >= 0.0f) || !std::isfinite(eps0))
+    return fail(RABITQ_EINVAL, "rabitq_estimate: eps0 must be finite and >= 0");
+  if (opts.rot_precision != RABITQ_ROT_FP32 && opts.rot_precision != RABITQ_ROT_TF32 &&
+      opts.rot_precision != RABITQ_ROT_BF16)
+    return fail(RABITQ_EINVAL, "rabitq_estimate: unknown rot_precision");
+  cudaStream_t s = static_cast<cudaStream_t>(opts.stream);
+  DevBuf qb, ib, ob, eb;
+  const float* dq = queries;
+  const int64_t* dids = ids;
+  float* dout = out;
+  if (!opts.io_on_device) {
+    RBQ_CHECK(qb.alloc(sizeof(float) * nq * X->d, s));
+    RBQ_CHECK(ib.alloc(sizeof(int64_t) * nq * m, s));
+    RBQ_CHECK(ob.alloc(sizeof(float) * nq * m * 3, s));
+    RBQ_CUDA(cudaMemcpyAsync(qb.p, queries, sizeof(float) * nq * X->d, cudaMemcpyHostToDevice, s));
+    RBQ_CUDA(cudaMemcpyAsync(ib.p, ids, sizeof(int64_t) * nq * m, cudaMemcpyHostToDevice, s));
+    dq = qb.as<float>();
+    dids = ib.as<int64_t>();
+    dout = ob.as<float>();
+  } else if (!is_device_ptr(queries) || !is_device_ptr(ids) || !is_device_ptr(out)) {
+    return fail(RABITQ_EINVAL,
+                "rabitq_estimate: io_on_device set but a pointer is not device memory");
+  }
+  RBQ_CHECK(eb.alloc(sizeof(int), s));
+  RBQ_CUDA(cudaMemsetAsync(eb.p, 0, sizeof(int), s));
+  RBQ_CHECK(estimate_dev(X, dq, nq, dids, m, bq, eps0, opts.quant_seed, opts.rot_precision, dout,
+                         eb.as<int>(), s));
+  if (!opts.io_on_device)
+    RBQ_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * nq * m * 3, cudaMemcpyDeviceToHost, s));
+  int h_err = 0;
+  RBQ_CUDA(cudaMemcpyAsync(&h_err, eb.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RBQ_CUDA(cudaStreamSynchronize(s));
+  if (h_err == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired in the query rotation");
+  if (h_err) return fail(RABITQ_EINVAL, "rabitq_estimate: an id is outside [-1, n)");
   return RABITQ_OK;
 }
 
@@ -544,6 +612,7 @@ int rabitq_index_save(const rabitq_index* X, const char* path) {
   std::memset(&h, 0, sizeof h);
   std::memcpy(h.magic, "RABITQ\0\1", 8);
   h.version = 1;
+  h.metric = (uint32_t)X->metric;
   h.n = X->n;
   h.d = X->d;
   h.dpad = X->dpad;
@@ -577,7 +646,8 @@ int rabitq_index_load(const char* path, const rabitq_build_opts* opts, rabitq_in
   FileHeader h;
   if (std::fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, "RABITQ\0\1", 8) != 0 ||
       h.header_crc != crc32_update(0, &h, offsetof(FileHeader, header_crc)) || h.version != 1 ||
-      h.n < 1 || h.d < 1 || h.K < 1 || h.dpad < h.d || h.dpad % 64 || h.W != h.dpad / 64) {
+      h.n < 1 || h.d < 1 || h.K < 1 || h.dpad < h.d || h.dpad % 64 || h.W != h.dpad / 64 ||
+      h.metric > RABITQ_METRIC_COSINE) {
     std::fclose(f);
     return fail(RABITQ_EIO, std::string("not a valid index file (header): ") + path);
   }
@@ -587,6 +657,7 @@ int rabitq_index_load(const char* path, const rabitq_build_opts* opts, rabitq_in
   X->dpad = h.dpad;
   X->K = h.K;
   X->W = h.W;
+  X->metric = (int32_t)h.metric;
   cudaGetDevice(&X->device);
   int st = alloc_index_arrays(X);
   struct Part {

@@ -67,6 +67,8 @@ int rabitq_predictor_train(const rabitq_index* X, const float* train_q, int64_t 
   if (!out) return fail(RABITQ_EINVAL, "rabitq_predictor_train: out is null");
   *out = nullptr;
   if (!X || !train_q) return fail(RABITQ_EINVAL, "rabitq_predictor_train: null index or queries");
+  if (X->metric != RABITQ_METRIC_L2)
+    return fail(RABITQ_EUNSUPPORTED, "rabitq_predictor_train: learned probe counts need a squared-distance (L2) index");
   rabitq_predictor_opts o;
   rabitq_predictor_opts_default(&o);
   if (opts_in) o = *opts_in;
@@ -196,6 +198,8 @@ int rabitq_predict_nprobe(const rabitq_index* X, const rabitq_predictor* pr,
   if (!X || !pr) return fail(RABITQ_EINVAL, "rabitq_predict_nprobe: null index or predictor");
   if (pr->K != X->K)
     return fail(RABITQ_EINVAL, "rabitq_predict_nprobe: predictor made for another bucket count");
+  if (X->metric != RABITQ_METRIC_L2)
+    return fail(RABITQ_EUNSUPPORTED, "rabitq_predict_nprobe: learned probe counts need a squared-distance (L2) index");
   if (nq < 0) return fail(RABITQ_EINVAL, "rabitq_predict_nprobe: nq < 0");
   if (nq == 0) return RABITQ_OK;
   if (!queries || !out_nprobe) return fail(RABITQ_EINVAL, "rabitq_predict_nprobe: null pointer");
@@ -247,6 +251,8 @@ int rabitq_compute_labels(const rabitq_index* X, const float* queries, int64_t n
                           int32_t nprobe_max, int32_t* ranks, int32_t* label_r) {
   set_error("");
   if (!X) return fail(RABITQ_EINVAL, "rabitq_compute_labels: index is null");
+  if (X->metric != RABITQ_METRIC_L2)
+    return fail(RABITQ_EUNSUPPORTED, "rabitq_compute_labels: learned probe counts need a squared-distance (L2) index");
   if (nq < 0) return fail(RABITQ_EINVAL, "rabitq_compute_labels: nq < 0");
   if (nq == 0) return RABITQ_OK;
   if (!queries || !gt_ids || !ranks || !label_r)

@@ -12,6 +12,7 @@
 struct rabitq_index {
   int64_t n = 0;
   int32_t d = 0, dpad = 0, K = 0, W = 0;  // W = dpad / 64 code words
+  int32_t metric = 0;                     // RABITQ_METRIC_*
   int device = 0;
   int32_t max_bucket = 0;
   // device arrays; "bucket order" = sorted by (cluster, id)
@@ -88,7 +89,8 @@ struct DevBuf {
 // ---- canonical SIMT "GEMM" (kernels_gemm.cu) ----------------------------
 // C[m][n] = fold_k op(A'[m][k], B[k][n]) in ascending k, where
 // A'[m][k] = A[arow(m)][k] - (sub ? sub[srow(m)][k] : 0); arow(m) = a_rows ? a_rows[m] : m.
-enum GemmOp { kDot = 0, kSqDist = 1 };
+// kNegDot stores -dot (the inner-product metric ranks by -<q, c>).
+enum GemmOp { kDot = 0, kSqDist = 1, kNegDot = 2 };
 int gemm_canon(GemmOp op, const float* A, int64_t lda, const int32_t* a_rows, const float* sub,
                int64_t ld_sub, const int32_t* sub_rows, const float* B, int64_t ldb, float* C,
                int64_t ldc, int64_t M, int N, int K, cudaStream_t s);
@@ -110,6 +112,8 @@ int sample_rotation_dev(uint64_t seed, int32_t dpad, double* P64, float* P32, cu
 int kmeans_dev(const float* data, int64_t n, int32_t d, int32_t K, int32_t iters, int64_t sample,
                uint64_t seed, float* centroids, cudaStream_t s);
 int encode_dev(rabitq_index* X, const float* adist_b, cudaStream_t s);
+// unit rows (canonical FP32 norm, zero rows unchanged); in and out distinct
+int normalize_rows(const float* in, int64_t n, int32_t d, float* out, cudaStream_t s);
 int gather_rows_f32(const float* in, int64_t ld, const int32_t* rows, int64_t m, int32_t d,
                     float* out, cudaStream_t s);
 int invert_perm(const int32_t* perm, int64_t n, int32_t* inv, cudaStream_t s);
@@ -162,6 +166,11 @@ int select_buckets(const rabitq_index* X, const float* Q, int64_t nq, int nsel, 
                    float* dist, cudaStream_t s);
 int search_dev_prealloc(const SearchArgs& a, unsigned char* scratch, size_t scratch_bytes,
                         cudaStream_t s);
+// Single-code estimates (§3.3.2, first case): out nq x m x 3; *err (device,
+// zeroed by the caller) is set for an id outside [-1, n).
+int estimate_dev(const rabitq_index* X, const float* Q, int64_t nq, const int64_t* ids, int m,
+                 int bq, float eps0, uint64_t seed, int rot_precision, float* out, int* err,
+                 cudaStream_t s);
 // The allocation-free, synchronization-free launch sequence of the popcount
 // search (capturable in a CUDA graph). The scratch's first int is the error
 // flag (1 = candidate overflow, 2 = tensor-core wait expired), which this call

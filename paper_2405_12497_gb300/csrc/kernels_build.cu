@@ -335,9 +335,16 @@ __global__ void position_cluster_kernel(const int32_t* __restrict__ off,
 
 // One warp per row of R = P^{-1}(o_r - c): sign code, popcount, ||r||_1 and
 // the per-vector factors of the estimator (Alg. 1 line 4, App. B.1).
+// Inner-product metric (closing footnote of §6: <o_r, q_r> = ||o_r - c||
+// ||q_r - c|| <o, q> + <o_r - c, c> + <q_r, c>): the score -<o_r, q_r> takes
+// the estimator's form (F1 + add) - F2 xq with F1 = -<o_r - c, c> (canonical
+// dot of the FP32 residual and c), F2 and F3 halved (exact scaling).
 __global__ void encode_epilogue_kernel(const float* __restrict__ R, int64_t rows, int dpad,
                                        const float* __restrict__ adist,
-                                       uint64_t* __restrict__ codes, float4* __restrict__ fac) {
+                                       uint64_t* __restrict__ codes, float4* __restrict__ fac,
+                                       int ip, const float* __restrict__ data_b,
+                                       const float* __restrict__ centroids,
+                                       const int32_t* __restrict__ cl, int d) {
   const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
@@ -361,10 +368,38 @@ __global__ void encode_epilogue_kernel(const float* __restrict__ R, int64_t rows
     a_o = __fdiv_rn(l1, den);
     if (a_o > 1.0f) a_o = 1.0f;
   }
-  const float F2 = __fdiv_rn(__fmul_rn(2.0f, n_o), a_o);
+  float F2 = __fdiv_rn(__fmul_rn(2.0f, n_o), a_o);
   const float om = __fsub_rn(1.0f, __fmul_rn(a_o, a_o));
-  const float F3 = __fdiv_rn(__fmul_rn(n_o, __fsqrt_rn(om)), a_o);
-  fac[r] = make_float4(F1, F2, F3, (float)(2 * pc - dpad));
+  float F3 = __fdiv_rn(__fmul_rn(n_o, __fsqrt_rn(om)), a_o);
+  float f1 = F1;
+  if (ip) {  // RABITQ_METRIC_IP and RABITQ_METRIC_COSINE (unit rows)
+    const float* o = data_b + r * d;
+    const float* c = centroids + (int64_t)cl[r] * d;
+    float oc = 0.0f;
+    for (int i = 0; i < d; ++i) oc = __fmaf_rn(__fsub_rn(o[i], c[i]), c[i], oc);
+    f1 = -oc;
+    F2 = __fmul_rn(0.5f, F2);
+    F3 = __fmul_rn(0.5f, F3);
+  }
+  fac[r] = make_float4(f1, F2, F3, (float)(2 * pc - dpad));
+}
+
+// Unit rows: one warp per row; lane 0 folds the canonical sum of squares,
+// every lane divides its elements by the root (zero rows unchanged).
+__global__ void normalize_rows_kernel(const float* __restrict__ in, int64_t n, int d,
+                                      float* __restrict__ out) {
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const float* x = in + r * d;
+  float ss = 0.0f;
+  if (lane == 0)
+    for (int i = 0; i < d; ++i) ss = __fmaf_rn(x[i], x[i], ss);
+  const float nrm = __fsqrt_rn(__shfl_sync(kFull, ss, 0));
+  for (int i = lane; i < d; i += 32) {
+    const float v = x[i];
+    out[r * d + i] = nrm > 0.0f ? __fdiv_rn(v, nrm) : v;
+  }
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -574,9 +609,18 @@ int encode_dev(rabitq_index* X, const float* adist_b, cudaStream_t s) {
     RBQ_CHECK(gemm_canon(kDot, X->data_b + p0 * d, d, nullptr, X->centroids, d,
                          cl.as<int32_t>() + p0, X->P32, dpad, R.as<float>(), dpad, m, dpad, d, s));
     encode_epilogue_kernel<<<blocks_for(m * 32, 256), 256, 0, s>>>(
-        R.as<float>(), m, dpad, adist_b + p0, X->codes + p0 * X->W, X->factors + p0);
+        R.as<float>(), m, dpad, adist_b + p0, X->codes + p0 * X->W, X->factors + p0,
+        X->metric != RABITQ_METRIC_L2 ? 1 : 0,
+        X->data_b + p0 * d, X->centroids, cl.as<int32_t>() + p0, d);
     RBQ_CUDA(cudaGetLastError());
   }
+  return RABITQ_OK;
+}
+
+int normalize_rows(const float* in, int64_t n, int32_t d, float* out, cudaStream_t s) {
+  if (n <= 0) return RABITQ_OK;
+  normalize_rows_kernel<<<blocks_for(n * 32, 256), 256, 0, s>>>(in, n, d, out);
+  RBQ_CUDA(cudaGetLastError());
   return RABITQ_OK;
 }
 

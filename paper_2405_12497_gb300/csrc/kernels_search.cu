@@ -129,7 +129,8 @@ struct FusedParams {
   const float* queries;     // nq x d
   const float* rq;          // nq x dpad
   const int32_t* probe_ids; // nq x nprobe
-  const float* probe_dist;  // nq x nprobe
+  const float* probe_dist;  // nq x nprobe: centroid scores, the estimator's additive term
+  const float* probe_nq2;   // nq x nprobe ||q_r - c||^2 (IP metric), null = probe_dist
   const int32_t* nprobe_q;  // nq or null
   const float* ptc;         // K x dpad
   const uint64_t* codes;    // n x W (bucket order)
@@ -143,6 +144,7 @@ struct FusedParams {
   float eps0;
   uint64_t seed;
   int cand_cap;
+  int metric;               // 0: squared distance; 1: inner product (score -<o_r, q_r>)
   int4* cand;               // gridDim.x x cand_cap: {pos, LB, estimate, -}
   int64_t* out_ids;
   float* out_dist;
@@ -255,18 +257,19 @@ __device__ __forceinline__ int quant_core(const float* rq, const float* pc, int 
 }
 
 // Per-(query, cluster) constants of the estimator: A = Delta/sqrt(D'),
-// B = v_l/sqrt(D'), E = ||q_r - c|| 2 eps0/sqrt(D'-1), nq2 = ||q_r - c||^2.
-__device__ __forceinline__ float4 quant_meta(float delta, float vl, float nq2, float eps0,
-                                             int dpad) {
+// B = v_l/sqrt(D'), E = ||q_r - c|| 2 eps0/sqrt(D'-1) and the additive term
+// add: ||q_r - c||^2 for distances, -<q_r, c> for inner products (§6).
+__device__ __forceinline__ float4 quant_meta(float delta, float vl, float nq2, float add,
+                                             float eps0, int dpad) {
   const float sqd = __fsqrt_rn((float)dpad);
   const float keps = __fdiv_rn(__fmul_rn(2.0f, eps0), __fsqrt_rn((float)(dpad - 1)));
   const float n_q = __fsqrt_rn(nq2);
-  return make_float4(__fdiv_rn(delta, sqd), __fdiv_rn(vl, sqd), __fmul_rn(n_q, keps), nq2);
+  return make_float4(__fdiv_rn(delta, sqd), __fdiv_rn(vl, sqd), __fmul_rn(n_q, keps), add);
 }
 
 // Quantize for the popcount scan: B_q bit-planes of q_u into shared memory.
 __device__ __forceinline__ void quantize_probe(const FusedParams& P, const FusedSmem& S, int64_t q,
-                                               int j, int jg, int c, float nq2) {
+                                               int j, int jg, int c, float nq2, float add) {
   const int lane = threadIdx.x & 31;
   const int dpad = P.dpad, W = P.W, bq = P.bq;
   uint64_t* planes = S.planes + (size_t)j * bq * W;
@@ -291,7 +294,7 @@ __device__ __forceinline__ void quantize_probe(const FusedParams& P, const Fused
         }
       });
   if (lane == 0) {
-    const float4 m = quant_meta(delta, vl, nq2, P.eps0, dpad);
+    const float4 m = quant_meta(delta, vl, nq2, add, P.eps0, dpad);
     S.pmeta[j] = m;
     S.psum[j] = sum;
     S.pbeg[j] = P.bucket_off[c];
@@ -561,16 +564,59 @@ __device__ __forceinline__ void compact_cand(int4* cand, int* cnt, int cap, int*
   __syncthreads();
 }
 
-// Exact squared distances of a list of rows: each lane streams its own row
-// with 16-byte loads (eight in flight per lane, a warp has 256 rows' worth of
-// loads outstanding) and folds it in ascending dimension order (canonical
-// squared distance). Keys (distance, id) go to the top-k buffer.
+// One term of the canonical exact score: squared distance, fold of
+// (q - x)^2; inner product, fold of q x (negated at the end).
+template <bool IP>
+__device__ __forceinline__ float score_step(float acc, float q, float x) {
+  if (IP) return __fmaf_rn(q, x, acc);
+  const float t = __fsub_rn(q, x);
+  return __fmaf_rn(t, t, acc);
+}
+
+// Canonical exact score of row x against the query qv (shared memory), in
+// ascending dimension order: ||q - x||^2, or -<q, x> for inner products.
+// 16-byte loads, eight in flight, when d is a multiple of 4.
+template <bool IP>
+__device__ __forceinline__ float row_score(const float* __restrict__ x, const float* qv, int d) {
+  float acc = 0.0f;
+  if ((d & 3) == 0) {
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* q4 = reinterpret_cast<const float4*>(qv);
+    int c = 0;
+    for (; c + 8 <= (d >> 2); c += 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldg(x4 + c + u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 qq = q4[c + u];
+        acc = score_step<IP>(acc, qq.x, v[u].x);
+        acc = score_step<IP>(acc, qq.y, v[u].y);
+        acc = score_step<IP>(acc, qq.z, v[u].z);
+        acc = score_step<IP>(acc, qq.w, v[u].w);
+      }
+    }
+    for (; c < (d >> 2); ++c) {
+      const float4 vv = __ldg(x4 + c), qq = q4[c];
+      acc = score_step<IP>(acc, qq.x, vv.x);
+      acc = score_step<IP>(acc, qq.y, vv.y);
+      acc = score_step<IP>(acc, qq.z, vv.z);
+      acc = score_step<IP>(acc, qq.w, vv.w);
+    }
+  } else {
+    for (int dd = 0; dd < d; ++dd) acc = score_step<IP>(acc, qv[dd], __ldg(x + dd));
+  }
+  return IP ? -acc : acc;
+}
+
+// Exact scores of a list of rows: each lane streams its own row (a warp has
+// 256 rows' worth of loads outstanding) and folds it in ascending dimension
+// order. Keys (score, id) go to the top-k buffer.
 // SRC 0: the pilot (ids in S.estk); SRC 1: the candidate list (positions).
 template <int SRC>
 __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q, int count,
                             const int4* cand, int* top_cnt, int* surv_cnt) {
   const int d = P.d;
-  const bool vec = (d & 3) == 0;
   // Ask L2 for every row of the set first (no registers held, no waiting):
   // the loads below then find most rows in L2 instead of waiting on DRAM
   // eight loads at a time.
@@ -597,36 +643,7 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
     float acc = 0.0f;
     if (valid) {
       const float* x = P.data_b + (int64_t)pos * d;
-      if (vec) {
-        const float4* x4 = reinterpret_cast<const float4*>(x);
-        const float4* q4 = reinterpret_cast<const float4*>(S.qv);
-        int c = 0;
-        for (; c + 8 <= (d >> 2); c += 8) {
-          float4 v[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = __ldg(x4 + c + u);
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const float4 qq = q4[c + u];
-            float t = __fsub_rn(qq.x, v[u].x); acc = __fmaf_rn(t, t, acc);
-            t = __fsub_rn(qq.y, v[u].y); acc = __fmaf_rn(t, t, acc);
-            t = __fsub_rn(qq.z, v[u].z); acc = __fmaf_rn(t, t, acc);
-            t = __fsub_rn(qq.w, v[u].w); acc = __fmaf_rn(t, t, acc);
-          }
-        }
-        for (; c < (d >> 2); ++c) {
-          const float4 vv = __ldg(x4 + c), qq = q4[c];
-          float t = __fsub_rn(qq.x, vv.x); acc = __fmaf_rn(t, t, acc);
-          t = __fsub_rn(qq.y, vv.y); acc = __fmaf_rn(t, t, acc);
-          t = __fsub_rn(qq.z, vv.z); acc = __fmaf_rn(t, t, acc);
-          t = __fsub_rn(qq.w, vv.w); acc = __fmaf_rn(t, t, acc);
-        }
-      } else {
-        for (int dd = 0; dd < d; ++dd) {
-          const float t = __fsub_rn(S.qv[dd], __ldg(x + dd));
-          acc = __fmaf_rn(t, t, acc);
-        }
-      }
+      acc = P.metric ? row_score<true>(x, S.qv, d) : row_score<false>(x, S.qv, d);
     }
     const int slot = warp_reserve(valid, top_cnt);
     if (valid) {
@@ -728,8 +745,8 @@ __device__ void finish_query(const FusedParams& P, const FusedSmem& S, int64_t q
   for (int j2 = tid; j2 < k; j2 += blockDim.x) {
     const bool ok = j2 < got;
     P.out_ids[q * k + j2] = ok ? (int64_t)(S.topk[j2] & 0xffffffffu) : -1;
-    P.out_dist[q * k + j2] =
-        ok ? key_float((uint32_t)(S.topk[j2] >> 32)) : __int_as_float(0x7f800000);
+    const float v = ok ? key_float((uint32_t)(S.topk[j2] >> 32)) : __int_as_float(0x7f800000);
+    P.out_dist[q * k + j2] = P.metric ? -v : v;  // inner products: <o_r, q_r>, -inf pads
   }
   if (tid == 0) {
     if (P.tr.tau_ub) P.tr.tau_ub[q] = tau_ub;
@@ -878,8 +895,10 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
       const int npc = min(P.pch, pe - pc0);
       for (int j = wid; j < npc; j += nwarps) {
         const int jg = pc0 + j;
-        const int c = P.probe_ids[q * P.nprobe + jg];
-        quantize_probe(P, S, q, j, jg, c, P.probe_dist[q * P.nprobe + jg]);
+        const int64_t pj = q * P.nprobe + jg;
+        const int c = P.probe_ids[pj];
+        const float add = P.probe_dist[pj];
+        quantize_probe(P, S, q, j, jg, c, P.probe_nq2 ? P.probe_nq2[pj] : add, add);
       }
       __syncthreads();
       if (wid == 0) {  // inclusive prefix of the bucket lengths, 32 at a time
@@ -1430,6 +1449,7 @@ __global__ void __launch_bounds__(kTsThreads) tc_scan_kernel(TcScanParams P) {
 __global__ void quantize_pairs_kernel(const float* __restrict__ rq,
                                       const int32_t* __restrict__ probe_ids,
                                       const float* __restrict__ probe_dist,
+                                      const float* __restrict__ probe_nq2,
                                       const float* __restrict__ ptc, int64_t npairs, int nprobe,
                                       int dpad, int bq, float eps0, uint64_t seed,
                                       int64_t q_offset, __nv_bfloat16* __restrict__ qub,
@@ -1455,7 +1475,8 @@ __global__ void quantize_pairs_kernel(const float* __restrict__ rq,
                                }
                              });
   if (lane == 0) {
-    pmeta[pp] = quant_meta(delta, vl, probe_dist[pp], eps0, dpad);
+    pmeta[pp] = quant_meta(delta, vl, probe_nq2 ? probe_nq2[pp] : probe_dist[pp], probe_dist[pp],
+                           eps0, dpad);
     psum[pp] = sum;
   }
 }
@@ -1592,6 +1613,117 @@ int pow2_at_least(int x) {
   return p;
 }
 
+// ||q_r - c||^2 of every probed (query, cluster) pair, canonical order (the
+// bound's scale for the inner-product metrics, whose probe list holds
+// -<q_r, c>); one thread per pair, empty slots (-1) get 0.
+__global__ void probe_nq2_kernel(const float* __restrict__ Q, int d,
+                                 const float* __restrict__ centroids,
+                                 const int32_t* __restrict__ pid, int64_t npairs, int nprobe,
+                                 float* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npairs) return;
+  const int c = pid[i];
+  float acc = 0.0f;
+  if (c >= 0) {
+    const float* q = Q + (i / nprobe) * d;
+    const float* x = centroids + (int64_t)c * d;
+    for (int t = 0; t < d; ++t) acc = score_step<false>(acc, q[t], x[t]);
+  }
+  out[i] = acc;
+}
+
+// ---------------------------------------------------------- single-code estimator
+// §3.3.2, first case: one query against one code at a time. One warp per
+// (query, slot): the query is quantized against the code's own cluster with
+// the bucket scan's arithmetic and random stream (so the values equal the
+// scan's), <x_b, q_u> is taken nibble by nibble against the code while the
+// quantized values are produced, and lane 0 evaluates the estimator.
+struct EstParams {
+  const float* queries;     // nq x d (unit rows for the cosine metric)
+  const float* rq;          // nq x dpad
+  const int64_t* ids;       // nq x m
+  const int32_t* inv_perm;  // id -> bucket position
+  const int32_t* assign;    // id -> cluster
+  const uint64_t* codes;    // bucket order
+  const float4* factors;    // bucket order
+  const float* centroids;   // K x d
+  const float* ptc;         // K x dpad
+  int64_t nq, n, q_offset;  // q_offset: stream index of the first query
+  int m, d, dpad, bq, metric;
+  float eps0;
+  uint64_t seed;
+  float* out;               // nq x m x 3
+  int* err;                 // set to 1 for an id outside [-1, n)
+};
+
+__global__ void __launch_bounds__(256) estimate_kernel(EstParams E) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= E.nq * E.m) return;
+  const int64_t q = w / E.m;
+  const int64_t id = E.ids[w];
+  float* o = E.out + 3 * w;
+  if (id < 0 || id >= E.n) {
+    if (lane == 0) {
+      o[0] = o[1] = o[2] = __int_as_float(0x7fc00000);
+      if (id != -1) atomicExch(E.err, 1);
+    }
+    return;
+  }
+  const int c = E.assign[id];
+  const int64_t pos = E.inv_perm[id];
+  const int dpad = E.dpad;
+  // ||q_r - c||^2 and the additive term (-<q_r, c> for inner products):
+  // sequential folds, so one lane
+  float nq2 = 0.0f, qc = 0.0f;
+  if (lane == 0) {
+    const float* qv = E.queries + q * E.d;
+    const float* cv = E.centroids + (int64_t)c * E.d;
+    for (int t = 0; t < E.d; ++t) {
+      const float a = qv[t], b = cv[t];
+      nq2 = score_step<false>(nq2, a, b);
+      qc = score_step<true>(qc, a, b);
+    }
+  }
+  const uint32_t* code32 = reinterpret_cast<const uint32_t*>(E.codes + pos * (dpad >> 6));
+  int ipl = 0;
+  float vl, delta;
+  const int sum = quant_core(
+      E.rq + q * dpad, E.ptc + (int64_t)c * dpad, dpad, E.bq, E.seed, (uint64_t)(E.q_offset + q),
+      c, &vl, &delta,
+      [&](int, int k0, const int* qu) {
+        if (k0 < dpad) {  // the lane's four coordinates k0..k0+3 (code bit k at word k/32)
+          const uint32_t nib = (__ldg(code32 + (k0 >> 5)) >> (k0 & 31)) & 0xfu;
+          for (int b = 0; b < E.bq; ++b) {
+            const uint32_t qn = ((qu[0] >> b) & 1) | (((qu[1] >> b) & 1) << 1) |
+                                (((qu[2] >> b) & 1) << 2) | (((qu[3] >> b) & 1) << 3);
+            ipl += __popc(qn & nib) << b;
+          }
+        }
+      });
+  const int ip = warp_sum_i(ipl);
+  if (lane == 0) {
+    const float add = E.metric ? -qc : nq2;
+    const float4 mt = quant_meta(delta, vl, nq2, add, E.eps0, dpad);
+    const float4 f = E.factors[pos];
+    // the bucket scan's estimator, same FP32 order
+    const float t1 = (float)(2 * ip - sum);
+    const float xq = __fadd_rn(__fmul_rn(mt.x, t1), __fmul_rn(mt.y, f.w));
+    const float dist = __fsub_rn(__fadd_rn(f.x, mt.w), __fmul_rn(f.y, xq));
+    const float e = __fmul_rn(f.z, mt.z);
+    const float lb = __fsub_rn(dist, e), ub = __fadd_rn(dist, e);
+    if (E.metric) {  // inner product <o_r, q_r> = -score, bounds swapped
+      o[0] = -dist;
+      o[1] = -ub;
+      o[2] = -lb;
+    } else {
+      o[0] = dist;
+      o[1] = lb;
+      o[2] = ub;
+    }
+  }
+}
+
 // Shape of the fused kernel for a search: probes staged per chunk, buffer
 // sizes, and the shared-memory capacity for staging the tail's candidate
 // list -- the largest of 4096, 2048, 1024 entries that keeps the residency
@@ -1663,6 +1795,43 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s);
 int search_dev_popc(const SearchArgs& a, cudaStream_t s);
 
 namespace {
+
+// Metric plumbing shared by the search paths. COSINE searches the unit
+// query (normalized first); the inner-product metrics rank centroids by
+// -<q_r, c> and need ||q_r - c||^2 of each probed pair for the bound.
+bool metric_ip(const rabitq_index* X) { return X->metric != RABITQ_METRIC_L2; }
+bool metric_cos(const rabitq_index* X) { return X->metric == RABITQ_METRIC_COSINE; }
+
+// Q for the search: the caller's rows, or their unit rows in qn (COSINE).
+int search_queries(const rabitq_index* X, const float* Q, int64_t nq, float* qn,
+                   const float** out, cudaStream_t s) {
+  *out = Q;
+  if (metric_cos(X)) {
+    RBQ_CHECK(normalize_rows(Q, nq, X->d, qn, s));
+    *out = qn;
+  }
+  return RABITQ_OK;
+}
+
+int centroid_scores(const rabitq_index* X, const float* Q, int64_t nq, float* cd,
+                    cudaStream_t s) {
+  return gemm_canon(metric_ip(X) ? kNegDot : kSqDist, Q, X->d, nullptr, nullptr, 0, nullptr,
+                    X->centroids_t, X->K, cd, X->K, nq, X->K, X->d, s);
+}
+
+int probe_nq2(const rabitq_index* X, const float* Q, int64_t nq, int nprobe, const int32_t* pid,
+              float* out, cudaStream_t s) {
+  const int64_t np = nq * nprobe;
+  if (np == 0) return RABITQ_OK;
+  probe_nq2_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(Q, X->d, X->centroids, pid, np,
+                                                               nprobe, out);
+  RBQ_CUDA(cudaGetLastError());
+  return RABITQ_OK;
+}
+
+}  // namespace
+
+namespace {
 // Probe slices per query for a chunk of nqc queries: 1 when the queries fill
 // the GPU (full = resident CTAs); otherwise up to 16, no more than the probes,
 // and the slices' k smallest upper bounds must fit the merge's buffer.
@@ -1721,7 +1890,9 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   const int64_t grid = std::min<int64_t>(qchunk, full);
   // a batch too small to fill the GPU splits each query's probes over CTAs
   const int split = split_factor(a, std::min(qchunk, a.nq), full, fs);
-  DevBuf cd, rq, pid, pdist, cand, err, ubout, scnt, cand2;
+  DevBuf cd, rq, pid, pdist, cand, err, ubout, scnt, cand2, qn, pnq2;
+  if (metric_cos(X)) RBQ_CHECK(qn.alloc(sizeof(float) * qchunk * d, s));
+  if (metric_ip(X)) RBQ_CHECK(pnq2.alloc(sizeof(float) * qchunk * nprobe, s));
   RBQ_CHECK(cd.alloc(sizeof(float) * qchunk * K, s));
   RBQ_CHECK(rq.alloc(sizeof(float) * qchunk * dpad, s));
   RBQ_CHECK(pid.alloc(sizeof(int32_t) * qchunk * nprobe, s));
@@ -1761,10 +1932,10 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
                                 kSelMaxSmem));
   for (int64_t q0 = 0; q0 < a.nq; q0 += qchunk) {
     const int64_t nqc = std::min(qchunk, a.nq - q0);
-    const float* Q = a.queries + q0 * d;
     if (timing) RBQ_CUDA(cudaEventRecord(ev[0], s));
-    RBQ_CHECK(gemm_canon(kSqDist, Q, d, nullptr, nullptr, 0, nullptr, X->centroids_t, K,
-                         cd.as<float>(), K, nqc, K, d, s));
+    const float* Q = nullptr;
+    RBQ_CHECK(search_queries(X, a.queries + q0 * d, nqc, qn.as<float>(), &Q, s));
+    RBQ_CHECK(centroid_scores(X, Q, nqc, cd.as<float>(), s));
     if (timing) RBQ_CUDA(cudaEventRecord(ev[1], s));
     int32_t* probe_ids = a.trace && a.trace->probe_ids ? a.trace->probe_ids + q0 * nprobe
                                                        : pid.as<int32_t>();
@@ -1789,6 +1960,7 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
                           nullptr, s));
       npq = a.pred_nprobe + q0;
     }
+    if (metric_ip(X)) RBQ_CHECK(probe_nq2(X, Q, nqc, nprobe, probe_ids, pnq2.as<float>(), s));
     if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
     float* rqp = a.trace && a.trace->rq ? a.trace->rq + q0 * dpad : rq.as<float>();
     if (a.rot_precision == RABITQ_ROT_FP32)
@@ -1803,6 +1975,8 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
     P.rq = rqp;
     P.probe_ids = probe_ids;
     P.probe_dist = probe_dist;
+    P.probe_nq2 = metric_ip(X) ? pnq2.as<float>() : nullptr;
+    P.metric = metric_ip(X);
     P.nprobe_q = npq;
     P.ptc = X->ptc;
     P.codes = X->codes;
@@ -1914,7 +2088,8 @@ struct Carve {
   int64_t grid = 0, cap = 0, qchunk = 0;
   size_t o_ubout = 0, o_scnt = 0, o_cand2 = 0;  // split mode (grid-sized)
   size_t o_cand = 0, o_cd = 0, o_rq = 0, o_pid = 0, o_pdist = 0, o_pnp = 0, o_fid = 0,
-         o_fdist = 0, o_okey = 0, o_order = 0, o_ooff = 0, o_sortws = 0, end = 0;
+         o_fdist = 0, o_okey = 0, o_order = 0, o_ooff = 0, o_sortws = 0, o_qn = 0, o_pnq2 = 0,
+         end = 0;
 };
 
 constexpr size_t kCarveAlign = 256;
@@ -1947,6 +2122,8 @@ Carve carve_layout(const SearchArgs& a, int64_t grid, int64_t cap, int64_t qchun
   L.o_order = take(ordered ? sizeof(int32_t) * qchunk : 0);
   L.o_ooff = take(ordered ? sizeof(int32_t) * (nprobe + 2) : 0);
   L.o_sortws = take(ordered ? sizeof(int32_t) * counting_sort_ws_ints(qchunk, nprobe + 1) : 0);
+  L.o_qn = take(metric_cos(X) ? sizeof(float) * qchunk * X->d : 0);
+  L.o_pnq2 = take(metric_ip(X) ? sizeof(float) * qchunk * nprobe : 0);
   // split mode: at most grid items (slices) and grid / 2 queries
   L.o_ubout = take(a.allow_split ? sizeof(uint32_t) * grid * a.k : 0);
   L.o_scnt = take(a.allow_split ? sizeof(int) * grid * 2 : 0);
@@ -2023,14 +2200,16 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
   int32_t* order = reinterpret_cast<int32_t*>(scratch + L.o_order);
   int32_t* ooff = reinterpret_cast<int32_t*>(scratch + L.o_ooff);
   int32_t* sortws = reinterpret_cast<int32_t*>(scratch + L.o_sortws);
+  float* qn = reinterpret_cast<float*>(scratch + L.o_qn);
+  float* pnq2 = reinterpret_cast<float*>(scratch + L.o_pnq2);
   const int navail = std::min(kMlpIn, K);
   for (int64_t q0 = 0; q0 < a.nq; q0 += qchunk) {
     const int64_t nqc = std::min(qchunk, a.nq - q0);
-    const float* Q = a.queries + q0 * d;
     const bool ev = a.stage_ev && q0 == 0 && nqc == a.nq;
     if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[0], s, cudaEventRecordExternal));
-    RBQ_CHECK(gemm_canon(kSqDist, Q, d, nullptr, nullptr, 0, nullptr, X->centroids_t, K, cd, K,
-                         nqc, K, d, s));
+    const float* Q = nullptr;
+    RBQ_CHECK(search_queries(X, a.queries + q0 * d, nqc, qn, &Q, s));
+    RBQ_CHECK(centroid_scores(X, Q, nqc, cd, s));
     if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[1], s, cudaEventRecordExternal));
     const int32_t* npq = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
     const bool pred_from_list = a.pred && nprobe >= navail;
@@ -2052,6 +2231,7 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
     if (a.pred && a.pred_nprobe)
       RBQ_CUDA(cudaMemcpyAsync(a.pred_nprobe + q0, pnp, sizeof(int32_t) * nqc,
                                cudaMemcpyDeviceToDevice, s));
+    if (metric_ip(X)) RBQ_CHECK(probe_nq2(X, Q, nqc, nprobe, pid, pnq2, s));
     if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[2], s, cudaEventRecordExternal));
     if (a.rot_precision == RABITQ_ROT_FP32)
       RBQ_CHECK(gemm_canon(kDot, Q, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rq, dpad, nqc,
@@ -2065,6 +2245,8 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
     P.rq = rq;
     P.probe_ids = pid;
     P.probe_dist = pdist;
+    P.probe_nq2 = metric_ip(X) ? pnq2 : nullptr;
+    P.metric = metric_ip(X);
     P.nprobe_q = npq;
     P.ptc = X->ptc;
     P.codes = X->codes;
@@ -2168,7 +2350,9 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
   qchunk = std::max<int64_t>(1, std::min<int64_t>(qchunk, (int64_t(1) << 32) / ((int64_t)cap * 16)));
   const int64_t np = qchunk * nprobe;
   DevBuf cd, rq, pid, pdist, keys, pperm, poff, qub, pmeta, psum, tiles, toffA, lists, lcnt, qtau,
-      err;
+      err, qn, pnq2;
+  if (metric_cos(X)) RBQ_CHECK(qn.alloc(sizeof(float) * qchunk * d, s));
+  if (metric_ip(X)) RBQ_CHECK(pnq2.alloc(sizeof(float) * np, s));
   RBQ_CHECK(cd.alloc(sizeof(float) * qchunk * K, s));
   RBQ_CHECK(rq.alloc(sizeof(float) * qchunk * dpad, s));
   RBQ_CHECK(pid.alloc(sizeof(int32_t) * np, s));
@@ -2215,10 +2399,10 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
   for (int64_t q0 = 0; q0 < a.nq; q0 += qchunk) {
     const int64_t nqc = std::min(qchunk, a.nq - q0);
     const int64_t npc = nqc * nprobe;
-    const float* Q = a.queries + q0 * d;
     if (timing) RBQ_CUDA(cudaEventRecord(ev[0], s));
-    RBQ_CHECK(gemm_canon(kSqDist, Q, d, nullptr, nullptr, 0, nullptr, X->centroids_t, K,
-                         cd.as<float>(), K, nqc, K, d, s));
+    const float* Q = nullptr;
+    RBQ_CHECK(search_queries(X, a.queries + q0 * d, nqc, qn.as<float>(), &Q, s));
+    RBQ_CHECK(centroid_scores(X, Q, nqc, cd.as<float>(), s));
     int32_t* probe_ids = a.trace && a.trace->probe_ids ? a.trace->probe_ids + q0 * nprobe
                                                        : pid.as<int32_t>();
     float* probe_dist = a.trace && a.trace->probe_dist ? a.trace->probe_dist + q0 * nprobe
@@ -2233,6 +2417,7 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
         cd.as<float>(), K, nprobe, npq,
         sort_n, probe_ids, probe_dist);
     RBQ_CUDA(cudaGetLastError());
+    if (metric_ip(X)) RBQ_CHECK(probe_nq2(X, Q, nqc, nprobe, probe_ids, pnq2.as<float>(), s));
     if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
     float* rqp = a.trace && a.trace->rq ? a.trace->rq + q0 * dpad : rq.as<float>();
     if (a.rot_precision == RABITQ_ROT_FP32)
@@ -2247,7 +2432,8 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
     RBQ_CHECK(counting_sort(keys.as<int32_t>(), npc, 3 * K + 4, pperm.as<int32_t>(),
                             poff.as<int32_t>(), s));
     quantize_pairs_kernel<<<(unsigned)((npc * 32 + 255) / 256), 256, 0, s>>>(
-        rqp, probe_ids, probe_dist, X->ptc, npc, nprobe, dpad, a.bq, a.eps0, a.seed, q0,
+        rqp, probe_ids, probe_dist, metric_ip(X) ? pnq2.as<float>() : nullptr, X->ptc, npc,
+        nprobe, dpad, a.bq, a.eps0, a.seed, q0,
         qub.as<__nv_bfloat16>(), pmeta.as<float4>(), psum.as<int32_t>());
     RBQ_CUDA(cudaGetLastError());
     for (int pass = 0; pass < 3; ++pass) {
@@ -2293,6 +2479,7 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
     P.queries = Q;
     P.probe_ids = probe_ids;
     P.nprobe_q = npq;
+    P.metric = metric_ip(X);
     P.data_b = X->data_b;
     P.perm = X->perm;
     P.inv_perm = X->inv_perm;
@@ -2391,6 +2578,57 @@ int predict_dev(const rabitq_index* X, const rabitq_predictor* pr, const float* 
     RBQ_CHECK(select_buckets(X, Q + q0 * X->d, m, navail, ids.as<int32_t>(), dist.as<float>(), s));
     RBQ_CHECK(mlp_infer(pr, dist.as<float>(), navail, m, navail, nprobe_out + q0,
                         feat ? feat + q0 * kMlpIn : nullptr, y ? y + q0 : nullptr, s));
+  }
+  return RABITQ_OK;
+}
+
+// Single-code estimates of nq queries against ids (nq x m) into out
+// (nq x m x 3), in query chunks that bound the rotated-query scratch. The
+// error flag (device int, zeroed by the caller) is set for an id outside
+// [-1, n).
+int estimate_dev(const rabitq_index* X, const float* Q, int64_t nq, const int64_t* ids, int m,
+                 int bq, float eps0, uint64_t seed, int rot_precision, float* out, int* err,
+                 cudaStream_t s) {
+  if (nq <= 0 || m <= 0) return RABITQ_OK;
+  const int d = X->d, dpad = X->dpad;
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t(1) << 26) / dpad));
+  DevBuf rq, qn;
+  RBQ_CHECK(rq.alloc(sizeof(float) * chunk * dpad, s));
+  if (metric_cos(X)) RBQ_CHECK(qn.alloc(sizeof(float) * chunk * d, s));
+  for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+    const int64_t nqc = std::min(chunk, nq - q0);
+    const float* Qc = nullptr;
+    RBQ_CHECK(search_queries(X, Q + q0 * d, nqc, qn.as<float>(), &Qc, s));
+    if (rot_precision == RABITQ_ROT_FP32)
+      RBQ_CHECK(gemm_canon(kDot, Qc, d, nullptr, nullptr, 0, nullptr, X->P32, dpad, rq.as<float>(),
+                           dpad, nqc, dpad, d, s));
+    else
+      RBQ_CHECK(rotate_tc(X, Qc, nqc, rot_precision, rq.as<float>(), err, s));
+    EstParams E;
+    E.queries = Qc;
+    E.rq = rq.as<float>();
+    E.ids = ids + q0 * m;
+    E.inv_perm = X->inv_perm;
+    E.assign = X->assign;
+    E.codes = X->codes;
+    E.factors = X->factors;
+    E.centroids = X->centroids;
+    E.ptc = X->ptc;
+    E.nq = nqc;
+    E.n = X->n;
+    E.m = m;
+    E.d = d;
+    E.dpad = dpad;
+    E.bq = bq;
+    E.metric = metric_ip(X);
+    E.eps0 = eps0;
+    E.seed = seed;
+    E.out = out + q0 * m * 3;
+    E.err = err;
+    E.q_offset = q0;  // the quantization stream is the query's index in the call
+    const int64_t warps = nqc * m;
+    estimate_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(E);
+    RBQ_CUDA(cudaGetLastError());
   }
   return RABITQ_OK;
 }

@@ -96,6 +96,8 @@ int rabitq_plan_create(const rabitq_index* X, const rabitq_predictor* pr, int64_
   if (pr) {
     if (pr->K != X->K)
       return fail(RABITQ_EINVAL, "rabitq_plan_create: predictor made for another bucket count");
+    if (X->metric != RABITQ_METRIC_L2)
+      return fail(RABITQ_EUNSUPPORTED, "rabitq_plan_create: learned probe counts need a squared-distance (L2) index");
     nprobe = pr->nprobe_max;
   }
   if (nq_max < 1 || nq_max > (int64_t(1) << 24))

@@ -19,6 +19,8 @@ _lib = None
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EIO, EUNSUPPORTED, EOVERFLOW = 0, -1, -2, -3, -4, -5, -6, -7
 ROT_FP32, ROT_TF32, ROT_BF16 = 0, 1, 2
 SCAN_AUTO, SCAN_POPC, SCAN_TC = 0, 1, 2
+METRIC_L2, METRIC_IP, METRIC_COSINE = 0, 1, 2
+METRICS = {"l2": METRIC_L2, "ip": METRIC_IP, "cosine": METRIC_COSINE}
 
 # Every symbol include/rabitq.h declares.
 EXPORTS = (
@@ -32,7 +34,8 @@ EXPORTS = (
     "rabitq_predictor_free", "rabitq_predict_nprobe", "rabitq_search_learned",
     "rabitq_compute_labels", "rabitq_mlp_grad", "rabitq_mlp_adam", "rabitq_autotune",
     "rabitq_plan_create", "rabitq_plan_buffers", "rabitq_plan_run", "rabitq_plan_sync",
-    "rabitq_plan_search", "rabitq_plan_free", "rabitq_plan_stats",
+    "rabitq_plan_search", "rabitq_plan_free", "rabitq_plan_stats", "rabitq_index_metric",
+    "rabitq_estimate",
 )
 
 MLP_IN, MLP_HIDDEN = 64, 256
@@ -48,7 +51,7 @@ class RabitqError(RuntimeError):
 class BuildOpts(C.Structure):
     _fields_ = [("kmeans_iters", C.c_int32), ("kmeans_sample", C.c_int64),
                 ("code_bits", C.c_int32), ("data_on_device", C.c_int32),
-                ("stream", C.c_void_p), ("centroids", C.c_void_p)]
+                ("stream", C.c_void_p), ("centroids", C.c_void_p), ("metric", C.c_int32)]
 
 
 class SearchOpts(C.Structure):
@@ -133,6 +136,8 @@ def lib():
             "rabitq_plan_search": (C.c_int, [vp, vp, i64, vp, vp, vp]),
             "rabitq_plan_free": (None, [vp]),
             "rabitq_plan_stats": (C.c_int, [vp, vp, i32]),
+            "rabitq_index_metric": (C.c_int, [vp, vp]),
+            "rabitq_estimate": (C.c_int, [vp, vp, i64, vp, i32, i32, f32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -194,13 +199,20 @@ class Index:
         n, d, dp, K = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
         _check(lib().rabitq_index_info(self._h, C.byref(n), C.byref(d), C.byref(dp), C.byref(K)))
         self.n, self.d, self.dpad, self.K = n.value, d.value, dp.value, K.value
+        m = C.c_int32()
+        _check(lib().rabitq_index_metric(self._h, C.byref(m)))
+        self.metric = {v: k for k, v in METRICS.items()}[m.value]
 
     # ---------------------------------------------------------------- build
     @classmethod
     def build(cls, data, n_clusters: int, seed: int, code_bits: int = 0, kmeans_iters: int = 10,
-              kmeans_sample: int = 0, centroids=None, stream=None) -> "Index":
+              kmeans_sample: int = 0, centroids=None, stream=None, metric: str = "l2") -> "Index":
+        """metric: "l2" (squared distance), "ip" (inner product) or "cosine"."""
+        if metric not in METRICS:
+            raise ValueError(f"metric must be one of {sorted(METRICS)}")
         opts = BuildOpts()
         lib().rabitq_build_opts_default(C.byref(opts))
+        opts.metric = METRICS[metric]
         opts.kmeans_iters = kmeans_iters
         opts.kmeans_sample = kmeans_sample
         opts.code_bits = code_bits
@@ -296,7 +308,9 @@ class Index:
                stats: bool = False, stream=None, out=None, rot_precision=ROT_FP32,
                scan_path=SCAN_AUTO):
         """k-NN search. numpy queries -> numpy (ids int64, dists float32) via
-        host buffers; torch CUDA queries -> torch CUDA outputs."""
+        host buffers; torch CUDA queries -> torch CUDA outputs. Values are
+        squared distances (ascending) for l2, inner products / cosines
+        (descending) for ip / cosine."""
         dev = _is_torch(queries)
         o = self._opts(quant_seed, per_query_nprobe, max_candidates, stats, stream, dev,
                        rot_precision, scan_path)
@@ -328,6 +342,31 @@ class Index:
         _check(lib().rabitq_search(self._h, _np_ptr(queries), nq, k, nprobe, bq, eps0,
                                    _np_ptr(ids), _np_ptr(dist), C.byref(o)))
         return ids, dist
+
+    def estimate(self, queries, ids, bq: int = 4, eps0: float = 1.9, quant_seed: int = 3,
+                 rot_precision=ROT_FP32, stream=None):
+        """Single-code estimates (§3.3.2, first case): for query i and code
+        ids[i, j], {estimate, lower bound, upper bound} of the squared distance
+        (l2) or of the inner product (ip, cosine), shape (nq, m, 3); -1 ids
+        give NaNs. numpy in -> numpy out; torch CUDA in -> torch CUDA out."""
+        dev = _is_torch(queries)
+        o = self._opts(quant_seed, None, 65536, False, stream, dev, rot_precision)
+        if dev:
+            import torch
+            queries = queries.contiguous()
+            ids = ids.to(torch.int64).contiguous()
+            nq, m = ids.shape
+            out = torch.empty((nq, m, 3), dtype=torch.float32, device=queries.device)
+            _check(lib().rabitq_estimate(self._h, _dptr(queries), nq, _dptr(ids), m, bq, eps0,
+                                         _dptr(out), C.byref(o)))
+            return out
+        queries = np.ascontiguousarray(queries, np.float32)
+        ids = np.ascontiguousarray(ids, np.int64)
+        nq, m = ids.shape
+        out = np.empty((nq, m, 3), np.float32)
+        _check(lib().rabitq_estimate(self._h, _np_ptr(queries), nq, _np_ptr(ids), m, bq, eps0,
+                                     _np_ptr(out), C.byref(o)))
+        return out
 
     def search_trace(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
                      quant_seed: int = 3, pair_cap: int = 0, surv_cap: int = 0,
