@@ -533,31 +533,53 @@ __device__ __forceinline__ void sort_kept_u64(unsigned long long* a, int cnt, in
   __syncthreads();
 }
 
-// In-place, order-keeping compaction of the candidate list with predicate f.
+// In-place, order-keeping compaction of the candidate list with predicate f:
+// blocks of kCompactU x blockDim entries (kCompactU loads in flight per
+// thread, two barriers per block); every read of a block precedes its
+// writes, which land below the block's end. scratch: kCompactU x
+// (blockDim / 32) ints. (Two entries per thread: four cost the fused kernel
+// register spills that outweighed the fewer barriers.)
+constexpr int kCompactU = 2;
 template <class F>
 __device__ __forceinline__ void compact_cand(int4* cand, int* cnt, int cap, int* scratch, F keep_f) {
   const int n = min(*cnt, cap);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
   int out = 0;
   __syncthreads();
-  for (int b = 0; b < n; b += blockDim.x) {
-    const int i = b + threadIdx.x;
-    int4 e = make_int4(0, 0, 0, 0);
-    bool keep = false;
-    if (i < n) {
-      e = cand[i];
-      keep = keep_f(e);
+  for (int b = 0; b < n; b += kCompactU * blockDim.x) {
+    int4 e[kCompactU];
+    bool keep[kCompactU];
+#pragma unroll
+    for (int u = 0; u < kCompactU; ++u) {
+      const int i = b + u * blockDim.x + threadIdx.x;
+      e[u] = make_int4(0, 0, 0, 0);
+      keep[u] = false;
+      if (i < n) {
+        e[u] = cand[i];
+        keep[u] = keep_f(e[u]);
+      }
     }
-    const unsigned bal = __ballot_sync(kFull, keep);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) scratch[wid] = __popc(bal);
+    unsigned bal[kCompactU];
+#pragma unroll
+    for (int u = 0; u < kCompactU; ++u) {
+      bal[u] = __ballot_sync(kFull, keep[u]);
+      if (lane == 0) scratch[u * nw + wid] = __popc(bal[u]);
+    }
     __syncthreads();
-    int before = out, tot = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      if (w < wid) before += scratch[w];
-      tot += scratch[w];
+    // entry (u, thread) follows every kept entry of sub-blocks < u and of
+    // the warps before it in sub-block u
+#pragma unroll
+    for (int u = 0; u < kCompactU; ++u) {
+      int before = out, tot = 0;
+      for (int w = 0; w < nw; ++w) {
+        const int c = scratch[u * nw + w];
+        if (w < wid) before += c;
+        tot += c;
+      }
+      if (keep[u]) cand[before + __popc(bal[u] & below)] = e[u];
+      out += tot;
     }
-    if (keep) cand[before + __popc(bal & ((1u << lane) - 1u))] = e;
-    out += tot;
     __syncthreads();
   }
   if (threadIdx.x == 0) *cnt = out;
@@ -613,9 +635,12 @@ __device__ __forceinline__ float row_score(const float* __restrict__ x, const fl
 // 256 rows' worth of loads outstanding) and folds it in ascending dimension
 // order. Keys (score, id) go to the top-k buffer.
 // SRC 0: the pilot (ids in S.estk); SRC 1: the candidate list (positions).
+// kmax: keys above it cannot enter the result and are not kept (the rest
+// of the re-rank set, once the pilot's k smallest keys are known).
 template <int SRC>
 __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q, int count,
-                            const int4* cand, int* top_cnt, int* surv_cnt) {
+                            const int4* cand, int* top_cnt, int* surv_cnt,
+                            unsigned long long kmax = ~0ull) {
   const int d = P.d;
   // Ask L2 for every row of the set first (no registers held, no waiting):
   // the loads below then find most rows in L2 instead of waiting on DRAM
@@ -645,9 +670,11 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
       const float* x = P.data_b + (int64_t)pos * d;
       acc = P.metric ? row_score<true>(x, S.qv, d) : row_score<false>(x, S.qv, d);
     }
-    const int slot = warp_reserve(valid, top_cnt);
+    const unsigned long long key = ((unsigned long long)float_key(acc) << 32) | (uint32_t)id;
+    const bool take = valid && key <= kmax;
+    const int slot = warp_reserve(take, top_cnt);
+    if (take) S.topk[slot] = key;
     if (valid) {
-      S.topk[slot] = ((unsigned long long)float_key(acc) << 32) | (uint32_t)id;
       const int si = i + (SRC == 0 ? 0 : *surv_cnt);
       if (P.tr.surv_ids && si < P.tr.surv_cap) P.tr.surv_ids[q * P.tr.surv_cap + si] = id;
     }
@@ -666,7 +693,7 @@ struct TailShared {
   int* cand_cnt;
   int* top_cnt;
   int* surv;
-  int* scratch;  // kThreads / 32 ints
+  int* scratch;  // kCompactU x kThreads / 32 ints
 };
 
 // The per-query end of the search (§4, reading R1): given the list of
@@ -738,15 +765,38 @@ __device__ void finish_query(const FusedParams& P, const FusedSmem& S, int64_t q
   // the rest of the re-rank set: LB <= tau, outside the pilot
   compact_cand(cand, ts.cand_cnt, cand_cap, ts.scratch,
                [tau](const int4& e) { return e.x >= 0 && __int_as_float(e.y) <= tau; });
-  rerank_rows<1>(P, S, q, *ts.cand_cnt, cand, ts.top_cnt, ts.surv);
-  select_keep_dk(S.topk, ts.top_cnt, k, *S.sel);
-  const int got = min(*ts.top_cnt, k);
-  sort_kept_u64(S.topk, got, k);
-  for (int j2 = tid; j2 < k; j2 += blockDim.x) {
-    const bool ok = j2 < got;
-    P.out_ids[q * k + j2] = ok ? (int64_t)(S.topk[j2] & 0xffffffffu) : -1;
-    const float v = ok ? key_float((uint32_t)(S.topk[j2] >> 32)) : __int_as_float(0x7f800000);
-    P.out_dist[q * k + j2] = P.metric ? -v : v;  // inner products: <o_r, q_r>, -inf pads
+  // with k pilot keys kept, a key above the k-th of them cannot be in the
+  // result (keys are distinct): such keys are not kept
+  rerank_rows<1>(P, S, q, *ts.cand_cnt, cand, ts.top_cnt, ts.surv, T1);
+  const int n_top = *ts.top_cnt;
+  if (n_top <= (int)blockDim.x) {
+    // few keys (the usual case): each thread ranks its key against all of
+    // them (distinct keys, so the ranks are a permutation) and writes it to
+    // its place in the result
+    const bool has = tid < n_top;
+    const unsigned long long mine = has ? S.topk[tid] : 0ull;
+    int r = 0;
+    if (has)
+      for (int j2 = 0; j2 < n_top; ++j2) r += S.topk[j2] < mine ? 1 : 0;
+    if (has && r < k) {
+      P.out_ids[q * k + r] = (int64_t)(mine & 0xffffffffu);
+      const float v = key_float((uint32_t)(mine >> 32));
+      P.out_dist[q * k + r] = P.metric ? -v : v;  // inner products: <o_r, q_r>
+    }
+    for (int j2 = n_top + tid; j2 < k; j2 += blockDim.x) {
+      P.out_ids[q * k + j2] = -1;
+      P.out_dist[q * k + j2] = P.metric ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+    }
+  } else {
+    select_keep_dk(S.topk, ts.top_cnt, k, *S.sel);
+    const int got = min(*ts.top_cnt, k);
+    sort_kept_u64(S.topk, got, k);
+    for (int j2 = tid; j2 < k; j2 += blockDim.x) {
+      const bool ok = j2 < got;
+      P.out_ids[q * k + j2] = ok ? (int64_t)(S.topk[j2] & 0xffffffffu) : -1;
+      const float v = ok ? key_float((uint32_t)(S.topk[j2] >> 32)) : __int_as_float(0x7f800000);
+      P.out_dist[q * k + j2] = P.metric ? -v : v;  // inner products: <o_r, q_r>, -inf pads
+    }
   }
   if (tid == 0) {
     if (P.tr.tau_ub) P.tr.tau_ub[q] = tau_ub;
@@ -839,7 +889,7 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_ub_cnt, s_cand_cnt, s_top_cnt, s_surv, s_overflow;
   __shared__ float s_tau;
-  __shared__ int s_scratch[kThreads / 32];
+  __shared__ int s_scratch[kCompactU * kThreads / 32];
   __shared__ SelState s_sel;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
   size_t off[10];
@@ -1159,7 +1209,7 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
 __global__ void __launch_bounds__(kThreads) split_merge_kernel(FusedParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_cand_cnt, s_top_cnt, s_surv, s_fill;
-  __shared__ int s_scratch[kThreads / 32];
+  __shared__ int s_scratch[kCompactU * kThreads / 32];
   __shared__ SelState s_sel;
   __shared__ int s_off[33];
   const int tid = threadIdx.x;
@@ -1518,7 +1568,7 @@ __global__ void __launch_bounds__(kThreads) list_threshold_kernel(int4* __restri
                                                                   float* __restrict__ qtau) {
   __shared__ SelState sel;
   __shared__ int s_cnt;
-  __shared__ int s_scratch[kThreads / 32];
+  __shared__ int s_scratch[kCompactU * kThreads / 32];
   for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
     int4* L = lists + q * cap;
     if (threadIdx.x == 0) s_cnt = min(lcnt[q], cap);
@@ -1546,7 +1596,7 @@ __global__ void __launch_bounds__(kThreads) tc_tail_kernel(FusedParams P, int4* 
                                                            int32_t* lcnt, int cap) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_cand_cnt, s_top_cnt, s_surv;
-  __shared__ int s_scratch[kThreads / 32];
+  __shared__ int s_scratch[kCompactU * kThreads / 32];
   __shared__ SelState s_sel;
   size_t off[10];
   fused_smem_bytes(P.pch, P.bq, P.W, P.d, P.cu, P.ce, P.ct, blockDim.x >> 5, off);
