@@ -433,6 +433,139 @@ __device__ K block_select(const K* a, int n, int want, SelState& st) {
   return block_select_f<K>(n, want, st, [a](int i) { return a[i]; });
 }
 
+// The want-th smallest (1-based, want <= n) of n 32-bit keys: one histogram
+// of kHistBins equal-width bins over [min, max] (bin = (key - min) kHistBins
+// / (max - min + 1): monotone in the key, so the bins order the keys), then
+// an exact selection among the keys of the boundary bin, collected into coll
+// (ranked directly when they fit one per thread). rem = how many keys equal
+// to the result are among the want smallest, eq = how many keys equal it in
+// all. hist: kHistBins ints; coll: coll_cap keys. Falls back to the radix
+// select when the boundary bin does not fit coll. Whole block (kThreads
+// threads); synchronized on return.
+constexpr int kHistBins = 1024;
+template <class F>
+__device__ uint32_t hist_select(int n, int want, SelState& st, int* hist, uint32_t* coll,
+                                int coll_cap, int& rem, int& eq, F keyf) {
+  static_assert(kHistBins == 4 * kThreads, "four bins per thread");
+  __shared__ int s_hs[5];  // boundary bin, keys below it, fill, rem, eq
+  __shared__ uint32_t s_T;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  uint32_t kmin = 0xffffffffu, kmax = 0u;
+  for (int i = tid; i < n; i += blockDim.x) {
+    const uint32_t key = keyf(i);
+    kmin = key < kmin ? key : kmin;
+    kmax = key > kmax ? key : kmax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t a = __shfl_xor_sync(kFull, kmin, o), b = __shfl_xor_sync(kFull, kmax, o);
+    kmin = a < kmin ? a : kmin;
+    kmax = b > kmax ? b : kmax;
+  }
+  if (lane == 0) {
+    st.wmin[wid] = kmin;
+    st.wmax[wid] = kmax;
+  }
+  __syncthreads();
+  kmin = 0xffffffffu;
+  kmax = 0u;
+  for (int w = 0; w < nw; ++w) {
+    kmin = (uint32_t)st.wmin[w] < kmin ? (uint32_t)st.wmin[w] : kmin;
+    kmax = (uint32_t)st.wmax[w] > kmax ? (uint32_t)st.wmax[w] : kmax;
+  }
+  if (kmin == kmax) {  // all keys equal
+    rem = want;
+    eq = n;
+    __syncthreads();
+    return kmin;
+  }
+  const uint64_t span = (uint64_t)(kmax - kmin) + 1u;
+  auto bin_of = [kmin, span](uint32_t key) {
+    return (int)(((uint64_t)(key - kmin) * (uint64_t)kHistBins) / span);
+  };
+  for (int i = tid; i < kHistBins; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) atomicAdd(&hist[bin_of(keyf(i))], 1);
+  __syncthreads();
+  // the bin holding the want-th key: four bins per thread, block prefix sum
+  int c[4], sum = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    c[u] = hist[4 * tid + u];
+    sum += c[u];
+  }
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) st.warp_cnt[wid] = incl;
+  __syncthreads();
+  for (int w = 0; w < wid; ++w) incl += st.warp_cnt[w];
+  const int excl = incl - sum;
+  if (excl < want && incl >= want) {  // exactly one thread
+    int cum = excl;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (cum + c[u] >= want) {
+        s_hs[0] = 4 * tid + u;
+        s_hs[1] = cum;
+        break;
+      }
+      cum += c[u];
+    }
+  }
+  if (tid == 0) s_hs[2] = 0;
+  __syncthreads();
+  const int B = s_hs[0], below = s_hs[1], nB = hist[B], want_b = want - below;
+  uint32_t T;
+  if (nB <= coll_cap) {
+    for (int b0 = 0; b0 < n; b0 += blockDim.x) {
+      const int i = b0 + tid;
+      uint32_t key = 0u;
+      bool in = false;
+      if (i < n) {
+        key = keyf(i);
+        in = bin_of(key) == B;
+      }
+      const int slot = warp_reserve(in, &s_hs[2]);
+      if (in) coll[slot] = key;
+    }
+    __syncthreads();
+    if (nB <= (int)blockDim.x) {  // rank each key of the bin against the others
+      if (tid < nB) {
+        const uint32_t mine = coll[tid];
+        int lt = 0, le = 0;
+        for (int j = 0; j < nB; ++j) {
+          const uint32_t v = coll[j];
+          lt += v < mine ? 1 : 0;
+          le += v <= mine ? 1 : 0;
+        }
+        if (lt < want_b && want_b <= le) {  // the threads holding the result
+          s_T = mine;
+          s_hs[3] = want_b - lt;
+          s_hs[4] = le - lt;
+        }
+      }
+      __syncthreads();
+      T = s_T;
+      rem = s_hs[3];
+      eq = s_hs[4];
+    } else {
+      T = block_select_f<uint32_t>(nB, want_b, st, [coll](int i) { return coll[i]; });
+      rem = st.rem;
+      eq = st.hist[st.bin];
+    }
+  } else {
+    T = block_select_f<uint32_t>(n, want, st, keyf);
+    rem = st.rem;
+    eq = st.hist[st.bin];
+  }
+  __syncthreads();
+  return T;
+}
+
 // In place, keep the keys below T and `ties` of the keys equal to T; returns
 // the new count (whole block; synchronized on return).
 template <class K>
@@ -720,14 +853,16 @@ __device__ void finish_query(const FusedParams& P, const FusedSmem& S, int64_t q
   const bool pilot_all = nl <= m;
   uint32_t T_e = 0xffffffffu, T_id = 0xffffffffu;
   if (!pilot_all) {
-    T_e = block_select_f<uint32_t>(nl, m, *S.sel,
-                                   [cand](int i) { return float_key(__int_as_float(cand[i].z)); });
-    const int ties = S.sel->rem;
+    // the top-k buffer is free until the pilot's re-rank: histogram and
+    // boundary-bin keys go there
+    int ties = 0, eqn = 0;
+    T_e = hist_select(nl, m, *S.sel, reinterpret_cast<int*>(S.topk),
+                      reinterpret_cast<uint32_t*>(S.topk) + kHistBins, 2 * P.ct - kHistBins, ties,
+                      eqn, [cand](int i) { return float_key(__int_as_float(cand[i].z)); });
     // among the list entries whose estimate equals the m-th one, the
-    // `ties` smallest ids belong to the pilot; the last pass's histogram
-    // counts those entries, and when all of them belong (the usual case:
-    // one entry) no id selection is needed
-    if (S.sel->hist[S.sel->bin] > ties)
+    // `ties` smallest ids belong to the pilot; when all of them belong (the
+    // usual case: one entry) no id selection is needed
+    if (eqn > ties)
       T_id = block_select_f<uint32_t>(nl, ties, *S.sel, [cand, T_e, &P](int i) {
         const int4 e = cand[i];
         return float_key(__int_as_float(e.z)) == T_e ? (uint32_t)__ldg(P.perm + e.x) : 0xffffffffu;
@@ -748,12 +883,18 @@ __device__ void finish_query(const FusedParams& P, const FusedSmem& S, int64_t q
     }
     const int slot = warp_reserve(in, &s_pilot);
     if (in) {
-      S.estk[slot] = ((unsigned long long)(uint32_t)__ldg(P.perm + e.x) << 32) | (uint32_t)e.x;
+      S.estk[slot] = (uint32_t)e.x;
       cand[i].x = e.x | (int)0x80000000;
     }
   }
   __syncthreads();
   const int pilot = s_pilot;
+  // the pilot's ids, all loads in flight together
+  for (int i = tid; i < pilot; i += blockDim.x) {
+    const unsigned long long e = S.estk[i];
+    S.estk[i] = ((unsigned long long)(uint32_t)__ldg(P.perm + (uint32_t)e) << 32) | e;
+  }
+  __syncthreads();
   // exact distances of the pilot; tau1 = k-th smallest of them
   rerank_rows<0>(P, S, q, pilot, cand, ts.top_cnt, ts.surv);
   // tau1: the k-th smallest exact distance of the pilot; only the k smallest
