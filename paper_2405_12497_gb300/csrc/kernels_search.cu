@@ -613,23 +613,50 @@ __device__ K select_keep(K* a, int* cnt, int keep, SelState& st) {
   return T;
 }
 
+// select_keep for 32-bit keys by the histogram select (hist, coll: shared
+// memory the caller has free at this point).
+__device__ uint32_t select_keep_h(uint32_t* a, int* cnt, int keep, SelState& st, int* hist,
+                                  uint32_t* coll, int coll_cap) {
+  const int n = *cnt;
+  if (n < keep) {
+    __syncthreads();
+    return 0xffffffffu;
+  }
+  int rem = 0, eq = 0;
+  const uint32_t T =
+      hist_select(n, keep, st, hist, coll, coll_cap, rem, eq, [a](int i) { return a[i]; });
+  const int kept = block_keep_below<uint32_t>(a, n, T, rem, st);
+  if (threadIdx.x == 0) *cnt = kept;
+  __syncthreads();
+  return T;
+}
+
 // Keep the `keep` smallest of the *cnt distinct (distance key << 32 | id)
-// keys of a: a 32-bit select on the distance half, then -- only when more
+// keys of a: a 32-bit select on the distance half (by the histogram select
+// when hist/coll are given, else the radix select), then -- only when more
 // keys share the boundary distance than are kept -- one on the id half of
 // those. Returns the keep-th smallest key (~0 if there are fewer than keep).
 // Whole block; synchronized on return.
 __device__ unsigned long long select_keep_dk(unsigned long long* a, int* cnt, int keep,
-                                             SelState& st) {
+                                             SelState& st, int* hist = nullptr,
+                                             uint32_t* coll = nullptr, int coll_cap = 0) {
   const int n = *cnt;
   if (n < keep) {
     __syncthreads();
     return ~0ull;
   }
-  const uint32_t Td =
-      block_select_f<uint32_t>(n, keep, st, [a](int i) { return (uint32_t)(a[i] >> 32); });
-  const int ties = st.rem;
+  uint32_t Td;
+  int ties = 0, eqn = 0;
+  if (hist) {
+    Td = hist_select(n, keep, st, hist, coll, coll_cap, ties, eqn,
+                     [a](int i) { return (uint32_t)(a[i] >> 32); });
+  } else {
+    Td = block_select_f<uint32_t>(n, keep, st, [a](int i) { return (uint32_t)(a[i] >> 32); });
+    ties = st.rem;
+    eqn = st.hist[st.bin];
+  }
   uint32_t Tid = 0xffffffffu;
-  if (st.hist[st.bin] > ties)
+  if (eqn > ties)
     Tid = block_select_f<uint32_t>(n, ties, st, [a, Td](int i) {
       return (uint32_t)(a[i] >> 32) == Td ? (uint32_t)(a[i] & 0xffffffffu) : 0xffffffffu;
     });
@@ -899,8 +926,13 @@ __device__ void finish_query(const FusedParams& P, const FusedSmem& S, int64_t q
   rerank_rows<0>(P, S, q, pilot, cand, ts.top_cnt, ts.surv);
   // tau1: the k-th smallest exact distance of the pilot; only the k smallest
   // pilot keys can be in the result, so the rest are dropped here
+  // (the pilot list is free now and holds the histogram when large enough;
+  // the upper-bound buffer, free since tau_ub, holds the boundary keys)
+  const bool hsel = 2 * P.ce >= kHistBins && P.cu >= 256;
   const unsigned long long T1 =
-      (pilot >= k) ? select_keep_dk(S.topk, ts.top_cnt, k, *S.sel) : ~0ull;
+      (pilot >= k) ? select_keep_dk(S.topk, ts.top_cnt, k, *S.sel,
+                                    hsel ? reinterpret_cast<int*>(S.estk) : nullptr, S.ubk, P.cu)
+                   : ~0ull;
   const float tau1 = (pilot >= k) ? key_float((uint32_t)(T1 >> 32)) : __int_as_float(0x7f800000);
   const float tau = fminf(tau_ub, tau1);
   // the rest of the re-rank set: LB <= tau, outside the pilot
@@ -1013,7 +1045,8 @@ __device__ __forceinline__ int code_ip(const CodeRegs<WT>& r, const uint64_t* __
 
 constexpr int kPPT = 4;  // most pairs per thread per scan round (buffer sizing)
 
-// Pairs per thread per round: as many as the code registers allow.
+// Pairs per thread per round: two (four cost spills at the four-CTA register
+// budget), one for codes longer than 512 bits.
 template <int WT>
 __host__ __device__ constexpr int pairs_per_thread() {
   return WT == 0 ? 2 : (WT <= 4 ? 2 : (WT <= 8 ? 2 : 1));
@@ -1113,23 +1146,19 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
       constexpr int PPT = pairs_per_thread<WT>();
       const int step = PPT * blockDim.x;
       // each thread takes PPT consecutive pairs per round (mostly of one
-      // probe), so the probe's bit-planes and constants stay in registers
-      // and are reloaded only when the thread's pairs move to another probe
-      constexpr bool kRegPlanes = WT > 0 && WT <= 4 && BQT > 0;
-      uint64_t rpl[kRegPlanes ? BQT * WT : 1];
-      float4 rmt = make_float4(0.f, 0.f, 0.f, 0.f);
-      int rsum = 0, rj = -1;
+      // probe); the probe's bit-planes are read from shared memory (holding
+      // them in registers cost spills at the four-CTA register budget)
       for (int base = 0; base < total; base += step) {
         // issue every load of this thread's PPT pairs first (they are
         // independent), then evaluate; keeps PPT code/factor loads in flight
         const int t0 = base + tid * PPT;
-        int64_t posv[PPT];
+        int posv[PPT];
         int jv[PPT];
         CodeRegs<WT> cr[PPT];
         float4 fv[PPT];
         // consecutive pairs advance through a bucket: the prefix array is
         // consulted again only at a bucket boundary
-        int64_t pos = 0;
+        int pos = 0;
         int next_b = 0;
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp) {
@@ -1139,15 +1168,15 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
           if (t < total) {
             if (pp == 0 || t >= next_b) {
               while (S.pref[j + 1] <= t) ++j;
-              pos = (int64_t)S.pbeg[j] + (t - S.pref[j]);
+              pos = S.pbeg[j] + (t - S.pref[j]);
               next_b = S.pref[j + 1];
             } else {
               ++pos;
             }
             posv[pp] = pos;
             jv[pp] = j;
-            load_code<WT>(cr[pp], P.codes + posv[pp] * W);
-            fv[pp] = __ldg(P.factors + posv[pp]);
+            load_code<WT>(cr[pp], P.codes + (size_t)(uint32_t)posv[pp] * (uint32_t)W);
+            fv[pp] = __ldg(P.factors + (uint32_t)posv[pp]);
           }
         }
         // evaluate the estimator and its bounds for every pair of the round
@@ -1162,34 +1191,10 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
           ipv[pp] = 0;
           if (posv[pp] >= 0) {
             const int jj = jv[pp];
-            int ip;
-            float4 mt;
-            int psum;
-            if constexpr (kRegPlanes) {
-              if (jj != rj) {  // the thread's pairs entered another probe
-                const uint64_t* pl = S.planes + (size_t)jj * BQT * WT;
-#pragma unroll
-                for (int w = 0; w < BQT * WT; ++w) rpl[w] = pl[w];
-                rmt = S.pmeta[jj];
-                rsum = S.psum[jj];
-                rj = jj;
-              }
-              ip = 0;
-#pragma unroll
-              for (int b = 0; b < BQT; ++b) {
-                int pb = 0;
-#pragma unroll
-                for (int w = 0; w < WT; ++w) pb += __popcll(cr[pp].c[w] & rpl[b * WT + w]);
-                ip += pb << b;
-              }
-              mt = rmt;
-              psum = rsum;
-            } else {
-              ip = code_ip<WT, BQT>(cr[pp], P.codes + posv[pp] * W,
-                                    S.planes + (size_t)jj * bq * W, W, bq);
-              mt = S.pmeta[jj];
-              psum = S.psum[jj];
-            }
+            const int ip = code_ip<WT, BQT>(cr[pp], P.codes + (size_t)(uint32_t)posv[pp] * (uint32_t)W,
+                                            S.planes + (size_t)jj * bq * W, W, bq);
+            const float4 mt = S.pmeta[jj];
+            const int psum = S.psum[jj];
             const float4 f = fv[pp];
             // estimator (§3.3.2 + Theorem 3.2) and its bound, fixed FP32 order
             const float t1 = (float)(2 * ip - psum);
@@ -1260,7 +1265,11 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
         bool ovf = s_overflow != 0;
         __syncthreads();
         if (ub_cnt > P.cu - room) {  // keep the k smallest upper bounds
-          const uint32_t T = select_keep<uint32_t>(S.ubk, &s_ub_cnt, k, *S.sel);
+          // (the top-k buffer is free during the scan)
+          const uint32_t T = select_keep_h(S.ubk, &s_ub_cnt, k, *S.sel,
+                                           reinterpret_cast<int*>(S.topk),
+                                           reinterpret_cast<uint32_t*>(S.topk) + kHistBins,
+                                           2 * P.ct - kHistBins);
           if (tid == 0) s_tau = key_float(T);
           __syncthreads();
         }
@@ -1292,7 +1301,13 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
     }
     // tau_ub: k-th smallest upper bound; pilot: the m smallest estimates
     const int n_ub = s_ub_cnt;
-    const uint32_t T_ub = (n_ub >= k) ? block_select<uint32_t>(S.ubk, n_ub, k, *S.sel) : 0u;
+    int ub_rem = 0, ub_eq = 0;
+    const uint32_t T_ub =
+        (n_ub >= k) ? hist_select(n_ub, k, *S.sel, reinterpret_cast<int*>(S.topk),
+                                  reinterpret_cast<uint32_t*>(S.topk) + kHistBins,
+                                  2 * P.ct - kHistBins, ub_rem, ub_eq,
+                                  [&S](int i) { return S.ubk[i]; })
+                    : 0u;
     const float tau_ub = (n_ub >= k) ? key_float(T_ub) : __int_as_float(0x7f800000);
     TailShared ts{&s_cand_cnt, &s_top_cnt, &s_surv, s_scratch};
     // Stage the entries with LB <= tau_ub in shared memory (one pass with
