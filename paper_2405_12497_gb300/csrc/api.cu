@@ -53,6 +53,9 @@ void free_index_arrays(rabitq_index* X) {
   cudaFree(X->P32);
   cudaFree(X->ptb);
   cudaFree(X->ptf);
+  cudaFree(X->ctf);
+  cudaFree(X->cn2);
+  cudaFree(X->cnorm);
 }
 
 int alloc_index_arrays(rabitq_index* X) {
@@ -72,6 +75,9 @@ int alloc_index_arrays(rabitq_index* X) {
   X->kp = (X->d + 63) / 64 * 64;
   RBQ_CHECK(dev_alloc(reinterpret_cast<uint16_t**>(&X->ptb), (size_t)X->dpad * X->kp));
   RBQ_CHECK(dev_alloc(&X->ptf, (size_t)X->dpad * X->kp));
+  RBQ_CHECK(dev_alloc(&X->ctf, (size_t)X->K * X->kp));
+  RBQ_CHECK(dev_alloc(&X->cn2, (size_t)X->K));
+  RBQ_CHECK(dev_alloc(&X->cnorm, (size_t)X->K));
   return RABITQ_OK;
 }
 
@@ -219,6 +225,7 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
                            X->centroids, s));
     }
     RBQ_CHECK(transpose_f32(X->centroids, n_clusters, d, X->centroids_t, s));
+    RBQ_CHECK(pack_centroids(X, s));
     RBQ_CHECK(adist.alloc(sizeof(float) * n, s));
     RBQ_CHECK(argmin_sqdist(ddata, d, X->centroids_t, n_clusters, n, n_clusters, d, X->assign,
                             adist.as<float>(), s));
@@ -506,7 +513,7 @@ int rabitq_estimate(const rabitq_index* X, const float* queries, int64_t nq, con
   int h_err = 0;
   RBQ_CUDA(cudaMemcpyAsync(&h_err, eb.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   RBQ_CUDA(cudaStreamSynchronize(s));
-  if (h_err == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired in the query rotation");
+  if (h_err == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired (probe scores or query rotation)");
   if (h_err) return fail(RABITQ_EINVAL, "rabitq_estimate: an id is outside [-1, n)");
   return RABITQ_OK;
 }
@@ -689,6 +696,7 @@ int rabitq_index_load(const char* path, const rabitq_build_opts* opts, rabitq_in
   if (st == RABITQ_OK && (crc != h.payload_crc || total != h.payload_bytes))
     st = fail(RABITQ_EIO, std::string("index file checksum mismatch: ") + path);
   if (st == RABITQ_OK) st = transpose_f32(X->centroids, X->K, X->d, X->centroids_t, nullptr);
+  if (st == RABITQ_OK) st = pack_centroids(X, nullptr);
   if (st == RABITQ_OK) st = invert_perm(X->perm, X->n, X->inv_perm, nullptr);
   if (st == RABITQ_OK) {
     const int64_t tot = (int64_t)X->dpad * X->dpad;

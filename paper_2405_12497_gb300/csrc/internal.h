@@ -34,6 +34,11 @@ struct rabitq_index {
   int32_t tuned_path = 0;         // scan path AUTO uses (rabitq_autotune)
   void* ptb = nullptr;            // dpad x kp BF16
   float* ptf = nullptr;           // dpad x kp TF32-rounded FP32
+  // centroids for the tensor-core probe scores: K x kp TF32-rounded rows,
+  // and the FP32 norms ||c||^2 (canonical fold) and ||c||
+  float* ctf = nullptr;
+  float* cn2 = nullptr;
+  float* cnorm = nullptr;
 };
 
 // Learned probe-count predictor (kernels_mlp.cu): MLP weights with BF16
@@ -89,8 +94,7 @@ struct DevBuf {
 // ---- canonical SIMT "GEMM" (kernels_gemm.cu) ----------------------------
 // C[m][n] = fold_k op(A'[m][k], B[k][n]) in ascending k, where
 // A'[m][k] = A[arow(m)][k] - (sub ? sub[srow(m)][k] : 0); arow(m) = a_rows ? a_rows[m] : m.
-// kNegDot stores -dot (the inner-product metric ranks by -<q, c>).
-enum GemmOp { kDot = 0, kSqDist = 1, kNegDot = 2 };
+enum GemmOp { kDot = 0, kSqDist = 1 };
 int gemm_canon(GemmOp op, const float* A, int64_t lda, const int32_t* a_rows, const float* sub,
                int64_t ld_sub, const int32_t* sub_rows, const float* B, int64_t ldb, float* C,
                int64_t ldc, int64_t M, int N, int K, cudaStream_t s);
@@ -122,6 +126,13 @@ int check_finite(const float* x, int64_t count, cudaStream_t s, bool* finite);
 
 // ---- tensor-core query rotation (kernels_tc.cu) --------------------------
 int pack_pt(rabitq_index* X, cudaStream_t s);
+// TF32 centroid rows and their norms (after the centroids are final)
+int pack_centroids(rabitq_index* X, cudaStream_t s);
+// out[m][c] = <q_m, c> for all K centroids with TF32 operands on tensor
+// cores, FP32 accumulation (the probe filter's approximate scores); *err = 2
+// when a bounded wait expired
+int centroid_dot_tc(const rabitq_index* X, const float* Q, int64_t M, float* out, int* err,
+                    cudaStream_t s);
 // out[M x dpad] = Q[M x d] P (mode RABITQ_ROT_BF16 or RABITQ_ROT_TF32);
 // a bounded wait that expires sets *err = 2
 int rotate_tc(const rabitq_index* X, const float* Q, int64_t M, int mode, float* out, int* err,

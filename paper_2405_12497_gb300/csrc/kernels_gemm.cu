@@ -5,9 +5,7 @@
 // squared distance: t = a - b, fma(t, t, s)), so the result is bit-identical
 // to a plain sequential loop whatever the tile shape. Used for the residual
 // rotation P^{-1}(o_r - c) of the index phase (§3.1.3), the query rotation
-// (§3.3, FP32 mode), P^T c per centroid, the query-centroid distances of the
-// IVF probe (§4: squared distances, or negated inner products for the
-// inner-product metric) and the k-means assignment.
+// (§3.3, FP32 mode), P^T c per centroid and the k-means assignment.
 //
 // Register-tiled: 128 x 128 block tile, 8-deep k slices staged in shared
 // memory, an 8 x 8 micro-tile per thread (256 threads).
@@ -21,7 +19,7 @@ constexpr int BM = 128, BN = 128, BK = 8, NT = 256;
 
 template <int OP>
 __device__ __forceinline__ float accum(float acc, float a, float b) {
-  if (OP != kSqDist) return __fmaf_rn(a, b, acc);
+  if (OP == kDot) return __fmaf_rn(a, b, acc);
   const float t = __fsub_rn(a, b);
   return __fmaf_rn(t, t, acc);
 }
@@ -124,7 +122,7 @@ __global__ void __launch_bounds__(NT) gemm_canon_kernel(
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int gn = n0 + tx + 16 * j;
-      if (gn < N) C[gm * ldc + gn] = OP == kNegDot ? -acc[i][j] : acc[i][j];
+      if (gn < N) C[gm * ldc + gn] = acc[i][j];
     }
   }
 }
@@ -207,9 +205,6 @@ int gemm_canon(GemmOp op, const float* A, int64_t lda, const int32_t* a_rows, co
     else
       gemm_canon_kernel<kDot, false><<<grid, NT, 0, s>>>(A, lda, a_rows, nullptr, 0, nullptr, B,
                                                           ldb, C, ldc, M, N, K);
-  } else if (op == kNegDot) {
-    gemm_canon_kernel<kNegDot, false><<<grid, NT, 0, s>>>(A, lda, a_rows, nullptr, 0, nullptr,
-                                                           B, ldb, C, ldc, M, N, K);
   } else {
     gemm_canon_kernel<kSqDist, false><<<grid, NT, 0, s>>>(A, lda, a_rows, nullptr, 0, nullptr,
                                                            B, ldb, C, ldc, M, N, K);

@@ -25,26 +25,20 @@ namespace rbq {
 namespace {
 
 constexpr int kThreads = 256;
-// select_kernel's shared-memory limit: every caller sets the same value (the
-// largest selection, 16384 entries), so concurrent searches never lower it
-// under one another's launch
-constexpr int kSelMaxSmem = 8 * 16384;
 
 // ------------------------------------------------------------ selection
-// Top-nsel of a row of K non-negative distances by (distance, id): radix
-// select of the nsel-th smallest key, collection of everything below it plus
-// the lowest ids among its ties, then a bitonic sort of the selection.
-__global__ void __launch_bounds__(kThreads) select_kernel(
-    const float* __restrict__ CD, int K, int nprobe, const int32_t* __restrict__ nprobe_q,
-    int sort_n, int32_t* __restrict__ out_ids, float* __restrict__ out_dist) {
-  extern __shared__ unsigned long long sel[];  // sort_n entries
+// Top-nsel of K scores score(c) by (score, id): radix select of the nsel-th
+// smallest key, collection of everything below it plus the lowest ids among
+// its ties, then a bitonic sort of the selection (sel: sort_n entries of
+// shared memory). Writes nprobe slots of out_ids/out_dist (-1/+inf after
+// nsel). Whole block.
+template <class F>
+__device__ void select_row(F score, int K, int nsel, int nprobe, int sort_n,
+                           unsigned long long* sel, int32_t* out_ids, float* out_dist) {
   __shared__ int hist[256];
   __shared__ uint32_t s_prefix, s_mask;
   __shared__ int s_remaining, s_less, s_tie_base;
-  const int q = blockIdx.x;
-  const float* row = CD + (int64_t)q * K;
-  int nsel = nprobe;
-  if (nprobe_q) nsel = min(max(nprobe_q[q], 1), nprobe);
+  __syncthreads();
   if (threadIdx.x == 0) {
     s_prefix = 0;
     s_mask = 0;
@@ -57,7 +51,7 @@ __global__ void __launch_bounds__(kThreads) select_kernel(
     __syncthreads();
     const uint32_t prefix = s_prefix, mask = s_mask;
     for (int c = threadIdx.x; c < K; c += blockDim.x) {
-      const uint32_t key = float_key(row[c]);
+      const uint32_t key = float_key(score(c));
       if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255], 1);
     }
     __syncthreads();
@@ -79,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) select_kernel(
   __syncthreads();
   const int n_less = nsel - need_ties;
   for (int c = threadIdx.x; c < K; c += blockDim.x) {
-    const uint32_t key = float_key(row[c]);
+    const uint32_t key = float_key(score(c));
     if (key < T) sel[atomicAdd(&s_less, 1)] = ((unsigned long long)key << 32) | (uint32_t)c;
   }
   __syncthreads();
@@ -88,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) select_kernel(
   for (int c0 = 0; c0 < K; c0 += blockDim.x) {
     if (s_tie_base >= need_ties) break;
     const int c = c0 + threadIdx.x;
-    const bool tie = (c < K) && float_key(row[c]) == T;
+    const bool tie = (c < K) && float_key(score(c)) == T;
     const unsigned b = __ballot_sync(kFull, tie);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) warp_cnt[wid] = __popc(b);
@@ -110,11 +104,12 @@ __global__ void __launch_bounds__(kThreads) select_kernel(
   block_bitonic_sort_u64(sel, sort_n);
   for (int j = threadIdx.x; j < nprobe; j += blockDim.x) {
     const bool ok = j < nsel;
-    out_ids[(int64_t)q * nprobe + j] = ok ? (int32_t)(sel[j] & 0xffffffffu) : -1;
-    out_dist[(int64_t)q * nprobe + j] = ok ? key_float((uint32_t)(sel[j] >> 32))
-                                           : __int_as_float(0x7f800000);
+    out_ids[j] = ok ? (int32_t)(sel[j] & 0xffffffffu) : -1;
+    out_dist[j] = ok ? key_float((uint32_t)(sel[j] >> 32)) : __int_as_float(0x7f800000);
   }
+  __syncthreads();
 }
+
 
 // ------------------------------------------------------ fused query kernel
 // Shared state of the block radix select.
@@ -846,6 +841,269 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
   __syncthreads();
   if (threadIdx.x == 0) *surv_cnt += count;
   __syncthreads();
+}
+
+// ------------------------------------------------------------ probe selection
+// The nsel nearest centroids of each query (§4's probe; for inner products
+// the largest <q_r, c>), exactly as a full canonical scan would rank them,
+// from tensor-core scores. For centroid c the TF32 product <q, c>~ (inputs
+// rounded to 10-bit mantissas, FP32 accumulation) gives the approximate score
+// s~ = ||q||^2 + ||c||^2 - 2 <q, c>~ (or -<q, c>~), within eps_c of the
+// canonical FP32 score (the bound is derived below). U_c = s~ + eps_c is an
+// upper and L_c = s~ - eps_c a lower bound of c's canonical score, so any T
+// at least the nsel-th smallest upper bound is at least the nsel-th smallest
+// canonical score, and every centroid of the exact top nsel has L_c <= T --
+// the same bound-and-filter step as the paper's re-ranking (§4). T is the
+// upper edge of the histogram bin of the upper bounds that holds the nsel-th
+// smallest. The candidates with L_c <= T get their canonical scores (the fold
+// the full scan uses) and the nsel smallest (score, id) are written in order.
+// If the candidates exceed the shared-memory list, the row select ranks every
+// centroid by its canonical score (computed on the fly). ip: nq x K
+// approximate products (read only).
+//
+// The bound: |t - x| <= 2^-11 |x| for each TF32 operand t, the products of
+// two TF32 values are exact in FP32, and the accumulation of d products in
+// FP32 is taken to lose at most (d + 2) 2^-21 of sum |q_i c_i| <= ||q|| ||c||
+// (four units of FP32 rounding per addition, to cover accumulation orders the
+// hardware does not document), so |<q,c>~ - <q,c>| <= a ||q|| ||c|| with
+// a = 2^-10 + (d + 2) 2^-21. The canonical dot and squared distance are
+// within d 2^-23 ||q|| ||c|| and (d + 2) 2^-24 (||q|| + ||c||)^2 of exact,
+// and the FP32 operations forming s~, U and L add a few units of
+// 2^-24 (||q|| + ||c||)^2; eps_c takes all of these with a 5% margin.
+constexpr int kProbeCandMax = 2048;  // candidates kept in shared memory
+constexpr int kProbeSmemK = 16384;   // up to this many centroids, keys in shared memory
+
+__device__ __forceinline__ float probe_eps(int ip_metric, float nq, float nc, int d) {
+  const float a = 0x1.0p-10f + (float)(d + 2) * 0x1.0p-21f;
+  const float qc = nq * nc, sq = (nq + nc) * (nq + nc);
+  const float e = ip_metric ? a * qc + (float)(d + 8) * 0x1.0p-22f * qc
+                            : 2.0f * a * qc + (float)(2 * d + 8) * 0x1.0p-23f * sq;
+  return 1.05f * e;
+}
+
+__global__ void __launch_bounds__(kThreads) probe_select_kernel(
+    const float* __restrict__ Q, int d, const float* __restrict__ ip, const float* __restrict__ C,
+    const float* __restrict__ cn2, const float* __restrict__ cnorm, int K, int metric,
+    int nprobe, const int32_t* __restrict__ nprobe_q, int sort_n, int smem_keys,
+    int32_t* __restrict__ out_ids, float* __restrict__ out_dist) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  // layout: q (d floats) | upper-bound keys (K, when smem_keys) | work area:
+  // the histogram, then the candidates, or the fallback's sort buffer
+  float* qs = reinterpret_cast<float*>(psm);
+  uint32_t* uk = reinterpret_cast<uint32_t*>(psm + align_up(sizeof(float) * d, 16));
+  unsigned char* work = reinterpret_cast<unsigned char*>(uk) +
+                        (smem_keys ? align_up(sizeof(uint32_t) * K, 16) : 0);
+  __shared__ SelState st;
+  __shared__ float s_nq2;
+  __shared__ int s_nc, s_bin;
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nw = blockDim.x >> 5;
+  const float* qg = Q + (int64_t)q * d;
+  const float* row = ip + (int64_t)q * K;
+  int nsel = nprobe;
+  if (nprobe_q) nsel = min(max(nprobe_q[q], 1), nprobe);
+  nsel = min(nsel, K);
+  // ||q||^2 (any summation order: the bound needs an FP32 value, not the fold)
+  float part = 0.0f;
+  for (int i = tid; i < d; i += blockDim.x) {
+    const float v = qg[i];
+    qs[i] = v;
+    part = __fmaf_rn(v, v, part);
+  }
+  part = warp_sum_f(part);
+  if (lane == 0) st.wmin[wid] = __float_as_uint(part);
+  if (tid == 0) s_nc = 0;
+  __syncthreads();
+  if (tid == 0) {
+    float a = 0.0f;
+    for (int w = 0; w < nw; ++w) a = __fadd_rn(a, __uint_as_float((uint32_t)st.wmin[w]));
+    s_nq2 = a;
+  }
+  __syncthreads();
+  const float nq2 = s_nq2, nq = __fsqrt_rn(nq2);
+  auto approx = [row, cn2, nq2, metric](int c) {
+    const float v = row[c];
+    return metric ? -v : __fsub_rn(__fadd_rn(nq2, cn2[c]), __fmul_rn(2.0f, v));
+  };
+  auto ukey = [&](int c) {
+    return smem_keys ? uk[c]
+                     : float_key(__fadd_rn(approx(c), probe_eps(metric, nq, cnorm[c], d)));
+  };
+  // L_c = U_c - 2 eps_c (its rounding is inside the bound's margin)
+  auto lkey = [&](int c) {
+    return float_key(
+        __fsub_rn(key_float(ukey(c)), __fmul_rn(2.0f, probe_eps(metric, nq, cnorm[c], d))));
+  };
+  // pass 1: the upper bounds' keys and their range; four centroids per
+  // thread per step, loads first
+  uint32_t kmin = 0xffffffffu, kmax = 0u;
+  for (int c0 = 0; c0 < K; c0 += 4 * blockDim.x) {
+    float v[4], n2[4], nn[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u * blockDim.x + tid;
+      v[u] = 0.0f;
+      n2[u] = 0.0f;
+      nn[u] = 0.0f;
+      if (c < K) {
+        v[u] = row[c];
+        n2[u] = cn2[c];
+        nn[u] = cnorm[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u * blockDim.x + tid;
+      if (c < K) {
+        const float sc = metric ? -v[u] : __fsub_rn(__fadd_rn(nq2, n2[u]), __fmul_rn(2.0f, v[u]));
+        const uint32_t key = float_key(__fadd_rn(sc, probe_eps(metric, nq, nn[u], d)));
+        if (smem_keys) uk[c] = key;
+        kmin = key < kmin ? key : kmin;
+        kmax = key > kmax ? key : kmax;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t a = __shfl_xor_sync(kFull, kmin, o), b = __shfl_xor_sync(kFull, kmax, o);
+    kmin = a < kmin ? a : kmin;
+    kmax = b > kmax ? b : kmax;
+  }
+  __syncthreads();  // (st.wmin held the norm partials)
+  if (lane == 0) {
+    st.wmin[wid] = kmin;
+    st.wmax[wid] = kmax;
+  }
+  int* hist = reinterpret_cast<int*>(work);
+  for (int i = tid; i < kHistBins; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  kmin = 0xffffffffu;
+  kmax = 0u;
+  for (int w = 0; w < nw; ++w) {
+    kmin = (uint32_t)st.wmin[w] < kmin ? (uint32_t)st.wmin[w] : kmin;
+    kmax = (uint32_t)st.wmax[w] > kmax ? (uint32_t)st.wmax[w] : kmax;
+  }
+  // pass 2: histogram of the upper bounds over [kmin, kmax]; T = the upper
+  // edge of the bin holding the nsel-th smallest (an upper bound of it)
+  const uint64_t span = (uint64_t)(kmax - kmin) + 1u;
+  for (int c = tid; c < K; c += blockDim.x)
+    atomicAdd(&hist[(int)(((uint64_t)(ukey(c) - kmin) * (uint64_t)kHistBins) / span)], 1);
+  __syncthreads();
+  {
+    int cb[4], sum = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      cb[u] = hist[4 * tid + u];
+      sum += cb[u];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) st.warp_cnt[wid] = incl;
+    __syncthreads();
+    for (int w = 0; w < wid; ++w) incl += st.warp_cnt[w];
+    const int excl = incl - sum;
+    if (excl < nsel && incl >= nsel) {  // exactly one thread
+      int cum = excl;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (cum + cb[u] >= nsel) {
+          s_bin = 4 * tid + u;
+          break;
+        }
+        cum += cb[u];
+      }
+    }
+  }
+  __syncthreads();
+  // keys of bin B are below kmin + ceil((B + 1) span / kHistBins)
+  const uint64_t edge = ((uint64_t)(s_bin + 1) * span + kHistBins - 1) / kHistBins;
+  const uint32_t T = (uint32_t)min((uint64_t)kmax, (uint64_t)kmin + edge - 1u);
+  // pass 3: candidates, L_c <= T (ids now, (score key, id) after the
+  // refine); four centroids per thread per step, loads first
+  unsigned long long* ckey = reinterpret_cast<unsigned long long*>(work);
+  for (int c0 = 0; c0 < K; c0 += 4 * blockDim.x) {
+    uint32_t lk4[4];
+    if (smem_keys) {
+      float nn[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u * blockDim.x + tid;
+        nn[u] = c < K ? cnorm[c] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u * blockDim.x + tid;
+        lk4[u] = c < K ? float_key(__fsub_rn(key_float(uk[c]),
+                                             __fmul_rn(2.0f, probe_eps(metric, nq, nn[u], d))))
+                       : 0xffffffffu;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u * blockDim.x + tid;
+        lk4[u] = c < K ? lkey(c) : 0xffffffffu;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u * blockDim.x + tid;
+      const bool in = c < K && lk4[u] <= T;
+      const int slot = warp_reserve(in, &s_nc);
+      if (in && slot < kProbeCandMax) ckey[slot] = (unsigned long long)(uint32_t)c;
+    }
+  }
+  __syncthreads();
+  const int nc = s_nc;
+  int32_t* oid = out_ids + (int64_t)q * nprobe;
+  float* od = out_dist + (int64_t)q * nprobe;
+  if (nc <= kProbeCandMax) {
+    // canonical scores of the candidates (one thread each, the full scan's
+    // fold, 16-byte loads eight in flight)
+    for (int i = tid; i < nc; i += blockDim.x) {
+      const int c = (int)(uint32_t)ckey[i];
+      const float* x = C + (int64_t)c * d;
+      const float a = metric ? row_score<true>(x, qs, d) : row_score<false>(x, qs, d);
+      ckey[i] = ((unsigned long long)float_key(a) << 32) | (uint32_t)c;
+    }
+    __syncthreads();
+    // rank each candidate among all of them (distinct keys: the ids differ)
+    for (int i = tid; i < nc; i += blockDim.x) {
+      const unsigned long long mine = ckey[i];
+      int r = 0;
+      for (int j = 0; j < nc; ++j) r += ckey[j] < mine ? 1 : 0;
+      if (r < nsel) {
+        oid[r] = (int32_t)(mine & 0xffffffffu);
+        od[r] = key_float((uint32_t)(mine >> 32));
+      }
+    }
+    for (int j = nsel + tid; j < nprobe; j += blockDim.x) {
+      oid[j] = -1;
+      od[j] = __int_as_float(0x7f800000);
+    }
+  } else {
+    // too many candidates: the row select over canonical scores computed on
+    // the fly (every pass refolds them; a rare path)
+    select_row(
+        [qs, C, d, metric](int c) {
+          const float* x = C + (int64_t)c * d;
+          return metric ? row_score<true>(x, qs, d) : row_score<false>(x, qs, d);
+        },
+        K, nsel, nprobe, sort_n, reinterpret_cast<unsigned long long*>(work), oid, od);
+  }
+}
+
+// Shared memory of probe_select_kernel for dimension d, K centroids (keys
+// held in shared memory or not) and sort size sort_n.
+inline size_t probe_select_smem(int d, int K, int sort_n, bool smem_keys) {
+  const size_t work = std::max({sizeof(int) * kHistBins,
+                                sizeof(unsigned long long) * kProbeCandMax,
+                                sizeof(unsigned long long) * (size_t)sort_n});
+  const size_t keys = smem_keys ? align_up(sizeof(uint32_t) * K, 16) : 0;
+  return align_up(sizeof(float) * d, 16) + keys + work;
 }
 
 // Shared counters the per-query finishing step works with.
@@ -1981,16 +2239,38 @@ int fused_shape(const SearchArgs& a, FusedShape* f) {
   return RABITQ_OK;
 }
 
-// Learned probe counts of one query chunk from its centroid distances cd
-// (nqc x K): the min(64, K) nearest buckets, then the fused MLP kernel.
-int predict_chunk(const SearchArgs& a, const float* cd, int64_t nqc, int64_t q0, int32_t* fid,
-                  float* fdist, cudaStream_t s) {
-  const int K = a.X->K;
-  const int navail = std::min(kMlpIn, K);
-  const int sn = pow2_at_least(navail);
-  select_kernel<<<(unsigned)nqc, kThreads, sizeof(unsigned long long) * sn, s>>>(
-      cd, K, navail, nullptr, sn, fid, fdist);
+// Probe lists from the tensor-core products cd (nqc x K, centroid_dot_tc):
+// the nsel (= nprobe, or npq[q] clamped to it) best centroids of each query
+// by exact canonical score, ascending (score, id), in rows of nprobe.
+int probe_select(const rabitq_index* X, const float* Q, int64_t nqc, const float* cd, int nprobe,
+                 const int32_t* npq, int32_t* ids, float* dist, cudaStream_t s) {
+  if (nqc <= 0) return RABITQ_OK;
+  const int sort_n = pow2_at_least(nprobe);
+  int dev = 0, optin = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
+  RBQ_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  RBQ_CUDA(cudaFuncGetAttributes(&fa, probe_select_kernel));
+  const size_t limit = (size_t)(optin - (int)fa.sharedSizeBytes);
+  RBQ_CUDA(cudaFuncSetAttribute(probe_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)limit));
+  // the bounds' keys stay in shared memory when they fit beside the rest
+  bool smem_keys = X->K <= kProbeSmemK && probe_select_smem(X->d, X->K, sort_n, true) <= limit;
+  const size_t smem = probe_select_smem(X->d, X->K, sort_n, smem_keys);
+  if (smem > limit) return fail(RABITQ_EINVAL, "probe selection does not fit shared memory");
+  probe_select_kernel<<<(unsigned)nqc, kThreads, smem, s>>>(
+      Q, X->d, cd, X->centroids, X->cn2, X->cnorm, X->K, X->metric != RABITQ_METRIC_L2 ? 1 : 0,
+      nprobe, npq, sort_n, smem_keys ? 1 : 0, ids, dist);
   RBQ_CUDA(cudaGetLastError());
+  return RABITQ_OK;
+}
+
+// Learned probe counts of one query chunk from its centroid products cd
+// (nqc x K): the min(64, K) nearest buckets, then the fused MLP kernel.
+int predict_chunk(const SearchArgs& a, const float* Q, const float* cd, int64_t nqc, int64_t q0,
+                  int32_t* fid, float* fdist, cudaStream_t s) {
+  const int navail = std::min(kMlpIn, a.X->K);
+  RBQ_CHECK(probe_select(a.X, Q, nqc, cd, navail, nullptr, fid, fdist, s));
   return mlp_infer(a.pred, fdist, navail, nqc, navail, a.pred_nprobe + q0, nullptr, nullptr, s);
 }
 
@@ -2019,10 +2299,11 @@ int search_queries(const rabitq_index* X, const float* Q, int64_t nq, float* qn,
   return RABITQ_OK;
 }
 
-int centroid_scores(const rabitq_index* X, const float* Q, int64_t nq, float* cd,
+// The approximate probe scores' products <q, c> for all K centroids on
+// tensor cores (probe_select turns them into exact probe lists).
+int centroid_scores(const rabitq_index* X, const float* Q, int64_t nq, float* cd, int* err,
                     cudaStream_t s) {
-  return gemm_canon(metric_ip(X) ? kNegDot : kSqDist, Q, X->d, nullptr, nullptr, 0, nullptr,
-                    X->centroids_t, X->K, cd, X->K, nq, X->K, X->d, s);
+  return centroid_dot_tc(X, Q, nq, cd, err, s);
 }
 
 int probe_nq2(const rabitq_index* X, const float* Q, int64_t nq, int nprobe, const int32_t* pid,
@@ -2132,16 +2413,12 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   if (timing)
     for (auto& e : ev) RBQ_CUDA(cudaEventCreate(&e));
 
-  const int sort_n = pow2_at_least(nprobe);
-  const size_t sel_smem = sizeof(unsigned long long) * sort_n;
-  RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSelMaxSmem));
   for (int64_t q0 = 0; q0 < a.nq; q0 += qchunk) {
     const int64_t nqc = std::min(qchunk, a.nq - q0);
     if (timing) RBQ_CUDA(cudaEventRecord(ev[0], s));
     const float* Q = nullptr;
     RBQ_CHECK(search_queries(X, a.queries + q0 * d, nqc, qn.as<float>(), &Q, s));
-    RBQ_CHECK(centroid_scores(X, Q, nqc, cd.as<float>(), s));
+    RBQ_CHECK(centroid_scores(X, Q, nqc, cd.as<float>(), err.as<int>(), s));
     if (timing) RBQ_CUDA(cudaEventRecord(ev[1], s));
     int32_t* probe_ids = a.trace && a.trace->probe_ids ? a.trace->probe_ids + q0 * nprobe
                                                        : pid.as<int32_t>();
@@ -2154,13 +2431,12 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
     const int navail = std::min(kMlpIn, K);
     const bool pred_from_list = a.pred && nprobe >= navail;
     if (a.pred && !pred_from_list) {
-      RBQ_CHECK(predict_chunk(a, cd.as<float>(), nqc, q0, fid.as<int32_t>(), fdist.as<float>(), s));
+      RBQ_CHECK(predict_chunk(a, Q, cd.as<float>(), nqc, q0, fid.as<int32_t>(),
+                              fdist.as<float>(), s));
       npq = a.pred_nprobe + q0;
     }
-    select_kernel<<<(unsigned)nqc, kThreads, sel_smem, s>>>(
-        cd.as<float>(), K, nprobe, pred_from_list ? nullptr : npq,
-        sort_n, probe_ids, probe_dist);
-    RBQ_CUDA(cudaGetLastError());
+    RBQ_CHECK(probe_select(X, Q, nqc, cd.as<float>(), nprobe, pred_from_list ? nullptr : npq,
+                           probe_ids, probe_dist, s));
     if (pred_from_list) {
       RBQ_CHECK(mlp_infer(a.pred, probe_dist, nprobe, nqc, navail, a.pred_nprobe + q0, nullptr,
                           nullptr, s));
@@ -2274,7 +2550,7 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
     for (auto& e : ev) cudaEventDestroy(e);
   }
   if (h_err == 2)
-    return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired in the query rotation");
+    return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired (probe scores or query rotation)");
   if (h_err)
     return fail(RABITQ_EOVERFLOW,
                 "a query's candidate list exceeded max_candidates; raise max_candidates");
@@ -2376,10 +2652,6 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
   const int pch = fs.pch, pilot_m = fs.pilot_m, cu = fs.cu, ce = fs.ce, ct = fs.ct;
   const size_t smem = fs.smem;
   const FusedFn fn = fs.fn;
-  const int sort_n = pow2_at_least(nprobe);
-  const size_t sel_smem = sizeof(unsigned long long) * sort_n;
-  RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSelMaxSmem));
   if (cap < 4096) return fail(RABITQ_EINVAL, "search scratch too small for the candidate lists");
   int64_t lo = 1, hi = a.nq;
   if (carve_layout(a, grid, cap, 1).end > scratch_bytes)
@@ -2415,21 +2687,16 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
     if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[0], s, cudaEventRecordExternal));
     const float* Q = nullptr;
     RBQ_CHECK(search_queries(X, a.queries + q0 * d, nqc, qn, &Q, s));
-    RBQ_CHECK(centroid_scores(X, Q, nqc, cd, s));
+    RBQ_CHECK(centroid_scores(X, Q, nqc, cd, err, s));
     if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[1], s, cudaEventRecordExternal));
     const int32_t* npq = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
     const bool pred_from_list = a.pred && nprobe >= navail;
     if (a.pred && !pred_from_list) {
-      const int sn = pow2_at_least(navail);
-      select_kernel<<<(unsigned)nqc, kThreads, sizeof(unsigned long long) * sn, s>>>(
-          cd, K, navail, nullptr, sn, fid, fdist);
-      RBQ_CUDA(cudaGetLastError());
+      RBQ_CHECK(probe_select(X, Q, nqc, cd, navail, nullptr, fid, fdist, s));
       RBQ_CHECK(mlp_infer(a.pred, fdist, navail, nqc, navail, pnp, nullptr, nullptr, s));
       npq = pnp;
     }
-    select_kernel<<<(unsigned)nqc, kThreads, sel_smem, s>>>(
-        cd, K, nprobe, pred_from_list ? nullptr : npq, sort_n, pid, pdist);
-    RBQ_CUDA(cudaGetLastError());
+    RBQ_CHECK(probe_select(X, Q, nqc, cd, nprobe, pred_from_list ? nullptr : npq, pid, pdist, s));
     if (pred_from_list) {
       RBQ_CHECK(mlp_infer(a.pred, pdist, nprobe, nqc, navail, pnp, nullptr, nullptr, s));
       npq = pnp;
@@ -2526,7 +2793,7 @@ int search_dev_prealloc(const SearchArgs& a_in, unsigned char* scratch, size_t s
   int h_err = 0;
   RBQ_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   RBQ_CUDA(cudaStreamSynchronize(s));
-  if (h_err == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired in the query rotation");
+  if (h_err == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired (probe scores or query rotation)");
   if (h_err)
     return fail(RABITQ_EOVERFLOW,
                 "a query's candidate list exceeded the fixed scratch's capacity");
@@ -2583,10 +2850,6 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
   RBQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
   RBQ_CUDA(cudaMemsetAsync(tiles.p, 0, sizeof(int32_t) * (K + 1), s));
 
-  const int sort_n = pow2_at_least(nprobe);
-  const size_t sel_smem = sizeof(unsigned long long) * sort_n;
-  RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSelMaxSmem));
   const size_t scan_smem = 64 * 1024;  // 32 KB of operands; caps residency at 3 CTAs/SM
   RBQ_CUDA(cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)scan_smem));
@@ -2608,7 +2871,7 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
     if (timing) RBQ_CUDA(cudaEventRecord(ev[0], s));
     const float* Q = nullptr;
     RBQ_CHECK(search_queries(X, a.queries + q0 * d, nqc, qn.as<float>(), &Q, s));
-    RBQ_CHECK(centroid_scores(X, Q, nqc, cd.as<float>(), s));
+    RBQ_CHECK(centroid_scores(X, Q, nqc, cd.as<float>(), err.as<int>(), s));
     int32_t* probe_ids = a.trace && a.trace->probe_ids ? a.trace->probe_ids + q0 * nprobe
                                                        : pid.as<int32_t>();
     float* probe_dist = a.trace && a.trace->probe_dist ? a.trace->probe_dist + q0 * nprobe
@@ -2616,13 +2879,11 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
     if (timing) RBQ_CUDA(cudaEventRecord(ev[1], s));
     const int32_t* npq = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
     if (a.pred) {
-      RBQ_CHECK(predict_chunk(a, cd.as<float>(), nqc, q0, fid.as<int32_t>(), fdist.as<float>(), s));
+      RBQ_CHECK(predict_chunk(a, Q, cd.as<float>(), nqc, q0, fid.as<int32_t>(),
+                              fdist.as<float>(), s));
       npq = a.pred_nprobe + q0;
     }
-    select_kernel<<<(unsigned)nqc, kThreads, sel_smem, s>>>(
-        cd.as<float>(), K, nprobe, npq,
-        sort_n, probe_ids, probe_dist);
-    RBQ_CUDA(cudaGetLastError());
+    RBQ_CHECK(probe_select(X, Q, nqc, cd.as<float>(), nprobe, npq, probe_ids, probe_dist, s));
     if (metric_ip(X)) RBQ_CHECK(probe_nq2(X, Q, nqc, nprobe, probe_ids, pnq2.as<float>(), s));
     if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
     float* rqp = a.trace && a.trace->rq ? a.trace->rq + q0 * dpad : rq.as<float>();
@@ -2755,18 +3016,19 @@ int select_buckets(const rabitq_index* X, const float* Q, int64_t nq, int nsel, 
   const int64_t qchunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t(1) << 28) / K));
   DevBuf cd;
   RBQ_CHECK(cd.alloc(sizeof(float) * qchunk * K, s));
-  const int sn = pow2_at_least(nsel);
-  const size_t smem = sizeof(unsigned long long) * sn;
-  RBQ_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSelMaxSmem));
+  DevBuf err;
+  RBQ_CHECK(err.alloc(sizeof(int), s));
+  RBQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
   for (int64_t q0 = 0; q0 < nq; q0 += qchunk) {
     const int64_t m = std::min(qchunk, nq - q0);
-    RBQ_CHECK(gemm_canon(kSqDist, Q + q0 * d, d, nullptr, nullptr, 0, nullptr, X->centroids_t, K,
-                         cd.as<float>(), K, m, K, d, s));
-    select_kernel<<<(unsigned)m, kThreads, smem, s>>>(cd.as<float>(), K, nsel, nullptr, sn,
-                                                       ids + q0 * nsel, dist + q0 * nsel);
-    RBQ_CUDA(cudaGetLastError());
+    RBQ_CHECK(centroid_dot_tc(X, Q + q0 * d, m, cd.as<float>(), err.as<int>(), s));
+    RBQ_CHECK(probe_select(X, Q + q0 * d, m, cd.as<float>(), nsel, nullptr, ids + q0 * nsel,
+                           dist + q0 * nsel, s));
   }
+  int h_err = 0;
+  RBQ_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RBQ_CUDA(cudaStreamSynchronize(s));
+  if (h_err) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired in the probe scores");
   return RABITQ_OK;
 }
 

@@ -161,10 +161,19 @@ __global__ void __launch_bounds__(kTcThreads) rotate_tc_kernel(const float* __re
           : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (row < M) {
+        const int gb = n0 + c0;
+        if (gb + 16 <= N && (N & 3) == 0) {  // whole chunk: four 16-byte stores
+          float4* dst = reinterpret_cast<float4*>(C + row * N + gb);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int gn = n0 + c0 + e;
-          if (gn < N) C[row * N + gn] = __uint_as_float(r[e]);
+          for (int v = 0; v < 4; ++v)
+            dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                 __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int gn = gb + e;
+            if (gn < N) C[row * N + gn] = __uint_as_float(r[e]);
+          }
         }
       }
     }
@@ -188,7 +197,50 @@ __global__ void pack_pt_kernel(const float* __restrict__ P32, int d, int dpad, i
   ptf[i] = to_tf32(v);
 }
 
+// Centroid rows rounded to TF32 (K-major, zero-padded to Kp), and the FP32
+// norms ||c||^2 (ascending fold) and ||c|| that scale the probe filter's
+// error bound. One thread per (centroid, column); column 0 also folds the
+// norm.
+__global__ void pack_centroids_kernel(const float* __restrict__ C, int K, int d, int Kp,
+                                      float* __restrict__ ctf, float* __restrict__ cn2,
+                                      float* __restrict__ cnorm) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)K * Kp) return;
+  const int c = (int)(i / Kp), k = (int)(i % Kp);
+  const float* row = C + (int64_t)c * d;
+  ctf[i] = (k < d) ? to_tf32(row[k]) : 0.0f;
+  if (k == 0) {
+    float s2 = 0.0f;
+    for (int t = 0; t < d; ++t) s2 = __fmaf_rn(row[t], row[t], s2);
+    cn2[c] = s2;
+    cnorm[c] = __fsqrt_rn(s2);
+  }
+}
+
 }  // namespace
+
+int pack_centroids(rabitq_index* X, cudaStream_t s) {
+  const int64_t total = (int64_t)X->K * X->kp;
+  pack_centroids_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+      X->centroids, X->K, X->d, X->kp, X->ctf, X->cn2, X->cnorm);
+  RBQ_CUDA(cudaGetLastError());
+  return RABITQ_OK;
+}
+
+int centroid_dot_tc(const rabitq_index* X, const float* Q, int64_t M, float* out, int* err,
+                    cudaStream_t s) {
+  if (M <= 0) return RABITQ_OK;
+  const int N = X->K;
+  const int NT = 256;
+  const int ntiles = (N + NT - 1) / NT;
+  const size_t smem = 100 * 1024;  // at most two CTAs (256 TMEM columns each) per SM
+  dim3 grid((unsigned)((M + kTcM - 1) / kTcM), (unsigned)ntiles);
+  RBQ_CUDA(cudaFuncSetAttribute(rotate_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  rotate_tc_kernel<1><<<grid, kTcThreads, smem, s>>>(Q, M, X->d, X->ctf, X->kp, N, NT, out, err);
+  RBQ_CUDA(cudaGetLastError());
+  return RABITQ_OK;
+}
 
 int pack_pt(rabitq_index* X, cudaStream_t s) {
   const int64_t total = (int64_t)X->dpad * X->kp;

@@ -200,7 +200,7 @@ int rabitq_plan_sync(rabitq_plan* P, void* stream) {
   RBQ_CUDA(cudaMemcpyAsync(&h_err, P->scratch, sizeof(int), cudaMemcpyDeviceToHost, s));
   RBQ_CUDA(cudaMemsetAsync(P->scratch, 0, sizeof(int), s));
   RBQ_CUDA(cudaStreamSynchronize(s));
-  if (h_err == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired in the query rotation");
+  if (h_err == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired (probe scores or query rotation)");
   if (h_err)
     return fail(RABITQ_EOVERFLOW,
                 "a query's candidate list exceeded max_candidates; raise max_candidates");
