@@ -873,18 +873,35 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
 constexpr int kProbeCandMax = 2048;  // candidates kept in shared memory
 constexpr int kProbeSmemK = 16384;   // up to this many centroids, keys in shared memory
 
-__device__ __forceinline__ float probe_eps(int ip_metric, float nq, float nc, int d) {
-  const float a = 0x1.0p-10f + (float)(d + 2) * 0x1.0p-21f;
-  const float qc = nq * nc, sq = (nq + nc) * (nq + nc);
-  const float e = ip_metric ? a * qc + (float)(d + 8) * 0x1.0p-22f * qc
-                            : 2.0f * a * qc + (float)(2 * d + 8) * 0x1.0p-23f * sq;
-  return 1.05f * e;
-}
+// eps_c as a quadratic in ||c|| with per-query coefficients: squared
+// distances 1.05 [2a ||q|| ||c|| + b (||q|| + ||c||)^2], b = (2d + 8) 2^-23,
+// = ||c|| (kb ||c|| + ka) + kg; inner products 1.05 (a + (d + 8) 2^-22)
+// ||q|| ||c||. (Evaluated in FP32: a few units of rounding, inside the 5%.)
+struct ProbeEps {
+  float ka, kb, kg;
+  __device__ __forceinline__ ProbeEps(int ip_metric, float nq, int d) {
+    const float a = 0x1.0p-10f + (float)(d + 2) * 0x1.0p-21f;
+    if (ip_metric) {
+      ka = 1.05f * (a + (float)(d + 8) * 0x1.0p-22f) * nq;
+      kb = 0.0f;
+      kg = 0.0f;
+    } else {
+      const float b = (float)(2 * d + 8) * 0x1.0p-23f;
+      ka = 1.05f * (2.0f * a + 2.0f * b) * nq;
+      kb = 1.05f * b;
+      kg = 1.05f * b * nq * nq;
+    }
+  }
+  __device__ __forceinline__ float operator()(float nc) const {
+    return __fmaf_rn(nc, __fmaf_rn(kb, nc, ka), kg);
+  }
+};
 
 __global__ void __launch_bounds__(kThreads) probe_select_kernel(
     const float* __restrict__ Q, int d, const float* __restrict__ ip, const float* __restrict__ C,
     const float* __restrict__ cn2, const float* __restrict__ cnorm, int K, int metric,
     int nprobe, const int32_t* __restrict__ nprobe_q, int sort_n, int smem_keys,
+    const int32_t* __restrict__ pre_ids, const float* __restrict__ pre_dist, int pre_n,
     int32_t* __restrict__ out_ids, float* __restrict__ out_dist) {
   extern __shared__ __align__(16) unsigned char psm[];
   // layout: q (d floats) | upper-bound keys (K, when smem_keys) | work area:
@@ -903,6 +920,17 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
   int nsel = nprobe;
   if (nprobe_q) nsel = min(max(nprobe_q[q], 1), nprobe);
   nsel = min(nsel, K);
+  if (pre_ids && nsel <= pre_n) {
+    // a list of this query's pre_n best is already selected: its prefix is
+    // the answer (the same order by (score, id))
+    for (int j = tid; j < nprobe; j += blockDim.x) {
+      const bool ok = j < nsel;
+      out_ids[(int64_t)q * nprobe + j] = ok ? pre_ids[(int64_t)q * pre_n + j] : -1;
+      out_dist[(int64_t)q * nprobe + j] =
+          ok ? pre_dist[(int64_t)q * pre_n + j] : __int_as_float(0x7f800000);
+    }
+    return;
+  }
   // ||q||^2 (any summation order: the bound needs an FP32 value, not the fold)
   float part = 0.0f;
   for (int i = tid; i < d; i += blockDim.x) {
@@ -921,18 +949,19 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
   }
   __syncthreads();
   const float nq2 = s_nq2, nq = __fsqrt_rn(nq2);
+  const ProbeEps eps(metric, nq, d);
   auto approx = [row, cn2, nq2, metric](int c) {
     const float v = row[c];
     return metric ? -v : __fsub_rn(__fadd_rn(nq2, cn2[c]), __fmul_rn(2.0f, v));
   };
   auto ukey = [&](int c) {
     return smem_keys ? uk[c]
-                     : float_key(__fadd_rn(approx(c), probe_eps(metric, nq, cnorm[c], d)));
+                     : float_key(__fadd_rn(approx(c), eps(cnorm[c])));
   };
   // L_c = U_c - 2 eps_c (its rounding is inside the bound's margin)
   auto lkey = [&](int c) {
     return float_key(
-        __fsub_rn(key_float(ukey(c)), __fmul_rn(2.0f, probe_eps(metric, nq, cnorm[c], d))));
+        __fsub_rn(key_float(ukey(c)), __fmul_rn(2.0f, eps(cnorm[c]))));
   };
   // pass 1: the upper bounds' keys and their range; four centroids per
   // thread per step, loads first
@@ -956,7 +985,7 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
       const int c = c0 + u * blockDim.x + tid;
       if (c < K) {
         const float sc = metric ? -v[u] : __fsub_rn(__fadd_rn(nq2, n2[u]), __fmul_rn(2.0f, v[u]));
-        const uint32_t key = float_key(__fadd_rn(sc, probe_eps(metric, nq, nn[u], d)));
+        const uint32_t key = float_key(__fadd_rn(sc, eps(nn[u])));
         if (smem_keys) uk[c] = key;
         kmin = key < kmin ? key : kmin;
         kmax = key > kmax ? key : kmax;
@@ -1038,7 +1067,7 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
       for (int u = 0; u < 4; ++u) {
         const int c = c0 + u * blockDim.x + tid;
         lk4[u] = c < K ? float_key(__fsub_rn(key_float(uk[c]),
-                                             __fmul_rn(2.0f, probe_eps(metric, nq, nn[u], d))))
+                                             __fmul_rn(2.0f, eps(nn[u]))))
                        : 0xffffffffu;
       }
     } else {
@@ -2241,9 +2270,13 @@ int fused_shape(const SearchArgs& a, FusedShape* f) {
 
 // Probe lists from the tensor-core products cd (nqc x K, centroid_dot_tc):
 // the nsel (= nprobe, or npq[q] clamped to it) best centroids of each query
-// by exact canonical score, ascending (score, id), in rows of nprobe.
+// by exact canonical score, ascending (score, id), in rows of nprobe. With
+// pre_ids/pre_dist (rows of pre_n such lists), a query with nsel <= pre_n
+// copies its prefix instead.
 int probe_select(const rabitq_index* X, const float* Q, int64_t nqc, const float* cd, int nprobe,
-                 const int32_t* npq, int32_t* ids, float* dist, cudaStream_t s) {
+                 const int32_t* npq, int32_t* ids, float* dist, cudaStream_t s,
+                 const int32_t* pre_ids = nullptr, const float* pre_dist = nullptr,
+                 int pre_n = 0) {
   if (nqc <= 0) return RABITQ_OK;
   const int sort_n = pow2_at_least(nprobe);
   int dev = 0, optin = 0;
@@ -2260,7 +2293,7 @@ int probe_select(const rabitq_index* X, const float* Q, int64_t nqc, const float
   if (smem > limit) return fail(RABITQ_EINVAL, "probe selection does not fit shared memory");
   probe_select_kernel<<<(unsigned)nqc, kThreads, smem, s>>>(
       Q, X->d, cd, X->centroids, X->cn2, X->cnorm, X->K, X->metric != RABITQ_METRIC_L2 ? 1 : 0,
-      nprobe, npq, sort_n, smem_keys ? 1 : 0, ids, dist);
+      nprobe, npq, sort_n, smem_keys ? 1 : 0, pre_ids, pre_dist, pre_n, ids, dist);
   RBQ_CUDA(cudaGetLastError());
   return RABITQ_OK;
 }
@@ -2401,7 +2434,7 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
     RBQ_CHECK(ooff.alloc(sizeof(int32_t) * (nprobe + 2), s));
   }
   DevBuf fid, fdist;  // learned probe counts: the 64 nearest buckets per query
-  if (a.pred && nprobe < std::min(kMlpIn, K)) {
+  if (a.pred) {
     RBQ_CHECK(fid.alloc(sizeof(int32_t) * qchunk * kMlpIn, s));
     RBQ_CHECK(fdist.alloc(sizeof(float) * qchunk * kMlpIn, s));
   }
@@ -2425,23 +2458,17 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
     float* probe_dist = a.trace && a.trace->probe_dist ? a.trace->probe_dist + q0 * nprobe
                                                        : pdist.as<float>();
     const int32_t* npq = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
-    // learned counts: when the probe list holds the 64 nearest buckets, the
-    // features come from it (one selection); otherwise from a selection of
-    // their own. The scan reads only the first nprobe_q entries either way.
-    const int navail = std::min(kMlpIn, K);
-    const bool pred_from_list = a.pred && nprobe >= navail;
-    if (a.pred && !pred_from_list) {
+    // learned counts: the 64 nearest buckets give the features, the network
+    // gives each query's count, and the probe list then holds that many (a
+    // selection of nprobe_max for every query would cost more: most need few)
+    if (a.pred) {
       RBQ_CHECK(predict_chunk(a, Q, cd.as<float>(), nqc, q0, fid.as<int32_t>(),
                               fdist.as<float>(), s));
       npq = a.pred_nprobe + q0;
     }
-    RBQ_CHECK(probe_select(X, Q, nqc, cd.as<float>(), nprobe, pred_from_list ? nullptr : npq,
-                           probe_ids, probe_dist, s));
-    if (pred_from_list) {
-      RBQ_CHECK(mlp_infer(a.pred, probe_dist, nprobe, nqc, navail, a.pred_nprobe + q0, nullptr,
-                          nullptr, s));
-      npq = a.pred_nprobe + q0;
-    }
+    RBQ_CHECK(probe_select(X, Q, nqc, cd.as<float>(), nprobe, npq, probe_ids, probe_dist, s,
+                           a.pred ? fid.as<int32_t>() : nullptr, fdist.as<float>(),
+                           std::min(kMlpIn, K)));
     if (metric_ip(X)) RBQ_CHECK(probe_nq2(X, Q, nqc, nprobe, probe_ids, pnq2.as<float>(), s));
     if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
     float* rqp = a.trace && a.trace->rq ? a.trace->rq + q0 * dpad : rq.as<float>();
@@ -2581,7 +2608,7 @@ Carve carve_layout(const SearchArgs& a, int64_t grid, int64_t cap, int64_t qchun
   const rabitq_index* X = a.X;
   const int K = X->K, nprobe = std::min(a.nprobe, K);
   const bool ordered = a.pred || a.per_query_nprobe;
-  const bool own_select = a.pred && nprobe < std::min(kMlpIn, K);
+  const bool own_select = a.pred != nullptr;
   Carve L;
   L.grid = grid;
   L.cap = cap;
@@ -2690,17 +2717,13 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
     RBQ_CHECK(centroid_scores(X, Q, nqc, cd, err, s));
     if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[1], s, cudaEventRecordExternal));
     const int32_t* npq = a.per_query_nprobe ? a.per_query_nprobe + q0 : nullptr;
-    const bool pred_from_list = a.pred && nprobe >= navail;
-    if (a.pred && !pred_from_list) {
+    if (a.pred) {  // the 64 nearest give the features, the network each query's count
       RBQ_CHECK(probe_select(X, Q, nqc, cd, navail, nullptr, fid, fdist, s));
       RBQ_CHECK(mlp_infer(a.pred, fdist, navail, nqc, navail, pnp, nullptr, nullptr, s));
       npq = pnp;
     }
-    RBQ_CHECK(probe_select(X, Q, nqc, cd, nprobe, pred_from_list ? nullptr : npq, pid, pdist, s));
-    if (pred_from_list) {
-      RBQ_CHECK(mlp_infer(a.pred, pdist, nprobe, nqc, navail, pnp, nullptr, nullptr, s));
-      npq = pnp;
-    }
+    RBQ_CHECK(probe_select(X, Q, nqc, cd, nprobe, npq, pid, pdist, s, a.pred ? fid : nullptr,
+                           fdist, navail));
     if (a.pred && a.pred_nprobe)
       RBQ_CUDA(cudaMemcpyAsync(a.pred_nprobe + q0, pnp, sizeof(int32_t) * nqc,
                                cudaMemcpyDeviceToDevice, s));
@@ -2883,7 +2906,9 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
                               fdist.as<float>(), s));
       npq = a.pred_nprobe + q0;
     }
-    RBQ_CHECK(probe_select(X, Q, nqc, cd.as<float>(), nprobe, npq, probe_ids, probe_dist, s));
+    RBQ_CHECK(probe_select(X, Q, nqc, cd.as<float>(), nprobe, npq, probe_ids, probe_dist, s,
+                           a.pred ? fid.as<int32_t>() : nullptr, fdist.as<float>(),
+                           std::min(kMlpIn, K)));
     if (metric_ip(X)) RBQ_CHECK(probe_nq2(X, Q, nqc, nprobe, probe_ids, pnq2.as<float>(), s));
     if (timing) RBQ_CUDA(cudaEventRecord(ev[2], s));
     float* rqp = a.trace && a.trace->rq ? a.trace->rq + q0 * dpad : rq.as<float>();
