@@ -871,7 +871,10 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
 // and the FP32 operations forming s~, U and L add a few units of
 // 2^-24 (||q|| + ||c||)^2; eps_c takes all of these with a 5% margin.
 constexpr int kProbeCandMax = 2048;  // candidates kept in shared memory
-constexpr int kProbeSmemK = 16384;   // up to this many centroids, keys in shared memory
+// up to this many centroids the upper-bound keys stay in shared memory; for
+// more, the passes recompute them (keeping 64 KB of keys cost more in
+// residency than the recomputation: K = 16384 took 1.78 ms per 10k queries)
+constexpr int kProbeSmemK = 8192;
 
 // eps_c as a quadratic in ||c|| with per-query coefficients: squared
 // distances 1.05 [2a ||q|| ||c|| + b (||q|| + ||c||)^2], b = (2d + 8) 2^-23,
