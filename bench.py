@@ -61,6 +61,22 @@ def recall_at(ids: np.ndarray, gt: np.ndarray) -> float:
     return float(np.mean(hits) / k)
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of the ranks' values (a job's time is its slowest rank's);
+    x itself on a single rank."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region: samples
     every 25 ms, stamped on arrival; the sampler is running (first sample in)
@@ -240,13 +256,16 @@ def run_ours(args, rank, world):
     dh = torch.empty((w.nq, w.k), dtype=torch.float32).pin_memory().numpy()
     bplan.search(qh, out=(ih, dh))
     e2e_ms = []
+    if dist:
+        dist.barrier()
     for _ in range(max(3, args.steps // 2)):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         bplan.search(qh, out=(ih, dh))
         e2e_ms.append((time.perf_counter() - t1) * 1e3)
-    e2e_qps = world * w.nq / (np.mean(e2e_ms) / 1e3)
+    e2e_mean_ms = max_over_ranks(float(np.mean(e2e_ms)), dist, dev)
+    e2e_qps = job_rate(world, w.nq, e2e_mean_ms / 1e3)
     e2e_rec = recall_at(ih, gt)
     latency = batch1_latency(G, bplan_args(best_name, legs, chosen), qd, w, flush)
 
@@ -263,7 +282,8 @@ def run_ours(args, rank, world):
                    "rotation": "fp32", "scan": "popcount",
                    "launch": "CUDA graph replay of the whole search (rabitq_plan_run)",
                    "l2": "flushed before each step",
-                   "parallelism": f"replicas x{world} (queries sharded, no collective)",
+                   "parallelism": f"replicas x{world} (every rank searches its own copy of "
+                                  "the batch; no collective in the search)",
                    "build_s": round(build_s, 3)},
         "stage_ms": best["stage_ms"],
         "roofline": best["roofline"],
@@ -517,15 +537,11 @@ def time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=False, name="
     if sampler:
         sampler.__exit__(None, None, None)
     plan.sync()   # raises if any replay overflowed its candidate lists
-    total_ms = float(np.sum(ms))
-    world = 1
-    if dist:
-        world = dist.get_world_size()
-        t = torch.tensor([total_ms], device=qd.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    world = dist.get_world_size() if dist else 1
+    total_ms = max_over_ranks(float(np.sum(ms)), dist, qd.device)
     st = np.mean(np.array(stages), axis=0)
-    out = {"value": round(world * w.nq * args.steps / (total_ms / 1e3), 1), "unit": "queries/s",
+    out = {"value": round(job_rate(world, w.nq * args.steps, total_ms / 1e3), 1),
+           "unit": "queries/s",
            "ms_per_step": round(total_ms / args.steps, 4), "recall_at_100": round(rec, 4),
            "fused_ms": float(st[3]),
            "stage_ms": {"centroid_dist": round(float(st[0]), 4),
