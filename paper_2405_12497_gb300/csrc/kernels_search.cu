@@ -2,15 +2,21 @@
 // and error-bound re-ranking of §4).
 //
 // Stages per batch of queries:
-//   1. canonical squared distances to every centroid (kernels_gemm.cu);
-//   2. probe selection: the nprobe nearest centroids by (distance, id);
-//   3. query rotation P^{-1}[q_r; 0] (kernels_gemm.cu, FP32 canonical);
+//   1. TF32 tensor-core products <q, c> with every centroid (kernels_tc.cu);
+//   2. probe selection: the nprobe nearest centroids by canonical (distance,
+//      id), exactly, from bounds on those products (probe_select_kernel);
+//      with learned probe counts, the 64 nearest first (the network's
+//      features), then each query's count;
+//   3. query rotation P^{-1}[q_r; 0] (kernels_gemm.cu FP32 canonical, or
+//      kernels_tc.cu BF16 / TF32);
 //   4. one persistent fused kernel, a CTA per query at a time: randomized
 //      B_q-bit quantization of q' per probed cluster (§3.3.1), bucket scan
 //      with the bit-plane popcount form of <x_b, q_u> (§3.3.2), the unbiased
 //      estimator and its error bound (Theorem 3.2), the k-th smallest upper
 //      bound tau, the survivors LB <= tau, their exact distances and the
 //      top-k by (distance, id).
+// Also here: the split-mode merge, the bucket-major tensor-core scan path,
+// the single-code estimator (§3.3.2, first case) and the host launchers.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -2291,7 +2297,8 @@ int probe_select(const rabitq_index* X, const float* Q, int64_t nqc, const float
   RBQ_CUDA(cudaFuncSetAttribute(probe_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)limit));
   // the bounds' keys stay in shared memory when they fit beside the rest
-  bool smem_keys = X->K <= kProbeSmemK && probe_select_smem(X->d, X->K, sort_n, true) <= limit;
+  const bool smem_keys =
+      X->K <= kProbeSmemK && probe_select_smem(X->d, X->K, sort_n, true) <= limit;
   const size_t smem = probe_select_smem(X->d, X->K, sort_n, smem_keys);
   if (smem > limit) return fail(RABITQ_EINVAL, "probe selection does not fit shared memory");
   probe_select_kernel<<<(unsigned)nqc, kThreads, smem, s>>>(
