@@ -53,6 +53,18 @@ def test_invalid_arguments_fail_before_device_work(L):
     so = L.SearchOpts()
     lib.rabitq_search_opts_default(C.byref(so))
     assert so.quant_seed == 3 and so.max_candidates == 65536
+    opts = L.BuildOpts()
+    lib.rabitq_build_opts_default(C.byref(opts))
+    assert opts.metric == L.METRIC_L2
+    opts.metric = 7
+    assert lib.rabitq_build(p, 10, 8, 2, 1, C.byref(opts), C.byref(h)) == L.EINVAL
+    assert b"metric" in lib.rabitq_last_error()
+    ids = np.zeros((1, 1), np.int64)
+    out = np.zeros((1, 1, 3), np.float32)
+    assert lib.rabitq_estimate(None, p, 1, ids.ctypes.data_as(C.c_void_p), 1, 4, 1.9,
+                               out.ctypes.data_as(C.c_void_p), None) == L.EINVAL
+    m = C.c_int32(-1)
+    assert lib.rabitq_index_metric(None, C.byref(m)) == L.EINVAL
     lib.rabitq_free(None)
 
 
