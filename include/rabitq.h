@@ -127,8 +127,9 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
  * k-th smallest of those, tau_ub the k-th smallest upper bound over all
  * estimated codes; every other code is re-ranked iff its distance lower
  * bound is at most min(tau_ub, tau1).
- * Errors: EINVAL; ENOMEM; ECUDA; EOVERFLOW when more than max_candidates
- * codes of one query pass the bound (raise max_candidates).
+ * Errors: EINVAL (also for a non-finite query value, found during the search:
+ * the outputs are then undefined); ENOMEM; ECUDA; EOVERFLOW when more than
+ * max_candidates codes of one query pass the bound (raise max_candidates).
  */
 int rabitq_search(const rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
                   int32_t nprobe, int32_t bq, float eps0, int64_t* out_ids, float* out_dist,

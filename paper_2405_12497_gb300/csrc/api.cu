@@ -343,11 +343,21 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   }
   float stage[5] = {0, 0, 0, 0, 0};
   a.stage_ms = opts.collect_stats ? stage : nullptr;
+  // non-finite query values are reported after the search (no extra wait)
+  DevBuf fin;
+  RBQ_CHECK(fin.alloc(sizeof(int), s));
+  RBQ_CUDA(cudaMemsetAsync(fin.p, 0, sizeof(int), s));
+  RBQ_CHECK(finite_flag(dq, nq * X->d, fin.as<int>(), s));
   RBQ_CHECK(search_dev(a, s));
   if (!on_dev) {
     RBQ_CUDA(cudaMemcpyAsync(out_ids, dids, sizeof(int64_t) * nq * k, cudaMemcpyDeviceToHost, s));
     RBQ_CUDA(cudaMemcpyAsync(out_dist, ddist, sizeof(float) * nq * k, cudaMemcpyDeviceToHost, s));
   }
+  int h_fin = 0;
+  RBQ_CUDA(cudaMemcpyAsync(&h_fin, fin.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RBQ_CUDA(cudaStreamSynchronize(s));
+  if (h_fin)
+    return fail(RABITQ_EINVAL, "rabitq_search: a query has a non-finite value (outputs undefined)");
   if (opts.collect_stats) {
     RBQ_CUDA(cudaEventRecord(t1, s));
     RBQ_CUDA(cudaEventSynchronize(t1));

@@ -123,6 +123,9 @@ int gather_rows_f32(const float* in, int64_t ld, const int32_t* rows, int64_t m,
 int invert_perm(const int32_t* perm, int64_t n, int32_t* inv, cudaStream_t s);
 int transpose_f32(const float* in, int64_t rows, int64_t cols, float* out, cudaStream_t s);
 int check_finite(const float* x, int64_t count, cudaStream_t s, bool* finite);
+// sets *flag (device, zeroed by the caller) to 1 if x has a non-finite value;
+// no synchronization
+int finite_flag(const float* x, int64_t count, int* flag, cudaStream_t s);
 
 // ---- tensor-core query rotation (kernels_tc.cu) --------------------------
 int pack_pt(rabitq_index* X, cudaStream_t s);

@@ -500,6 +500,14 @@ int transpose_f32(const float* in, int64_t rows, int64_t cols, float* out, cudaS
   return RABITQ_OK;
 }
 
+int finite_flag(const float* x, int64_t count, int* flag, cudaStream_t s) {
+  if (count <= 0) return RABITQ_OK;
+  finite_kernel<<<(unsigned)std::min<int64_t>(blocks_for(count, 256), 4096), 256, 0, s>>>(
+      x, count, flag);
+  RBQ_CUDA(cudaGetLastError());
+  return RABITQ_OK;
+}
+
 int check_finite(const float* x, int64_t count, cudaStream_t s, bool* finite) {
   DevBuf bad;
   RBQ_CHECK(bad.alloc(sizeof(int), s));

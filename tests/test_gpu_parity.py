@@ -183,6 +183,13 @@ def test_invalid_search_arguments(R, tiny_gpu_index, tiny_workload):
         assert e.value.code == R.EINVAL
     ids, dist = tiny_gpu_index.search(Q[:0], 10, 4)
     assert ids.shape == (0, 10)
+    bad = Q[:5].copy()
+    bad[2, 7] = np.nan
+    with pytest.raises(R.RabitqError) as e:
+        tiny_gpu_index.search(bad, 10, 4)
+    assert e.value.code == R.EINVAL and "non-finite" in str(e.value)
+    ids, _ = tiny_gpu_index.search(Q[:5], 10, 4)   # the index is still usable
+    assert (ids >= 0).all()
 
 
 # ------------------------------------------------- tensor-core rotation modes
