@@ -39,3 +39,23 @@ def test_recall_counts_overlap():
     gt = np.array([[1, 2, 3, 4], [5, 6, 7, 8]])
     ids = np.array([[4, 3, 9, 9, 1], [0, 0, 0, 0, 5]])
     assert bench.recall_at(ids, gt) == (2 / 4 + 0 / 4) / 2   # only the first k ids count
+
+
+def test_clock_summary_keeps_the_timed_region_and_flags_throttling():
+    import bench
+    s = bench.ClockSampler(0)
+    row = "0, {sm}, 2070, 900.00, 0x0000000000000000, {hw}, Not Active, Not Active, {pc}"
+    s.lines = [(0.5, row.format(sm=1200, hw="Not Active", pc="Not Active")),   # before
+               (1.1, row.format(sm=2070, hw="Not Active", pc="Active")),
+               (1.2, row.format(sm=1965, hw="Not Active", pc="Not Active")),
+               (1.3, row.format(sm=2070, hw="Not Active", pc="Not Active")),
+               (2.5, row.format(sm=900, hw="Active", pc="Not Active"))]      # after
+    s.t0, s.t1 = 1.0, 1.35
+    out = s.summary()
+    assert out["samples"] == 3 and out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    s.t0, s.t1 = 2.0, 2.1          # a region shorter than a period: the next sample
+    out = s.summary()
+    assert out["samples"] == 1 and out["reasons"] == ["hw_slowdown"]
+    s.lines = []
+    assert s.summary()["reasons"] == ["unsampled"]
