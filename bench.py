@@ -44,6 +44,7 @@ NPROBES = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256)
 NPROBES_WIDE = NPROBES + (384, 512, 768, 1024)  # inner products need more probes
 WORKLOADS = {"sift": synth.SIFT_LIKE, "gist": synth.GIST_LIKE, "deep": synth.DEEP_LIKE}
 TARGET = 0.95
+RECALL_TOL = 0.002  # ~3 standard errors of a 10k-query mean recall@100
 METRIC = "QPS at recall@100=0.95 on 1 GB300; code-scan GB/s vs HBM peak"
 
 
@@ -196,22 +197,24 @@ def run_ours(args, rank, world):
         gt = exact_mips(dd, qd, w.k, cosine=args.metric == "cosine")
     tag = "" if args.metric == "l2" else "-" + args.metric  # traffic records are per metric
 
-    # nprobe sweep (untimed): smallest nprobe with mean recall@100 >= 0.95
+    # Calibration (untimed) on a held-out query set drawn separately (seed
+    # 11), never on the evaluation queries: the fixed leg's nprobe is the
+    # smallest whose calibration recall@100 reaches 0.95 (integer bisection),
+    # and the learned leg's multiplier is chosen the same way below. Both
+    # legs are then run once on the evaluation queries, whose recall is
+    # reported as measured.
+    n_cal = min(w.nq, 10_000)
+    _, cq = synth.make(w, nq=n_cal, seed_query=11, with_data=False)
+    cqd = torch.from_numpy(cq).to(dev)
+    cgt = exact_knn(dd, cqd, w.k) if args.metric == "l2" else \
+        exact_mips(dd, cqd, w.k, cosine=args.metric == "cosine")
     sweep = {}
     chosen = args.nprobe
     if chosen is None:
-        grid = NPROBES if args.metric == "l2" else NPROBES_WIDE
-        for npb in grid:
-            ids, _ = G.search(qd, w.k, npb, bq=w.bq, eps0=w.eps0)
-            sweep[npb] = recall_at(ids.cpu().numpy(), gt)
-            if sweep[npb] >= TARGET:
-                chosen = npb
-                break
-        if chosen is None:
-            chosen = grid[-1]
+        hi = min(G.K, 256 if args.metric == "l2" else 1024)
+        chosen, sweep = smallest_nprobe(G, cqd, cgt, w, hi)
     ids, _ = G.search(qd, w.k, chosen, bq=w.bq, eps0=w.eps0)
     rec = recall_at(ids.cpu().numpy(), gt)
-    sweep[chosen] = rec
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
@@ -220,7 +223,10 @@ def run_ours(args, rank, world):
     # ---- leg 1: fixed nprobe (the paper's method)
     plan = rabitq.Plan(G, w.k, chosen, w.nq, bq=w.bq, eps0=w.eps0, stats=True)
     fixed = time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=True, name="fixed")
-    fixed.update({"nprobe": chosen, "nprobe_sweep": {str(a): round(b, 4) for a, b in sweep.items()}})
+    fixed.update({"nprobe": chosen,
+                  "calibration_recall_by_nprobe": {str(a): round(b, 4)
+                                                   for a, b in sorted(sweep.items())},
+                  "calibrated_on": f"{n_cal} held-out calibration queries (seed 11)"})
     fixed["roofline"] = roofline(G, qd, w, chosen, None, fixed["fused_ms"], hbm, src,
                                  "fixed" + tag)
     fixed["scan_gbs"] = fixed["roofline"].pop("scan_gbs")
@@ -230,7 +236,8 @@ def run_ours(args, rank, world):
 
     # ---- leg 2: learned per-query nprobe
     if not args.no_learned:
-        legs["learned"] = learned_leg(args, G, qd, gt, w, chosen, flush, stream, dist, hbm, src)
+        legs["learned"] = learned_leg(args, G, qd, gt, w, chosen, flush, stream, dist, hbm, src,
+                                      cqd, cgt)
 
     cold = None
     if args.cold_scan or args.workload == "deep":
@@ -240,8 +247,11 @@ def run_ours(args, rank, world):
     if args.workload == "gist" or args.precision:
         precision = precision_legs(args, G, qd, gt, w, chosen, flush, stream, dist, data)
 
-    best_name = max(legs, key=lambda n: legs[n]["value"] if legs[n]["recall_at_100"] >= TARGET
-                    else -1.0)
+    # the headline is the faster leg among those at the target on the
+    # evaluation queries, within the sampling error of a 10k-query recall
+    # (both legs were calibrated on other queries)
+    best_name = max(legs, key=lambda n: legs[n]["value"]
+                    if legs[n]["recall_at_100"] >= TARGET - RECALL_TOL else -1.0)
     best = legs[best_name]
     qps = best["value"]
     rec = best["recall_at_100"]
@@ -269,8 +279,18 @@ def run_ours(args, rank, world):
     e2e_rec = recall_at(ih, gt)
     latency = batch1_latency(G, bplan_args(best_name, legs, chosen), qd, w, flush)
 
+    parity = None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.metric == "l2":
+        X = oracle_on_index(G, data)
+        cpu, o_ids, o_dist = cpu_baseline(X, queries, w, chosen, budget_s=args.cpu_budget)
+        parity = parity_block(X, G, data, queries, qd, w, chosen, legs, o_ids, o_dist)
+        del X
     for lg in legs.values():
         lg.pop("_pred_obj", None)
+        lg.pop("_ids", None)
+        lg.pop("_dist", None)
+        lg.pop("_npq", None)
     res = {
         "metric": METRIC, "value": round(qps, 1), "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_step"],
@@ -279,6 +299,9 @@ def run_ours(args, rank, world):
         "config": {"workload": w.name, "mode": f"{best_name} nprobe", "n": w.n, "d": w.d,
                    "nq_per_gpu": w.nq, "n_clusters": w.n_clusters, "k": w.k, "bq": w.bq,
                    "eps0": w.eps0, "recall_at_100": round(rec, 4), "similarity": args.metric,
+                   "operating_point": "nprobe / multiplier calibrated on 10k held-out "
+                                      "calibration queries; recall measured on the "
+                                      "evaluation queries",
                    "rotation": "fp32", "scan": "popcount",
                    "launch": "CUDA graph replay of the whole search (rabitq_plan_run)",
                    "l2": "flushed before each step",
@@ -303,8 +326,10 @@ def run_ours(args, rank, world):
         res["rotation_precision"] = precision
     if cold is not None:
         res["cold_scan"] = cold
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.metric == "l2":
-        res["cpu_baseline"] = cpu_baseline(G, data, queries, w, chosen, budget_s=args.cpu_budget)
+    if cpu is not None:
+        res["cpu_baseline"] = cpu
+    if parity is not None:
+        res["parity"] = parity
     if rank == 0:
         print(json.dumps(res), flush=True)
     if dist:
@@ -548,7 +573,9 @@ def time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=False, name="
                         "probe_select": round(float(st[1]), 4),
                         "rotation": round(float(st[2]), 4),
                         "order_quantize_scan_prune_rerank": round(float(st[3]), 4)},
-           "_plan": plan}
+           "_plan": plan,
+           "_ids": plan.ids.cpu().numpy().copy(), "_dist": plan.dist.cpu().numpy().copy(),
+           "_npq": None if plan.nprobe is None else plan.nprobe.cpu().numpy().copy()}
     if sampler:
         out["clocks"] = sampler.summary()
     return out
@@ -594,12 +621,13 @@ def roofline(G, qd, w, nprobe, per_query, fused_ms, hbm, src, leg):
             "ns_per_code": round(fused_ms * 1e6 / (w.nq * pairs_per_q), 4)}
 
 
-def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, dist, hbm, src):
+def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, dist, hbm, src, cqd, cgt):
     """Learned probe counts: train the predictor on separately drawn training
     queries (labels from the library's own search over nprobe_max buckets),
-    raise its multiplier on the benchmark queries until recall@100 >= 0.95
-    (the same rule that picks the fixed nprobe), then time the learned search
-    exactly like the fixed one."""
+    set its multiplier to the smallest value of the grid 2^(i/32) whose
+    recall@100 on the held-out calibration queries reaches 0.95 (bisection,
+    the same rule that picks the fixed nprobe), freeze it, then time the
+    learned search on the evaluation queries exactly like the fixed one."""
     import torch
     from paper_2405_12497_gb300 import rabitq
     dev = qd.device
@@ -612,13 +640,8 @@ def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, dist, hbm, src)
     torch.cuda.synchronize()
     train_s = time.time() - t0
     info = pr.info()
-    mult = info["mult"]
-    for _ in range(48):
-        pr.set_mult(mult)
-        ids, _ = G.search_learned(pr, qd, w.k, bq=w.bq, eps0=w.eps0)
-        if recall_at(ids.cpu().numpy(), gt) >= TARGET:
-            break
-        mult *= 2.0 ** 0.125
+    mult, cal_rec = calibrate_mult(G, pr, cqd, cgt, w)
+    pr.set_mult(mult)
     npq = G.predict_nprobe(pr, qd)
     plan = rabitq.Plan(G, w.k, 0, w.nq, bq=w.bq, eps0=w.eps0, predictor=pr, stats=True)
     leg = time_leg(args, plan, qd, gt, w, flush, stream, dist, name="learned")
@@ -633,7 +656,9 @@ def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, dist, hbm, src)
         "mean_nprobe": round(float(npf.mean()), 2),
         "nprobe_p50_p90_p99": [float(np.percentile(npf, p)) for p in (50, 90, 99)],
         "fixed_nprobe_same_recall": fixed_nprobe, "mult": round(mult, 5),
-        "calibrated_mult": round(info["mult"], 5), "val_recall": round(info["val_recall"], 4),
+        "calibration_recall": round(cal_rec, 4),
+        "calibrated_on": f"{cqd.shape[0]} held-out calibration queries (seed 11)",
+        "coverage_mult": round(info["mult"], 5), "val_coverage": round(info["val_recall"], 4),
         "val_mean_nprobe": round(info["val_mean_nprobe"], 2),
         "train_loss": round(info["train_loss"], 4), "val_loss": round(info["val_loss"], 4),
         "train_queries": args.train_nq, "epochs": args.epochs, "nprobe_max": args.nprobe_max,
@@ -641,13 +666,89 @@ def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, dist, hbm, src)
     return leg
 
 
-def cpu_baseline(G, data, queries, w, nprobe, budget_s=15.0):
-    """The oracle's search, as it stands, on the host cores, over a bounded
-    sample of the same queries. Its index arrays are the ones this run built
-    (timing input only; nothing here is compared for parity)."""
+def smallest_nprobe(G, cqd, cgt, w, hi):
+    """The smallest nprobe in [1, hi] whose recall@100 on the calibration
+    queries reaches the target, by integer bisection (recall grows with
+    nprobe); returns it with every recall measured on the way."""
+    seen = {}
+
+    def rec(npb):
+        if npb not in seen:
+            ids, _ = G.search(cqd, w.k, npb, bq=w.bq, eps0=w.eps0)
+            seen[npb] = recall_at(ids.cpu().numpy(), cgt)
+        return seen[npb]
+
+    if rec(hi) < TARGET:
+        return hi, seen
+    lo = 1
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if rec(mid) >= TARGET:
+            hi = mid
+        else:
+            lo = mid + 1
+    rec(lo)
+    return lo, seen
+
+
+def calibrate_mult(G, pr, cqd, cgt, w):
+    """The smallest multiplier 2^(i/32), i in [-256, 255], whose learned
+    search reaches the target recall@100 on the calibration queries
+    (bisection over i); returns (multiplier, its calibration recall)."""
+    seen = {}
+
+    def rec(i):
+        if i not in seen:
+            pr.set_mult(2.0 ** (i / 32))
+            ids, _ = G.search_learned(pr, cqd, w.k, bq=w.bq, eps0=w.eps0)
+            seen[i] = recall_at(ids.cpu().numpy(), cgt)
+        return seen[i]
+
+    lo, hi = -256, 255
+    if rec(hi) < TARGET:
+        return 2.0 ** (hi / 32), seen[hi]
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if rec(mid) >= TARGET:
+            hi = mid
+        else:
+            lo = mid + 1
+    return 2.0 ** (lo / 32), rec(lo)
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_on_index(G, data):
+    """The oracle's index over the arrays this run built (centroids,
+    assignment, P, codes, factors); parity_block checks every array the
+    oracle can recompute from the data before its search results count."""
     from oracle import oracle as O
-    X = O.OracleIndex.from_arrays(data, G.centroids(), G.rotation(), G.assign(), G.codes(),
-                                  G.factors())
+    return O.OracleIndex.from_arrays(data, G.centroids(), G.rotation(), G.assign(), G.codes(),
+                                     G.factors())
+
+
+def cpu_baseline(X, queries, w, nprobe, budget_s=15.0):
+    """The oracle's search, as it stands, on the host cores, over a bounded
+    prefix of the same queries (query i draws quantization stream i, as on
+    the GPU). Returns the timing record and the oracle's results."""
     cores = os.cpu_count() or 1
     m = min(len(queries), 4 * cores)
     t0 = time.perf_counter()
@@ -655,18 +756,71 @@ def cpu_baseline(G, data, queries, w, nprobe, budget_s=15.0):
     dt = time.perf_counter() - t0
     m2 = int(min(len(queries), max(m, m * budget_s / max(dt, 1e-3))))
     t0 = time.perf_counter()
-    X.search(queries[:m2], w.k, nprobe, bq=w.bq, eps0=w.eps0, threads=cores)
+    ids, dist = X.search(queries[:m2], w.k, nprobe, bq=w.bq, eps0=w.eps0, threads=cores)
     dt = time.perf_counter() - t0
     # the paper's protocol: one thread, one query at a time (a short sample)
     m1 = min(len(queries), 200)
     t1 = time.perf_counter()
     X.search(queries[:m1], w.k, nprobe, bq=w.bq, eps0=w.eps0, threads=1)
     d1 = time.perf_counter() - t1
-    return {"value": round(m2 / dt, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {m2} of {len(queries)} queries, nprobe {nprobe}, k {w.k}, "
-                      f"{cores} threads, {dt:.1f} s",
-            "single_thread": {"value": round(m1 / d1, 2), "unit": "queries/s",
-                              "sample": f"first {m1} queries, 1 thread, {d1:.1f} s"}}
+    rec = {"value": round(m2 / dt, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
+           "cpu_model": cpu_model(),
+           "sample": f"first {m2} of {len(queries)} queries, nprobe {nprobe}, k {w.k}, "
+                     f"{cores} threads, {dt:.1f} s",
+           "single_thread": {"value": round(m1 / d1, 2), "unit": "queries/s",
+                             "sample": f"first {m1} queries, 1 thread, {d1:.1f} s"}}
+    return rec, ids, dist
+
+
+def parity_block(X, G, data, queries, qd, w, nprobe, legs, o_ids, o_dist, n_learned=1000):
+    """Parity of the benchmarked searches with the oracle at the full size.
+    The oracle first recomputes what it can of the index from the data: its
+    own P for the build seed, the codes and factors of every point (given the
+    centroids and assignment), the argmin assignment of a 2048-point sample;
+    the centroids are the one array it takes as built (k-means is compared
+    bit for bit with the oracle's own on smaller sets in the tests). Then the
+    fixed leg's results for every query the oracle searched, the probe lists
+    of the first 1000 queries, and the learned leg's results for its first
+    n_learned queries searched by the oracle with the same per-query counts
+    (the network's outputs)."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    out = {}
+    P = O.sample_rotation(2, G.dpad)
+    out["rotation_bits_equal"] = bool(np.array_equal(P.view(np.uint64), X.P.view(np.uint64)))
+    codes, fac = O.encode(data, X.centroids, X.assign, P.astype(np.float32), threads=cores)
+    out["codes_equal"] = bool(np.array_equal(codes, X.codes))
+    out["factors_bits_equal"] = bool(np.array_equal(fac.view(np.uint32), X.factors.view(np.uint32)))
+    smp = np.random.default_rng(5).choice(len(data), 2048, replace=False)
+    a_ids, _ = O.select(O.sqdist_matrix(data[smp], X.centroids), 1)
+    out["assign_sample_equal"] = bool(np.array_equal(a_ids[:, 0], X.assign[smp]))
+    m = o_ids.shape[0]
+    g_ids, g_dist = legs["fixed"]["_ids"][:m], legs["fixed"]["_dist"][:m]
+    row_eq = (g_ids == o_ids).all(1) & (g_dist.view(np.uint32) == o_dist.view(np.uint32)).all(1)
+    mp = min(1000, m)
+    t = G.search_trace(qd[:mp], w.k, nprobe, bq=w.bq, eps0=w.eps0)
+    o_probe, _ = O.select(O.sqdist_matrix(queries[:mp], X.centroids), nprobe)
+    out["fixed"] = {"queries": int(m), "nprobe": int(nprobe),
+                    "ids_equal": bool(np.array_equal(g_ids, o_ids)),
+                    "dist_bits_equal": bool(np.array_equal(g_dist.view(np.uint32),
+                                                           o_dist.view(np.uint32))),
+                    "queries_identical": int(row_eq.sum()),
+                    "probe_lists_equal": bool(np.array_equal(t["probe_ids"].cpu().numpy(),
+                                                             o_probe)),
+                    "probe_list_queries": int(mp)}
+    del t
+    lg = legs.get("learned")
+    if lg is not None and lg.get("_npq") is not None:
+        ml = min(n_learned, len(queries))
+        npq = lg["_npq"][:ml]
+        l_ids, l_dist = X.search(queries[:ml], w.k, int(lg["nprobe_max"]), bq=w.bq, eps0=w.eps0,
+                                 threads=cores, per_query_nprobe=npq)
+        out["learned"] = {"queries": int(ml),
+                          "ids_equal": bool(np.array_equal(lg["_ids"][:ml], l_ids)),
+                          "dist_bits_equal": bool(np.array_equal(lg["_dist"][:ml].view(np.uint32),
+                                                                 l_dist.view(np.uint32))),
+                          "per_query_nprobe": "the network's counts from the timed plan"}
+    return out
 
 
 # ------------------------------------------------------------- reference

@@ -122,14 +122,16 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
  *             descending by (value, then ascending id); -inf pads. The
  *             search ranks by the score -<o_r, q_r> with the same bounds
  *             and re-ranking rule.
- * Re-ranking (§4, order-independent form): the 4k codes with the smallest
- * estimated distances (the pilot) get exact distances first; tau1 is the
- * k-th smallest of those, tau_ub the k-th smallest upper bound over all
- * estimated codes; every other code is re-ranked iff its distance lower
- * bound is at most min(tau_ub, tau1).
+ * Re-ranking (§4, order-independent form): tau_ub is the k-th smallest upper
+ * bound over all estimated codes; among the codes whose distance lower bound
+ * is at most tau_ub, the 4k with the smallest estimated distances (the pilot,
+ * ties by id) get exact distances first; tau1 is the k-th smallest of those;
+ * every other code is re-ranked iff its lower bound is at most
+ * min(tau_ub, tau1).
  * Errors: EINVAL (also for a non-finite query value, found during the search:
- * the outputs are then undefined); ENOMEM; ECUDA; EOVERFLOW when more than
- * max_candidates codes of one query pass the bound (raise max_candidates).
+ * the outputs are then undefined; and when the current device is not the one
+ * the index lives on); ENOMEM; ECUDA; EOVERFLOW when more than max_candidates
+ * codes of one query pass the bound (raise max_candidates).
  */
 int rabitq_search(const rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
                   int32_t nprobe, int32_t bq, float eps0, int64_t* out_ids, float* out_dist,
@@ -156,8 +158,8 @@ int rabitq_search(const rabitq_index* idx, const float* queries, int64_t nq, int
  *                          (IP / COSINE: of the score -<o_r, q_r>)
  *   tau_ub                 nq: k-th smallest UB (+inf if fewer than k codes)
  *   tau1                   nq: k-th smallest exact distance among the pilot,
- *                          the 4k codes with the smallest estimates (+inf if
- *                          fewer than k)
+ *                          the 4k codes with the smallest estimates among
+ *                          those with LB <= tau_ub (+inf if fewer than k)
  *   tau                    nq: min(tau_ub, tau1), the drop threshold
  *   surv_cap, n_surv, surv_ids  the re-rank set (pilot plus every code with
  *                          LB <= tau), in no particular order
@@ -203,7 +205,9 @@ int rabitq_search_trace(const rabitq_index* idx, const float* queries, int64_t n
  * query whose candidates do not fit returns EOVERFLOW. The first call on a
  * device looks up the array's device address with that device current; make
  * that first call before any stream capture. All calls share the array:
- * calls that overlap on the GPU race. Errors: those of rabitq_search, plus
+ * calls that overlap on the GPU race. Errors: those of rabitq_search
+ * (including EINVAL for a non-finite query value, read with the call's own
+ * completion wait, and for a current device other than the index's), plus
  * EINVAL for host pointers or for a K so large that one query's centroid
  * distances do not fit in the scratch.
  */

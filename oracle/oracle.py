@@ -91,6 +91,7 @@ def lib():
             "orc_select": (None, [vp, i64, i32, i32, vp, vp]),
             "orc_search_trace": (None, [vp, vp, vp, i32, vp, vp, vp]),
             "orc_search": (None, [vp, vp, vp, i64, i32, vp, vp]),
+            "orc_search_pq": (None, [vp, vp, vp, i64, vp, i32, vp, vp]),
             "orc_bruteforce_knn": (None, [vp, i64, i32, vp, i64, i32, vp, vp, vp, i32]),
             "orc_estimator_fp64": (None, [vp, i32, vp, vp, vp]),
         }
@@ -337,15 +338,21 @@ class OracleIndex:
         return normalize_rows(Q) if self.metric == "cosine" else Q
 
     def search(self, Q, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9, seed: int = 3,
-               mode: int = 0, threads: int = 1):
+               mode: int = 0, threads: int = 1, per_query_nprobe=None):
         """Top-k ids and exact values: squared distances ascending (l2), or
-        inner products / cosines descending (ip, cosine)."""
+        inner products / cosines descending (ip, cosine). per_query_nprobe
+        (nq ints): query i probes its own count of nearest buckets, clamped
+        to [1, nprobe]; query i draws its quantization stream as query i."""
         Q = self._queries(Q)
         nq = Q.shape[0]
         par = _Params(k, nprobe, bq, mode, eps0, seed)
         ids = np.zeros((nq, k), np.int64)
         dist = np.zeros((nq, k), np.float32)
-        lib().orc_search(C.byref(self._s), C.byref(par), _p(Q), nq, threads, _p(ids), _p(dist))
+        npq = None if per_query_nprobe is None else _c(per_query_nprobe, np.int32)
+        if npq is not None and npq.shape != (nq,):
+            raise ValueError("per_query_nprobe must hold one count per query")
+        lib().orc_search_pq(C.byref(self._s), C.byref(par), _p(Q), nq, _p(npq), threads,
+                            _p(ids), _p(dist))
         return ids, dist
 
     def trace(self, q, qid: int, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,

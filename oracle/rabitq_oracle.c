@@ -24,11 +24,12 @@
  * Compiled with -O2 -ffp-contract=off and without -ffast-math so that every
  * float operation written here is one IEEE-754 round-to-nearest operation.
  *
- * Parity status: k-means (orc_kmeans) has no external pin -- parity
- * unpinned; its invariants (argmin assignment, mean update, non-increasing
- * objective) are tested instead. Every other function is pinned by the
- * tests in tests/test_oracle_pins.py (the inner-product / cosine metric and
- * the single-code estimator in tests/test_oracle_ip_pins.py).
+ * Parity status: every function is pinned by the tests in
+ * tests/test_oracle_pins.py (the inner-product / cosine metric and the
+ * single-code estimator in tests/test_oracle_ip_pins.py). k-means, whose
+ * variant the paper does not fix, is pinned by Lloyd iterates worked out by
+ * hand (ties to the lower centroid id, an empty cluster keeping its value,
+ * the FP32 mean in id order) besides its invariants.
  *
  * Metrics: squared Euclidean distance (the paper's setting) and the inner
  * product of the paper's closing footnote (§6), which also gives the cosine
@@ -282,7 +283,7 @@ ORC_API void orc_rotate(const float* x, int64_t n, int32_t d, const float* P32,
 
 /* ------------------------------------------------------------------------ */
 /* IVF k-means (paper §4: "clusters them with the KMeans algorithm").         */
-/* parity unpinned: the paper fixes no k-means variant. Reading: training    */
+/* The paper fixes no k-means variant. Reading: training                    */
 /* set = all points, or the ids whose Philox(seed; id, 0, 0, TAG_SAMPLE) w0   */
 /* lies below floor(2^32 * sample / n) when 0 < sample < n; init = K distinct */
 /* training points chosen by Floyd's algorithm (Philox(seed; t, 0, 0,        */
@@ -867,6 +868,7 @@ typedef struct {
   const orc_index* X;
   const orc_params* p;
   const float* Q;
+  const int32_t* npq;  /* per-query probe counts or NULL */
   int64_t q0, q1;
   int64_t* ids;
   float* dist;
@@ -877,23 +879,32 @@ static void* search_range(void* arg) {
   float* cd = (float*)malloc(sizeof(float) * (size_t)J->X->K);
   int32_t* ids = (int32_t*)malloc(sizeof(int32_t) * (size_t)J->X->K);
   float* pd = (float*)malloc(sizeof(float) * (size_t)J->X->K);
-  for (int64_t i = J->q0; i < J->q1; ++i)
-    search_one(J->X, J->p, J->Q + i * J->X->d, (int32_t)i, J->ids + i * J->p->k,
+  for (int64_t i = J->q0; i < J->q1; ++i) {
+    orc_params pi = *J->p;
+    if (J->npq) {  /* this query's own count, within [1, nprobe] */
+      int32_t v = J->npq[i];
+      pi.nprobe = v < 1 ? 1 : (v > J->p->nprobe ? J->p->nprobe : v);
+    }
+    search_one(J->X, &pi, J->Q + i * J->X->d, (int32_t)i, J->ids + i * J->p->k,
                J->dist + i * J->p->k, NULL, cd, ids, pd);
+  }
   free(cd); free(ids); free(pd);
   return NULL;
 }
 
 /* Search nq queries, split evenly over `threads` POSIX threads (query i uses
- * qid = qid0 + i for its quantization stream). */
-ORC_API void orc_search(const orc_index* X, const orc_params* p, const float* Q, int64_t nq,
-                        int32_t threads, int64_t* out_ids, float* out_dist) {
+ * qid = i for its quantization stream). npq (NULL = every query probes
+ * p->nprobe buckets): query i probes its npq[i] nearest buckets, clamped to
+ * [1, p->nprobe] -- the search of a per-query (learned) probe count. */
+ORC_API void orc_search_pq(const orc_index* X, const orc_params* p, const float* Q, int64_t nq,
+                           const int32_t* npq, int32_t threads, int64_t* out_ids,
+                           float* out_dist) {
   if (threads < 1) threads = 1;
   if (threads > nq) threads = (int32_t)(nq > 0 ? nq : 1);
   pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
   orc_job* jobs = (orc_job*)malloc(sizeof(orc_job) * (size_t)threads);
   for (int32_t t = 0; t < threads; ++t) {
-    jobs[t].X = X; jobs[t].p = p; jobs[t].Q = Q;
+    jobs[t].X = X; jobs[t].p = p; jobs[t].Q = Q; jobs[t].npq = npq;
     jobs[t].q0 = nq * t / threads;
     jobs[t].q1 = nq * (t + 1) / threads;
     jobs[t].ids = out_ids; jobs[t].dist = out_dist;
@@ -906,6 +917,12 @@ ORC_API void orc_search(const orc_index* X, const orc_params* p, const float* Q,
   }
   free(th);
   free(jobs);
+}
+
+/* Search nq queries, every one probing p->nprobe buckets. */
+ORC_API void orc_search(const orc_index* X, const orc_params* p, const float* Q, int64_t nq,
+                        int32_t threads, int64_t* out_ids, float* out_dist) {
+  orc_search_pq(X, p, Q, nq, NULL, threads, out_ids, out_dist);
 }
 
 typedef struct {

@@ -24,6 +24,16 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+int check_device(int device, const char* who) {
+  int cur = 0;
+  RBQ_CUDA(cudaGetDevice(&cur));
+  if (cur != device)
+    return fail(RABITQ_EINVAL, std::string(who) + ": the current device (" + std::to_string(cur) +
+                                   ") is not the device the index lives on (" +
+                                   std::to_string(device) + ")");
+  return RABITQ_OK;
+}
+
 namespace {
 
 template <class T>
@@ -261,6 +271,7 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   g_err.clear();
   g_nstats = 0;
   if (!X) return fail(RABITQ_EINVAL, "rabitq_search: index is null");
+  RBQ_CHECK(check_device(X->device, "rabitq_search"));
   rabitq_search_opts opts;
   rabitq_search_opts_default(&opts);
   if (opts_in) opts = *opts_in;
@@ -293,11 +304,17 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   cudaStream_t s = static_cast<cudaStream_t>(opts.stream);
   const bool on_dev = trace ? true : opts.io_on_device != 0;
 
-  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  struct Events {  // destroyed on every return path
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    ~Events() {
+      if (t0) cudaEventDestroy(t0);
+      if (t1) cudaEventDestroy(t1);
+    }
+  } ev;
   if (opts.collect_stats) {
-    RBQ_CUDA(cudaEventCreate(&t0));
-    RBQ_CUDA(cudaEventCreate(&t1));
-    RBQ_CUDA(cudaEventRecord(t0, s));
+    RBQ_CUDA(cudaEventCreate(&ev.t0));
+    RBQ_CUDA(cudaEventCreate(&ev.t1));
+    RBQ_CUDA(cudaEventRecord(ev.t0, s));
   }
   DevBuf qb, ib, db, nb, pb;
   const float* dq = queries;
@@ -353,17 +370,15 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
     RBQ_CUDA(cudaMemcpyAsync(out_ids, dids, sizeof(int64_t) * nq * k, cudaMemcpyDeviceToHost, s));
     RBQ_CUDA(cudaMemcpyAsync(out_dist, ddist, sizeof(float) * nq * k, cudaMemcpyDeviceToHost, s));
   }
+  // the total ends with the search and its output copies (before the flag read)
+  if (opts.collect_stats) RBQ_CUDA(cudaEventRecord(ev.t1, s));
   int h_fin = 0;
   RBQ_CUDA(cudaMemcpyAsync(&h_fin, fin.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   RBQ_CUDA(cudaStreamSynchronize(s));
   if (h_fin)
     return fail(RABITQ_EINVAL, "rabitq_search: a query has a non-finite value (outputs undefined)");
   if (opts.collect_stats) {
-    RBQ_CUDA(cudaEventRecord(t1, s));
-    RBQ_CUDA(cudaEventSynchronize(t1));
-    RBQ_CUDA(cudaEventElapsedTime(&stage[4], t0, t1));
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
+    RBQ_CUDA(cudaEventElapsedTime(&stage[4], ev.t0, ev.t1));
     for (int i = 0; i < 5; ++i) g_stats[i] = stage[i];
     g_nstats = 5;
   }
@@ -389,6 +404,7 @@ int rabitq_search_learned(const rabitq_index* idx, const rabitq_predictor* pr,
                           const float* queries, int64_t nq, int32_t k, int32_t bq, float eps0,
                           int64_t* out_ids, float* out_dist, const rabitq_search_opts* opts) {
   if (!idx || !pr) return fail(RABITQ_EINVAL, "rabitq_search_learned: null index or predictor");
+  RBQ_CHECK(check_device(pr->device, "rabitq_search_learned (predictor)"));
   if (pr->K != idx->K)
     return fail(RABITQ_EINVAL, "rabitq_search_learned: predictor made for another bucket count");
   if (idx->metric != RABITQ_METRIC_L2)
@@ -404,6 +420,7 @@ int rabitq_autotune(rabitq_index* X, const float* queries, int64_t nq, int32_t k
                     const rabitq_search_opts* opts_in, int32_t* chosen, float* times_ms) {
   g_err.clear();
   if (!X) return fail(RABITQ_EINVAL, "rabitq_autotune: index is null");
+  RBQ_CHECK(check_device(X->device, "rabitq_autotune"));
   if (nq < 1 || !queries) return fail(RABITQ_EINVAL, "rabitq_autotune: need queries (nq >= 1)");
   if (reps < 1 || reps > 1000) return fail(RABITQ_EINVAL, "rabitq_autotune: need 1 <= reps <= 1000");
   rabitq_search_opts opts;
@@ -482,6 +499,7 @@ int rabitq_estimate(const rabitq_index* X, const float* queries, int64_t nq, con
                     const rabitq_search_opts* opts_in) {
   g_err.clear();
   if (!X) return fail(RABITQ_EINVAL, "rabitq_estimate: index is null");
+  RBQ_CHECK(check_device(X->device, "rabitq_estimate"));
   rabitq_search_opts opts;
   rabitq_search_opts_default(&opts);
   if (opts_in) opts = *opts_in;

@@ -67,6 +67,7 @@ int rabitq_predictor_train(const rabitq_index* X, const float* train_q, int64_t 
   if (!out) return fail(RABITQ_EINVAL, "rabitq_predictor_train: out is null");
   *out = nullptr;
   if (!X || !train_q) return fail(RABITQ_EINVAL, "rabitq_predictor_train: null index or queries");
+  RBQ_CHECK(check_device(X->device, "rabitq_predictor_train"));
   if (X->metric != RABITQ_METRIC_L2)
     return fail(RABITQ_EUNSUPPORTED, "rabitq_predictor_train: learned probe counts need a squared-distance (L2) index");
   rabitq_predictor_opts o;
@@ -196,6 +197,8 @@ int rabitq_predict_nprobe(const rabitq_index* X, const rabitq_predictor* pr,
                           float* out_features, float* out_y, const rabitq_search_opts* opts_in) {
   set_error("");
   if (!X || !pr) return fail(RABITQ_EINVAL, "rabitq_predict_nprobe: null index or predictor");
+  RBQ_CHECK(check_device(X->device, "rabitq_predict_nprobe"));
+  RBQ_CHECK(check_device(pr->device, "rabitq_predict_nprobe (predictor)"));
   if (pr->K != X->K)
     return fail(RABITQ_EINVAL, "rabitq_predict_nprobe: predictor made for another bucket count");
   if (X->metric != RABITQ_METRIC_L2)
@@ -251,6 +254,7 @@ int rabitq_compute_labels(const rabitq_index* X, const float* queries, int64_t n
                           int32_t nprobe_max, int32_t* ranks, int32_t* label_r) {
   set_error("");
   if (!X) return fail(RABITQ_EINVAL, "rabitq_compute_labels: index is null");
+  RBQ_CHECK(check_device(X->device, "rabitq_compute_labels"));
   if (X->metric != RABITQ_METRIC_L2)
     return fail(RABITQ_EUNSUPPORTED, "rabitq_compute_labels: learned probe counts need a squared-distance (L2) index");
   if (nq < 0) return fail(RABITQ_EINVAL, "rabitq_compute_labels: nq < 0");

@@ -60,6 +60,10 @@ namespace rbq {
 // error plumbing (thread-local message)
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
+// EINVAL (message names `who`) unless the calling thread's current device is
+// `device`, the device an index, predictor or plan lives on: its arrays are
+// device pointers of that GPU only.
+int check_device(int device, const char* who);
 
 #define RBQ_CUDA(call)                                                              \
   do {                                                                              \

@@ -2814,8 +2814,13 @@ int search_dev_prealloc(const SearchArgs& a_in, unsigned char* scratch, size_t s
   if (a_in.nq == 0) return RABITQ_OK;
   SearchArgs a = a_in;
   a.allow_split = 0;  // the fixed scratch has no room for the split buffers
+  // flags: err[0] = search error (1 = candidate overflow, 2 = expired wait),
+  // err[1] = a query value is not finite; both must start at zero (the
+  // carved layout keeps the first 256 bytes for flags; the work counter is at
+  // byte 64)
   int* err = reinterpret_cast<int*>(scratch);
-  RBQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));  // the flag must start at zero
+  RBQ_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
+  RBQ_CHECK(finite_flag(a.queries, a.nq * a.X->d, err + 1, s));
   // one CTA per SM; the candidate lists take at most half of the scratch
   int dev = 0, sms = 0;
   RBQ_CUDA(cudaGetDevice(&dev));
@@ -2823,11 +2828,13 @@ int search_dev_prealloc(const SearchArgs& a_in, unsigned char* scratch, size_t s
   const int64_t cap = std::min<int64_t>(
       a.cand_cap, (int64_t)((scratch_bytes / 2 - kCarveAlign) / (sizeof(int4) * sms)));
   RBQ_CHECK(search_enqueue_carved(a, scratch, scratch_bytes, sms, cap, s));
-  int h_err = 0;
-  RBQ_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int h_err[2] = {0, 0};
+  RBQ_CUDA(cudaMemcpyAsync(h_err, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   RBQ_CUDA(cudaStreamSynchronize(s));
-  if (h_err == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired (probe scores or query rotation)");
-  if (h_err)
+  if (h_err[1])
+    return fail(RABITQ_EINVAL, "a query has a non-finite value (outputs undefined)");
+  if (h_err[0] == 2) return fail(RABITQ_ETIMEOUT, "a tensor-core wait expired (probe scores or query rotation)");
+  if (h_err[0])
     return fail(RABITQ_EOVERFLOW,
                 "a query's candidate list exceeded the fixed scratch's capacity");
   return RABITQ_OK;

@@ -17,7 +17,8 @@
 // device current, looks its address up with cudaGetSymbolAddress and keeps it;
 // make that first call before any stream capture. All calls share the one
 // array and it keeps the last call's contents; the only state that must start
-// at zero (the overflow flag) is cleared by every call. Calls whose work
+// at zero (the overflow flag and the non-finite-query flag) is cleared by
+// every call. Calls whose work
 // overlaps on the GPU (two streams, two host threads) race on the array.
 #include <mutex>
 
@@ -74,6 +75,9 @@ extern "C" int rabitq_search_noalloc(const rabitq_index* X, const float* queries
     return fail(RABITQ_EINVAL,
                 "rabitq_search_noalloc: queries, outputs and per_query_nprobe must be device "
                 "memory (host buffers would need staging memory)");
+  // the scratch address below belongs to the current device, and the index's
+  // arrays to the device it was built or loaded on: they must be the same
+  RBQ_CHECK(check_device(X->device, "rabitq_search_noalloc"));
   int dev = 0;
   RBQ_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices)

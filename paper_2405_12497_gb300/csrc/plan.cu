@@ -89,6 +89,8 @@ int rabitq_plan_create(const rabitq_index* X, const rabitq_predictor* pr, int64_
   if (!out) return fail(RABITQ_EINVAL, "rabitq_plan_create: out is null");
   *out = nullptr;
   if (!X) return fail(RABITQ_EINVAL, "rabitq_plan_create: index is null");
+  RBQ_CHECK(check_device(X->device, "rabitq_plan_create"));
+  if (pr) RBQ_CHECK(check_device(pr->device, "rabitq_plan_create (predictor)"));
   rabitq_search_opts opts;
   rabitq_search_opts_default(&opts);
   if (opts_in) opts = *opts_in;
@@ -186,6 +188,7 @@ int rabitq_plan_run(rabitq_plan* P, int64_t nq, void* stream) {
   set_error("");
   if (!P) return fail(RABITQ_EINVAL, "rabitq_plan_run: plan is null");
   if (nq < 0 || nq > P->nq_max) return fail(RABITQ_EINVAL, "rabitq_plan_run: need 0 <= nq <= nq_max");
+  RBQ_CHECK(check_device(P->device, "rabitq_plan_run"));
   if (nq == 0) return RABITQ_OK;
   cudaGraphExec_t ex = nullptr;
   RBQ_CHECK(graph_for(P, nq, &ex));

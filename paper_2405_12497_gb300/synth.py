@@ -123,6 +123,39 @@ def deep_like(n: int, nq: int, d: int = 256, n_comp: int = 10_000, seed_data: in
     return (draw(n, seed_data) if with_data else None), draw(nq, seed_query)
 
 
+def deep_like_device(n: int, nq: int, device, d: int = 256, n_comp: int | None = None,
+                     sigma: float = 1.0, seed_data: int = 0, seed_query: int = 1,
+                     with_data: bool = True):
+    """DEEP-shaped unit vectors drawn directly in device memory (torch CUDA
+    generator; the 10M-point set would take minutes with numpy): n_comp
+    (default n/100) components mu ~ N(0, I/d), x = normalize(mu + sigma
+    N(0, I/d)). With n/100 components of about 100 points each and sigma near
+    1, a query's 100 nearest neighbours spread over several IVF buckets (the
+    10k-component recipe puts them all in one or two). Returns torch tensors
+    (data or None, queries)."""
+    import math
+
+    import torch
+    n_comp = n_comp or max(10, n // 100)
+    gc = torch.Generator(device=device)
+    gc.manual_seed(seed_data)
+    mu = torch.randn((n_comp, d), generator=gc, device=device) / math.sqrt(d)
+
+    def draw(m, seed):
+        g = torch.Generator(device=device)
+        g.manual_seed(seed + 1000)
+        out = torch.empty((m, d), dtype=torch.float32, device=device)
+        for s in range(0, m, 1 << 20):
+            e = min(m, s + (1 << 20))
+            comp = torch.randint(0, n_comp, (e - s,), generator=g, device=device)
+            x = mu[comp] + (sigma / math.sqrt(d)) * torch.randn((e - s, d), generator=g,
+                                                                device=device)
+            out[s:e] = x / x.norm(dim=1, keepdim=True)
+        return out
+
+    return (draw(n, seed_data) if with_data else None), draw(nq, seed_query)
+
+
 def make(w: Workload, n: int | None = None, nq: int | None = None, seed_query: int = 1,
          with_data: bool = True):
     """Data and queries of a workload (optionally with fewer points/queries;

@@ -198,9 +198,56 @@ def test_assignment_and_distances_are_canonical(oracle_mod, tiny_oracle_index):
     assert np.allclose(D32, d64[:50], rtol=1e-5, atol=1e-6)
 
 
+def _seed_with_init(oracle_mod, n, K, want):
+    """A seed whose Floyd initialisation picks exactly the ids `want` (in
+    that order); Floyd's sampling itself is pinned by test_floyd_sampling_is_uniform."""
+    for seed in range(200_000):
+        if oracle_mod.kmeans_init_ids(n, K, seed).tolist() == want:
+            return seed
+    raise AssertionError(f"no seed initialises with {want}")
+
+
+def test_kmeans_lloyd_iterates_by_hand(oracle_mod):
+    """Lloyd iterations of §4's KMeans, worked out by hand on seven 1-D points
+    x = [1, 1, 3, 5, 9, 11, 7] with K = 3 initial centroids x0, x1, x4 =
+    (1, 1, 9). The two equal centroids and the point 5 (16 from both 1 and 9)
+    pin the tie rule (lower centroid id), centroid 1 pins the empty-cluster
+    rule (it keeps its value), the means pin the update.
+
+    iteration 1: assign [0 0 0 0 2 2 2] (5 ties 0/2 -> 0; 1 ties 0/1 -> 0;
+                 cluster 1 empty) -> centroids (10/4, 1, 27/3) = (2.5, 1, 9)
+    iteration 2: assign [1 1 0 0 2 2 2] -> centroids (4, 1, 9)
+    iteration 3: assign [1 1 0 0 2 2 2] -> unchanged (4, 1, 9)
+    The final pass assigns every point with the final centroids."""
+    x = np.array([[1], [1], [3], [5], [9], [11], [7]], np.float32)
+    seed = _seed_with_init(oracle_mod, 7, 3, [0, 1, 4])
+    want = {
+        0: ([1.0, 1.0, 9.0], [0, 0, 0, 0, 2, 2, 2], [0, 0, 4, 16, 0, 4, 4]),
+        1: ([2.5, 1.0, 9.0], [1, 1, 0, 0, 2, 2, 2], [0, 0, 0.25, 6.25, 0, 4, 4]),
+        2: ([4.0, 1.0, 9.0], [1, 1, 0, 0, 2, 2, 2], [0, 0, 1, 1, 0, 4, 4]),
+        3: ([4.0, 1.0, 9.0], [1, 1, 0, 0, 2, 2, 2], [0, 0, 1, 1, 0, 4, 4]),
+    }
+    for iters, (cent, assign, adist) in want.items():
+        c, a, ad = oracle_mod.kmeans(x, 3, iters, seed=seed)
+        assert c[:, 0].tolist() == cent, iters
+        assert a.tolist() == assign, iters
+        assert ad.tolist() == adist, iters
+
+
+def test_kmeans_mean_is_an_fp32_sum_in_id_order(oracle_mod):
+    """The update's mean is the FP32 sum of the members in ascending id order
+    divided by the count: for the members 1, 1e8, -1e8 (in id order) that sum
+    is (1 + 1e8) - 1e8 = 1e8 - 1e8 = 0 in FP32 (1e8 + 1 rounds to 1e8), so the
+    centroid is 0, not the real mean 1/3."""
+    x = np.array([[1.0], [1e8], [-1e8]], np.float32)
+    assert np.float32(np.float32(1.0) + np.float32(1e8)) == np.float32(1e8)
+    c, a, _ = oracle_mod.kmeans(x, 1, 1, seed=0)
+    assert c[0, 0] == 0.0 and a.tolist() == [0, 0, 0]
+
+
 def test_kmeans_invariants(oracle_mod, tiny_workload):
-    """parity unpinned: the paper fixes no k-means variant, so only the
-    invariants of Lloyd's algorithm are checked."""
+    """Invariants of Lloyd's algorithm on a larger case: non-increasing
+    objective, centroids equal to the member means, distinct init points."""
     data = tiny_workload[0][:3000]
     objs = []
     for it in range(0, 5):
@@ -217,7 +264,8 @@ def test_kmeans_invariants(oracle_mod, tiny_workload):
             assert np.allclose(cent2[c], mem.mean(0), rtol=1e-5, atol=1e-5)
     ids = oracle_mod.kmeans_init_ids(3000, 12, 9)
     assert len(set(ids.tolist())) == 12 and ids.min() >= 0 and ids.max() < 3000
-    assert np.array_equal(cent[0] if False else data[ids[0]], data[ids[0]])
+    c0, _, _ = oracle_mod.kmeans(data, 12, 0, seed=9)   # no iteration: the init points
+    assert np.array_equal(c0, data[ids])
 
 
 def test_floyd_sampling_is_uniform(oracle_mod):
@@ -351,24 +399,76 @@ def test_select_matches_lexsort(oracle_mod):
         assert np.array_equal(sd[r], d[r][order])
 
 
-def test_search_equals_exact_knn_over_probed_buckets(oracle_mod, tiny_oracle_index, tiny_workload):
-    """With every true member inside its bound, the error-bound re-ranking
-    returns the exact kNN of the union of the probed buckets (§4)."""
+@pytest.mark.parametrize("k,nprobe,eps0", [(10, 4, 1.9), (10, 8, 1.0), (30, 4, 0.5)])
+def test_search_equals_exact_knn_over_probed_buckets(oracle_mod, tiny_oracle_index, tiny_workload,
+                                                     k, nprobe, eps0):
+    """The error-bound re-ranking of §4 returns the exact kNN of the union of
+    the probed buckets unless a bound failed, and every query where it does
+    not is explained by a failed bound:
+
+    * paper-literal sequential rule (mode 1): a true neighbour o is dropped
+      only when LB_o exceeds the exact distance of the current k-th best,
+      which is at least the k-th true distance d_k >= |o - q|^2; so a missing
+      neighbour's own lower bound failed (LB_o > its exact distance);
+    * order-independent rule (mode 0): o is dropped when LB_o > min(tau_ub,
+      tau1); tau1 >= d_k always, so either o's own lower bound failed or
+      tau_ub < d_k, which needs some code whose upper bound is below its exact
+      distance.
+    Lowering eps0 makes failures common, so the rule is exercised; every
+    mismatching query must be explained (zero unexplained queries), and where
+    the ids agree the distances are the canonical exact ones."""
     X = tiny_oracle_index
     _, Q = tiny_workload
-    k, nprobe = 10, 4
-    ids, dist = X.search(Q, k, nprobe)
+    Q = Q[:60]
     cd = oracle_mod.sqdist_matrix(Q, X.centroids)
     probes, _ = oracle_mod.select(cd, nprobe)
-    allowed = np.isin(X.assign[None, :], probes[:, :, None]).any(1) if False else \
-        np.stack([np.isin(X.assign, probes[i]) for i in range(len(Q))]).astype(np.uint8)
+    allowed = np.stack([np.isin(X.assign, probes[i]) for i in range(len(Q))]).astype(np.uint8)
     bids, bdist = oracle_mod.bruteforce_knn(X.data, Q, k, allowed)
-    same = (ids == bids).all(1)
-    assert same.mean() >= 0.97
-    assert np.array_equal(dist[same], bdist[same])
-    # mode 1 (paper-literal sequential drop rule) agrees on nearly all queries
-    ids1, _ = X.search(Q, k, nprobe, mode=1)
-    assert (ids1 == ids).all(1).mean() >= 0.97
+    # the brute force itself against an FP64 reference (no near-ties here)
+    for i in range(0, len(Q), 7):
+        cand = np.flatnonzero(allowed[i])
+        d64 = ((X.data[cand].astype(np.float64) - Q[i]) ** 2).sum(1)
+        assert set(cand[np.argsort(d64, kind="stable")[:k]].tolist()) == set(bids[i].tolist())
+    mism = {0: 0, 1: 0}
+    for mode in (0, 1):
+        ids, dist = X.search(Q, k, nprobe, eps0=eps0, mode=mode)
+        for i in range(len(Q)):
+            if np.array_equal(ids[i], bids[i]):
+                assert np.array_equal(dist[i].view(np.uint32), bdist[i].view(np.uint32))
+                continue
+            mism[mode] += 1
+            t = X.trace(Q[i], i, k, nprobe, eps0=eps0)
+            pos = {int(v): j for j, v in enumerate(t["pair_id"])}
+            ex = oracle_mod.sqdist_matrix(Q[i:i + 1], X.data[t["pair_id"]])[0]
+            missing = [int(o) for o in set(bids[i].tolist()) - set(ids[i].tolist())]
+            own_failed = any(t["pair_est"][pos[o], 1] > ex[pos[o]] for o in missing)
+            if mode == 1:
+                assert own_failed, (mode, i)
+            else:
+                ub_failed = t["tau_ub"] < bdist[i, k - 1] and \
+                    bool((t["pair_est"][:, 2] < ex).any())
+                assert own_failed or ub_failed, (mode, i)
+    if eps0 < 1.9:
+        assert mism[0] + mism[1] > 0   # the explanation rule was exercised
+    else:
+        assert mism[0] <= 0.1 * len(Q) and mism[1] <= 0.1 * len(Q)
+
+
+def test_per_query_probe_counts(oracle_mod, tiny_oracle_index, tiny_workload):
+    """A per-query probe count gives each query exactly the result of the
+    fixed-count search at its own count (same quantization stream)."""
+    X = tiny_oracle_index
+    _, Q = tiny_workload
+    Q = Q[:24]
+    npq = (np.arange(24) % 6 + 1).astype(np.int32)
+    npq[5] = 0    # clamped to 1
+    npq[11] = 99  # clamped to nprobe
+    ids, dist = X.search(Q, 10, 6, per_query_nprobe=npq)
+    for c in range(1, 7):
+        ids_c, dist_c = X.search(Q, 10, c)
+        rows = np.flatnonzero(np.clip(npq, 1, 6) == c)
+        assert np.array_equal(ids[rows], ids_c[rows])
+        assert np.array_equal(dist[rows], dist_c[rows])
 
 
 def test_trace_rerank_set_definition(oracle_mod, tiny_oracle_index, tiny_workload):

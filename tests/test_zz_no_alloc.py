@@ -69,3 +69,25 @@ def test_noalloc_rejects_host_buffers():
                                        dist.ctypes.data_as(C.c_void_p), None)
     assert rc == R.EINVAL
     assert b"device memory" in R.lib().rabitq_last_error()
+
+
+def test_noalloc_reports_non_finite_query():
+    """A NaN or infinite query value is an EINVAL, as for rabitq_search; a
+    clean call right after it succeeds (the flag starts at zero each call)."""
+    import torch
+    from paper_2405_12497_gb300 import build, rabitq as R, synth
+    build.build()
+    data, Q = synth.tiny(n=2000, nq=8)
+    G = R.Index.build(data, 8, seed=2)
+    for bad in (float("nan"), float("inf")):
+        Qb = Q.copy()
+        Qb[3, 17] = bad
+        rc, _, _ = _noalloc(R, G, torch.from_numpy(Qb).cuda(), 5, 2)
+        assert rc == R.EINVAL
+        assert b"non-finite" in R.lib().rabitq_last_error()
+    qd = torch.from_numpy(Q).cuda()
+    rc, ids, dist = _noalloc(R, G, qd, 5, 2)
+    assert rc == R.OK, R.lib().rabitq_last_error()
+    ref_ids, ref_dist = G.search(qd, 5, 2)
+    assert np.array_equal(ids, ref_ids.cpu().numpy())
+    assert np.array_equal(dist.view(np.uint32), ref_dist.cpu().numpy().view(np.uint32))
