@@ -61,6 +61,13 @@ enum { RABITQ_METRIC_L2 = 0, RABITQ_METRIC_IP = 1, RABITQ_METRIC_COSINE = 2 };
  * an exact integer product on tensor cores; AUTO picks per shape. */
 enum { RABITQ_SCAN_AUTO = 0, RABITQ_SCAN_POPC = 1, RABITQ_SCAN_TC = 2 };
 
+/* Work layout of the popcount scan: one CTA (8 warps) per query, or one warp
+ * per query (no block barriers; D' of 128 or 256, B_q = 4, k <= 128 and
+ * batches large enough to fill the GPU; other searches use the CTA layout).
+ * AUTO follows rabitq_autotune's choice, else the warp layout where it
+ * applies. Results are identical in every layout. */
+enum { RABITQ_LAYOUT_AUTO = 0, RABITQ_LAYOUT_CTA = 1, RABITQ_LAYOUT_WARP = 2 };
+
 typedef struct {
   int32_t kmeans_iters;     /* Lloyd iterations (default 10)                    */
   int64_t kmeans_sample;    /* train k-means on about this many points, 0 = all */
@@ -83,6 +90,7 @@ typedef struct {
   int32_t max_candidates;   /* per-query capacity of the candidate list that
                                survives the error bound, 4096..2^26 (0 = 65536) */
   int32_t collect_stats;    /* record per-stage device times (rabitq_last_stats) */
+  int32_t scan_layout;      /* RABITQ_LAYOUT_* of the popcount scan (default AUTO) */
 } rabitq_search_opts;
 
 /* Fill the option structs with their defaults. */

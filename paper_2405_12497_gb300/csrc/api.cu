@@ -293,6 +293,8 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   if (opts.scan_path != RABITQ_SCAN_AUTO && opts.scan_path != RABITQ_SCAN_POPC &&
       opts.scan_path != RABITQ_SCAN_TC)
     return fail(RABITQ_EINVAL, "rabitq_search: unknown scan_path");
+  if (opts.scan_layout < RABITQ_LAYOUT_AUTO || opts.scan_layout > RABITQ_LAYOUT_WARP)
+    return fail(RABITQ_EINVAL, "rabitq_search: unknown scan_layout");
   if (trace && opts.scan_path != RABITQ_SCAN_POPC &&
       (trace->planes || trace->sum_qu || trace->meta || trace->pair_id))
     opts.scan_path = RABITQ_SCAN_POPC;  // bit-planes and per-pair values come from that path
@@ -353,6 +355,7 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   a.trace = trace;
   a.rot_precision = opts.rot_precision;
   a.scan_path = opts.scan_path;
+  a.layout = opts.scan_layout;
   if (pr) {
     RBQ_CHECK(pb.alloc(sizeof(int32_t) * nq, s));
     a.pred = pr;

@@ -32,6 +32,7 @@ struct rabitq_index {
   // tensor-core operand types of the BF16 / TF32 query rotation
   int32_t kp = 0;
   int32_t tuned_path = 0;         // scan path AUTO uses (rabitq_autotune)
+  int32_t tuned_layout = 0;       // scan layout AUTO uses (rabitq_autotune), 0 = default
   void* ptb = nullptr;            // dpad x kp BF16
   float* ptf = nullptr;           // dpad x kp TF32-rounded FP32
   // centroids for the tensor-core probe scores: K x kp TF32-rounded rows,
@@ -173,6 +174,10 @@ struct SearchArgs {
   // a batch too small to fill the GPU may split each query's probes over
   // several CTAs and merge them (identical results); off where scratch is fixed
   int allow_split = 1;
+  // work layout of the popcount scan (RABITQ_LAYOUT_*); the warp-per-query
+  // kernel also needs allow_warp (off where the scratch is fixed)
+  int32_t layout = 0;
+  int allow_warp = 1;
 };
 int search_dev(const SearchArgs& a, cudaStream_t s);
 // Probe counts of nq queries from a predictor: query-centroid distances, the

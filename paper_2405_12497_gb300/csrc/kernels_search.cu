@@ -167,6 +167,14 @@ struct FusedParams {
   uint32_t* ub_out;
   int* slice_cnt;
   int4* cand2;
+  // Warp-per-query kernel: candidate region of capw entries per warp; a
+  // query whose list outgrows it goes to redo[*redo_cnt++]. The CTA kernel
+  // redoing them reads its query count from *nq_dev when that is set.
+  int4* candw;
+  int capw;
+  int32_t* redo;
+  int* redo_cnt;
+  const int* nq_dev;
 };
 
 struct FusedSmem {
@@ -1390,7 +1398,7 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
     return s_next;
   };
   const int split = P.split > 1 ? P.split : 1;
-  const int64_t n_items = P.nq * split;
+  const int64_t n_items = (P.nq_dev ? (int64_t)*P.nq_dev : P.nq) * split;
   for (int64_t it = P.next ? fetch(0) : (int64_t)blockIdx.x; it < n_items; it = fetch(it)) {
     const int64_t qi = it / split;
     const int sl = (int)(it % split);
@@ -1728,6 +1736,501 @@ __global__ void __launch_bounds__(kThreads) split_merge_kernel(FusedParams P) {
     finish_query(P, S, q, in_smem ? S.scand : merged, in_smem ? P.scap : P.cand_cap, tau_ub, ts,
                  true);
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------ warp-per-query fused scan
+// The same search as fused_search_kernel with one WARP per query instead of
+// one CTA, for the common shapes (D' = 128 or 256, B_q = 4, k <= 128): no
+// block barrier anywhere. Per probe the warp quantizes the query against the
+// bucket's centroid with its lanes owning dimensions 32 r + lane, so that
+// each bit-plane word of q_u is one ballot and the planes sit in registers;
+// the bucket's codes are then scanned with lanes on consecutive codes
+// (coalesced 16-byte loads, PPL codes per lane per step). The warp keeps the
+// exact running k-th smallest upper bound tau (a 256-key buffer, sorted when
+// full) and appends every code with LB <= tau to its own candidate region
+// (compacted by the current tau when full). The end of the query follows the
+// same rule as finish_query (§4, reading R1): tau_ub, the pilot, tau1, the
+// rest of the re-rank set and the top-k by (distance, id). A query whose
+// candidates do not fit the region is handed to the CTA kernel (redo list).
+constexpr int kWarpMaxK = 128;     // largest k of the warp kernel
+constexpr int kWarpBuf = 256;      // keys per per-warp buffer
+constexpr int kWarpThreads = 128;  // 4 warps (queries) per CTA
+
+struct __align__(16) WarpSmem {
+  uint32_t ubk[kWarpBuf];               // running upper-bound keys
+  unsigned long long top[kWarpBuf];     // (exact score key << 32) | id
+  int hist[256];                        // radix-select histogram / row staging
+  float qv[256];                        // the query (d <= 256)
+};
+
+template <class T>
+__device__ __forceinline__ T shfl_xor_t(T v, int m) {
+  return __shfl_xor_sync(kFull, v, m);
+}
+
+// Ascending bitonic sort of 256 keys held eight per lane (element 8 lane + i).
+template <class T>
+__device__ __forceinline__ void warp_sort256(T (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 256; size <<= 1) {
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1) {
+      if (j >= 8) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int e = 8 * lane + i;
+          const T o = shfl_xor_t(v[i], j >> 3);
+          const bool up = (e & size) == 0, lower = (e & j) == 0;
+          v[i] = (lower == up) ? (o < v[i] ? o : v[i]) : (o > v[i] ? o : v[i]);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if ((i & j) == 0) {
+            const int e = 8 * lane + i;
+            const bool up = (e & size) == 0;
+            const T a = v[i], b = v[i + j];
+            const bool sw = up ? (b < a) : (a < b);
+            v[i] = sw ? b : a;
+            v[i + j] = sw ? a : b;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Sort the first n (<= 256) keys of buf in place (the rest of the 256 slots
+// become the largest key). Whole warp.
+template <class T>
+__device__ __forceinline__ void warp_sort_buf(T* buf, int n, T pad) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  T v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int e = 8 * lane + i;
+    v[i] = e < n ? buf[e] : pad;
+  }
+  warp_sort256(v);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) buf[8 * lane + i] = v[i];
+  __syncwarp();
+}
+
+// The want-th smallest (1-based, want <= n) of n 32-bit keys keyf(i), by an
+// MSD radix select over the bits below the keys' common prefix (hist: 256
+// ints of per-warp shared memory). ties: how many keys equal to the result
+// are among the want smallest; eqn: how many keys equal it. Whole warp.
+template <class F>
+__device__ uint32_t warp_select_u32(int* hist, int n, int want, int& ties, int& eqn, F keyf) {
+  const int lane = threadIdx.x & 31;
+  uint32_t mn = 0xffffffffu, mx = 0u;
+  for (int i = lane; i < n; i += 32) {
+    const uint32_t k = keyf(i);
+    mn = min(mn, k);
+    mx = max(mx, k);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+    mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+  }
+  if (mn == mx) {
+    ties = want;
+    eqn = n;
+    return mn;
+  }
+  const int hb = 31 - __clz(mn ^ mx);  // highest bit where keys differ
+  int shift = hb + 1;
+  uint32_t mask = hb == 31 ? 0u : ~((2u << hb) - 1u);
+  uint32_t prefix = mn & mask;
+  int rem = want, last = 0;
+  while (shift > 0) {
+    const int nb = shift >= 8 ? 8 : shift;
+    shift -= nb;
+    const uint32_t dm = (1u << nb) - 1u;
+    __syncwarp();
+    for (int t = lane; t < 256; t += 32) hist[t] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const uint32_t k = keyf(i);
+      if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & dm], 1);
+    }
+    __syncwarp();
+    int c[8], s = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      c[t] = hist[8 * lane + t];
+      s += c[t];
+    }
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - s;
+    const unsigned bal = __ballot_sync(kFull, excl < rem && rem <= incl);
+    const int src = __ffs(bal) - 1;
+    int digit = 0, nrem = 0, cnt = 0;
+    if (lane == src) {
+      int cum = excl;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (digit == 0 && nrem == 0 && cum + c[t] >= rem) {
+          digit = 8 * lane + t;
+          nrem = rem - cum;
+          cnt = c[t];
+        }
+        cum += c[t];
+      }
+    }
+    digit = __shfl_sync(kFull, digit, src);
+    rem = __shfl_sync(kFull, nrem, src);
+    last = __shfl_sync(kFull, cnt, src);
+    prefix |= (uint32_t)digit << shift;
+    mask |= dm << shift;
+  }
+  ties = rem;
+  eqn = last;
+  return prefix;
+}
+
+// In-place stable compaction of the first n entries of L by keep(e).
+template <class F>
+__device__ __forceinline__ int warp_compact(int4* L, int n, F keep_f) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int out = 0;
+  __syncwarp();  // entries other lanes wrote are visible
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    const int i = b0 + lane;
+    int4 e = make_int4(0, 0, 0, 0);
+    bool keep = false;
+    if (i < n) {
+      e = L[i];
+      keep = keep_f(e);
+    }
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (keep) L[out + __popc(bal & lt)] = e;
+    out += __popc(bal);
+  }
+  __syncwarp();
+  return out;
+}
+
+// Randomized B_q = 4 quantization of the query against cluster c (§3.3.1)
+// with the same arithmetic and random stream as quant_core, lane l owning the
+// dimensions 32 r + l (r < NW): the Philox call of dimensions 4m..4m+3 is
+// computed by lane m % 32 and its words are exchanged by shuffles. Plane b's
+// u32 word r is then one ballot. Returns sum(q_u); writes the planes and the
+// estimator constants (quant_meta).
+template <int NW>
+__device__ __forceinline__ int quant_warp(const FusedParams& P, int64_t q, int c, float nq2,
+                                          float add, uint32_t (&pl)[4][NW], float4* meta) {
+  const int lane = threadIdx.x & 31;
+  constexpr int dpad = 32 * NW;
+  const float* rq = P.rq + q * dpad;
+  const float* pc = P.ptc + (int64_t)c * dpad;
+  float qd[NW];
+  float vl = __int_as_float(0x7f800000), vr = __int_as_float(0xff800000);
+#pragma unroll
+  for (int r = 0; r < NW; ++r) {
+    qd[r] = __fsub_rn(rq[32 * r + lane], pc[32 * r + lane]);
+    vl = fminf(vl, qd[r]);
+    vr = fmaxf(vr, qd[r]);
+  }
+  vl = warp_min_f(vl);
+  vr = warp_max_f(vr);
+  const float delta = __fdiv_rn(__fsub_rn(vr, vl), 15.0f);
+  const uint64_t gq = (uint64_t)(P.q_offset + q);
+  U4 w[NW / 4];
+#pragma unroll
+  for (int cc = 0; cc < NW / 4; ++cc)
+    w[cc] = philox4x32_10(P.seed, (uint32_t)(lane + 32 * cc), (uint32_t)gq, (uint32_t)c, kTagQuant);
+  int sum = 0;
+  int qu[NW];
+#pragma unroll
+  for (int r = 0; r < NW; ++r) {
+    // dimension 32 r + lane: Philox call 8 r + lane / 4 (lane 8 (r % 4) + lane / 4,
+    // call index r / 4), word lane % 4
+    const int src = 8 * (r & 3) + (lane >> 2);
+    const uint32_t a0 = __shfl_sync(kFull, w[r >> 2].x, src);
+    const uint32_t a1 = __shfl_sync(kFull, w[r >> 2].y, src);
+    const uint32_t a2 = __shfl_sync(kFull, w[r >> 2].z, src);
+    const uint32_t a3 = __shfl_sync(kFull, w[r >> 2].w, src);
+    const int s = lane & 3;
+    const uint32_t word = s == 0 ? a0 : (s == 1 ? a1 : (s == 2 ? a2 : a3));
+    int v = 0;
+    if (delta > 0.0f) {
+      const float u = __fmul_rn(__uint2float_rn(word >> 8), 0x1.0p-24f);
+      const float x = __fdiv_rn(__fsub_rn(qd[r], vl), delta);
+      v = __float2int_rd(__fadd_rn(x, u));
+      v = v > 15 ? 15 : v;
+    }
+    qu[r] = v;
+    sum += v;
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int r = 0; r < NW; ++r) pl[b][r] = __ballot_sync(kFull, (qu[r] >> b) & 1);
+  *meta = quant_meta(delta, vl, nq2, add, P.eps0, dpad);
+  return warp_sum_i(sum);
+}
+
+// Exact scores of staged rows: stage[0..n) hold bucket positions (n <= 32),
+// lane l scores row l; keys <= kmax are appended to the top buffer. Returns
+// the new buffer count (whole warp; the buffer keeps room for 32).
+__device__ __forceinline__ int warp_score_rows(const FusedParams& P, WarpSmem& S, const int* stage,
+                                               int n, int tn, unsigned long long kmax) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long key = ~0ull;
+  const bool valid = lane < n;
+  if (valid) {
+    const int pos = stage[lane];
+    const float* x = P.data_b + (int64_t)pos * P.d;
+    const float acc = P.metric ? row_score<true>(x, S.qv, P.d) : row_score<false>(x, S.qv, P.d);
+    const int id = __ldg(P.perm + pos);
+    key = ((unsigned long long)float_key(acc) << 32) | (uint32_t)id;
+  }
+  const bool take = valid && key <= kmax;
+  const unsigned bal = __ballot_sync(kFull, take);
+  if (take) S.top[tn + __popc(bal & lt)] = key;
+  __syncwarp();
+  return tn + __popc(bal);
+}
+
+// Keep the k smallest keys of the top buffer (sorted); returns the k-th
+// smallest (all ones if fewer than k).
+__device__ __forceinline__ unsigned long long warp_top_keep(WarpSmem& S, int& tn, int k) {
+  warp_sort_buf<unsigned long long>(S.top, tn, ~0ull);
+  const unsigned long long T = tn >= k ? S.top[k - 1] : ~0ull;
+  tn = min(tn, k);
+  return T;
+}
+
+// Score the entries of L (n of them) that pass sel(e), 32 rows at a time
+// (staged in hist); keys <= kmax go to the top buffer, which keeps the k
+// smallest whenever it fills. Returns the buffer count.
+template <class F>
+__device__ int warp_rerank(const FusedParams& P, WarpSmem& S, const int4* L, int n, F sel, int tn,
+                           unsigned long long kmax) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int* stage = S.hist;  // 64 slots
+  int staged = 0;
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    const int i = b0 + lane;
+    bool in = false;
+    int pos = 0;
+    if (i < n) {
+      const int4 e = L[i];
+      in = sel(e);
+      pos = e.x & 0x7fffffff;
+    }
+    const unsigned bal = __ballot_sync(kFull, in);
+    if (in) stage[staged + __popc(bal & lt)] = pos;
+    staged += __popc(bal);
+    __syncwarp();
+    if (staged >= 32) {
+      if (tn > kWarpBuf - 32) warp_top_keep(S, tn, P.k);
+      tn = warp_score_rows(P, S, stage, 32, tn, kmax);
+      staged -= 32;
+      int mv = lane < staged ? stage[32 + lane] : 0;
+      __syncwarp();
+      if (lane < staged) stage[lane] = mv;
+      __syncwarp();
+    }
+  }
+  if (staged > 0) {
+    if (tn > kWarpBuf - 32) warp_top_keep(S, tn, P.k);
+    tn = warp_score_rows(P, S, stage, staged, tn, kmax);
+  }
+  return tn;
+}
+
+// The end of one query (the rule of finish_query, for one warp): L holds
+// every code with LB <= tau_ub (n entries {position, LB, estimate, UB}).
+__device__ void warp_finish(const FusedParams& P, WarpSmem& S, int64_t q, int4* L, int n, int ubn) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int k = P.k, m = P.m;
+  float tau_ub = __int_as_float(0x7f800000);
+  if (ubn >= k) {
+    warp_sort_buf<uint32_t>(S.ubk, ubn, 0xffffffffu);
+    tau_ub = key_float(S.ubk[k - 1]);
+  }
+  n = warp_compact(L, n, [tau_ub](const int4& e) { return __int_as_float(e.y) <= tau_ub; });
+  // pilot: the m smallest (estimate, id) of the list
+  uint32_t T_e = 0xffffffffu, T_id = 0xffffffffu;
+  const bool pilot_all = n <= m;
+  if (!pilot_all) {
+    int ties = 0, eqn = 0;
+    T_e = warp_select_u32(S.hist, n, m, ties, eqn,
+                          [L](int i) { return float_key(__int_as_float(L[i].z)); });
+    if (eqn > ties) {
+      int t2 = 0, e2 = 0;
+      T_id = warp_select_u32(S.hist, n, ties, t2, e2, [L, T_e, &P](int i) {
+        const int4 e = L[i];
+        return float_key(__int_as_float(e.z)) == T_e ? (uint32_t)__ldg(P.perm + e.x) : 0xffffffffu;
+      });
+    }
+  }
+  // mark the pilot (bit 31 of the position)
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    const int i = b0 + lane;
+    if (i < n) {
+      const int4 e = L[i];
+      const uint32_t ek = float_key(__int_as_float(e.z));
+      const bool in = pilot_all || ek < T_e || (ek == T_e && (uint32_t)__ldg(P.perm + e.x) <= T_id);
+      if (in) L[i].x = e.x | (int)0x80000000;
+    }
+  }
+  __syncwarp();
+  // exact scores of the pilot; tau1 = the k-th smallest of them
+  int tn = warp_rerank(P, S, L, n, [](const int4& e) { return e.x < 0; }, 0, ~0ull);
+  const unsigned long long T1 = warp_top_keep(S, tn, k);
+  const float tau1 = T1 != ~0ull ? key_float((uint32_t)(T1 >> 32)) : __int_as_float(0x7f800000);
+  const float tau = fminf(tau_ub, tau1);
+  // the rest of the re-rank set (LB <= tau, outside the pilot); keys above
+  // the pilot's k-th cannot enter the result
+  tn = warp_rerank(P, S, L, n, [tau](const int4& e) { return e.x >= 0 && __int_as_float(e.y) <= tau; },
+                   tn, T1);
+  warp_sort_buf<unsigned long long>(S.top, tn, ~0ull);
+  const int got = min(tn, k);
+  for (int j = lane; j < k; j += 32) {
+    const bool ok = j < got;
+    const unsigned long long key = ok ? S.top[j] : 0ull;
+    P.out_ids[q * k + j] = ok ? (int64_t)(key & 0xffffffffu) : -1;
+    const float v = ok ? key_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000);
+    P.out_dist[q * k + j] = P.metric ? -v : v;
+  }
+  __syncwarp();
+  (void)lt;
+}
+
+template <int WT>
+constexpr int warp_min_blocks() {
+  return WT <= 2 ? 8 : 6;
+}
+
+template <int WT>
+__global__ void __launch_bounds__(kWarpThreads, warp_min_blocks<WT>()) fused_warp_kernel(FusedParams P) {
+  constexpr int NW = 2 * WT;                // u32 words per code and per plane
+  constexpr int PPL = WT <= 2 ? 2 : 1;      // codes per lane per step
+  __shared__ WarpSmem sm[kWarpThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpSmem& S = sm[wid];
+  const int64_t gw = (int64_t)blockIdx.x * (kWarpThreads / 32) + wid;
+  int4* L = P.candw + gw * P.capw;
+  const unsigned lt = (1u << lane) - 1u;
+  const int k = P.k;
+  const int room = P.capw - 32 * PPL;
+  for (;;) {
+    int qi = 0;
+    if (lane == 0) qi = atomicAdd(P.next, 1);
+    qi = __shfl_sync(kFull, qi, 0);
+    if (qi >= P.nq) break;
+    const int64_t q = P.order ? (int64_t)P.order[qi] : (int64_t)qi;
+    int np = P.nprobe;
+    if (P.nprobe_q) np = min(max(P.nprobe_q[q], 1), P.nprobe);
+    __syncwarp();
+    for (int i = lane; i < P.d; i += 32) S.qv[i] = P.queries[q * P.d + i];
+    __syncwarp();
+    int ubn = 0, nc = 0;
+    float tau = __int_as_float(0x7f800000);
+    bool ovf = false;
+    for (int j = 0; j < np && !ovf; ++j) {
+      const int64_t pj = q * P.nprobe + j;
+      const int c = P.probe_ids[pj];
+      const float add = P.probe_dist[pj];
+      const float nq2 = P.probe_nq2 ? P.probe_nq2[pj] : add;
+      uint32_t pl[4][NW];
+      float4 mt;
+      const int psum = quant_warp<NW>(P, q, c, nq2, add, pl, &mt);
+      const int beg = P.bucket_off[c], end = P.bucket_off[c + 1];
+      for (int base = beg; base < end; base += 32 * PPL) {
+        int pos[PPL];
+        uint32_t cw[PPL][NW];
+        float4 f[PPL];
+#pragma unroll
+        for (int u = 0; u < PPL; ++u) {
+          pos[u] = base + 32 * u + lane;
+          if (pos[u] < end) {
+            const uint4* cp = reinterpret_cast<const uint4*>(P.codes) + (size_t)pos[u] * (NW / 4);
+#pragma unroll
+            for (int v = 0; v < NW / 4; ++v) {
+              const uint4 x = __ldg(cp + v);
+              cw[u][4 * v] = x.x;
+              cw[u][4 * v + 1] = x.y;
+              cw[u][4 * v + 2] = x.z;
+              cw[u][4 * v + 3] = x.w;
+            }
+            f[u] = __ldg(P.factors + pos[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < PPL; ++u) {
+          const bool valid = pos[u] < end;
+          float est = 0.0f, lb = __int_as_float(0x7f800000), ub = __int_as_float(0x7f800000);
+          if (valid) {
+            int ip = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              int pb = 0;
+#pragma unroll
+              for (int r = 0; r < NW; ++r) pb += __popc(cw[u][r] & pl[b][r]);
+              ip += pb << b;
+            }
+            // estimator (§3.3.2 + Theorem 3.2) and its bound, fixed FP32 order
+            const float t1 = (float)(2 * ip - psum);
+            const float xq = __fadd_rn(__fmul_rn(mt.x, t1), __fmul_rn(mt.y, f[u].w));
+            est = __fsub_rn(__fadd_rn(f[u].x, mt.w), __fmul_rn(f[u].y, xq));
+            const float e = __fmul_rn(f[u].z, mt.z);
+            lb = __fsub_rn(est, e);
+            ub = __fadd_rn(est, e);
+          }
+          const bool wu = valid && ub < tau;
+          const unsigned bu = __ballot_sync(kFull, wu);
+          if (wu) S.ubk[ubn + __popc(bu & lt)] = float_key(ub);
+          ubn += __popc(bu);
+          const bool wc = valid && lb <= tau;
+          const unsigned bc = __ballot_sync(kFull, wc);
+          if (wc) {
+            const int slot = nc + __popc(bc & lt);
+            if (slot < P.capw)
+              L[slot] = make_int4(pos[u], __float_as_int(lb), __float_as_int(est), __float_as_int(ub));
+          }
+          nc += __popc(bc);
+        }
+        // upkeep (warp-uniform): keep the k smallest upper bounds; compact
+        // the candidate list by the current threshold when it fills
+        if (ubn > kWarpBuf - 32 * PPL) {
+          warp_sort_buf<uint32_t>(S.ubk, ubn, 0xffffffffu);
+          tau = key_float(S.ubk[k - 1]);
+          ubn = k;
+        }
+        if (nc > room) {
+          const float t = tau;
+          nc = warp_compact(L, min(nc, P.capw), [t](const int4& e) { return __int_as_float(e.y) <= t; });
+          if (nc > room) {
+            ovf = true;
+            break;
+          }
+        }
+      }
+    }
+    if (ovf) {  // the CTA kernel redoes this query
+      if (lane == 0) P.redo[atomicAdd(P.redo_cnt, 1)] = (int)q;
+      __syncwarp();
+      continue;
+    }
+    warp_finish(P, S, q, L, nc, ubn);
   }
 }
 
@@ -2101,6 +2604,43 @@ FusedFn pick_fused(int W, int bq) {
   return fused_search_kernel<0, 0>;
 }
 
+// The warp-per-query kernel for these parameters (null: the CTA kernel
+// runs). It covers D' = 128 / 256, B_q = 4, k <= 128, d <= 256, unsplit
+// searches without a trace, and batches of at least min_nq queries.
+typedef void (*WarpFn)(FusedParams);
+constexpr int kWarpCap = 8192;  // candidate entries per warp region (at most max_candidates)
+
+WarpFn pick_warp(const SearchArgs& a) {
+  const rabitq_index* X = a.X;
+  const int layout = a.layout == RABITQ_LAYOUT_AUTO ? X->tuned_layout : a.layout;
+  if (layout == RABITQ_LAYOUT_CTA || !a.allow_warp || a.trace || a.bq != 4 || a.k > kWarpMaxK ||
+      X->d > 256)
+    return nullptr;
+  if (X->W == 2) return fused_warp_kernel<2>;
+  if (X->W == 4) return fused_warp_kernel<4>;
+  return nullptr;
+}
+
+int warp_capw(const SearchArgs& a) { return std::min<int>(a.cand_cap, kWarpCap); }
+
+// Resident CTAs of the warp kernel on this device (every SM full).
+int warp_ctas(WarpFn fn, int64_t* ctas) {
+  int dev = 0, sms = 0, per = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
+  RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kWarpThreads, 0));
+  *ctas = (int64_t)sms * std::max(per, 1);
+  return RABITQ_OK;
+}
+
+// The warp layout pays off once the batch gives every SM several queries
+// per scheduler; smaller batches keep eight warps per query (explicit
+// RABITQ_LAYOUT_WARP takes it whatever the batch).
+bool warp_batch_ok(const SearchArgs& a, int64_t nqc, int64_t ctas) {
+  const int layout = a.layout == RABITQ_LAYOUT_AUTO ? a.X->tuned_layout : a.layout;
+  return layout == RABITQ_LAYOUT_WARP || nqc * 4 >= ctas * (kWarpThreads / 32);
+}
+
 // Longest-first order of queries with per-query probe counts: key =
 // nprobe - (clamped count), sorted stably (ties keep ascending query id).
 __global__ void order_key_kernel(const int32_t* __restrict__ npq, int64_t n, int nprobe,
@@ -2385,6 +2925,31 @@ int set_merge_attr() {
 }
 }  // namespace
 
+// One warp-layout launch for the queries of P (P.next zeroed by the
+// caller), then the CTA kernel over the queries it handed back (redo: [0]
+// count, [32] work counter, list from [64]; an empty list ends that launch at
+// once). Allocation- and synchronization-free (graph capturable).
+int launch_warp(WarpFn wfn, int64_t wctas, const FusedParams& P, int4* candw, int capw, int* redo,
+                FusedFn fn, unsigned grid, size_t smem, cudaStream_t s) {
+  RBQ_CUDA(cudaMemsetAsync(redo, 0, sizeof(int) * 64, s));
+  FusedParams W = P;
+  W.candw = candw;
+  W.capw = capw;
+  W.redo = redo + 64;
+  W.redo_cnt = redo;
+  const int64_t need = (P.nq + (kWarpThreads / 32) - 1) / (kWarpThreads / 32);
+  wfn<<<(unsigned)std::min<int64_t>(wctas, need), kWarpThreads, 0, s>>>(W);
+  RBQ_CUDA(cudaGetLastError());
+  FusedParams R = P;
+  R.order = redo + 64;
+  R.nq_dev = redo;
+  R.next = redo + 32;
+  R.split = 1;
+  fn<<<grid, kThreads, smem, s>>>(R);
+  RBQ_CUDA(cudaGetLastError());
+  return RABITQ_OK;
+}
+
 // Scan-path choice: the index's tuned choice for AUTO (set by
 // rabitq_autotune), the popcount path otherwise; a TC search whose candidate
 // lists overflow under AUTO is redone on the popcount path.
@@ -2420,6 +2985,18 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   const int64_t grid = std::min<int64_t>(qchunk, full);
   // a batch too small to fill the GPU splits each query's probes over CTAs
   const int split = split_factor(a, std::min(qchunk, a.nq), full, fs);
+  // the warp-per-query layout, where it applies: per-warp candidate regions
+  // and the redo list ([0] count, [32] the redo launch's work counter, the
+  // list from [64])
+  const WarpFn wfn = split > 1 ? nullptr : pick_warp(a);
+  int64_t wctas = 0;
+  if (wfn) RBQ_CHECK(warp_ctas(wfn, &wctas));
+  const int capw = warp_capw(a);
+  DevBuf candw, redo;
+  if (wfn) {
+    RBQ_CHECK(candw.alloc(sizeof(int4) * wctas * (kWarpThreads / 32) * capw, s));
+    RBQ_CHECK(redo.alloc(sizeof(int32_t) * (qchunk + 64), s));
+  }
   DevBuf cd, rq, pid, pdist, cand, err, ubout, scnt, cand2, qn, pnq2;
   if (metric_cos(X)) RBQ_CHECK(qn.alloc(sizeof(float) * qchunk * d, s));
   if (metric_ip(X)) RBQ_CHECK(pnq2.alloc(sizeof(float) * qchunk * nprobe, s));
@@ -2562,12 +3139,17 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
       P.slice_cnt = scnt.as<int>();
       P.cand2 = cand2.as<int4>();
     }
-    const unsigned g = (unsigned)std::min<int64_t>(nqc * split, split > 1 ? full : grid);
-    fn<<<g, kThreads, smem, s>>>(P);
-    RBQ_CUDA(cudaGetLastError());
-    if (split > 1) {
-      split_merge_kernel<<<(unsigned)std::min<int64_t>(nqc, full), kThreads, smem, s>>>(P);
+    if (wfn && warp_batch_ok(a, nqc, wctas)) {
+      RBQ_CHECK(launch_warp(wfn, wctas, P, candw.as<int4>(), capw, redo.as<int>(), fn,
+                            (unsigned)grid, smem, s));
+    } else {
+      const unsigned g = (unsigned)std::min<int64_t>(nqc * split, split > 1 ? full : grid);
+      fn<<<g, kThreads, smem, s>>>(P);
       RBQ_CUDA(cudaGetLastError());
+      if (split > 1) {
+        split_merge_kernel<<<(unsigned)std::min<int64_t>(nqc, full), kThreads, smem, s>>>(P);
+        RBQ_CUDA(cudaGetLastError());
+      }
     }
     if (timing) {
       RBQ_CUDA(cudaEventRecord(ev[4], s));
@@ -2609,6 +3191,12 @@ struct Carve {
   size_t o_cand = 0, o_cd = 0, o_rq = 0, o_pid = 0, o_pdist = 0, o_pnp = 0, o_fid = 0,
          o_fdist = 0, o_okey = 0, o_order = 0, o_ooff = 0, o_sortws = 0, o_qn = 0, o_pnq2 = 0,
          end = 0;
+  // warp layout: its kernel (null = not used), resident CTAs, per-warp
+  // candidate regions and the redo list
+  WarpFn wfn = nullptr;
+  int64_t wctas = 0;
+  int capw = 0;
+  size_t o_candw = 0, o_redo = 0;
 };
 
 constexpr size_t kCarveAlign = 256;
@@ -2647,6 +3235,13 @@ Carve carve_layout(const SearchArgs& a, int64_t grid, int64_t cap, int64_t qchun
   L.o_ubout = take(a.allow_split ? sizeof(uint32_t) * grid * a.k : 0);
   L.o_scnt = take(a.allow_split ? sizeof(int) * grid * 2 : 0);
   L.o_cand2 = take(a.allow_split ? sizeof(int4) * (grid / 2) * cap : 0);
+  L.wfn = pick_warp(a);
+  if (L.wfn && warp_ctas(L.wfn, &L.wctas) != RABITQ_OK) L.wfn = nullptr;
+  if (L.wfn) {
+    L.capw = warp_capw(a);
+    L.o_candw = take(sizeof(int4) * L.wctas * (kWarpThreads / 32) * L.capw);
+    L.o_redo = take(sizeof(int32_t) * (qchunk + 64));
+  }
   L.end = o;
   return L;
 }
@@ -2797,12 +3392,18 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
       P.slice_cnt = reinterpret_cast<int*>(scratch + L.o_scnt);
       P.cand2 = reinterpret_cast<int4*>(scratch + L.o_cand2);
     }
-    fn<<<(unsigned)std::min<int64_t>(nqc * split, grid), kThreads, smem, s>>>(P);
-    RBQ_CUDA(cudaGetLastError());
-    if (split > 1) {
-      RBQ_CHECK(set_merge_attr());
-      split_merge_kernel<<<(unsigned)std::min<int64_t>(nqc, grid), kThreads, smem, s>>>(P);
+    if (split == 1 && L.wfn && warp_batch_ok(a, nqc, L.wctas)) {
+      RBQ_CHECK(launch_warp(L.wfn, L.wctas, P, reinterpret_cast<int4*>(scratch + L.o_candw),
+                            L.capw, reinterpret_cast<int*>(scratch + L.o_redo), fn, (unsigned)grid,
+                            smem, s));
+    } else {
+      fn<<<(unsigned)std::min<int64_t>(nqc * split, grid), kThreads, smem, s>>>(P);
       RBQ_CUDA(cudaGetLastError());
+      if (split > 1) {
+        RBQ_CHECK(set_merge_attr());
+        split_merge_kernel<<<(unsigned)std::min<int64_t>(nqc, grid), kThreads, smem, s>>>(P);
+        RBQ_CUDA(cudaGetLastError());
+      }
     }
     if (ev) RBQ_CUDA(cudaEventRecordWithFlags(a.stage_ev[4], s, cudaEventRecordExternal));
   }

@@ -112,6 +112,7 @@ extern "C" int rabitq_search_noalloc(const rabitq_index* X, const float* queries
   a.rot_precision = opts.rot_precision;
   a.scan_path = opts.scan_path;
   a.stage_ms = nullptr;
+  a.allow_warp = 0;  // the warp layout's candidate regions do not fit the fixed scratch
   return search_dev_prealloc(a, static_cast<unsigned char*>(scratch), kScratchBytes,
                              static_cast<cudaStream_t>(opts.stream));
 }

@@ -118,6 +118,8 @@ int rabitq_plan_create(const rabitq_index* X, const rabitq_predictor* pr, int64_
   if (opts.per_query_nprobe)
     return fail(RABITQ_EUNSUPPORTED, "rabitq_plan_create: per_query_nprobe is not supported "
                                      "(use a predictor)");
+  if (opts.scan_layout < RABITQ_LAYOUT_AUTO || opts.scan_layout > RABITQ_LAYOUT_WARP)
+    return fail(RABITQ_EINVAL, "rabitq_plan_create: unknown scan_layout");
   auto* P = new rabitq_plan();
   RBQ_CUDA(cudaGetDevice(&P->device));
   SearchArgs& a = P->a;
@@ -133,6 +135,7 @@ int rabitq_plan_create(const rabitq_index* X, const rabitq_predictor* pr, int64_
   a.trace = nullptr;
   a.rot_precision = opts.rot_precision;
   a.scan_path = RABITQ_SCAN_POPC;
+  a.layout = opts.scan_layout;
   a.stage_ms = nullptr;
   a.pred = pr;
   P->nq_max = nq_max;

@@ -19,6 +19,7 @@ _lib = None
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EIO, EUNSUPPORTED, EOVERFLOW = 0, -1, -2, -3, -4, -5, -6, -7
 ROT_FP32, ROT_TF32, ROT_BF16 = 0, 1, 2
 SCAN_AUTO, SCAN_POPC, SCAN_TC = 0, 1, 2
+LAYOUT_AUTO, LAYOUT_CTA, LAYOUT_WARP = 0, 1, 2
 METRIC_L2, METRIC_IP, METRIC_COSINE = 0, 1, 2
 METRICS = {"l2": METRIC_L2, "ip": METRIC_IP, "cosine": METRIC_COSINE}
 
@@ -58,7 +59,8 @@ class SearchOpts(C.Structure):
     _fields_ = [("rot_precision", C.c_int32), ("scan_path", C.c_int32),
                 ("quant_seed", C.c_uint64), ("io_on_device", C.c_int32),
                 ("stream", C.c_void_p), ("per_query_nprobe", C.c_void_p),
-                ("max_candidates", C.c_int32), ("collect_stats", C.c_int32)]
+                ("max_candidates", C.c_int32), ("collect_stats", C.c_int32),
+                ("scan_layout", C.c_int32)]
 
 
 class Trace(C.Structure):
@@ -291,7 +293,7 @@ class Index:
 
     # --------------------------------------------------------------- search
     def _opts(self, quant_seed, per_query_nprobe, max_candidates, stats, stream, on_device,
-              rot_precision=ROT_FP32, scan_path=SCAN_AUTO):
+              rot_precision=ROT_FP32, scan_path=SCAN_AUTO, layout=LAYOUT_AUTO):
         o = SearchOpts()
         lib().rabitq_search_opts_default(C.byref(o))
         o.quant_seed = quant_seed
@@ -301,19 +303,20 @@ class Index:
         o.stream = _stream_handle(stream)
         o.rot_precision = rot_precision
         o.scan_path = scan_path
+        o.scan_layout = layout
         return o
 
     def search(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
                quant_seed: int = 3, per_query_nprobe=None, max_candidates: int = 65536,
                stats: bool = False, stream=None, out=None, rot_precision=ROT_FP32,
-               scan_path=SCAN_AUTO):
+               scan_path=SCAN_AUTO, layout=LAYOUT_AUTO):
         """k-NN search. numpy queries -> numpy (ids int64, dists float32) via
         host buffers; torch CUDA queries -> torch CUDA outputs. Values are
         squared distances (ascending) for l2, inner products / cosines
         (descending) for ip / cosine."""
         dev = _is_torch(queries)
         o = self._opts(quant_seed, per_query_nprobe, max_candidates, stats, stream, dev,
-                       rot_precision, scan_path)
+                       rot_precision, scan_path, layout)
         if dev:
             import torch
             queries = queries.contiguous()
@@ -442,11 +445,11 @@ class Index:
     def search_learned(self, predictor: "Predictor", queries, k: int, bq: int = 4,
                        eps0: float = 1.9, quant_seed: int = 3, max_candidates: int = 65536,
                        stats: bool = False, stream=None, out=None, rot_precision=ROT_FP32,
-                       scan_path=SCAN_AUTO):
+                       scan_path=SCAN_AUTO, layout=LAYOUT_AUTO):
         """Search with each query's probe count from the predictor."""
         dev = _is_torch(queries)
         o = self._opts(quant_seed, None, max_candidates, stats, stream, dev, rot_precision,
-                       scan_path)
+                       scan_path, layout)
         if dev:
             import torch
             queries = queries.contiguous()
@@ -614,10 +617,11 @@ class Plan:
 
     def __init__(self, index: Index, k: int, nprobe: int, nq_max: int, bq: int = 4,
                  eps0: float = 1.9, predictor: "Predictor | None" = None, quant_seed: int = 3,
-                 max_candidates: int = 65536, rot_precision=ROT_FP32, stats: bool = False):
+                 max_candidates: int = 65536, rot_precision=ROT_FP32, stats: bool = False,
+                 layout=LAYOUT_AUTO):
         import torch
         o = index._opts(quant_seed, None, max_candidates, stats, None, True, rot_precision,
-                        SCAN_POPC)
+                        SCAN_POPC, layout)
         h = C.c_void_p()
         _check(lib().rabitq_plan_create(index._h, predictor._h if predictor else None, nq_max, k,
                                         nprobe, bq, eps0, C.byref(o), C.byref(h)))
