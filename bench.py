@@ -220,13 +220,20 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     hbm, src = peaks()
 
+    # tile autotuner (a11) on the calibration queries: the work layout of the
+    # scan for this shape, cached in the index; the plan below takes it
+    t_best, t_all = G.autotune_tiles(cqd, w.k, chosen, bq=w.bq, eps0=w.eps0, reps=2)
+
     # ---- leg 1: fixed nprobe (the paper's method)
     plan = rabitq.Plan(G, w.k, chosen, w.nq, bq=w.bq, eps0=w.eps0, stats=True)
     fixed = time_leg(args, plan, qd, gt, w, flush, stream, dist, clocks_on=True, name="fixed")
     fixed.update({"nprobe": chosen,
                   "calibration_recall_by_nprobe": {str(a): round(b, 4)
                                                    for a, b in sorted(sweep.items())},
-                  "calibrated_on": f"{n_cal} held-out calibration queries (seed 11)"})
+                  "calibrated_on": f"{n_cal} held-out calibration queries (seed 11)",
+                  "tile": plan.tile(),
+                  "autotune": {"chosen": t_best, "candidates": t_all,
+                               "tuned_on": "the calibration queries"}})
     fixed["roofline"] = roofline(G, qd, w, chosen, None, fixed["fused_ms"], hbm, src,
                                  "fixed" + tag)
     fixed["scan_gbs"] = fixed["roofline"].pop("scan_gbs")
@@ -642,6 +649,11 @@ def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, dist, hbm, src,
     info = pr.info()
     mult, cal_rec = calibrate_mult(G, pr, cqd, cgt, w)
     pr.set_mult(mult)
+    # tiles for the learned shape, timed on the calibration queries with the
+    # network's probe counts
+    npq_cal = G.predict_nprobe(pr, cqd)
+    t_best, t_all = G.autotune_tiles(cqd, w.k, args.nprobe_max, bq=w.bq, eps0=w.eps0, reps=2,
+                                     per_query_nprobe=npq_cal)
     npq = G.predict_nprobe(pr, qd)
     plan = rabitq.Plan(G, w.k, 0, w.nq, bq=w.bq, eps0=w.eps0, predictor=pr, stats=True)
     leg = time_leg(args, plan, qd, gt, w, flush, stream, dist, name="learned")
@@ -657,6 +669,9 @@ def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, dist, hbm, src,
         "nprobe_p50_p90_p99": [float(np.percentile(npf, p)) for p in (50, 90, 99)],
         "fixed_nprobe_same_recall": fixed_nprobe, "mult": round(mult, 5),
         "calibration_recall": round(cal_rec, 4),
+        "tile": plan.tile(),
+        "autotune": {"chosen": t_best, "candidates": t_all,
+                     "tuned_on": "the calibration queries with the network's counts"},
         "calibrated_on": f"{cqd.shape[0]} held-out calibration queries (seed 11)",
         "coverage_mult": round(info["mult"], 5), "val_coverage": round(info["val_recall"], 4),
         "val_mean_nprobe": round(info["val_mean_nprobe"], 2),

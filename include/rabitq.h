@@ -91,6 +91,8 @@ typedef struct {
                                survives the error bound, 4096..2^26 (0 = 65536) */
   int32_t collect_stats;    /* record per-stage device times (rabitq_last_stats) */
   int32_t scan_layout;      /* RABITQ_LAYOUT_* of the popcount scan (default AUTO) */
+  int32_t lane_pairs;       /* codes per lane per step in the warp layout: 1 or 2;
+                               0 = the tuned or default value                    */
 } rabitq_search_opts;
 
 /* Fill the option structs with their defaults. */
@@ -380,6 +382,38 @@ int rabitq_autotune(rabitq_index* idx, const float* queries, int64_t nq, int32_t
                     const rabitq_search_opts* opts, int32_t* chosen, float* times_ms);
 
 /*
+ * rabitq_autotune_tiles -- the batched scheduler's tile autotuner: time every
+ * work decomposition of the scan on a sample of queries at the given search
+ * parameters and cache the fastest for this index and shape, where the AUTO
+ * options (scan_path, scan_layout, lane_pairs) of later searches and plans
+ * with a k and nprobe in the same class find it (classes: k <= 16, <= 64,
+ * <= 128, larger; nprobe <= 16, <= 64, <= 256, larger). The candidates:
+ *   {POPC, CTA}              one CTA (8 warps) per query, pairs in rounds of
+ *                            512 with a block-wide running threshold
+ *   {POPC, WARP, 1 or 2}     one warp per query (four queries per CTA), 1 or
+ *                            2 codes per lane per step (where the warp layout
+ *                            applies: D' of 128 or 256, B_q = 4, k <= 128)
+ *   {TC}                     bucket-major tensor-core products (an overflow
+ *                            of its lists rules it out)
+ * Every candidate returns identical results. best receives the chosen tile
+ * (time_ms its best time); all (may be NULL) receives up to cap candidates,
+ * *n_all their count (time_ms -1 for one that could not run). reps >= 1
+ * timed runs each after a warm-up run. Not thread-safe against searches on
+ * the same index. Errors: those of rabitq_search.
+ */
+typedef struct {
+  int32_t scan_path;   /* RABITQ_SCAN_POPC or RABITQ_SCAN_TC             */
+  int32_t scan_layout; /* RABITQ_LAYOUT_CTA or _WARP (popcount path)      */
+  int32_t lane_pairs;  /* codes per lane per step (warp layout), else 0   */
+  float time_ms;       /* best measured time of one search of the sample  */
+} rabitq_tile;
+
+int rabitq_autotune_tiles(rabitq_index* idx, const float* queries, int64_t nq, int32_t k,
+                          int32_t nprobe, int32_t bq, float eps0, int32_t reps,
+                          const rabitq_search_opts* opts, rabitq_tile* best, rabitq_tile* all,
+                          int32_t cap, int32_t* n_all);
+
+/*
  * ---- Search plans (CUDA-graph replay of a whole search) -------------------
  *
  * rabitq_plan_create -- a search of up to nq_max queries at fixed k, nprobe,
@@ -427,6 +461,10 @@ int rabitq_plan_search(rabitq_plan* plan, const float* queries, int64_t nq, int6
  * recorded by event nodes inside the graph. Waits for the last run. Returns
  * the number of entries written (0 without collect_stats). */
 int rabitq_plan_stats(rabitq_plan* plan, float* ms, int32_t cap);
+
+/* The tile a plan runs (its AUTO options resolved when the plan was made:
+ * the index's tuned tile for its shape, else the defaults); time_ms is 0. */
+int rabitq_plan_tile(const rabitq_plan* plan, rabitq_tile* out);
 
 /* Release a plan (NULL is a no-op). */
 void rabitq_plan_free(rabitq_plan* plan);

@@ -295,6 +295,8 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
     return fail(RABITQ_EINVAL, "rabitq_search: unknown scan_path");
   if (opts.scan_layout < RABITQ_LAYOUT_AUTO || opts.scan_layout > RABITQ_LAYOUT_WARP)
     return fail(RABITQ_EINVAL, "rabitq_search: unknown scan_layout");
+  if (opts.lane_pairs < 0 || opts.lane_pairs > 2)
+    return fail(RABITQ_EINVAL, "rabitq_search: lane_pairs must be 0, 1 or 2");
   if (trace && opts.scan_path != RABITQ_SCAN_POPC &&
       (trace->planes || trace->sum_qu || trace->meta || trace->pair_id))
     opts.scan_path = RABITQ_SCAN_POPC;  // bit-planes and per-pair values come from that path
@@ -356,6 +358,7 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   a.rot_precision = opts.rot_precision;
   a.scan_path = opts.scan_path;
   a.layout = opts.scan_layout;
+  a.ppl = opts.lane_pairs;
   if (pr) {
     RBQ_CHECK(pb.alloc(sizeof(int32_t) * nq, s));
     a.pred = pr;
@@ -487,6 +490,99 @@ int rabitq_autotune(rabitq_index* X, const float* queries, int64_t nq, int32_t k
     times_ms[0] = best[0];
     times_ms[1] = best[1];
   }
+  g_err.clear();
+  return RABITQ_OK;
+}
+
+int rabitq_autotune_tiles(rabitq_index* X, const float* queries, int64_t nq, int32_t k,
+                          int32_t nprobe, int32_t bq, float eps0, int32_t reps,
+                          const rabitq_search_opts* opts_in, rabitq_tile* best, rabitq_tile* all,
+                          int32_t cap, int32_t* n_all) {
+  g_err.clear();
+  if (!X) return fail(RABITQ_EINVAL, "rabitq_autotune_tiles: index is null");
+  RBQ_CHECK(check_device(X->device, "rabitq_autotune_tiles"));
+  if (nq < 1 || !queries) return fail(RABITQ_EINVAL, "rabitq_autotune_tiles: need queries (nq >= 1)");
+  if (reps < 1 || reps > 1000)
+    return fail(RABITQ_EINVAL, "rabitq_autotune_tiles: need 1 <= reps <= 1000");
+  if (!best || cap < 0 || (cap > 0 && !all))
+    return fail(RABITQ_EINVAL, "rabitq_autotune_tiles: null output");
+  rabitq_search_opts opts;
+  rabitq_search_opts_default(&opts);
+  if (opts_in) opts = *opts_in;
+  opts.collect_stats = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(opts.stream);
+  DevBuf qb, ib, db, nb;
+  const float* dq = queries;
+  const int32_t* dnp = opts.per_query_nprobe;
+  if (!opts.io_on_device) {
+    RBQ_CHECK(qb.alloc(sizeof(float) * nq * X->d, s));
+    RBQ_CUDA(cudaMemcpyAsync(qb.p, queries, sizeof(float) * nq * X->d, cudaMemcpyHostToDevice, s));
+    dq = qb.as<float>();
+    if (dnp) {
+      RBQ_CHECK(nb.alloc(sizeof(int32_t) * nq, s));
+      RBQ_CUDA(cudaMemcpyAsync(nb.p, dnp, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, s));
+      dnp = nb.as<int32_t>();
+    }
+  }
+  RBQ_CHECK(ib.alloc(sizeof(int64_t) * nq * k, s));
+  RBQ_CHECK(db.alloc(sizeof(float) * nq * k, s));
+  opts.io_on_device = 1;
+  opts.per_query_nprobe = dnp;
+  // the candidates: the warp layout only where it applies
+  const bool warp_ok = bq == 4 && k <= 128 && X->d <= 256 && (X->W == 2 || X->W == 4);
+  rabitq_tile cand[4];
+  int nc = 0;
+  cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_CTA, 0, -1.0f};
+  if (warp_ok) {
+    cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_WARP, 1, -1.0f};
+    cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_WARP, 2, -1.0f};
+  }
+  cand[nc++] = rabitq_tile{RABITQ_SCAN_TC, 0, 0, -1.0f};
+  struct Ev {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Ev() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    }
+  } ev;
+  RBQ_CUDA(cudaEventCreate(&ev.e0));
+  RBQ_CUDA(cudaEventCreate(&ev.e1));
+  // time with the warp-layout batch rule waived (the tuned tile is then
+  // taken for every batch of the class)
+  for (int c = 0; c < nc; ++c) {
+    opts.scan_path = cand[c].scan_path;
+    opts.scan_layout = cand[c].scan_layout;
+    opts.lane_pairs = cand[c].lane_pairs;
+    for (int r = 0; r <= reps; ++r) {  // run 0 warms up
+      RBQ_CUDA(cudaEventRecord(ev.e0, s));
+      const int st = search_common(X, dq, nq, k, nprobe, bq, eps0, ib.as<int64_t>(),
+                                   db.as<float>(), &opts, nullptr);
+      // the tensor-core path is ruled out by an overflow of its lists or a
+      // shape it does not take
+      if ((st == RABITQ_EOVERFLOW || st == RABITQ_EUNSUPPORTED) &&
+          cand[c].scan_path == RABITQ_SCAN_TC) {
+        cand[c].time_ms = -1.0f;
+        break;
+      }
+      if (st != RABITQ_OK) return st;
+      RBQ_CUDA(cudaEventRecord(ev.e1, s));
+      RBQ_CUDA(cudaEventSynchronize(ev.e1));
+      float ms = 0.0f;
+      RBQ_CUDA(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
+      if (r > 0 && (cand[c].time_ms < 0.0f || ms < cand[c].time_ms)) cand[c].time_ms = ms;
+    }
+  }
+  int pick = 0;
+  for (int c = 1; c < nc; ++c)
+    if (cand[c].time_ms >= 0.0f && cand[c].time_ms < cand[pick].time_ms) pick = c;
+  rabitq_index::Tile& t = X->tune[tile_class_k(k)][tile_class_np(std::min(nprobe, X->K))];
+  t.valid = 1;
+  t.path = cand[pick].scan_path;
+  t.layout = cand[pick].scan_path == RABITQ_SCAN_POPC ? cand[pick].scan_layout : RABITQ_LAYOUT_CTA;
+  t.ppl = cand[pick].lane_pairs;
+  *best = cand[pick];
+  for (int c = 0; c < nc && c < cap; ++c) all[c] = cand[c];
+  if (n_all) *n_all = nc;
   g_err.clear();
   return RABITQ_OK;
 }

@@ -33,6 +33,10 @@ struct rabitq_index {
   int32_t kp = 0;
   int32_t tuned_path = 0;         // scan path AUTO uses (rabitq_autotune)
   int32_t tuned_layout = 0;       // scan layout AUTO uses (rabitq_autotune), 0 = default
+  // tiles chosen by rabitq_autotune_tiles per (k class, nprobe class)
+  struct Tile {
+    int32_t valid, path, layout, ppl;
+  } tune[4][4] = {};
   void* ptb = nullptr;            // dpad x kp BF16
   float* ptf = nullptr;           // dpad x kp TF32-rounded FP32
   // centroids for the tensor-core probe scores: K x kp TF32-rounded rows,
@@ -178,7 +182,18 @@ struct SearchArgs {
   // kernel also needs allow_warp (off where the scratch is fixed)
   int32_t layout = 0;
   int allow_warp = 1;
+  int32_t ppl = 0;  // codes per lane per step in the warp layout (0 = default)
+  // the layout AUTO resolves to (resolve_tile; set by search_dev and plans):
+  // taken for batches that fill the GPU, while an explicit RABITQ_LAYOUT_WARP
+  // request is taken for every batch
+  int32_t tile_layout = 0;
 };
+// Resolve the AUTO choices of a search (scan path, layout, codes per lane)
+// from the index's tuned tiles for the shape's class, else the defaults.
+void resolve_tile(const rabitq_index* X, int k, int nprobe, int32_t* path, int32_t* layout,
+                  int32_t* ppl);
+int tile_class_k(int k);
+int tile_class_np(int nprobe);
 int search_dev(const SearchArgs& a, cudaStream_t s);
 // Probe counts of nq queries from a predictor: query-centroid distances, the
 // 64 smallest, features, MLP, multiplier. feat (nq x 64) and y (nq) optional.

@@ -1764,60 +1764,35 @@ struct __align__(16) WarpSmem {
   float qv[256];                        // the query (d <= 256)
 };
 
+// Ascending bitonic sort of the first n (<= 256) keys of buf in place (the
+// other slots of the 256 become `pad`, the largest key): 36 compare-exchange
+// steps over shared memory, four pairs per lane per step. One out-of-line
+// copy per key type keeps the kernel's code small. Whole warp.
 template <class T>
-__device__ __forceinline__ T shfl_xor_t(T v, int m) {
-  return __shfl_xor_sync(kFull, v, m);
-}
-
-// Ascending bitonic sort of 256 keys held eight per lane (element 8 lane + i).
-template <class T>
-__device__ __forceinline__ void warp_sort256(T (&v)[8]) {
+__device__ __noinline__ void warp_sort_buf(T* buf, int n, T pad) {
   const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int size = 2; size <= 256; size <<= 1) {
-#pragma unroll
+  __syncwarp();
+  for (int e = n + lane; e < kWarpBuf; e += 32) buf[e] = pad;
+  __syncwarp();
+#pragma unroll 1
+  for (int size = 2; size <= kWarpBuf; size <<= 1) {
+#pragma unroll 1
     for (int j = size >> 1; j > 0; j >>= 1) {
-      if (j >= 8) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int e = 8 * lane + i;
-          const T o = shfl_xor_t(v[i], j >> 3);
-          const bool up = (e & size) == 0, lower = (e & j) == 0;
-          v[i] = (lower == up) ? (o < v[i] ? o : v[i]) : (o > v[i] ? o : v[i]);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          if ((i & j) == 0) {
-            const int e = 8 * lane + i;
-            const bool up = (e & size) == 0;
-            const T a = v[i], b = v[i + j];
-            const bool sw = up ? (b < a) : (a < b);
-            v[i] = sw ? b : a;
-            v[i + j] = sw ? a : b;
-          }
+      for (int u = 0; u < 4; ++u) {
+        const int t = lane + 32 * u;            // pair index, 0..127
+        const int lo = 2 * t - (t & (j - 1));
+        const int hi = lo + j;
+        const bool up = (lo & size) == 0;
+        const T a = buf[lo], b = buf[hi];
+        if (up ? (b < a) : (a < b)) {
+          buf[lo] = b;
+          buf[hi] = a;
         }
       }
+      __syncwarp();
     }
   }
-}
-
-// Sort the first n (<= 256) keys of buf in place (the rest of the 256 slots
-// become the largest key). Whole warp.
-template <class T>
-__device__ __forceinline__ void warp_sort_buf(T* buf, int n, T pad) {
-  const int lane = threadIdx.x & 31;
-  __syncwarp();
-  T v[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int e = 8 * lane + i;
-    v[i] = e < n ? buf[e] : pad;
-  }
-  warp_sort256(v);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) buf[8 * lane + i] = v[i];
-  __syncwarp();
 }
 
 // The want-th smallest (1-based, want <= n) of n 32-bit keys keyf(i), by an
@@ -1985,7 +1960,7 @@ __device__ __forceinline__ int quant_warp(const FusedParams& P, int64_t q, int c
 // Exact scores of staged rows: stage[0..n) hold bucket positions (n <= 32),
 // lane l scores row l; keys <= kmax are appended to the top buffer. Returns
 // the new buffer count (whole warp; the buffer keeps room for 32).
-__device__ __forceinline__ int warp_score_rows(const FusedParams& P, WarpSmem& S, const int* stage,
+__device__ __noinline__ int warp_score_rows(const FusedParams& P, WarpSmem& S, const int* stage,
                                                int n, int tn, unsigned long long kmax) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -2007,56 +1982,60 @@ __device__ __forceinline__ int warp_score_rows(const FusedParams& P, WarpSmem& S
 
 // Keep the k smallest keys of the top buffer (sorted); returns the k-th
 // smallest (all ones if fewer than k).
-__device__ __forceinline__ unsigned long long warp_top_keep(WarpSmem& S, int& tn, int k) {
+__device__ __noinline__ unsigned long long warp_top_keep(WarpSmem& S, int& tn, int k) {
   warp_sort_buf<unsigned long long>(S.top, tn, ~0ull);
   const unsigned long long T = tn >= k ? S.top[k - 1] : ~0ull;
   tn = min(tn, k);
   return T;
 }
 
-// Score the entries of L (n of them) that pass sel(e), 32 rows at a time
-// (staged in hist); keys <= kmax go to the top buffer, which keeps the k
-// smallest whenever it fills. Returns the buffer count.
-template <class F>
-__device__ int warp_rerank(const FusedParams& P, WarpSmem& S, const int4* L, int n, F sel, int tn,
-                           unsigned long long kmax) {
+// List entries per lane per step in the passes of the warp's query end (so
+// that a pass over a few thousand entries is a few dependent steps, not one
+// per 32 entries).
+constexpr int kTU = 4;
+
+// Stage the rows of the entries with in[u] for exact scoring (32 at a time;
+// stage: 64 ints); each staged row is requested from L2 at once.
+template <int U>
+__device__ __forceinline__ int warp_stage_rows(const FusedParams& P, WarpSmem& S, const int (&pos)[U],
+                                               const bool (&in)[U], int& staged, int tn,
+                                               unsigned long long kmax) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  int* stage = S.hist;  // 64 slots
-  int staged = 0;
-  for (int b0 = 0; b0 < n; b0 += 32) {
-    const int i = b0 + lane;
-    bool in = false;
-    int pos = 0;
-    if (i < n) {
-      const int4 e = L[i];
-      in = sel(e);
-      pos = e.x & 0x7fffffff;
+  int* stage = S.hist;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const unsigned bal = __ballot_sync(kFull, in[u]);
+    if (in[u]) {
+      stage[staged + __popc(bal & lt)] = pos[u];
+      const char* x = reinterpret_cast<const char*>(P.data_b + (int64_t)pos[u] * P.d);
+      for (int o = 0; o < P.d * (int)sizeof(float); o += 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(x + o));
     }
-    const unsigned bal = __ballot_sync(kFull, in);
-    if (in) stage[staged + __popc(bal & lt)] = pos;
     staged += __popc(bal);
     __syncwarp();
     if (staged >= 32) {
       if (tn > kWarpBuf - 32) warp_top_keep(S, tn, P.k);
       tn = warp_score_rows(P, S, stage, 32, tn, kmax);
       staged -= 32;
-      int mv = lane < staged ? stage[32 + lane] : 0;
+      const int mv = lane < staged ? stage[32 + lane] : 0;
       __syncwarp();
       if (lane < staged) stage[lane] = mv;
       __syncwarp();
     }
-  }
-  if (staged > 0) {
-    if (tn > kWarpBuf - 32) warp_top_keep(S, tn, P.k);
-    tn = warp_score_rows(P, S, stage, staged, tn, kmax);
   }
   return tn;
 }
 
 // The end of one query (the rule of finish_query, for one warp): L holds
 // every code with LB <= tau_ub (n entries {position, LB, estimate, UB}).
-__device__ void warp_finish(const FusedParams& P, WarpSmem& S, int64_t q, int4* L, int n, int ubn) {
+// Passes over the list, kTU entries per lane per step: keep LB <= tau_ub
+// (with the range of the kept estimates); a 256-bin histogram of their
+// estimate keys finds the bin of the m-th smallest; that bin's entries are
+// ranked exactly by (estimate, id) (a radix select if more than 256 share
+// it); the pilot's rows are scored as they are found; then the rest.
+__device__ __noinline__ void warp_finish(const FusedParams& P, WarpSmem& S, int64_t q, int4* L,
+                                        int n, int ubn) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int k = P.k, m = P.m;
@@ -2065,42 +2044,190 @@ __device__ void warp_finish(const FusedParams& P, WarpSmem& S, int64_t q, int4* 
     warp_sort_buf<uint32_t>(S.ubk, ubn, 0xffffffffu);
     tau_ub = key_float(S.ubk[k - 1]);
   }
-  n = warp_compact(L, n, [tau_ub](const int4& e) { return __int_as_float(e.y) <= tau_ub; });
-  // pilot: the m smallest (estimate, id) of the list
+  // keep LB <= tau_ub, with the smallest and largest estimate key kept
+  uint32_t kmin = 0xffffffffu, kmax = 0u;
+  {
+    int out = 0;
+    __syncwarp();
+    for (int b0 = 0; b0 < n; b0 += 32 * kTU) {
+      int4 e[kTU];
+      bool keep[kTU];
+#pragma unroll
+      for (int u = 0; u < kTU; ++u) {
+        const int i = b0 + 32 * u + lane;
+        keep[u] = false;
+        if (i < n) {
+          e[u] = L[i];
+          keep[u] = __int_as_float(e[u].y) <= tau_ub;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kTU; ++u) {
+        const unsigned bal = __ballot_sync(kFull, keep[u]);
+        if (keep[u]) {
+          L[out + __popc(bal & lt)] = e[u];
+          const uint32_t ek = float_key(__int_as_float(e[u].z));
+          kmin = min(kmin, ek);
+          kmax = max(kmax, ek);
+        }
+        out += __popc(bal);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kmin = min(kmin, __shfl_xor_sync(kFull, kmin, o));
+      kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
+    }
+    n = out;
+    __syncwarp();
+  }
+  // pilot threshold: the m-th smallest (estimate key, id) of the list
   uint32_t T_e = 0xffffffffu, T_id = 0xffffffffu;
   const bool pilot_all = n <= m;
   if (!pilot_all) {
-    int ties = 0, eqn = 0;
-    T_e = warp_select_u32(S.hist, n, m, ties, eqn,
-                          [L](int i) { return float_key(__int_as_float(L[i].z)); });
-    if (eqn > ties) {
-      int t2 = 0, e2 = 0;
-      T_id = warp_select_u32(S.hist, n, ties, t2, e2, [L, T_e, &P](int i) {
+    const uint64_t range = (uint64_t)(kmax - kmin) + 1u;
+    auto bin_of = [kmin, range](uint32_t ek) { return (int)(((uint64_t)(ek - kmin) << 8) / range); };
+    int* hist = S.hist;
+    for (int t = lane; t < 256; t += 32) hist[t] = 0;
+    __syncwarp();
+    for (int b0 = 0; b0 < n; b0 += 32 * kTU) {
+      uint32_t ek[kTU];
+#pragma unroll
+      for (int u = 0; u < kTU; ++u) {
+        const int i = b0 + 32 * u + lane;
+        ek[u] = i < n ? float_key(__int_as_float(L[i].z)) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kTU; ++u)
+        if (b0 + 32 * u + lane < n) atomicAdd(&hist[bin_of(ek[u])], 1);
+    }
+    __syncwarp();
+    int c[8], sum = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      c[t] = hist[8 * lane + t];
+      sum += c[t];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - sum;
+    const int src = __ffs(__ballot_sync(kFull, excl < m && m <= incl)) - 1;
+    int bstar = 0, need = 0, cnt = 0;
+    if (lane == src) {
+      int cum = excl;
+      bool found = false;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (!found && cum + c[t] >= m) {
+          found = true;
+          bstar = 8 * lane + t;
+          need = m - cum;
+          cnt = c[t];
+        }
+        cum += c[t];
+      }
+    }
+    bstar = __shfl_sync(kFull, bstar, src);
+    need = __shfl_sync(kFull, need, src);
+    cnt = __shfl_sync(kFull, cnt, src);
+    if (cnt <= kWarpBuf) {
+      // the boundary bin's entries, ranked by (estimate key, id)
+      int got = 0;
+      for (int b0 = 0; b0 < n; b0 += 32 * kTU) {
+        int4 e[kTU];
+        bool in[kTU];
+#pragma unroll
+        for (int u = 0; u < kTU; ++u) {
+          const int i = b0 + 32 * u + lane;
+          in[u] = false;
+          if (i < n) {
+            e[u] = L[i];
+            in[u] = bin_of(float_key(__int_as_float(e[u].z))) == bstar;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kTU; ++u) {
+          const unsigned bal = __ballot_sync(kFull, in[u]);
+          if (in[u])
+            S.top[got + __popc(bal & lt)] =
+                ((unsigned long long)float_key(__int_as_float(e[u].z)) << 32) |
+                (uint32_t)__ldg(P.perm + e[u].x);
+          got += __popc(bal);
+        }
+      }
+      warp_sort_buf<unsigned long long>(S.top, got, ~0ull);
+      const unsigned long long T = S.top[need - 1];
+      T_e = (uint32_t)(T >> 32);
+      T_id = (uint32_t)T;
+    } else {  // many equal estimates: radix selects by key, then by id
+      int ties = 0, eqn = 0;
+      T_e = warp_select_u32(S.hist, n, m, ties, eqn,
+                            [L](int i) { return float_key(__int_as_float(L[i].z)); });
+      if (eqn > ties) {
+        int t2 = 0, e2 = 0;
+        T_id = warp_select_u32(S.hist, n, ties, t2, e2, [L, T_e, &P](int i) {
+          const int4 e = L[i];
+          return float_key(__int_as_float(e.z)) == T_e ? (uint32_t)__ldg(P.perm + e.x) : 0xffffffffu;
+        });
+      }
+    }
+  }
+  // the pilot: marked (bit 31 of the position) and scored as found;
+  // tau1 = the k-th smallest of its exact scores
+  int tn = 0, staged = 0;
+  for (int b0 = 0; b0 < n; b0 += 32 * kTU) {
+    int pos[kTU];
+    bool in[kTU];
+#pragma unroll
+    for (int u = 0; u < kTU; ++u) {
+      const int i = b0 + 32 * u + lane;
+      in[u] = false;
+      pos[u] = 0;
+      if (i < n) {
         const int4 e = L[i];
-        return float_key(__int_as_float(e.z)) == T_e ? (uint32_t)__ldg(P.perm + e.x) : 0xffffffffu;
-      });
+        pos[u] = e.x;
+        const uint32_t ek = float_key(__int_as_float(e.z));
+        in[u] = pilot_all || ek < T_e || (ek == T_e && (uint32_t)__ldg(P.perm + e.x) <= T_id);
+        if (in[u]) L[i].x = e.x | (int)0x80000000;
+      }
     }
+    tn = warp_stage_rows<kTU>(P, S, pos, in, staged, tn, ~0ull);
   }
-  // mark the pilot (bit 31 of the position)
-  for (int b0 = 0; b0 < n; b0 += 32) {
-    const int i = b0 + lane;
-    if (i < n) {
-      const int4 e = L[i];
-      const uint32_t ek = float_key(__int_as_float(e.z));
-      const bool in = pilot_all || ek < T_e || (ek == T_e && (uint32_t)__ldg(P.perm + e.x) <= T_id);
-      if (in) L[i].x = e.x | (int)0x80000000;
-    }
+  if (staged > 0) {
+    if (tn > kWarpBuf - 32) warp_top_keep(S, tn, k);
+    tn = warp_score_rows(P, S, S.hist, staged, tn, ~0ull);
+    staged = 0;
   }
-  __syncwarp();
-  // exact scores of the pilot; tau1 = the k-th smallest of them
-  int tn = warp_rerank(P, S, L, n, [](const int4& e) { return e.x < 0; }, 0, ~0ull);
   const unsigned long long T1 = warp_top_keep(S, tn, k);
   const float tau1 = T1 != ~0ull ? key_float((uint32_t)(T1 >> 32)) : __int_as_float(0x7f800000);
   const float tau = fminf(tau_ub, tau1);
   // the rest of the re-rank set (LB <= tau, outside the pilot); keys above
   // the pilot's k-th cannot enter the result
-  tn = warp_rerank(P, S, L, n, [tau](const int4& e) { return e.x >= 0 && __int_as_float(e.y) <= tau; },
-                   tn, T1);
+  __syncwarp();
+  for (int b0 = 0; b0 < n; b0 += 32 * kTU) {
+    int pos[kTU];
+    bool in[kTU];
+#pragma unroll
+    for (int u = 0; u < kTU; ++u) {
+      const int i = b0 + 32 * u + lane;
+      in[u] = false;
+      pos[u] = 0;
+      if (i < n) {
+        const int4 e = L[i];
+        pos[u] = e.x & 0x7fffffff;
+        in[u] = e.x >= 0 && __int_as_float(e.y) <= tau;
+      }
+    }
+    tn = warp_stage_rows<kTU>(P, S, pos, in, staged, tn, T1);
+  }
+  if (staged > 0) {
+    if (tn > kWarpBuf - 32) warp_top_keep(S, tn, k);
+    tn = warp_score_rows(P, S, S.hist, staged, tn, T1);
+  }
   warp_sort_buf<unsigned long long>(S.top, tn, ~0ull);
   const int got = min(tn, k);
   for (int j = lane; j < k; j += 32) {
@@ -2111,7 +2238,6 @@ __device__ void warp_finish(const FusedParams& P, WarpSmem& S, int64_t q, int4* 
     P.out_dist[q * k + j] = P.metric ? -v : v;
   }
   __syncwarp();
-  (void)lt;
 }
 
 template <int WT>
@@ -2119,10 +2245,10 @@ constexpr int warp_min_blocks() {
   return WT <= 2 ? 8 : 6;
 }
 
-template <int WT>
+// PPL: codes per lane per step (their loads are in flight together).
+template <int WT, int PPL>
 __global__ void __launch_bounds__(kWarpThreads, warp_min_blocks<WT>()) fused_warp_kernel(FusedParams P) {
   constexpr int NW = 2 * WT;                // u32 words per code and per plane
-  constexpr int PPL = WT <= 2 ? 2 : 1;      // codes per lane per step
   __shared__ WarpSmem sm[kWarpThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpSmem& S = sm[wid];
@@ -2612,12 +2738,15 @@ constexpr int kWarpCap = 8192;  // candidate entries per warp region (at most ma
 
 WarpFn pick_warp(const SearchArgs& a) {
   const rabitq_index* X = a.X;
-  const int layout = a.layout == RABITQ_LAYOUT_AUTO ? X->tuned_layout : a.layout;
-  if (layout == RABITQ_LAYOUT_CTA || !a.allow_warp || a.trace || a.bq != 4 || a.k > kWarpMaxK ||
-      X->d > 256)
+  int32_t path = a.scan_path, layout = a.layout == RABITQ_LAYOUT_AUTO ? a.tile_layout : a.layout,
+          ppl = a.ppl;
+  resolve_tile(X, a.k, a.nprobe, &path, &layout, &ppl);
+  if (layout != RABITQ_LAYOUT_WARP || !a.allow_warp || a.trace || a.bq != 4 ||
+      a.k > kWarpMaxK || X->d > 256)
     return nullptr;
-  if (X->W == 2) return fused_warp_kernel<2>;
-  if (X->W == 4) return fused_warp_kernel<4>;
+  const int lp = ppl ? ppl : (X->W == 2 ? 2 : 1);
+  if (X->W == 2) return lp == 1 ? fused_warp_kernel<2, 1> : fused_warp_kernel<2, 2>;
+  if (X->W == 4) return lp == 1 ? fused_warp_kernel<4, 1> : fused_warp_kernel<4, 2>;
   return nullptr;
 }
 
@@ -2637,8 +2766,27 @@ int warp_ctas(WarpFn fn, int64_t* ctas) {
 // per scheduler; smaller batches keep eight warps per query (explicit
 // RABITQ_LAYOUT_WARP takes it whatever the batch).
 bool warp_batch_ok(const SearchArgs& a, int64_t nqc, int64_t ctas) {
-  const int layout = a.layout == RABITQ_LAYOUT_AUTO ? a.X->tuned_layout : a.layout;
-  return layout == RABITQ_LAYOUT_WARP || nqc * 4 >= ctas * (kWarpThreads / 32);
+  return a.layout == RABITQ_LAYOUT_WARP || nqc * 4 >= ctas * (kWarpThreads / 32);
+}
+
+// Work order of the warp layout: each query is one warp's serial work, so
+// the batch ends when its longest query does; queries are taken in
+// descending order of estimated codes (sum of the probed buckets' sizes, in
+// steps of 128; key = kWorkKeys - 1 - steps, sorted stably).
+constexpr int kWorkKeys = 1024, kWorkShift = 7;
+__global__ void work_key_kernel(const int32_t* __restrict__ probe_ids,
+                                const int32_t* __restrict__ npq, int64_t nq, int nprobe,
+                                const int32_t* __restrict__ bucket_off, int32_t* __restrict__ key) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int np = npq ? min(max(npq[q], 1), nprobe) : nprobe;
+  int64_t w = 0;
+  for (int j = 0; j < np; ++j) {
+    const int c = probe_ids[q * nprobe + j];
+    if (c >= 0) w += bucket_off[c + 1] - bucket_off[c];
+  }
+  const int64_t steps = w >> kWorkShift;
+  key[q] = kWorkKeys - 1 - (int)(steps < kWorkKeys - 1 ? steps : kWorkKeys - 1);
 }
 
 // Longest-first order of queries with per-query probe counts: key =
@@ -2929,12 +3077,28 @@ int set_merge_attr() {
 // caller), then the CTA kernel over the queries it handed back (redo: [0]
 // count, [32] work counter, list from [64]; an empty list ends that launch at
 // once). Allocation- and synchronization-free (graph capturable).
-int launch_warp(WarpFn wfn, int64_t wctas, const FusedParams& P, int4* candw, int capw, int* redo,
-                FusedFn fn, unsigned grid, size_t smem, cudaStream_t s) {
-  RBQ_CUDA(cudaMemsetAsync(redo, 0, sizeof(int) * 64, s));
+struct WarpScratch {
+  int4* candw;       // per-warp candidate regions
+  int capw;
+  int* redo;         // [0] count, [32] redo work counter, list from [64]
+  int32_t* wkey;     // nq work keys
+  int32_t* worder;   // nq: the work order
+  int32_t* wooff;    // kWorkKeys + 1
+  int32_t* wsortws;  // counting_sort_ws_ints(nq, kWorkKeys)
+};
+
+int launch_warp(WarpFn wfn, int64_t wctas, const FusedParams& P, const WarpScratch& ws, FusedFn fn,
+                unsigned grid, size_t smem, cudaStream_t s) {
+  RBQ_CUDA(cudaMemsetAsync(ws.redo, 0, sizeof(int) * 64, s));
+  work_key_kernel<<<(unsigned)((P.nq + 255) / 256), 256, 0, s>>>(
+      P.probe_ids, P.nprobe_q, P.nq, P.nprobe, P.bucket_off, ws.wkey);
+  RBQ_CUDA(cudaGetLastError());
+  RBQ_CHECK(counting_sort_ws(ws.wkey, P.nq, kWorkKeys, ws.worder, ws.wooff, ws.wsortws, s));
+  int* redo = ws.redo;
   FusedParams W = P;
-  W.candw = candw;
-  W.capw = capw;
+  W.candw = ws.candw;
+  W.capw = ws.capw;
+  W.order = ws.worder;
   W.redo = redo + 64;
   W.redo_cnt = redo;
   const int64_t need = (P.nq + (kWarpThreads / 32) - 1) / (kWarpThreads / 32);
@@ -2953,11 +3117,33 @@ int launch_warp(WarpFn wfn, int64_t wctas, const FusedParams& P, int4* candw, in
 // Scan-path choice: the index's tuned choice for AUTO (set by
 // rabitq_autotune), the popcount path otherwise; a TC search whose candidate
 // lists overflow under AUTO is redone on the popcount path.
-int search_dev(const SearchArgs& a, cudaStream_t s) {
-  if (a.scan_path == RABITQ_SCAN_TC) return search_dev_tc(a, s);
-  if (a.scan_path == RABITQ_SCAN_AUTO && a.X->tuned_path == RABITQ_SCAN_TC) {
+int tile_class_k(int k) { return k <= 16 ? 0 : (k <= 64 ? 1 : (k <= 128 ? 2 : 3)); }
+int tile_class_np(int nprobe) { return nprobe <= 16 ? 0 : (nprobe <= 64 ? 1 : (nprobe <= 256 ? 2 : 3)); }
+
+// AUTO choices: the tuned tile of the shape's class, else the index-wide
+// path choice of rabitq_autotune and the default layout (one warp per
+// query for k <= 32, where its shorter tail wins; one CTA per query above).
+void resolve_tile(const rabitq_index* X, int k, int nprobe, int32_t* path, int32_t* layout,
+                  int32_t* ppl) {
+  const rabitq_index::Tile& t = X->tune[tile_class_k(k)][tile_class_np(nprobe)];
+  if (*path == RABITQ_SCAN_AUTO)
+    *path = t.valid ? t.path : (X->tuned_path ? X->tuned_path : RABITQ_SCAN_POPC);
+  if (*layout == RABITQ_LAYOUT_AUTO)
+    *layout = t.valid ? t.layout
+                      : (X->tuned_layout ? X->tuned_layout
+                                         : (k <= 32 ? RABITQ_LAYOUT_WARP : RABITQ_LAYOUT_CTA));
+  if (*ppl == 0) *ppl = t.valid ? t.ppl : 0;
+}
+
+int search_dev(const SearchArgs& a_in, cudaStream_t s) {
+  SearchArgs a = a_in;
+  const bool auto_path = a.scan_path == RABITQ_SCAN_AUTO;
+  a.tile_layout = a.layout;
+  resolve_tile(a.X, a.k, a.nprobe, &a.scan_path, &a.tile_layout, &a.ppl);
+  if (a.scan_path == RABITQ_SCAN_TC) {
     const int st = search_dev_tc(a, s);
-    if (st != RABITQ_EOVERFLOW) return st;
+    if (!(auto_path && st == RABITQ_EOVERFLOW)) return st;
+    a.scan_path = RABITQ_SCAN_POPC;  // a tuned choice that overflowed: redone on popcount
   }
   return search_dev_popc(a, s);
 }
@@ -2992,10 +3178,14 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   int64_t wctas = 0;
   if (wfn) RBQ_CHECK(warp_ctas(wfn, &wctas));
   const int capw = warp_capw(a);
-  DevBuf candw, redo;
+  DevBuf candw, redo, wkey, worder, wooff, wsortws;
   if (wfn) {
     RBQ_CHECK(candw.alloc(sizeof(int4) * wctas * (kWarpThreads / 32) * capw, s));
     RBQ_CHECK(redo.alloc(sizeof(int32_t) * (qchunk + 64), s));
+    RBQ_CHECK(wkey.alloc(sizeof(int32_t) * qchunk, s));
+    RBQ_CHECK(worder.alloc(sizeof(int32_t) * qchunk, s));
+    RBQ_CHECK(wooff.alloc(sizeof(int32_t) * (kWorkKeys + 1), s));
+    RBQ_CHECK(wsortws.alloc(sizeof(int32_t) * counting_sort_ws_ints(qchunk, kWorkKeys), s));
   }
   DevBuf cd, rq, pid, pdist, cand, err, ubout, scnt, cand2, qn, pnq2;
   if (metric_cos(X)) RBQ_CHECK(qn.alloc(sizeof(float) * qchunk * d, s));
@@ -3140,8 +3330,9 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
       P.cand2 = cand2.as<int4>();
     }
     if (wfn && warp_batch_ok(a, nqc, wctas)) {
-      RBQ_CHECK(launch_warp(wfn, wctas, P, candw.as<int4>(), capw, redo.as<int>(), fn,
-                            (unsigned)grid, smem, s));
+      const WarpScratch ws{candw.as<int4>(), capw, redo.as<int>(), wkey.as<int32_t>(),
+                           worder.as<int32_t>(), wooff.as<int32_t>(), wsortws.as<int32_t>()};
+      RBQ_CHECK(launch_warp(wfn, wctas, P, ws, fn, (unsigned)grid, smem, s));
     } else {
       const unsigned g = (unsigned)std::min<int64_t>(nqc * split, split > 1 ? full : grid);
       fn<<<g, kThreads, smem, s>>>(P);
@@ -3196,7 +3387,7 @@ struct Carve {
   WarpFn wfn = nullptr;
   int64_t wctas = 0;
   int capw = 0;
-  size_t o_candw = 0, o_redo = 0;
+  size_t o_candw = 0, o_redo = 0, o_wkey = 0, o_worder = 0, o_wooff = 0, o_wsortws = 0;
 };
 
 constexpr size_t kCarveAlign = 256;
@@ -3241,6 +3432,10 @@ Carve carve_layout(const SearchArgs& a, int64_t grid, int64_t cap, int64_t qchun
     L.capw = warp_capw(a);
     L.o_candw = take(sizeof(int4) * L.wctas * (kWarpThreads / 32) * L.capw);
     L.o_redo = take(sizeof(int32_t) * (qchunk + 64));
+    L.o_wkey = take(sizeof(int32_t) * qchunk);
+    L.o_worder = take(sizeof(int32_t) * qchunk);
+    L.o_wooff = take(sizeof(int32_t) * (kWorkKeys + 1));
+    L.o_wsortws = take(sizeof(int32_t) * counting_sort_ws_ints(qchunk, kWorkKeys));
   }
   L.end = o;
   return L;
@@ -3393,9 +3588,13 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
       P.cand2 = reinterpret_cast<int4*>(scratch + L.o_cand2);
     }
     if (split == 1 && L.wfn && warp_batch_ok(a, nqc, L.wctas)) {
-      RBQ_CHECK(launch_warp(L.wfn, L.wctas, P, reinterpret_cast<int4*>(scratch + L.o_candw),
-                            L.capw, reinterpret_cast<int*>(scratch + L.o_redo), fn, (unsigned)grid,
-                            smem, s));
+      const WarpScratch ws{reinterpret_cast<int4*>(scratch + L.o_candw), L.capw,
+                           reinterpret_cast<int*>(scratch + L.o_redo),
+                           reinterpret_cast<int32_t*>(scratch + L.o_wkey),
+                           reinterpret_cast<int32_t*>(scratch + L.o_worder),
+                           reinterpret_cast<int32_t*>(scratch + L.o_wooff),
+                           reinterpret_cast<int32_t*>(scratch + L.o_wsortws)};
+      RBQ_CHECK(launch_warp(L.wfn, L.wctas, P, ws, fn, (unsigned)grid, smem, s));
     } else {
       fn<<<(unsigned)std::min<int64_t>(nqc * split, grid), kThreads, smem, s>>>(P);
       RBQ_CUDA(cudaGetLastError());

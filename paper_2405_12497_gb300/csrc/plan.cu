@@ -120,6 +120,8 @@ int rabitq_plan_create(const rabitq_index* X, const rabitq_predictor* pr, int64_
                                      "(use a predictor)");
   if (opts.scan_layout < RABITQ_LAYOUT_AUTO || opts.scan_layout > RABITQ_LAYOUT_WARP)
     return fail(RABITQ_EINVAL, "rabitq_plan_create: unknown scan_layout");
+  if (opts.lane_pairs < 0 || opts.lane_pairs > 2)
+    return fail(RABITQ_EINVAL, "rabitq_plan_create: lane_pairs must be 0, 1 or 2");
   auto* P = new rabitq_plan();
   RBQ_CUDA(cudaGetDevice(&P->device));
   SearchArgs& a = P->a;
@@ -136,6 +138,11 @@ int rabitq_plan_create(const rabitq_index* X, const rabitq_predictor* pr, int64_
   a.rot_precision = opts.rot_precision;
   a.scan_path = RABITQ_SCAN_POPC;
   a.layout = opts.scan_layout;
+  a.ppl = opts.lane_pairs;
+  // the plan keeps the tile resolved now (later tuning does not change it)
+  a.tile_layout = a.layout;
+  resolve_tile(X, k, nprobe, &a.scan_path, &a.tile_layout, &a.ppl);
+  a.scan_path = RABITQ_SCAN_POPC;  // plans run the popcount scan
   a.stage_ms = nullptr;
   a.pred = pr;
   P->nq_max = nq_max;
@@ -231,6 +238,18 @@ int rabitq_plan_search(rabitq_plan* P, const float* queries, int64_t nq, int64_t
   if (out_dist != P->dist)
     RBQ_CUDA(cudaMemcpyAsync(out_dist, P->dist, sizeof(float) * nq * k, cudaMemcpyDefault, s));
   return rabitq_plan_sync(P, stream);
+}
+
+int rabitq_plan_tile(const rabitq_plan* P, rabitq_tile* out) {
+  if (!P || !out) return fail(RABITQ_EINVAL, "rabitq_plan_tile: null argument");
+  out->scan_path = RABITQ_SCAN_POPC;
+  const rabitq_index* X = P->a.X;
+  const bool warp = P->a.tile_layout == RABITQ_LAYOUT_WARP && P->a.bq == 4 && P->a.k <= 128 &&
+                    X->d <= 256 && (X->W == 2 || X->W == 4);
+  out->scan_layout = warp ? RABITQ_LAYOUT_WARP : RABITQ_LAYOUT_CTA;
+  out->lane_pairs = warp ? (P->a.ppl ? P->a.ppl : (X->W == 2 ? 2 : 1)) : 0;
+  out->time_ms = 0.0f;
+  return RABITQ_OK;
 }
 
 int rabitq_plan_stats(rabitq_plan* P, float* ms, int32_t cap) {

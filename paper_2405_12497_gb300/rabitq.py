@@ -36,7 +36,7 @@ EXPORTS = (
     "rabitq_compute_labels", "rabitq_mlp_grad", "rabitq_mlp_adam", "rabitq_autotune",
     "rabitq_plan_create", "rabitq_plan_buffers", "rabitq_plan_run", "rabitq_plan_sync",
     "rabitq_plan_search", "rabitq_plan_free", "rabitq_plan_stats", "rabitq_index_metric",
-    "rabitq_estimate",
+    "rabitq_estimate", "rabitq_autotune_tiles", "rabitq_plan_tile",
 )
 
 MLP_IN, MLP_HIDDEN = 64, 256
@@ -60,7 +60,18 @@ class SearchOpts(C.Structure):
                 ("quant_seed", C.c_uint64), ("io_on_device", C.c_int32),
                 ("stream", C.c_void_p), ("per_query_nprobe", C.c_void_p),
                 ("max_candidates", C.c_int32), ("collect_stats", C.c_int32),
-                ("scan_layout", C.c_int32)]
+                ("scan_layout", C.c_int32), ("lane_pairs", C.c_int32)]
+
+
+class Tile(C.Structure):
+    _fields_ = [("scan_path", C.c_int32), ("scan_layout", C.c_int32),
+                ("lane_pairs", C.c_int32), ("time_ms", C.c_float)]
+
+    def as_dict(self):
+        return {"scan_path": {1: "popcount", 2: "tensor-core"}.get(self.scan_path, self.scan_path),
+                "layout": {1: "cta-per-query", 2: "warp-per-query"}.get(self.scan_layout,
+                                                                        self.scan_layout),
+                "lane_pairs": self.lane_pairs, "time_ms": round(float(self.time_ms), 4)}
 
 
 class Trace(C.Structure):
@@ -140,6 +151,9 @@ def lib():
             "rabitq_plan_stats": (C.c_int, [vp, vp, i32]),
             "rabitq_index_metric": (C.c_int, [vp, vp]),
             "rabitq_estimate": (C.c_int, [vp, vp, i64, vp, i32, i32, f32, vp, vp]),
+            "rabitq_autotune_tiles": (C.c_int, [vp, vp, i64, i32, i32, i32, f32, i32, vp, vp, vp,
+                                                i32, vp]),
+            "rabitq_plan_tile": (C.c_int, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -293,7 +307,7 @@ class Index:
 
     # --------------------------------------------------------------- search
     def _opts(self, quant_seed, per_query_nprobe, max_candidates, stats, stream, on_device,
-              rot_precision=ROT_FP32, scan_path=SCAN_AUTO, layout=LAYOUT_AUTO):
+              rot_precision=ROT_FP32, scan_path=SCAN_AUTO, layout=LAYOUT_AUTO, lane_pairs=0):
         o = SearchOpts()
         lib().rabitq_search_opts_default(C.byref(o))
         o.quant_seed = quant_seed
@@ -304,19 +318,20 @@ class Index:
         o.rot_precision = rot_precision
         o.scan_path = scan_path
         o.scan_layout = layout
+        o.lane_pairs = lane_pairs
         return o
 
     def search(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
                quant_seed: int = 3, per_query_nprobe=None, max_candidates: int = 65536,
                stats: bool = False, stream=None, out=None, rot_precision=ROT_FP32,
-               scan_path=SCAN_AUTO, layout=LAYOUT_AUTO):
+               scan_path=SCAN_AUTO, layout=LAYOUT_AUTO, lane_pairs=0):
         """k-NN search. numpy queries -> numpy (ids int64, dists float32) via
         host buffers; torch CUDA queries -> torch CUDA outputs. Values are
         squared distances (ascending) for l2, inner products / cosines
         (descending) for ip / cosine."""
         dev = _is_torch(queries)
         o = self._opts(quant_seed, per_query_nprobe, max_candidates, stats, stream, dev,
-                       rot_precision, scan_path, layout)
+                       rot_precision, scan_path, layout, lane_pairs)
         if dev:
             import torch
             queries = queries.contiguous()
@@ -440,6 +455,36 @@ class Index:
         _check(lib().rabitq_autotune(self._h, qp, q.shape[0], k, nprobe, bq, eps0, reps,
                                      C.byref(o), C.byref(chosen), _np_ptr(t)))
         return chosen.value, {"popc": float(t[0]), "tc": float(t[1])}
+
+    def autotune_tiles(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
+                       reps: int = 3, max_candidates: int = 65536, per_query_nprobe=None):
+        """Time every tile (scan path x layout x codes per lane) on these
+        queries and cache the fastest for this shape class; returns (best,
+        [every candidate]) as dicts. per_query_nprobe: probe counts of the
+        queries (as a learned search would use), same memory kind."""
+        dev = _is_torch(queries)
+        o = self._opts(3, None, max_candidates, False, None, dev)
+        keep = None
+        if per_query_nprobe is not None:
+            if dev:
+                import torch
+                keep = per_query_nprobe.to(torch.int32).contiguous()
+                o.per_query_nprobe = _dptr(keep)
+            else:
+                keep = np.ascontiguousarray(per_query_nprobe, np.int32)
+                o.per_query_nprobe = _np_ptr(keep)
+        if dev:
+            q = queries.contiguous()
+            qp = _dptr(q)
+        else:
+            q = np.ascontiguousarray(queries, np.float32)
+            qp = _np_ptr(q)
+        best = Tile()
+        allt = (Tile * 8)()
+        n = C.c_int32()
+        _check(lib().rabitq_autotune_tiles(self._h, qp, q.shape[0], k, nprobe, bq, eps0, reps,
+                                           C.byref(o), C.byref(best), allt, 8, C.byref(n)))
+        return best.as_dict(), [allt[i].as_dict() for i in range(n.value)]
 
     # ------------------------------------------------------ learned nprobe
     def search_learned(self, predictor: "Predictor", queries, k: int, bq: int = 4,
@@ -618,10 +663,10 @@ class Plan:
     def __init__(self, index: Index, k: int, nprobe: int, nq_max: int, bq: int = 4,
                  eps0: float = 1.9, predictor: "Predictor | None" = None, quant_seed: int = 3,
                  max_candidates: int = 65536, rot_precision=ROT_FP32, stats: bool = False,
-                 layout=LAYOUT_AUTO):
+                 layout=LAYOUT_AUTO, lane_pairs=0):
         import torch
         o = index._opts(quant_seed, None, max_candidates, stats, None, True, rot_precision,
-                        SCAN_POPC, layout)
+                        SCAN_POPC, layout, lane_pairs)
         h = C.c_void_p()
         _check(lib().rabitq_plan_create(index._h, predictor._h if predictor else None, nq_max, k,
                                         nprobe, bq, eps0, C.byref(o), C.byref(h)))
@@ -636,6 +681,14 @@ class Plan:
         self.dist = torch.as_tensor(_DevArray(dp.value, (nq_max, k), "<f4"), device=dev)
         self.nprobe = (torch.as_tensor(_DevArray(npp.value, (nq_max,), "<i4"), device=dev)
                        if npp.value else None)
+
+    def tile(self) -> dict:
+        """The tile (layout, codes per lane) this plan runs."""
+        t = Tile()
+        _check(lib().rabitq_plan_tile(self._h, C.byref(t)))
+        d = t.as_dict()
+        d.pop("time_ms")
+        return d
 
     def run(self, nq: int, stream=None):
         """Search rows [0, nq) of self.queries into self.ids / self.dist (async)."""

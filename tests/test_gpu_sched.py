@@ -140,3 +140,45 @@ def test_split_batches_equal_unsplit(R, tiny_workload, tiny_idx):
         ids, dist = plan.search(queries[:nq])
         assert np.array_equal(ids, ref_ids[:nq])
         assert np.array_equal(dist.view(np.uint32), ref_dist[:nq].view(np.uint32))
+
+
+def test_tile_autotuner_times_every_tile_and_auto_follows(R, tiny_workload):
+    """rabitq_autotune_tiles times every work decomposition of the scan
+    (CTA per query; warp per query with 1 or 2 codes per lane per step; the
+    tensor-core path), caches the fastest for the shape class, and AUTO
+    searches and new plans take it; every tile returns the oracle's bits."""
+    import torch
+    from oracle import oracle as O
+    O.build()
+    data, queries = tiny_workload
+    idx = R.Index.build(data, 16, seed=2, kmeans_iters=10)
+    best, every = idx.autotune_tiles(queries, 10, 4, reps=2)
+    kinds = {(t["scan_path"], t["layout"], t["lane_pairs"]) for t in every}
+    assert ("popcount", "cta-per-query", 0) in kinds
+    assert ("popcount", "warp-per-query", 1) in kinds and ("popcount", "warp-per-query", 2) in kinds
+    ok = [t for t in every if t["time_ms"] > 0]
+    assert best["time_ms"] == min(t["time_ms"] for t in ok)
+    ids_o, dist_o = O.OracleIndex(data, K=16, seed=2).search(queries, 10, 4)
+    qd = torch.from_numpy(queries).cuda()
+    for path, lay, lp in ((R.SCAN_POPC, R.LAYOUT_CTA, 0), (R.SCAN_POPC, R.LAYOUT_WARP, 1),
+                          (R.SCAN_POPC, R.LAYOUT_WARP, 2), (R.SCAN_TC, R.LAYOUT_AUTO, 0),
+                          (R.SCAN_AUTO, R.LAYOUT_AUTO, 0)):
+        ids, dist = idx.search(qd, 10, 4, scan_path=path, layout=lay, lane_pairs=lp)
+        assert np.array_equal(ids.cpu().numpy(), ids_o)
+        assert np.array_equal(dist.cpu().numpy().view(np.uint32), dist_o.view(np.uint32))
+    plan = R.Plan(idx, 10, 4, 100)
+    if best["scan_path"] == "popcount":
+        t = plan.tile()
+        assert t["layout"] == best["layout"] and t["lane_pairs"] == best["lane_pairs"]
+    plan.queries.copy_(qd)
+    plan.run(100)
+    plan.sync()
+    assert np.array_equal(plan.ids.cpu().numpy(), ids_o)
+
+
+def test_tile_options_are_checked(R, tiny_idx, tiny_workload):
+    _, queries = tiny_workload
+    with pytest.raises(R.RabitqError):
+        tiny_idx.search(queries, 10, 4, lane_pairs=3)
+    with pytest.raises(R.RabitqError):
+        tiny_idx.search(queries, 10, 4, layout=7)
