@@ -286,6 +286,10 @@ def run_ours(args, rank, world):
     e2e_rec = recall_at(ih, gt)
     latency = batch1_latency(G, bplan_args(best_name, legs, chosen), qd, w, flush)
 
+    deep = None
+    if args.metric == "l2" and args.workload == "sift" and not args.no_deep:
+        deep = deep_legs(args, flush, stream, dist, hbm, src)
+
     parity = None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.metric == "l2":
@@ -337,6 +341,8 @@ def run_ours(args, rank, world):
         res["cpu_baseline"] = cpu
     if parity is not None:
         res["parity"] = parity
+    if deep is not None:
+        res["learned_nprobe_config"] = deep
     if rank == 0:
         print(json.dumps(res), flush=True)
     if dist:
@@ -611,7 +617,7 @@ def roofline(G, qd, w, nprobe, per_query, fused_ms, hbm, src, leg):
     per estimated code D'/8 + 12 bytes, per survivor 4 D bytes -- counted on
     the first 2000 queries by the trace and scaled to the batch."""
     n = min(2000, w.nq)
-    t = G.search_trace(qd[:n], w.k, nprobe, bq=w.bq, eps0=w.eps0,
+    t = G.search_trace(qd[:n], w.k, nprobe, bq=w.bq, eps0=w.eps0, max_candidates=1 << 20,
                        per_query_nprobe=None if per_query is None else per_query[:n])
     pairs_per_q = float(t["n_pairs"].double().mean())
     surv_per_q = float(t["n_surv"].double().mean())
@@ -682,6 +688,10 @@ def learned_leg(args, G, qd, gt, w, fixed_nprobe, flush, stream, dist, hbm, src,
 
 
 def smallest_nprobe(G, cqd, cgt, w, hi):
+    return smallest_nprobe_cap(G, cqd, cgt, w, hi, 65536)
+
+
+def smallest_nprobe_cap(G, cqd, cgt, w, hi, cap):
     """The smallest nprobe in [1, hi] whose recall@100 on the calibration
     queries reaches the target, by integer bisection (recall grows with
     nprobe); returns it with every recall measured on the way."""
@@ -689,7 +699,7 @@ def smallest_nprobe(G, cqd, cgt, w, hi):
 
     def rec(npb):
         if npb not in seen:
-            ids, _ = G.search(cqd, w.k, npb, bq=w.bq, eps0=w.eps0)
+            ids, _ = G.search(cqd, w.k, npb, bq=w.bq, eps0=w.eps0, max_candidates=cap)
             seen[npb] = recall_at(ids.cpu().numpy(), cgt)
         return seen[npb]
 
@@ -706,7 +716,7 @@ def smallest_nprobe(G, cqd, cgt, w, hi):
     return lo, seen
 
 
-def calibrate_mult(G, pr, cqd, cgt, w):
+def calibrate_mult(G, pr, cqd, cgt, w, cap=65536):
     """The smallest multiplier 2^(i/32), i in [-256, 255], whose learned
     search reaches the target recall@100 on the calibration queries
     (bisection over i); returns (multiplier, its calibration recall)."""
@@ -715,7 +725,7 @@ def calibrate_mult(G, pr, cqd, cgt, w):
     def rec(i):
         if i not in seen:
             pr.set_mult(2.0 ** (i / 32))
-            ids, _ = G.search_learned(pr, cqd, w.k, bq=w.bq, eps0=w.eps0)
+            ids, _ = G.search_learned(pr, cqd, w.k, bq=w.bq, eps0=w.eps0, max_candidates=cap)
             seen[i] = recall_at(ids.cpu().numpy(), cgt)
         return seen[i]
 
@@ -835,6 +845,147 @@ def parity_block(X, G, data, queries, qd, w, nprobe, legs, o_ids, o_dist, n_lear
                           "dist_bits_equal": bool(np.array_equal(lg["_dist"][:ml].view(np.uint32),
                                                                  l_dist.view(np.uint32))),
                           "per_query_nprobe": "the network's counts from the timed plan"}
+    return out
+
+
+DEEP_SIGMA = 0.7  # noise of the DEEP-shaped recipe (fixed nprobe ~50 for recall@100 0.95)
+
+
+def deep_legs(args, flush, stream, dist, hbm, src):
+    """The learned-nprobe configuration on the DEEP-shaped set: 10M unit
+    vectors of dimension 256 (n/100 mixture components, noise 0.7, drawn in
+    device memory), IVF K = 16384, B_q = 4, eps0 = 1.9, k = 100. The
+    predictor is trained on 200k separately drawn training queries (labels
+    from the library's own search over 256 buckets); the fixed nprobe and
+    the learned multiplier are each calibrated on 10k held-out calibration
+    queries (the smallest value reaching recall@100 0.95 there), then both
+    are timed once on 10k evaluation queries and their recall reported as
+    measured. A cold-scan leg times nprobe 128 (codes and factors of 480 MB,
+    L2 flushed) against the HBM roof. The oracle checks a query sample."""
+    import torch
+    from paper_2405_12497_gb300 import rabitq
+    w = synth.dataclasses_replace(synth.DEEP_LIKE, nq=10_000)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.time()
+    dd, qd = synth.deep_like_device(w.n, w.nq, dev, d=w.d, sigma=DEEP_SIGMA)
+    _, cqd = synth.deep_like_device(w.n, 10_000, dev, d=w.d, sigma=DEEP_SIGMA, seed_query=11,
+                                    with_data=False)
+    _, tqd = synth.deep_like_device(w.n, args.deep_train_nq, dev, d=w.d, sigma=DEEP_SIGMA,
+                                    seed_query=7, with_data=False)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    t0 = time.time()
+    G = rabitq.Index.build(dd, w.n_clusters, seed=2, kmeans_iters=w.kmeans_iters,
+                           kmeans_sample=w.kmeans_sample)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    gt = exact_knn(dd, qd, w.k)
+    cgt = exact_knn(dd, cqd, w.k)
+    cap = 1 << 18
+    # fixed nprobe, calibrated
+    chosen, sweep = smallest_nprobe_cap(G, cqd, cgt, w, 256, cap)
+    t_best, t_all = G.autotune_tiles(cqd, w.k, chosen, bq=w.bq, eps0=w.eps0, reps=2,
+                                     max_candidates=cap)
+    plan = rabitq.Plan(G, w.k, chosen, w.nq, bq=w.bq, eps0=w.eps0, stats=True,
+                       max_candidates=cap)
+    fixed = time_leg(args, plan, qd, gt, w, flush, stream, dist, name="deep_fixed")
+    fixed.update({"nprobe": chosen, "tile": plan.tile(),
+                  "calibration_recall_by_nprobe": {str(a): round(b, 4)
+                                                   for a, b in sorted(sweep.items())},
+                  "autotune": {"chosen": t_best, "candidates": t_all}})
+    fixed["roofline"] = roofline(G, qd, w, chosen, None, fixed["fused_ms"], hbm, src,
+                                 "deep_fixed")
+    f_ids, f_dist = fixed.pop("_ids"), fixed.pop("_dist")
+    fixed.pop("_npq")
+    fixed.pop("_plan")
+    plan.free()
+    # learned probe counts: trained on the training queries, multiplier
+    # calibrated on the calibration queries, frozen, then evaluated
+    t0 = time.time()
+    pr = rabitq.Predictor.train(G, tqd, k=w.k, target_recall=TARGET, nprobe_max=256,
+                                epochs=args.epochs)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    info = pr.info()
+    mult, cal_rec = calibrate_mult(G, pr, cqd, cgt, w, cap)
+    pr.set_mult(mult)
+    npq_cal = G.predict_nprobe(pr, cqd)
+    lt_best, lt_all = G.autotune_tiles(cqd, w.k, 256, bq=w.bq, eps0=w.eps0, reps=2,
+                                       max_candidates=cap, per_query_nprobe=npq_cal)
+    npq = G.predict_nprobe(pr, qd)
+    lplan = rabitq.Plan(G, w.k, 0, w.nq, bq=w.bq, eps0=w.eps0, predictor=pr, stats=True,
+                        max_candidates=cap)
+    learned = time_leg(args, lplan, qd, gt, w, flush, stream, dist, name="deep_learned")
+    learned["roofline"] = roofline(G, qd, w, 256, npq, learned["fused_ms"], hbm, src,
+                                   "deep_learned")
+    l_ids, l_dist, l_npq = learned.pop("_ids"), learned.pop("_dist"), learned.pop("_npq")
+    learned.pop("_plan")
+    l_tile = lplan.tile()
+    lplan.free()
+    npf = npq.double().cpu().numpy()
+    learned.update({
+        "mult": round(mult, 5), "calibration_recall": round(cal_rec, 4),
+        "coverage_mult": round(info["mult"], 5), "val_coverage": round(info["val_recall"], 4),
+        "mean_nprobe": round(float(npf.mean()), 2),
+        "nprobe_p50_p90_p99": [float(np.percentile(npf, p)) for p in (50, 90, 99)],
+        "train_queries": args.deep_train_nq, "epochs": args.epochs, "train_s": round(train_s, 2),
+        "train_loss": round(info["train_loss"], 4), "val_loss": round(info["val_loss"], 4),
+        "tile": l_tile, "autotune": {"chosen": lt_best, "candidates": lt_all}})
+    # cold scan: a fixed 128 probes, L2 flushed, the index (480 MB of codes
+    # and factors) far larger than L2
+    cplan = rabitq.Plan(G, w.k, 128, w.nq, bq=w.bq, eps0=w.eps0, stats=True, max_candidates=cap)
+    cold = time_leg(args, cplan, qd, gt, w, flush, stream, dist, name="deep_cold")
+    for key in ("_ids", "_dist", "_npq", "_plan"):
+        cold.pop(key, None)
+    cold["nprobe"] = 128
+    cold["tile"] = cplan.tile()
+    cplan.free()
+    cold["roofline"] = roofline(G, qd, w, 128, None, cold["fused_ms"], hbm, src, "deep_cold128")
+    cold["codes_and_factors_mb"] = round(G.n * (G.dpad / 8 + 16) / 1e6, 1)
+    out = {"workload": w.name + f"-sigma{DEEP_SIGMA}", "n": w.n, "d": w.d,
+           "n_clusters": w.n_clusters, "k": w.k, "bq": w.bq, "eps0": w.eps0,
+           "eval_queries": w.nq, "calibration_queries": int(cqd.shape[0]),
+           "data_gen_s": round(gen_s, 2), "build_s": round(build_s, 2),
+           "legs": {"fixed": fixed, "learned": learned}, "cold_scan": cold,
+           "learned_vs_fixed_qps": round(learned["value"] / fixed["value"], 4)}
+    if not args.no_cpu_baseline:
+        out["parity"] = deep_parity(G, dd, qd, w, chosen, f_ids, f_dist, l_ids, l_dist, l_npq)
+    G.free()
+    pr.free()
+    del dd, qd, cqd, tqd
+    torch.cuda.empty_cache()
+    return out
+
+
+def deep_parity(G, dd, qd, w, nprobe, f_ids, f_dist, l_ids, l_dist, l_npq, m=300):
+    """The oracle on the DEEP-shaped index: its own P for the build seed, the
+    codes and factors of a 65536-point sample recomputed from the data, and
+    the first m queries of both timed legs searched by the oracle (the fixed
+    nprobe; the learned leg's per-query counts)."""
+    from oracle import oracle as O
+    X = oracle_on_index(G, dd.cpu().numpy())
+    cores = os.cpu_count() or 1
+    data = X.data
+    out = {}
+    P = O.sample_rotation(2, G.dpad)
+    out["rotation_bits_equal"] = bool(np.array_equal(P.view(np.uint64), X.P.view(np.uint64)))
+    smp = np.random.default_rng(5).choice(len(data), 65536, replace=False)
+    codes, fac = O.encode(data[smp], X.centroids, X.assign[smp], P.astype(np.float32),
+                          threads=cores)
+    out["codes_sample_equal"] = bool(np.array_equal(codes, X.codes[smp]))
+    out["factors_sample_bits_equal"] = bool(np.array_equal(fac.view(np.uint32),
+                                                           X.factors[smp].view(np.uint32)))
+    q = qd[:m].cpu().numpy()
+    o_ids, o_dist = X.search(q, w.k, nprobe, bq=w.bq, eps0=w.eps0, threads=cores)
+    out["fixed"] = {"queries": m, "ids_equal": bool(np.array_equal(o_ids, f_ids[:m])),
+                    "dist_bits_equal": bool(np.array_equal(o_dist.view(np.uint32),
+                                                           f_dist[:m].view(np.uint32)))}
+    if l_npq is not None:
+        o_ids, o_dist = X.search(q, w.k, 256, bq=w.bq, eps0=w.eps0, threads=cores,
+                                 per_query_nprobe=l_npq[:m])
+        out["learned"] = {"queries": m, "ids_equal": bool(np.array_equal(o_ids, l_ids[:m])),
+                          "dist_bits_equal": bool(np.array_equal(o_dist.view(np.uint32),
+                                                                 l_dist[:m].view(np.uint32)))}
     return out
 
 
@@ -1126,6 +1277,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-nprobe leg")
     ap.add_argument("--train-nq", type=int, default=100_000)
+    ap.add_argument("--no-deep", action="store_true",
+                    help="skip the learned-nprobe configuration (10M x 256 DEEP-shaped)")
+    ap.add_argument("--deep-train-nq", type=int, default=200_000)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--nprobe-max", type=int, default=256)
     ap.add_argument("--metric", default="l2", choices=["l2", "ip", "cosine"],

@@ -395,7 +395,9 @@ int rabitq_autotune(rabitq_index* idx, const float* queries, int64_t nq, int32_t
  *                            applies: D' of 128 or 256, B_q = 4, k <= 128)
  *   {TC}                     bucket-major tensor-core products (an overflow
  *                            of its lists rules it out)
- * Every candidate returns identical results. best receives the chosen tile
+ * Every candidate returns identical results. AUTO searches take the fastest
+ * tile; plans, which run the popcount scan, take the fastest popcount tile.
+ * best receives the chosen tile
  * (time_ms its best time); all (may be NULL) receives up to cap candidates,
  * *n_all their count (time_ms -1 for one that could not run). reps >= 1
  * timed runs each after a warm-up run. Not thread-safe against searches on

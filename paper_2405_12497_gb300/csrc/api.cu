@@ -572,14 +572,18 @@ int rabitq_autotune_tiles(rabitq_index* X, const float* queries, int64_t nq, int
       if (r > 0 && (cand[c].time_ms < 0.0f || ms < cand[c].time_ms)) cand[c].time_ms = ms;
     }
   }
-  int pick = 0;
-  for (int c = 1; c < nc; ++c)
-    if (cand[c].time_ms >= 0.0f && cand[c].time_ms < cand[pick].time_ms) pick = c;
+  int pick = 0, pick_popc = 0;  // candidate 0 is the popcount CTA tile, always timed
+  for (int c = 1; c < nc; ++c) {
+    if (cand[c].time_ms < 0.0f) continue;
+    if (cand[c].time_ms < cand[pick].time_ms) pick = c;
+    if (cand[c].scan_path == RABITQ_SCAN_POPC && cand[c].time_ms < cand[pick_popc].time_ms)
+      pick_popc = c;
+  }
   rabitq_index::Tile& t = X->tune[tile_class_k(k)][tile_class_np(std::min(nprobe, X->K))];
   t.valid = 1;
   t.path = cand[pick].scan_path;
-  t.layout = cand[pick].scan_path == RABITQ_SCAN_POPC ? cand[pick].scan_layout : RABITQ_LAYOUT_CTA;
-  t.ppl = cand[pick].lane_pairs;
+  t.layout = cand[pick_popc].scan_layout;
+  t.ppl = cand[pick_popc].lane_pairs;
   *best = cand[pick];
   for (int c = 0; c < nc && c < cap; ++c) all[c] = cand[c];
   if (n_all) *n_all = nc;

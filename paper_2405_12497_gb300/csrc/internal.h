@@ -34,6 +34,8 @@ struct rabitq_index {
   int32_t tuned_path = 0;         // scan path AUTO uses (rabitq_autotune)
   int32_t tuned_layout = 0;       // scan layout AUTO uses (rabitq_autotune), 0 = default
   // tiles chosen by rabitq_autotune_tiles per (k class, nprobe class)
+  // (path: the fastest overall; layout, ppl: the fastest popcount tile,
+  // which plans run)
   struct Tile {
     int32_t valid, path, layout, ppl;
   } tune[4][4] = {};

@@ -1,5 +1,6 @@
 // kernels_build.cu -- index phase (Alg. 1 of the paper, with the IVF of §4):
 // k-means buckets, the random orthogonal matrix P, sign codes and factors.
+#include <atomic>
 #include <algorithm>
 #include <vector>
 
@@ -407,9 +408,29 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
+// The stream-ordered scratch comes from the device's default memory pool,
+// which by default returns its memory to the system at every
+// synchronization, so each search would map its scratch again (a gigabyte
+// takes milliseconds). The pool is told once per device to keep what it
+// holds; it then grows to the largest scratch in use and is reused.
+static void keep_pool_memory() {
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  const uint64_t bit = uint64_t(1) << dev;
+  if (done.load() & bit) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~uint64_t(0);
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done.fetch_or(bit);
+}
+
 int DevBuf::alloc(size_t bytes, cudaStream_t st) {
   s = st;
   if (bytes == 0) bytes = 16;
+  keep_pool_memory();
   cudaError_t e = cudaMallocAsync(&p, bytes, st);
   if (e != cudaSuccess) {
     p = nullptr;
