@@ -68,6 +68,13 @@ enum { RABITQ_SCAN_AUTO = 0, RABITQ_SCAN_POPC = 1, RABITQ_SCAN_TC = 2 };
  * applies. Results are identical in every layout. */
 enum { RABITQ_LAYOUT_AUTO = 0, RABITQ_LAYOUT_CTA = 1, RABITQ_LAYOUT_WARP = 2 };
 
+/* Staging of the CTA layout's scan rounds (D' of 128 or 256, B_q = 4): each
+ * round's codes and factors are copied into shared memory by the bulk-copy
+ * (TMA) engine while the block evaluates the round before (BULK), or loaded
+ * by every thread on its own (OFF). AUTO follows rabitq_autotune_tiles'
+ * choice, else BULK. Results are identical either way. */
+enum { RABITQ_STAGING_AUTO = 0, RABITQ_STAGING_OFF = 1, RABITQ_STAGING_BULK = 2 };
+
 typedef struct {
   int32_t kmeans_iters;     /* Lloyd iterations (default 10)                    */
   int64_t kmeans_sample;    /* train k-means on about this many points, 0 = all */
@@ -93,6 +100,7 @@ typedef struct {
   int32_t scan_layout;      /* RABITQ_LAYOUT_* of the popcount scan (default AUTO) */
   int32_t lane_pairs;       /* codes per lane per step in the warp layout: 1 or 2;
                                0 = the tuned or default value                    */
+  int32_t scan_staging;     /* RABITQ_STAGING_* of the CTA layout (default AUTO) */
 } rabitq_search_opts;
 
 /* Fill the option structs with their defaults. */
@@ -388,8 +396,11 @@ int rabitq_autotune(rabitq_index* idx, const float* queries, int64_t nq, int32_t
  * options (scan_path, scan_layout, lane_pairs) of later searches and plans
  * with a k and nprobe in the same class find it (classes: k <= 16, <= 64,
  * <= 128, larger; nprobe <= 16, <= 64, <= 256, larger). The candidates:
- *   {POPC, CTA}              one CTA (8 warps) per query, pairs in rounds of
- *                            512 with a block-wide running threshold
+ *   {POPC, CTA, OFF | BULK}  one CTA (8 warps) per query, pairs in rounds
+ *                            with a block-wide running threshold; each
+ *                            round's codes loaded by the threads (rounds of
+ *                            512) or staged by bulk copies (rounds of 256;
+ *                            D' of 128 or 256, B_q = 4)
  *   {POPC, WARP, 1 or 2}     one warp per query (four queries per CTA), 1 or
  *                            2 codes per lane per step (where the warp layout
  *                            applies: D' of 128 or 256, B_q = 4, k <= 128)
@@ -407,6 +418,7 @@ typedef struct {
   int32_t scan_path;   /* RABITQ_SCAN_POPC or RABITQ_SCAN_TC             */
   int32_t scan_layout; /* RABITQ_LAYOUT_CTA or _WARP (popcount path)      */
   int32_t lane_pairs;  /* codes per lane per step (warp layout), else 0   */
+  int32_t staging;     /* RABITQ_STAGING_OFF or _BULK (CTA layout)        */
   float time_ms;       /* best measured time of one search of the sample  */
 } rabitq_tile;
 

@@ -297,6 +297,8 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
     return fail(RABITQ_EINVAL, "rabitq_search: unknown scan_layout");
   if (opts.lane_pairs < 0 || opts.lane_pairs > 2)
     return fail(RABITQ_EINVAL, "rabitq_search: lane_pairs must be 0, 1 or 2");
+  if (opts.scan_staging < RABITQ_STAGING_AUTO || opts.scan_staging > RABITQ_STAGING_BULK)
+    return fail(RABITQ_EINVAL, "rabitq_search: unknown scan_staging");
   if (trace && opts.scan_path != RABITQ_SCAN_POPC &&
       (trace->planes || trace->sum_qu || trace->meta || trace->pair_id))
     opts.scan_path = RABITQ_SCAN_POPC;  // bit-planes and per-pair values come from that path
@@ -359,6 +361,7 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   a.scan_path = opts.scan_path;
   a.layout = opts.scan_layout;
   a.ppl = opts.lane_pairs;
+  a.stage = opts.scan_staging;
   if (pr) {
     RBQ_CHECK(pb.alloc(sizeof(int32_t) * nq, s));
     a.pred = pr;
@@ -530,14 +533,17 @@ int rabitq_autotune_tiles(rabitq_index* X, const float* queries, int64_t nq, int
   opts.per_query_nprobe = dnp;
   // the candidates: the warp layout only where it applies
   const bool warp_ok = bq == 4 && k <= 128 && X->d <= 256 && (X->W == 2 || X->W == 4);
-  rabitq_tile cand[4];
+  const bool stage_ok = bq == 4 && (X->W == 2 || X->W == 4);
+  rabitq_tile cand[6];
   int nc = 0;
-  cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_CTA, 0, -1.0f};
+  cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_CTA, 0, RABITQ_STAGING_OFF, -1.0f};
+  if (stage_ok)
+    cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_CTA, 0, RABITQ_STAGING_BULK, -1.0f};
   if (warp_ok) {
-    cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_WARP, 1, -1.0f};
-    cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_WARP, 2, -1.0f};
+    cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_WARP, 1, RABITQ_STAGING_OFF, -1.0f};
+    cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_WARP, 2, RABITQ_STAGING_OFF, -1.0f};
   }
-  cand[nc++] = rabitq_tile{RABITQ_SCAN_TC, 0, 0, -1.0f};
+  cand[nc++] = rabitq_tile{RABITQ_SCAN_TC, 0, 0, 0, -1.0f};
   struct Ev {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     ~Ev() {
@@ -553,6 +559,7 @@ int rabitq_autotune_tiles(rabitq_index* X, const float* queries, int64_t nq, int
     opts.scan_path = cand[c].scan_path;
     opts.scan_layout = cand[c].scan_layout;
     opts.lane_pairs = cand[c].lane_pairs;
+    opts.scan_staging = cand[c].staging;
     for (int r = 0; r <= reps; ++r) {  // run 0 warms up
       RBQ_CUDA(cudaEventRecord(ev.e0, s));
       const int st = search_common(X, dq, nq, k, nprobe, bq, eps0, ib.as<int64_t>(),
@@ -584,6 +591,7 @@ int rabitq_autotune_tiles(rabitq_index* X, const float* queries, int64_t nq, int
   t.path = cand[pick].scan_path;
   t.layout = cand[pick_popc].scan_layout;
   t.ppl = cand[pick_popc].lane_pairs;
+  t.stage = cand[pick_popc].staging ? cand[pick_popc].staging : RABITQ_STAGING_OFF;
   *best = cand[pick];
   for (int c = 0; c < nc && c < cap; ++c) all[c] = cand[c];
   if (n_all) *n_all = nc;

@@ -37,7 +37,7 @@ struct rabitq_index {
   // (path: the fastest overall; layout, ppl: the fastest popcount tile,
   // which plans run)
   struct Tile {
-    int32_t valid, path, layout, ppl;
+    int32_t valid, path, layout, ppl, stage;
   } tune[4][4] = {};
   void* ptb = nullptr;            // dpad x kp BF16
   float* ptf = nullptr;           // dpad x kp TF32-rounded FP32
@@ -189,11 +189,14 @@ struct SearchArgs {
   // taken for batches that fill the GPU, while an explicit RABITQ_LAYOUT_WARP
   // request is taken for every batch
   int32_t tile_layout = 0;
+  // bulk-copy staging of the CTA layout's scan rounds (RABITQ_STAGING_*;
+  // AUTO resolves to the tuned or default choice)
+  int32_t stage = 0;
 };
 // Resolve the AUTO choices of a search (scan path, layout, codes per lane)
 // from the index's tuned tiles for the shape's class, else the defaults.
 void resolve_tile(const rabitq_index* X, int k, int nprobe, int32_t* path, int32_t* layout,
-                  int32_t* ppl);
+                  int32_t* ppl, int32_t* stage);
 int tile_class_k(int k);
 int tile_class_np(int nprobe);
 int search_dev(const SearchArgs& a, cudaStream_t s);

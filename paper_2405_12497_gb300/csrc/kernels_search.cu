@@ -1362,7 +1362,81 @@ constexpr int fused_min_blocks() {
   return (WT > 0 && WT <= 4) ? 4 : 3;
 }
 
-template <int WT, int BQT>
+// ---- bulk-copy staging of the scan rounds (STG kernels, D' = 128 / 256)
+// Round r of a probe chunk covers pairs [r * step, (r + 1) * step) of the
+// chunk's pair sequence (probe order, then bucket order); their codes and
+// factors are runs of consecutive bucket positions, one run per probed
+// bucket the round touches. Warp 0 copies the runs of round r + 1 into the
+// other of two shared-memory stages with cp.async.bulk (one per run and
+// array, completion counted in bytes on the stage's mbarrier) while the
+// block evaluates round r from its stage. Every wait is bounded (about a
+// second); a wait that expires sets the error flag to 2.
+__device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t b = smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+// Issue the copies of pairs [b0, b0 + cnt) of the chunk into stage buf
+// (codes at stg + buf * step * CB, factors after both code stages). Warp 0.
+template <int WT>
+__device__ __forceinline__ void stage_issue(const FusedParams& P, const FusedSmem& S,
+                                            unsigned char* stg, uint64_t* bars, int b0, int cnt,
+                                            int npc, int buf, int step) {
+  constexpr int CB = WT * 8;  // code bytes
+  const int lane = threadIdx.x & 31;
+  const uint32_t dc = smem_u32(stg) + (uint32_t)(buf * step * CB);
+  const uint32_t df = smem_u32(stg) + (uint32_t)(2 * step * CB + buf * step * 16);
+  const uint32_t bar = smem_u32(&bars[buf]);
+  if (lane == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((uint32_t)cnt * (uint32_t)(CB + 16))
+                 : "memory");
+  }
+  __syncwarp();
+  // the last probe whose pairs start at or before b0
+  int lo = 0, hi = npc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (S.pref[mid] <= b0) lo = mid; else hi = mid - 1;
+  }
+  for (int j = lo + lane; j < npc; j += 32) {
+    const int ps = S.pref[j], pe = S.pref[j + 1];
+    if (ps >= b0 + cnt) break;
+    const int t0 = max(ps, b0), t1 = min(pe, b0 + cnt);
+    if (t1 <= t0) continue;
+    const int pos0 = S.pbeg[j] + (t0 - ps);
+    const uint32_t n = (uint32_t)(t1 - t0);
+    const uint64_t* src_c = P.codes + (size_t)pos0 * WT;
+    const float4* src_f = P.factors + pos0;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dc + (uint32_t)((t0 - b0) * CB)), "l"(src_c), "r"(n * (uint32_t)CB), "r"(bar)
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(df + (uint32_t)((t0 - b0) * 16)), "l"(src_f), "r"(n * 16u), "r"(bar)
+        : "memory");
+  }
+}
+
+template <int WT>
+__host__ __device__ constexpr int stage_bytes(int step) {
+  return 2 * step * (WT * 8 + 16);
+}
+
+template <int WT, int BQT, bool STG = false>
 __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search_kernel(FusedParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_ub_cnt, s_cand_cnt, s_top_cnt, s_surv, s_overflow;
@@ -1386,6 +1460,20 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
   S.scand = reinterpret_cast<int4*>(smem + off[9]);
   const int W = P.W, bq = P.bq, k = P.k;
   int4* cand = P.cand + (int64_t)blockIdx.x * P.cand_cap;
+  // staging (STG): two stages in the tail's candidate area, one mbarrier each
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_stg_fail;
+  unsigned char* stg = reinterpret_cast<unsigned char*>(S.scand);
+  uint32_t par = 0;  // bit b: parity of stage b's next completion
+  if constexpr (STG) {
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_bar[0])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_bar[1])), "r"(1));
+      asm volatile("fence.mbarrier_init.release.cluster;");
+      s_stg_fail = 0;
+    }
+    __syncthreads();
+  }
 
   __shared__ int s_next, s_next_fill;
   // next work item: dynamic (one atomic per query, taken by thread 0 and
@@ -1447,12 +1535,27 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
       __syncthreads();
       const int total = S.pref[npc];
       int j = 0;
-      constexpr int PPT = pairs_per_thread<WT>();
+      constexpr int PPT = STG ? 1 : pairs_per_thread<WT>();
       const int step = PPT * blockDim.x;
+      if constexpr (STG) {
+        if (wid == 0 && total > 0) stage_issue<WT>(P, S, stg, s_bar, 0, min(step, total), npc, 0, step);
+      }
+      int rnd = 0;
       // each thread takes PPT consecutive pairs per round (mostly of one
       // probe); the probe's bit-planes are read from shared memory (holding
       // them in registers cost spills at the four-CTA register budget)
-      for (int base = 0; base < total; base += step) {
+      for (int base = 0; base < total; base += step, ++rnd) {
+        const int buf = rnd & 1;
+        if constexpr (STG) {
+          // the next round's copies go out now (its stage was last read in
+          // the round before this one, which ended with a barrier); then
+          // this round's stage is waited for
+          if (wid == 0 && base + step < total)
+            stage_issue<WT>(P, S, stg, s_bar, base + step, min(step, total - base - step), npc,
+                            buf ^ 1, step);
+          if (!stage_wait(&s_bar[buf], (par >> buf) & 1u)) s_stg_fail = 1;
+          par ^= 1u << buf;
+        }
         // issue every load of this thread's PPT pairs first (they are
         // independent), then evaluate; keeps PPT code/factor loads in flight
         const int t0 = base + tid * PPT;
@@ -1479,8 +1582,22 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
             }
             posv[pp] = pos;
             jv[pp] = j;
-            load_code<WT>(cr[pp], P.codes + (size_t)(uint32_t)posv[pp] * (uint32_t)W);
-            fv[pp] = __ldg(P.factors + (uint32_t)posv[pp]);
+            if constexpr (STG) {
+              // this pair's slot in the round's stage (shared memory: plain
+              // loads, not the read-only global path)
+              const int r = t - base;
+              const uint4* cs = reinterpret_cast<const uint4*>(stg + (size_t)(buf * step + r) * (WT * 8));
+#pragma unroll
+              for (int w = 0; w < WT; w += 2) {
+                const uint4 v = cs[w / 2];
+                cr[pp].c[w] = ((uint64_t)v.y << 32) | v.x;
+                cr[pp].c[w + 1] = ((uint64_t)v.w << 32) | v.z;
+              }
+              fv[pp] = reinterpret_cast<const float4*>(stg + (size_t)2 * step * (WT * 8))[buf * step + r];
+            } else {
+              load_code<WT>(cr[pp], P.codes + (size_t)(uint32_t)posv[pp] * (uint32_t)W);
+              fv[pp] = __ldg(P.factors + (uint32_t)posv[pp]);
+            }
           }
         }
         // evaluate the estimator and its bounds for every pair of the round
@@ -1585,7 +1702,15 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
           __syncthreads();
           if (ovf && tid == 0) s_overflow = 1;
         }
-        if (ovf) break;
+        if (ovf) {
+          if constexpr (STG) {  // the next round's copies are in flight: let them land
+            if (base + step < total) {
+              if (!stage_wait(&s_bar[buf ^ 1], (par >> (buf ^ 1)) & 1u)) s_stg_fail = 1;
+              par ^= 1u << (buf ^ 1);
+            }
+          }
+          break;
+        }
       }
       pairs_done += total;
       __syncthreads();
@@ -1596,6 +1721,7 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
       const int nk = min(s_ub_cnt, k);
       for (int i = tid; i < nk; i += blockDim.x) P.ub_out[it * k + i] = S.ubk[i];
       if (tid == 0) {
+        if (STG && s_stg_fail) atomicExch(P.err, 2);
         P.slice_cnt[2 * it] = nk;
         P.slice_cnt[2 * it + 1] = min(s_cand_cnt, P.cand_cap);
         if (s_overflow) atomicExch(P.err, 1);
@@ -1653,6 +1779,7 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
     }
     finish_query(P, S, q, tcand, tcap, tau_ub, ts, tcand == S.scand);
     if (tid == 0) {
+      if (STG && s_stg_fail) atomicExch(P.err, 2);
       if (s_overflow) atomicExch(P.err, 1);
       if (P.tr.n_pairs) P.tr.n_pairs[q] = pairs_done;
     }
@@ -2721,10 +2848,10 @@ typedef void (*FusedFn)(FusedParams);
 
 // Compile-time code lengths of the common shapes (D' = 128, 256, 1024 with
 // B_q = 4); everything else runs the generic instance.
-FusedFn pick_fused(int W, int bq) {
+FusedFn pick_fused(int W, int bq, bool staged = false) {
   if (bq == 4) {
-    if (W == 2) return fused_search_kernel<2, 4>;
-    if (W == 4) return fused_search_kernel<4, 4>;
+    if (W == 2) return staged ? fused_search_kernel<2, 4, true> : fused_search_kernel<2, 4>;
+    if (W == 4) return staged ? fused_search_kernel<4, 4, true> : fused_search_kernel<4, 4>;
     if (W == 16) return fused_search_kernel<16, 4>;
   }
   return fused_search_kernel<0, 0>;
@@ -2739,8 +2866,8 @@ constexpr int kWarpCap = 8192;  // candidate entries per warp region (at most ma
 WarpFn pick_warp(const SearchArgs& a) {
   const rabitq_index* X = a.X;
   int32_t path = a.scan_path, layout = a.layout == RABITQ_LAYOUT_AUTO ? a.tile_layout : a.layout,
-          ppl = a.ppl;
-  resolve_tile(X, a.k, a.nprobe, &path, &layout, &ppl);
+          ppl = a.ppl, stage = a.stage;
+  resolve_tile(X, a.k, a.nprobe, &path, &layout, &ppl, &stage);
   if (layout != RABITQ_LAYOUT_WARP || !a.allow_warp || a.trace || a.bq != 4 ||
       a.k > kWarpMaxK || X->d > 256)
     return nullptr;
@@ -2935,7 +3062,11 @@ int fused_shape(const SearchArgs& a, FusedShape* f) {
   f->cu = std::max(1024, pow2_at_least(a.k + kPPT * kThreads));
   f->ce = pow2_at_least(f->pilot_m);
   f->ct = std::max(1024, pow2_at_least(a.k + kThreads));
-  f->fn = pick_fused(W, a.bq);
+  // bulk-copy staging of the scan rounds (D' = 128 / 256, B_q = 4): its two
+  // stages live in the tail's candidate area, which must hold them
+  const bool staged = a.stage == RABITQ_STAGING_BULK && a.bq == 4 && (W == 2 || W == 4);
+  const int min_scap = !staged ? 0 : (W == 2 ? stage_bytes<2>(kThreads) : stage_bytes<4>(kThreads)) / 16;
+  f->fn = pick_fused(W, a.bq, staged);
   int dev = 0, optin = 0;
   RBQ_CUDA(cudaGetDevice(&dev));
   RBQ_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -2951,6 +3082,7 @@ int fused_shape(const SearchArgs& a, FusedShape* f) {
   f->smem = base;
   f->per_sm = std::max(per_base, 1);
   for (int scap = 4096; scap >= 1024; scap /= 2) {
+    if (scap < min_scap) break;
     const size_t sm = fused_smem_bytes(f->pch, a.bq, W, X->d, f->cu, f->ce, f->ct, kThreads / 32,
                                        nullptr, scap);
     if (sm > (size_t)optin) continue;
@@ -2961,6 +3093,16 @@ int fused_shape(const SearchArgs& a, FusedShape* f) {
       f->smem = sm;
       break;
     }
+  }
+  if (staged && f->scap < min_scap) {  // the stages first, residency second
+    int scap = 1024;
+    while (scap < min_scap) scap *= 2;
+    f->scap = scap;
+    f->smem = fused_smem_bytes(f->pch, a.bq, W, X->d, f->cu, f->ce, f->ct, kThreads / 32, nullptr,
+                               scap);
+    int per = 0;
+    RBQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f->fn, kThreads, f->smem));
+    f->per_sm = std::max(per, 1);
   }
   return RABITQ_OK;
 }
@@ -3124,7 +3266,7 @@ int tile_class_np(int nprobe) { return nprobe <= 16 ? 0 : (nprobe <= 64 ? 1 : (n
 // path choice of rabitq_autotune and the default layout (one warp per
 // query for k <= 32, where its shorter tail wins; one CTA per query above).
 void resolve_tile(const rabitq_index* X, int k, int nprobe, int32_t* path, int32_t* layout,
-                  int32_t* ppl) {
+                  int32_t* ppl, int32_t* stage) {
   const rabitq_index::Tile& t = X->tune[tile_class_k(k)][tile_class_np(nprobe)];
   if (*path == RABITQ_SCAN_AUTO)
     *path = t.valid ? t.path : (X->tuned_path ? X->tuned_path : RABITQ_SCAN_POPC);
@@ -3133,13 +3275,15 @@ void resolve_tile(const rabitq_index* X, int k, int nprobe, int32_t* path, int32
                       : (X->tuned_layout ? X->tuned_layout
                                          : (k <= 32 ? RABITQ_LAYOUT_WARP : RABITQ_LAYOUT_CTA));
   if (*ppl == 0) *ppl = t.valid ? t.ppl : 0;
+  if (*stage == RABITQ_STAGING_AUTO)
+    *stage = t.valid && t.stage ? t.stage : RABITQ_STAGING_BULK;
 }
 
 int search_dev(const SearchArgs& a_in, cudaStream_t s) {
   SearchArgs a = a_in;
   const bool auto_path = a.scan_path == RABITQ_SCAN_AUTO;
   a.tile_layout = a.layout;
-  resolve_tile(a.X, a.k, a.nprobe, &a.scan_path, &a.tile_layout, &a.ppl);
+  resolve_tile(a.X, a.k, a.nprobe, &a.scan_path, &a.tile_layout, &a.ppl, &a.stage);
   if (a.scan_path == RABITQ_SCAN_TC) {
     const int st = search_dev_tc(a, s);
     if (!(auto_path && st == RABITQ_EOVERFLOW)) return st;

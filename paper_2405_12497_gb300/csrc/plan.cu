@@ -122,6 +122,8 @@ int rabitq_plan_create(const rabitq_index* X, const rabitq_predictor* pr, int64_
     return fail(RABITQ_EINVAL, "rabitq_plan_create: unknown scan_layout");
   if (opts.lane_pairs < 0 || opts.lane_pairs > 2)
     return fail(RABITQ_EINVAL, "rabitq_plan_create: lane_pairs must be 0, 1 or 2");
+  if (opts.scan_staging < RABITQ_STAGING_AUTO || opts.scan_staging > RABITQ_STAGING_BULK)
+    return fail(RABITQ_EINVAL, "rabitq_plan_create: unknown scan_staging");
   auto* P = new rabitq_plan();
   RBQ_CUDA(cudaGetDevice(&P->device));
   SearchArgs& a = P->a;
@@ -139,9 +141,10 @@ int rabitq_plan_create(const rabitq_index* X, const rabitq_predictor* pr, int64_
   a.scan_path = RABITQ_SCAN_POPC;
   a.layout = opts.scan_layout;
   a.ppl = opts.lane_pairs;
+  a.stage = opts.scan_staging;
   // the plan keeps the tile resolved now (later tuning does not change it)
   a.tile_layout = a.layout;
-  resolve_tile(X, k, nprobe, &a.scan_path, &a.tile_layout, &a.ppl);
+  resolve_tile(X, k, nprobe, &a.scan_path, &a.tile_layout, &a.ppl, &a.stage);
   a.scan_path = RABITQ_SCAN_POPC;  // plans run the popcount scan
   a.stage_ms = nullptr;
   a.pred = pr;
@@ -248,6 +251,10 @@ int rabitq_plan_tile(const rabitq_plan* P, rabitq_tile* out) {
                     X->d <= 256 && (X->W == 2 || X->W == 4);
   out->scan_layout = warp ? RABITQ_LAYOUT_WARP : RABITQ_LAYOUT_CTA;
   out->lane_pairs = warp ? (P->a.ppl ? P->a.ppl : (X->W == 2 ? 2 : 1)) : 0;
+  out->staging = !warp && P->a.stage == RABITQ_STAGING_BULK && P->a.bq == 4 &&
+                         (X->W == 2 || X->W == 4)
+                     ? RABITQ_STAGING_BULK
+                     : RABITQ_STAGING_OFF;
   out->time_ms = 0.0f;
   return RABITQ_OK;
 }

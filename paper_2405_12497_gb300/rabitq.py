@@ -20,6 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EIO, EUNSUPPORTED, EOVERFLOW = 0, -1, -2, -
 ROT_FP32, ROT_TF32, ROT_BF16 = 0, 1, 2
 SCAN_AUTO, SCAN_POPC, SCAN_TC = 0, 1, 2
 LAYOUT_AUTO, LAYOUT_CTA, LAYOUT_WARP = 0, 1, 2
+STAGING_AUTO, STAGING_OFF, STAGING_BULK = 0, 1, 2
 METRIC_L2, METRIC_IP, METRIC_COSINE = 0, 1, 2
 METRICS = {"l2": METRIC_L2, "ip": METRIC_IP, "cosine": METRIC_COSINE}
 
@@ -60,18 +61,21 @@ class SearchOpts(C.Structure):
                 ("quant_seed", C.c_uint64), ("io_on_device", C.c_int32),
                 ("stream", C.c_void_p), ("per_query_nprobe", C.c_void_p),
                 ("max_candidates", C.c_int32), ("collect_stats", C.c_int32),
-                ("scan_layout", C.c_int32), ("lane_pairs", C.c_int32)]
+                ("scan_layout", C.c_int32), ("lane_pairs", C.c_int32),
+                ("scan_staging", C.c_int32)]
 
 
 class Tile(C.Structure):
     _fields_ = [("scan_path", C.c_int32), ("scan_layout", C.c_int32),
-                ("lane_pairs", C.c_int32), ("time_ms", C.c_float)]
+                ("lane_pairs", C.c_int32), ("staging", C.c_int32), ("time_ms", C.c_float)]
 
     def as_dict(self):
         return {"scan_path": {1: "popcount", 2: "tensor-core"}.get(self.scan_path, self.scan_path),
                 "layout": {1: "cta-per-query", 2: "warp-per-query"}.get(self.scan_layout,
                                                                         self.scan_layout),
-                "lane_pairs": self.lane_pairs, "time_ms": round(float(self.time_ms), 4)}
+                "lane_pairs": self.lane_pairs,
+                "staging": {1: "off", 2: "bulk-copy"}.get(self.staging, self.staging),
+                "time_ms": round(float(self.time_ms), 4)}
 
 
 class Trace(C.Structure):
@@ -307,7 +311,8 @@ class Index:
 
     # --------------------------------------------------------------- search
     def _opts(self, quant_seed, per_query_nprobe, max_candidates, stats, stream, on_device,
-              rot_precision=ROT_FP32, scan_path=SCAN_AUTO, layout=LAYOUT_AUTO, lane_pairs=0):
+              rot_precision=ROT_FP32, scan_path=SCAN_AUTO, layout=LAYOUT_AUTO, lane_pairs=0,
+              staging=STAGING_AUTO):
         o = SearchOpts()
         lib().rabitq_search_opts_default(C.byref(o))
         o.quant_seed = quant_seed
@@ -319,19 +324,20 @@ class Index:
         o.scan_path = scan_path
         o.scan_layout = layout
         o.lane_pairs = lane_pairs
+        o.scan_staging = staging
         return o
 
     def search(self, queries, k: int, nprobe: int, bq: int = 4, eps0: float = 1.9,
                quant_seed: int = 3, per_query_nprobe=None, max_candidates: int = 65536,
                stats: bool = False, stream=None, out=None, rot_precision=ROT_FP32,
-               scan_path=SCAN_AUTO, layout=LAYOUT_AUTO, lane_pairs=0):
+               scan_path=SCAN_AUTO, layout=LAYOUT_AUTO, lane_pairs=0, staging=STAGING_AUTO):
         """k-NN search. numpy queries -> numpy (ids int64, dists float32) via
         host buffers; torch CUDA queries -> torch CUDA outputs. Values are
         squared distances (ascending) for l2, inner products / cosines
         (descending) for ip / cosine."""
         dev = _is_torch(queries)
         o = self._opts(quant_seed, per_query_nprobe, max_candidates, stats, stream, dev,
-                       rot_precision, scan_path, layout, lane_pairs)
+                       rot_precision, scan_path, layout, lane_pairs, staging)
         if dev:
             import torch
             queries = queries.contiguous()
@@ -663,10 +669,10 @@ class Plan:
     def __init__(self, index: Index, k: int, nprobe: int, nq_max: int, bq: int = 4,
                  eps0: float = 1.9, predictor: "Predictor | None" = None, quant_seed: int = 3,
                  max_candidates: int = 65536, rot_precision=ROT_FP32, stats: bool = False,
-                 layout=LAYOUT_AUTO, lane_pairs=0):
+                 layout=LAYOUT_AUTO, lane_pairs=0, staging=STAGING_AUTO):
         import torch
         o = index._opts(quant_seed, None, max_candidates, stats, None, True, rot_precision,
-                        SCAN_POPC, layout, lane_pairs)
+                        SCAN_POPC, layout, lane_pairs, staging)
         h = C.c_void_p()
         _check(lib().rabitq_plan_create(index._h, predictor._h if predictor else None, nq_max, k,
                                         nprobe, bq, eps0, C.byref(o), C.byref(h)))
