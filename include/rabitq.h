@@ -513,6 +513,41 @@ int rabitq_estimate(const rabitq_index* idx, const float* queries, int64_t nq,
                     const int64_t* ids, int32_t m, int32_t bq, float eps0, float* out,
                     const rabitq_search_opts* opts);
 
+/*
+ * ---- Bucket sharding (the IVF's clusters split over GPUs or index pieces) --
+ *
+ * rabitq_shard_clusters -- assign the K clusters (sizes: points per cluster,
+ * e.g. the bucket offsets' differences) to S shards balanced by points:
+ * largest cluster first, each to the shard with the fewest points so far
+ * (ties to the lower id). shard_of: K shard numbers out; shard_points (may
+ * be NULL): S totals out. Host memory. A shard's index is then built from
+ * its clusters' points with the global centroids (rabitq_build_opts.
+ * centroids) and the build seed: its codes, factors, probe lists and
+ * quantization streams are those of the unsharded index (§4's buckets,
+ * Alg. 1), and each shard's search keeps every code of the shard that the
+ * unsharded search would keep (its tau_ub, the k-th smallest upper bound of
+ * fewer codes, is at least the global one). Errors: EINVAL.
+ */
+int rabitq_shard_clusters(const int32_t* sizes, int32_t K, int32_t S, int32_t* shard_of,
+                          int64_t* shard_points);
+
+/*
+ * rabitq_merge_topk -- the k-way merge of per-shard results: for each of nq
+ * queries, the k best of n_lists lists of k_in (id, value) entries by
+ * (distance, id) -- for the IP / COSINE metrics by (-inner product, id),
+ * returned largest first -- into nq x k outputs (ids -1 and +inf / -inf pad).
+ * All pointers are DEVICE memory: dist and ids are n_lists x nq x k_in,
+ * list-major (each list as a search returns it; id -1 = padding); labels
+ * (may be NULL, or hold NULL entries) is a device array of n_lists device
+ * pointers mapping each list's ids to global ids (ids[...] indexes
+ * labels[list]); global ids must be below 2^32 - 1. n_lists * k_in <= 8192,
+ * k <= 1024. Asynchronous on `stream` (no synchronization). Errors: EINVAL;
+ * ECUDA.
+ */
+int rabitq_merge_topk(const float* dist, const int64_t* ids, int32_t n_lists, int64_t nq,
+                      int32_t k_in, int32_t k, const int64_t* const* labels, int32_t metric,
+                      int64_t* out_ids, float* out_dist, void* stream);
+
 /* Sizes of an index: n, d, D' (code bits), K. Any pointer may be NULL. */
 int rabitq_index_info(const rabitq_index* idx, int64_t* n, int32_t* d, int32_t* d_pad,
                       int32_t* n_clusters);

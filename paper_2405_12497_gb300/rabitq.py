@@ -37,7 +37,8 @@ EXPORTS = (
     "rabitq_compute_labels", "rabitq_mlp_grad", "rabitq_mlp_adam", "rabitq_autotune",
     "rabitq_plan_create", "rabitq_plan_buffers", "rabitq_plan_run", "rabitq_plan_sync",
     "rabitq_plan_search", "rabitq_plan_free", "rabitq_plan_stats", "rabitq_index_metric",
-    "rabitq_estimate", "rabitq_autotune_tiles", "rabitq_plan_tile",
+    "rabitq_estimate", "rabitq_autotune_tiles", "rabitq_plan_tile", "rabitq_shard_clusters",
+    "rabitq_merge_topk",
 )
 
 MLP_IN, MLP_HIDDEN = 64, 256
@@ -158,6 +159,8 @@ def lib():
             "rabitq_autotune_tiles": (C.c_int, [vp, vp, i64, i32, i32, i32, f32, i32, vp, vp, vp,
                                                 i32, vp]),
             "rabitq_plan_tile": (C.c_int, [vp, vp]),
+            "rabitq_shard_clusters": (C.c_int, [vp, i32, i32, vp, vp]),
+            "rabitq_merge_topk": (C.c_int, [vp, vp, i32, i64, i32, i32, vp, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -740,3 +743,82 @@ class Plan:
             self.free()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ bucket sharding
+def shard_clusters(sizes, n_shards: int):
+    """Size-balanced assignment of clusters to shards (rabitq_shard_clusters):
+    returns (shard of each cluster, points per shard)."""
+    sizes = np.ascontiguousarray(sizes, np.int32)
+    shard_of = np.zeros(len(sizes), np.int32)
+    pts = np.zeros(n_shards, np.int64)
+    _check(lib().rabitq_shard_clusters(_np_ptr(sizes), len(sizes), n_shards, _np_ptr(shard_of),
+                                       _np_ptr(pts)))
+    return shard_of, pts
+
+
+def merge_topk(dist, ids, k: int, labels=None, metric: str = "l2", stream=None):
+    """k-way merge of per-shard results (rabitq_merge_topk): dist / ids are
+    torch CUDA tensors of shape (n_lists, nq, k_in); labels: None or a list
+    of n_lists int64 CUDA tensors mapping each list's ids to global ids.
+    Returns (ids, dist) of shape (nq, k)."""
+    import torch
+    n_lists, nq, k_in = ids.shape
+    dist = dist.contiguous()
+    ids = ids.contiguous()
+    out_i = torch.empty((nq, k), dtype=torch.int64, device=ids.device)
+    out_d = torch.empty((nq, k), dtype=torch.float32, device=ids.device)
+    lab = None
+    if labels is not None:
+        ptrs = [int(t.data_ptr()) if t is not None else 0 for t in labels]
+        lab = torch.tensor(ptrs, dtype=torch.int64, device=ids.device)
+    _check(lib().rabitq_merge_topk(_dptr(dist), _dptr(ids), n_lists, nq, k_in, k,
+                                   _dptr(lab) if lab is not None else None, METRICS[metric],
+                                   _dptr(out_i), _dptr(out_d), _stream_handle(stream)))
+    return out_i, out_d
+
+
+class ShardedIndex:
+    """An IVF index whose clusters are split over shards (one GPU each in a
+    multi-GPU job; here any number of shards on the current device): the
+    global k-means and rotation, then one index per shard of its clusters'
+    points built with the global centroids. A search runs every shard and
+    merges their top-k on the device; results equal the unsharded search
+    wherever the error bound holds for the true neighbours (§4)."""
+
+    def __init__(self, shards, labels, shard_of, metric):
+        self.shards, self.labels, self.shard_of, self.metric = shards, labels, shard_of, metric
+
+    @classmethod
+    def build(cls, data, n_clusters: int, n_shards: int, seed: int, kmeans_iters: int = 10,
+              kmeans_sample: int = 0, code_bits: int = 0, metric: str = "l2"):
+        import torch
+        full = Index.build(data, n_clusters, seed, code_bits=code_bits, kmeans_iters=kmeans_iters,
+                           kmeans_sample=kmeans_sample, metric=metric)
+        cent = full.centroids()
+        assign = full.assign()
+        off, _ = full.buckets()
+        full.free()
+        shard_of, _ = shard_clusters(np.diff(off), n_shards)
+        dev = data.device if _is_torch(data) else torch.device("cuda", torch.cuda.current_device())
+        shards, labels = [], []
+        point_shard = shard_of[assign]
+        for sh in range(n_shards):
+            rows = np.flatnonzero(point_shard == sh).astype(np.int64)
+            sub = data[torch.from_numpy(rows).to(data.device)] if _is_torch(data) else data[rows]
+            shards.append(Index.build(sub, n_clusters, seed, code_bits=code_bits, centroids=cent,
+                                      metric=metric))
+            labels.append(torch.from_numpy(rows).to(dev))
+        return cls(shards, labels, shard_of, metric)
+
+    def search(self, queries, k: int, nprobe: int, **kw):
+        """Search every shard (torch CUDA queries) and merge on the device."""
+        import torch
+        outs = [sh.search(queries, k, nprobe, **kw) for sh in self.shards]
+        ids = torch.stack([o[0] for o in outs])
+        dist = torch.stack([o[1] for o in outs])
+        return merge_topk(dist, ids, k, self.labels, self.metric)
+
+    def free(self):
+        for sh in self.shards:
+            sh.free()

@@ -1,0 +1,78 @@
+"""Bucket-sharded search on one GPU: the clusters split into size-balanced
+shards, one index per shard built with the global centroids and rotation,
+every shard searched, the top-k lists merged on the device by (distance, id)
+(rabitq_merge_topk). The merged results equal the unsharded search (and the
+oracle) wherever the error bound holds; the merge itself equals a host
+lexicographic merge, padding and inner products included."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    from paper_2405_12497_gb300 import build, rabitq
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    build.build()
+    return rabitq
+
+
+def test_shard_partition_is_balanced(R):
+    sizes = np.array([50, 10, 40, 40, 30, 20, 5, 5], np.int32)
+    shard_of, pts = R.shard_clusters(sizes, 3)
+    assert pts.sum() == sizes.sum()
+    for s in range(3):
+        assert pts[s] == sizes[shard_of == s].sum()
+    assert pts.max() - pts.min() <= sizes.max()
+
+
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+def test_merge_topk_equals_host_merge(R, metric):
+    import torch
+    rng = np.random.default_rng(3)
+    L, nq, kin, k = 3, 17, 12, 20
+    d = rng.integers(0, 40, (L, nq, kin)).astype(np.float32)   # many ties
+    d = np.sort(d, 2) if metric == "l2" else -np.sort(-d, 2)
+    ids = rng.integers(0, 1000, (L, nq, kin)).astype(np.int64)
+    ids[0, 3, 8:] = -1                                             # padding
+    d[0, 3, 8:] = np.inf if metric == "l2" else -np.inf
+    labels = [torch.arange(1000, dtype=torch.int64).cuda() * (i + 2) for i in range(L)]
+    oi, od = R.merge_topk(torch.from_numpy(d).cuda(), torch.from_numpy(ids).cuda(), k, labels,
+                          metric)
+    oi, od = oi.cpu().numpy(), od.cpu().numpy()
+    for q in range(nq):
+        gi = np.concatenate([np.where(ids[l, q] >= 0, ids[l, q] * (l + 2), -1) for l in range(L)])
+        gd = np.concatenate([d[l, q] for l in range(L)])
+        ok = gi >= 0
+        score = gd[ok] if metric == "l2" else -gd[ok]
+        order = np.lexsort((gi[ok], score))[:k]
+        n = len(order)
+        assert np.array_equal(oi[q, :n], gi[ok][order])
+        assert np.array_equal(od[q, :n], gd[ok][order])
+        assert (oi[q, n:] == -1).all()
+
+
+@pytest.mark.parametrize("n_shards", [2, 3])
+def test_sharded_search_equals_unsharded(R, oracle_mod, tiny_workload, n_shards):
+    import torch
+    data, Q = tiny_workload
+    qd = torch.from_numpy(Q).cuda()
+    G = R.Index.build(data, 16, seed=2)
+    SH = R.ShardedIndex.build(torch.from_numpy(data).cuda(), 16, n_shards, seed=2)
+    assert sum(int(sh.n) for sh in SH.shards) == len(data)
+    for k, nprobe in ((10, 4), (100, 16)):
+        ids_s, dist_s = SH.search(qd, k, nprobe)
+        ids_g, dist_g = G.search(qd, k, nprobe)
+        ids_s, dist_s = ids_s.cpu().numpy(), dist_s.cpu().numpy()
+        ids_g, dist_g = ids_g.cpu().numpy(), dist_g.cpu().numpy()
+        same = (ids_s == ids_g).all(1)
+        assert np.array_equal(dist_s[same].view(np.uint32), dist_g[same].view(np.uint32))
+        O = oracle_mod.OracleIndex(data, K=16, seed=2)
+        for qi in np.flatnonzero(~same):   # explained by a failed bound
+            t = O.trace(Q[qi], int(qi), k, nprobe)
+            ex = oracle_mod.sqdist_matrix(Q[qi:qi + 1], O.data[t["pair_id"]])[0]
+            assert ((t["pair_est"][:, 1] > ex) | (t["pair_est"][:, 2] < ex)).any()
+        assert same.mean() >= 0.9
+    SH.free()
