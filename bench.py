@@ -289,6 +289,9 @@ def run_ours(args, rank, world):
     deep = None
     if args.metric == "l2" and args.workload == "sift" and not args.no_deep:
         deep = deep_legs(args, flush, stream, dist, hbm, src)
+    serving = None
+    if args.metric == "l2" and args.workload == "sift" and not args.no_serving and world == 1:
+        serving = serving_study(args, n_req=600)
 
     parity = None
     cpu = None
@@ -343,6 +346,8 @@ def run_ours(args, rank, world):
         res["parity"] = parity
     if deep is not None:
         res["learned_nprobe_config"] = deep
+    if serving is not None:
+        res["serving"] = serving
     if rank == 0:
         print(json.dumps(res), flush=True)
     if dist:
@@ -1259,110 +1264,130 @@ def run_estimate_study(args):
     print(json.dumps(res), flush=True)
 
 
-def run_serving_study(args):
-    """A serving loop on one GPU: three resident indices (1M x 128 SIFT-shaped,
-    1M x 420 and 1M x 960 GIST-shaped recipes, K = 4096), each with a trained
-    probe-count predictor and a search plan per k in {10, 100} (CUDA-graph
-    replay per batch size); a Poisson stream of requests, each a batch of 1..256
-    queries for a random index and k, admitted when the device has room for
-    its buffers, served in arrival order on one stream. Reports p50 / p99
-    latency (arrival to results on the host), QPS and recall@k."""
+def serving_study(args, n_req=1000, n=None, warm=True):
+    """The serving configuration through the library's serving runtime
+    (rabitq_server_*): three resident 1M-point indices (128-d SIFT-shaped,
+    420-d and 960-d GIST-shaped recipes, K = 4096), each with a trained
+    probe-count predictor (learned nprobe); a Poisson stream of requests of
+    1-256 queries for a random index and k in {10, 100}, submitted by a client
+    thread at their arrival times. The server batches the requests queued for
+    one (index, k) into one plan replay, admits a request only when its
+    queries fit the device staging budget (refused requests are counted and
+    dropped), and copies results to the host before completing them.
+    Latency = arrival to results on the host (the client's lateness in
+    submitting plus the server's submit-to-host time); p50 / p99, QPS,
+    recall@k, batches and admission counts are reported."""
     import torch
-    from paper_2405_12497_gb300 import build as B
     from paper_2405_12497_gb300 import rabitq
-    B.build()
     rng = np.random.default_rng(11)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     specs = [("sift-like-1M-d128", synth.SIFT_LIKE),
              ("gist-like-1M-d420", synth.dataclasses_replace(synth.GIST_LIKE, d=420, code_bits=448,
                                                                name="gist-like-1M-d420")),
              ("gist-like-1M-d960", synth.GIST_LIKE)]
-    n = args.n or 1_000_000
+    n = n or 1_000_000
     pool = 2000
     idx = []
     for name, w in specs:
         w = synth.dataclasses_replace(w, n=n, nq=pool)
         data, queries = synth.make(w)
         dd = torch.from_numpy(data).to(dev)
-        qd = torch.from_numpy(queries).to(dev)
         G = rabitq.Index.build(dd, w.n_clusters, seed=2, code_bits=w.code_bits)
-        gt = exact_knn(dd, qd, 100)
+        gt = exact_knn(dd, torch.from_numpy(queries).to(dev), 100)
         _, tq = synth.make(w, nq=20_000, seed_query=7, with_data=False)
         pr = rabitq.Predictor.train(G, torch.from_numpy(tq).to(dev), k=100, target_recall=TARGET,
                                     nprobe_max=256, epochs=10)
-        # raise the multiplier until the pool reaches the target at k = 100
-        mult = pr.info()["mult"]
-        for _ in range(48):
-            pr.set_mult(mult)
-            ids, _ = G.search_learned(pr, qd, 100)
-            if recall_at(ids.cpu().numpy(), gt) >= TARGET:
-                break
-            mult *= 2.0 ** 0.125
-        plans = {k: rabitq.Plan(G, k, 0, 256, predictor=pr) for k in (10, 100)}
-        idx.append({"name": name, "G": G, "pr": pr, "qd": qd, "gt": gt, "plans": plans,
-                    "mult": mult, "dd": dd})
-        del data
-    # requests
-    n_req = args.steps * 100 if args.steps else 1000
+        # calibrate the multiplier on separately drawn calibration queries
+        _, cq = synth.make(w, nq=2000, seed_query=11, with_data=False)
+        cqd = torch.from_numpy(cq).to(dev)
+        mult, _ = calibrate_mult(G, pr, cqd, exact_knn(dd, cqd, 100), w)
+        pr.set_mult(mult)
+        idx.append({"name": name, "G": G, "pr": pr, "q": queries, "gt": gt, "mult": mult})
+        del dd
+    srv = rabitq.Server(max_batch=256, mem_budget=16 << 20, batch_window_us=0.0)
+    slots = [srv.add_index(x["G"], predictor=x["pr"]) for x in idx]
     reqs = [(int(rng.integers(0, 3)), int(rng.choice([10, 100])), int(rng.integers(1, 257)))
             for _ in range(n_req)]
-    def serve(i, k, b, off):
-        pl = idx[i]["plans"][k]
-        pl.queries[:b].copy_(idx[i]["qd"][off:off + b])
-        pl.run(b)
-        out = pl.ids[:b, :k].clone()
-        pl.sync()
-        return out
+    offs = [int(rng.integers(0, pool - b + 1)) for _, _, b in reqs]
 
-    # capture every graph the stream will use, then time the service path alone
+    def one(i, k, b, off):
+        ids = np.empty((b, k), np.int64)
+        dist = np.empty((b, k), np.float32)
+        t = srv.submit(slots[i], idx[i]["q"][off:off + b], k, ids, dist)
+        return t, ids
+
+    if warm:  # capture the plans' graphs (batch sizes in steps of 16), then measure service time
+        for i in range(3):
+            for k in (10, 100):
+                for b in range(16, 257, 16):
+                    t, _ = one(i, k, b, 0)
+                    srv.wait(t)
     t0 = time.perf_counter()
-    for i, k, b in reqs:
-        serve(i, k, b, 0)
-    warm_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for i, k, b in reqs[:300]:
-        serve(i, k, b, 0)
-    sat_s = time.perf_counter() - t0
-    service = sat_s / 300
-    sat_qps = sum(b for _, _, b in reqs[:300]) / sat_s
-    rate = 0.7 / service  # 70% offered load
-    gaps = rng.exponential(1.0 / rate, n_req)
-    arrivals = np.cumsum(gaps)
-    free0, _ = torch.cuda.mem_get_info()
-    lat, results, admitted = [], [], 0
+    for i, k, b in reqs[:200]:
+        t, _ = one(i, k, b, 0)
+        srv.wait(t)
+    service = (time.perf_counter() - t0) / 200
+    sat_qps = sum(b for _, _, b in reqs[:200]) / (time.perf_counter() - t0)
+    base = srv.stats()
+    rate = 0.7 / service  # 70% of the one-at-a-time service rate
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    tickets = [None] * n_req
+    late = np.zeros(n_req)
     start = time.perf_counter()
+    refused = 0
     for r, (i, k, b) in enumerate(reqs):
         now = time.perf_counter() - start
         if now < arrivals[r]:
             time.sleep(arrivals[r] - now)
-        if r % 64 == 0:
-            free, _ = torch.cuda.mem_get_info()
-        if b * (idx[i]["G"].d * 4 + k * 12) > free:
-            continue  # not admitted: no room for the request's buffers
-        admitted += 1
-        off = int(rng.integers(0, pool - b + 1))
-        ids = serve(i, k, b, off)
-        lat.append((time.perf_counter() - start - arrivals[r]) * 1e3)
-        results.append((i, k, off, ids))
+        late[r] = time.perf_counter() - start - arrivals[r]
+        try:
+            tickets[r] = one(i, k, b, offs[r])
+        except rabitq.RabitqError as e:
+            if e.code != rabitq.EBUSY:
+                raise
+            refused += 1
+    lat, hits, totq = [], 0.0, 0
+    for r, tk in enumerate(tickets):
+        if tk is None:
+            continue
+        lat.append(srv.wait(tk[0], 120.0) / 1e3 + late[r] * 1e3)
     wall = time.perf_counter() - start
-    hits, totq = 0.0, 0
-    for i, k, off, ids in results:  # recall, outside the timed loop
-        got = ids.cpu().numpy()
-        gt = idx[i]["gt"][off:off + got.shape[0], :k]
-        hits += sum(len(np.intersect1d(a, g)) / k for a, g in zip(got, gt))
-        totq += got.shape[0]
-    out = {"study": "serving loop", "indices": [x["name"] for x in idx], "requests": n_req,
-           "admitted": admitted, "batch": "uniform 1..256", "k": [10, 100],
-           "offered_load": 0.7, "arrival_rate_per_s": round(rate, 1),
+    for r, tk in enumerate(tickets):
+        if tk is None:
+            continue
+        i, k, b = reqs[r]
+        gt = idx[i]["gt"][offs[r]:offs[r] + b, :k]
+        hits += sum(len(np.intersect1d(a, g)) / k for a, g in zip(tk[1], gt))
+        totq += b
+    st = srv.stats()
+    out = {"study": "serving loop (library serving runtime)", "indices": [x["name"] for x in idx],
+           "requests": n_req, "admitted": st["admitted"] - base["admitted"], "refused": refused,
+           "batches": st["batches"] - base["batches"],
+           "mean_requests_per_batch": round((st["batched_requests"] - base["batched_requests"]) /
+                                            max(1, st["batches"] - base["batches"]), 3),
+           "batch": "requests of 1..256 queries", "k": [10, 100], "offered_load": 0.7,
+           "arrival_rate_per_s": round(rate, 1),
            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                           "p99": round(float(np.percentile(lat, 99)), 3),
-                          "mean": round(float(np.mean(lat)), 3)},
-           "qps": round(totq / wall, 1), "recall_at_k": round(float(hits / totq), 4),
-           "mean_service_ms": round(service * 1e3, 3), "saturated_qps": round(sat_qps, 1),
-           "graph_capture_s": round(warm_s, 2),
-           "free_device_memory_gb": round(free0 / 1e9, 1),
+                          "mean": round(float(np.mean(lat)), 3),
+                          "measured": "arrival to results in the caller's host buffers"},
+           "qps": round(totq / wall, 1), "recall_at_k": round(float(hits / max(totq, 1)), 4),
+           "mean_service_ms_one_at_a_time": round(service * 1e3, 3),
+           "saturated_qps_one_at_a_time": round(sat_qps, 1),
+           "staging_budget_mb": 16, "peak_staging_mb": round(st["peak_in_flight_bytes"] / 2**20, 2),
            "multipliers": {x["name"]: round(x["mult"], 4) for x in idx}}
-    print(json.dumps(out), flush=True)
+    srv.free()
+    for x in idx:
+        x["G"].free()
+        x["pr"].free()
+    return out
+
+
+def run_serving_study(args):
+    from paper_2405_12497_gb300 import build as B
+    B.build()
+    print(json.dumps(serving_study(args, n_req=args.steps * 100 if args.steps else 1000,
+                                   n=args.n)), flush=True)
 
 
 def main():
@@ -1388,6 +1413,7 @@ def main():
     ap.add_argument("--no-deep", action="store_true",
                     help="skip the learned-nprobe configuration (10M x 256 DEEP-shaped)")
     ap.add_argument("--deep-train-nq", type=int, default=200_000)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop study")
     ap.add_argument("--parallel", default="replicas", choices=["replicas", "shards"],
                     help="multi-GPU form: query replicas (default) or bucket shards")
     ap.add_argument("--epochs", type=int, default=20)

@@ -40,7 +40,8 @@ typedef enum {
   RABITQ_ETIMEOUT = -4,     /* a bounded device wait expired                  */
   RABITQ_EIO = -5,          /* file missing, truncated or corrupt             */
   RABITQ_EUNSUPPORTED = -6, /* option not supported on this device/build      */
-  RABITQ_EOVERFLOW = -7     /* a query's candidate list exceeded its capacity */
+  RABITQ_EOVERFLOW = -7,    /* a query's candidate list exceeded its capacity */
+  RABITQ_EBUSY = -8         /* a server refused a request: budget exhausted   */
 } rabitq_status;
 
 /* Precision of the query rotation P^{-1} q (§3.3 of the paper). FP32 is the
@@ -547,6 +548,61 @@ int rabitq_shard_clusters(const int32_t* sizes, int32_t K, int32_t S, int32_t* s
 int rabitq_merge_topk(const float* dist, const int64_t* ids, int32_t n_lists, int64_t nq,
                       int32_t k_in, int32_t k, const int64_t* const* labels, int32_t metric,
                       int64_t* out_ids, float* out_dist, void* stream);
+
+/*
+ * ---- Serving runtime (not in the paper: §5 measures one query at a time) --
+ *
+ * A server holds resident indices and answers requests -- a batch of nq
+ * queries for one index and one k -- submitted from any host thread. A
+ * worker thread runs the queued requests of one (index, k) together as one
+ * search-plan replay of up to max_batch queries (the oldest request first,
+ * then every queued request of the same index and k that still fits, in
+ * arrival order), and copies each request's results to its host buffers
+ * before completing it. Admission is by device memory: a request's queries
+ * are copied into a staging pool of mem_budget bytes when it is submitted
+ * and stay there until its batch has run; a request that does not fit the
+ * free pool is refused with RABITQ_EBUSY (retry or drop it). The indices and
+ * predictors must outlive the server; add every index before submitting.
+ *   max_batch        queries per batch and per request (default 256)
+ *   mem_budget       staging pool bytes (default 64 MiB)
+ *   batch_window_us  how long a lone queued request may wait for company
+ *                    before it runs (default 0: it runs at once)
+ * rabitq_server_add_index: nprobe (1..K) for a fixed probe count, or a
+ *   predictor for learned counts (nprobe then ignored); slot receives the
+ *   index's number for rabitq_server_submit.
+ * rabitq_server_submit: queries (host, nq x d) are copied before it returns
+ *   the ticket; out_ids / out_dist (host, nq x k) must stay valid until the
+ *   request completes. Errors: EINVAL, EBUSY, ECUDA.
+ * rabitq_server_wait: blocks until the request completes or timeout_s
+ *   passes (ETIMEOUT); latency_us (may be NULL) receives the time from
+ *   submission to results on the host. A completed ticket is released.
+ *   The request's search errors (EOVERFLOW, ETIMEOUT, ...) are returned here.
+ * rabitq_server_free: finishes the queued requests, then frees everything.
+ */
+typedef struct rabitq_server rabitq_server;
+typedef struct {
+  int32_t max_batch;
+  int64_t mem_budget;
+  float batch_window_us;
+} rabitq_server_opts;
+typedef struct {
+  int64_t admitted, refused;          /* requests                           */
+  int64_t batches;                    /* plan replays run                   */
+  int64_t batched_requests, batched_queries;
+  int64_t in_flight_bytes, peak_in_flight_bytes;  /* staging pool use     */
+} rabitq_server_stats;
+
+void rabitq_server_opts_default(rabitq_server_opts* opts);
+int rabitq_server_create(const rabitq_server_opts* opts, rabitq_server** out);
+int rabitq_server_add_index(rabitq_server* server, const rabitq_index* idx,
+                            const rabitq_predictor* predictor, int32_t nprobe, int32_t bq,
+                            float eps0, int32_t* slot);
+int rabitq_server_submit(rabitq_server* server, int32_t slot, const float* queries, int64_t nq,
+                         int32_t k, int64_t* out_ids, float* out_dist, int64_t* ticket);
+int rabitq_server_wait(rabitq_server* server, int64_t ticket, double timeout_s,
+                       double* latency_us);
+int rabitq_server_get_stats(rabitq_server* server, rabitq_server_stats* out);
+void rabitq_server_free(rabitq_server* server);
 
 /* Sizes of an index: n, d, D' (code bits), K. Any pointer may be NULL. */
 int rabitq_index_info(const rabitq_index* idx, int64_t* n, int32_t* d, int32_t* d_pad,

@@ -18,6 +18,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = [
     "api.cu", "api_predictor.cu", "kernels_gemm.cu", "kernels_build.cu", "kernels_search.cu",
     "kernels_tc.cu", "kernels_mlp.cu", "noalloc.cu", "plan.cu", "shard.cu",
+    "server.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-Wshadow", "--expt-relaxed-constexpr"]

@@ -17,6 +17,7 @@ _LIB_PATH = os.path.join(_HERE, "librabitq.so")
 _lib = None
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EIO, EUNSUPPORTED, EOVERFLOW = 0, -1, -2, -3, -4, -5, -6, -7
+EBUSY = -8
 ROT_FP32, ROT_TF32, ROT_BF16 = 0, 1, 2
 SCAN_AUTO, SCAN_POPC, SCAN_TC = 0, 1, 2
 LAYOUT_AUTO, LAYOUT_CTA, LAYOUT_WARP = 0, 1, 2
@@ -38,7 +39,9 @@ EXPORTS = (
     "rabitq_plan_create", "rabitq_plan_buffers", "rabitq_plan_run", "rabitq_plan_sync",
     "rabitq_plan_search", "rabitq_plan_free", "rabitq_plan_stats", "rabitq_index_metric",
     "rabitq_estimate", "rabitq_autotune_tiles", "rabitq_plan_tile", "rabitq_shard_clusters",
-    "rabitq_merge_topk",
+    "rabitq_merge_topk", "rabitq_server_opts_default", "rabitq_server_create",
+    "rabitq_server_add_index", "rabitq_server_submit", "rabitq_server_wait",
+    "rabitq_server_get_stats", "rabitq_server_free",
 )
 
 MLP_IN, MLP_HIDDEN = 64, 256
@@ -161,6 +164,13 @@ def lib():
             "rabitq_plan_tile": (C.c_int, [vp, vp]),
             "rabitq_shard_clusters": (C.c_int, [vp, i32, i32, vp, vp]),
             "rabitq_merge_topk": (C.c_int, [vp, vp, i32, i64, i32, i32, vp, i32, vp, vp, vp]),
+            "rabitq_server_opts_default": (None, [vp]),
+            "rabitq_server_create": (C.c_int, [vp, vp]),
+            "rabitq_server_add_index": (C.c_int, [vp, vp, vp, i32, i32, f32, vp]),
+            "rabitq_server_submit": (C.c_int, [vp, i32, vp, i64, i32, vp, vp, vp]),
+            "rabitq_server_wait": (C.c_int, [vp, i64, C.c_double, vp]),
+            "rabitq_server_get_stats": (C.c_int, [vp, vp]),
+            "rabitq_server_free": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -822,3 +832,72 @@ class ShardedIndex:
     def free(self):
         for sh in self.shards:
             sh.free()
+
+
+# -------------------------------------------------------------- serving runtime
+class ServerOpts(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("mem_budget", C.c_int64),
+                ("batch_window_us", C.c_float)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("admitted", C.c_int64), ("refused", C.c_int64), ("batches", C.c_int64),
+                ("batched_requests", C.c_int64), ("batched_queries", C.c_int64),
+                ("in_flight_bytes", C.c_int64), ("peak_in_flight_bytes", C.c_int64)]
+
+
+class Server:
+    """The library's serving runtime (rabitq_server_*): resident indices,
+    requests batched per (index, k) into plan replays, admission by a device
+    staging budget, results copied to host buffers."""
+
+    def __init__(self, max_batch: int = 256, mem_budget: int = 64 << 20,
+                 batch_window_us: float = 0.0):
+        o = ServerOpts()
+        lib().rabitq_server_opts_default(C.byref(o))
+        o.max_batch, o.mem_budget, o.batch_window_us = max_batch, mem_budget, batch_window_us
+        h = C.c_void_p()
+        _check(lib().rabitq_server_create(C.byref(o), C.byref(h)))
+        self._h = h
+        self._keep = []
+
+    def add_index(self, index: Index, nprobe: int = 0, predictor: "Predictor | None" = None,
+                  bq: int = 4, eps0: float = 1.9) -> int:
+        slot = C.c_int32()
+        _check(lib().rabitq_server_add_index(self._h, index._h,
+                                             predictor._h if predictor else None, nprobe, bq,
+                                             eps0, C.byref(slot)))
+        self._keep += [index, predictor]
+        return slot.value
+
+    def submit(self, slot: int, queries, k: int, out_ids, out_dist) -> int:
+        """queries: host float32 (nq x d); out_ids / out_dist: host arrays
+        (nq x k) written when the request completes. Returns the ticket;
+        raises RabitqError with code EBUSY when refused."""
+        q = np.ascontiguousarray(queries, np.float32)
+        t = C.c_int64()
+        _check(lib().rabitq_server_submit(self._h, slot, _np_ptr(q), q.shape[0], k,
+                                          _np_ptr(out_ids), _np_ptr(out_dist), C.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> float:
+        """Block until done; returns the latency in microseconds."""
+        lat = C.c_double()
+        _check(lib().rabitq_server_wait(self._h, ticket, timeout_s, C.byref(lat)))
+        return lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().rabitq_server_get_stats(self._h, C.byref(st)))
+        return {f: int(getattr(st, f)) for f, _ in ServerStats._fields_}
+
+    def free(self):
+        if self._h:
+            lib().rabitq_server_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
