@@ -286,6 +286,10 @@ def run_ours(args, rank, world):
     e2e_rec = recall_at(ih, gt)
     latency = batch1_latency(G, bplan_args(best_name, legs, chosen), qd, w, flush)
 
+    eps0_curve = None
+    if args.metric == "l2" and rank == 0:
+        eps0_curve = {"queries": 100, "k": w.k, "nprobe": "all buckets (every vector estimated)",
+                      "recall": eps0_recall_curve(G, dd, qd[:100], w.k, gt[:100])}
     deep = None
     if args.metric == "l2" and args.workload == "sift" and not args.no_deep:
         deep = deep_legs(args, flush, stream, dist, hbm, src)
@@ -348,6 +352,8 @@ def run_ours(args, rank, world):
         res["learned_nprobe_config"] = deep
     if serving is not None:
         res["serving"] = serving
+    if eps0_curve is not None:
+        res["eps0_recall"] = eps0_curve
     if rank == 0:
         print(json.dumps(res), flush=True)
     if dist:
@@ -1175,7 +1181,7 @@ def run_accuracy_study(args):
     eps_grid = (0.5, 1.0, 1.5, 1.9, 2.5, 3.0, 4.0)
     out = {"study": "distance-estimation accuracy", "workload": f"sift-like n={n} d={w.d}",
            "n_clusters": w.n_clusters, "queries": 50, "nprobe": 16, "rows": []}
-    for cb in (128, 256, 512):
+    for cb in (128, 256, 512, 1024):
         G = rabitq.Index.build(data, w.n_clusters, seed=2, code_bits=cb)
         for bq in (1, 2, 3, 4, 5, 6, 8):
             t = G.search_trace(qd, 10, 16, bq=bq, eps0=1.9, pair_cap=16384)
@@ -1199,7 +1205,37 @@ def run_accuracy_study(args):
                                 "fit_slope": float(slope), "fit_intercept_rel": float(icpt / ex.mean()),
                                 "bound_coverage": cover})
         G.free()
+    # the paper's eps0 study (§5.2.4): every vector estimated (all buckets
+    # probed), recall@100 of the error-bound re-ranking for eps0 in [0, 4]
+    curves = {}
+    for name, wl in (("sift-like", synth.dataclasses_replace(synth.SIFT_LIKE, n=n, nq=200,
+                                                               n_clusters=max(64, n // 244))),
+                     ("gist-like", synth.dataclasses_replace(synth.GIST_LIKE, n=n, nq=200,
+                                                               n_clusters=max(64, n // 244)))):
+        dd, qq = synth.make(wl)
+        G = rabitq.Index.build(dd, wl.n_clusters, seed=2, code_bits=wl.code_bits)
+        curves[name] = eps0_recall_curve(G, torch.from_numpy(dd).cuda(),
+                                         torch.from_numpy(qq).cuda(), 100)
+        G.free()
+    out["eps0_recall_all_vectors_estimated"] = curves
     print(json.dumps(out), flush=True)
+
+
+EPS0_GRID = (0.0, 0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75, 1.9, 2.0, 2.25, 2.5, 3.0, 3.5, 4.0)
+
+
+def eps0_recall_curve(G, dd, qd, k, gt=None):
+    """Recall@k when every vector of the index is estimated (nprobe = K)
+    and the error-bound re-ranking decides which get exact distances, for
+    eps0 from 0 to 4 (the paper's eps0 verification, §5.2.4): a true
+    neighbour is missed only when it is not re-ranked."""
+    if gt is None:
+        gt = exact_knn(dd, qd, k)
+    out = {}
+    for e in EPS0_GRID:
+        ids, _ = G.search(qd, k, G.K, eps0=e, max_candidates=min(1 << 20, max(4096, G.n)))
+        out[str(e)] = round(recall_at(ids.cpu().numpy(), gt), 4)
+    return out
 
 
 def run_estimate_study(args):
