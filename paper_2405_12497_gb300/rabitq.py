@@ -256,6 +256,10 @@ class Index:
             opts.data_on_device = 1
             ptr = _dptr(data)
             if centroids is not None:
+                if not _is_torch(centroids):  # same memory kind as the data
+                    import torch
+                    centroids = torch.from_numpy(np.ascontiguousarray(centroids, np.float32)).to(
+                        data.device)
                 centroids = centroids.contiguous()
                 opts.centroids = _dptr(centroids)
         else:
