@@ -1350,17 +1350,17 @@ def serving_study(args, n_req=1000, n=None, warm=True):
         ids = np.empty((b, k), np.int64)
         dist = np.empty((b, k), np.float32)
         t = srv.submit(slots[i], idx[i]["q"][off:off + b], k, ids, dist)
-        return t, ids
+        return t, ids, dist  # the buffers live until the request is waited for
 
     if warm:  # capture the plans' graphs (batch sizes in steps of 16), then measure service time
         for i in range(3):
             for k in (10, 100):
                 for b in range(16, 257, 16):
-                    t, _ = one(i, k, b, 0)
+                    t, _, _ = one(i, k, b, 0)
                     srv.wait(t)
     t0 = time.perf_counter()
     for i, k, b in reqs[:200]:
-        t, _ = one(i, k, b, 0)
+        t, _, _ = one(i, k, b, 0)
         srv.wait(t)
     service = (time.perf_counter() - t0) / 200
     sat_qps = sum(b for _, _, b in reqs[:200]) / (time.perf_counter() - t0)

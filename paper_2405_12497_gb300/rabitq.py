@@ -8,6 +8,7 @@ library cannot be loaded this module raises -- there is no fallback.
 from __future__ import annotations
 
 import ctypes as C
+import threading
 import os
 
 import numpy as np
@@ -864,6 +865,8 @@ class Server:
         _check(lib().rabitq_server_create(C.byref(o), C.byref(h)))
         self._h = h
         self._keep = []
+        self._pending = {}  # ticket -> output buffers the server still writes
+        self._mu = threading.Lock()
 
     def add_index(self, index: Index, nprobe: int = 0, predictor: "Predictor | None" = None,
                   bq: int = 4, eps0: float = 1.9) -> int:
@@ -879,15 +882,25 @@ class Server:
         (nq x k) written when the request completes. Returns the ticket;
         raises RabitqError with code EBUSY when refused."""
         q = np.ascontiguousarray(queries, np.float32)
+        if not (out_ids.flags.c_contiguous and out_dist.flags.c_contiguous and
+                out_ids.dtype == np.int64 and out_dist.dtype == np.float32 and
+                out_ids.size >= q.shape[0] * k and out_dist.size >= q.shape[0] * k):
+            raise ValueError("out_ids / out_dist: contiguous int64 / float32 of nq x k")
         t = C.c_int64()
-        _check(lib().rabitq_server_submit(self._h, slot, _np_ptr(q), q.shape[0], k,
-                                          _np_ptr(out_ids), _np_ptr(out_dist), C.byref(t)))
+        with self._mu:  # the buffers stay referenced until the request completes
+            _check(lib().rabitq_server_submit(self._h, slot, _np_ptr(q), q.shape[0], k,
+                                              _np_ptr(out_ids), _np_ptr(out_dist), C.byref(t)))
+            self._pending[t.value] = (out_ids, out_dist)
         return t.value
 
     def wait(self, ticket: int, timeout_s: float = 60.0) -> float:
         """Block until done; returns the latency in microseconds."""
         lat = C.c_double()
-        _check(lib().rabitq_server_wait(self._h, ticket, timeout_s, C.byref(lat)))
+        code = lib().rabitq_server_wait(self._h, ticket, timeout_s, C.byref(lat))
+        if code != ETIMEOUT:  # done (or unknown): the server no longer writes them
+            with self._mu:
+                self._pending.pop(ticket, None)
+        _check(code)
         return lat.value
 
     def stats(self) -> dict:
@@ -897,8 +910,9 @@ class Server:
 
     def free(self):
         if self._h:
-            lib().rabitq_server_free(self._h)
+            lib().rabitq_server_free(self._h)  # finishes the queued requests first
             self._h = C.c_void_p()
+            self._pending.clear()
 
     def __del__(self):
         try:
