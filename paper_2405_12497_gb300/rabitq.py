@@ -885,7 +885,7 @@ class Server:
         if not (out_ids.flags.c_contiguous and out_dist.flags.c_contiguous and
                 out_ids.dtype == np.int64 and out_dist.dtype == np.float32 and
                 out_ids.size >= q.shape[0] * k and out_dist.size >= q.shape[0] * k):
-            raise ValueError("out_ids / out_dist: contiguous int64 / float32 of nq x k")
+            raise RabitqError(EINVAL, "out_ids / out_dist: contiguous int64 / float32 of nq x k")
         t = C.c_int64()
         with self._mu:  # the buffers stay referenced until the request completes
             _check(lib().rabitq_server_submit(self._h, slot, _np_ptr(q), q.shape[0], k,
