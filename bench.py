@@ -1426,6 +1426,50 @@ def run_serving_study(args):
                                    n=args.n)), flush=True)
 
 
+def run_profile(args):
+    """Small, self-contained launches for ncu captures (the launch sizes the
+    profiling rules allow; not benchmark lines):
+      cold  a DEEP-shaped index of --n points (default 3M: 144 MB of codes
+            and factors, above L2), K = n / 610, --nq queries (default 2000)
+            at nprobe 128, L2 flushed before each plan replay;
+      tc    the SIFT-shaped 1M index, --nq queries (default 2000): one search
+            with the TF32 tensor-core rotation and the tensor-core scan path
+            (the probe products, the rotation and the bucket-major product)."""
+    import torch
+    from paper_2405_12497_gb300 import build as B
+    from paper_2405_12497_gb300 import rabitq
+    B.build()
+    dev = torch.device("cuda", 0)
+    nq = args.nq or 2000
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    if args.profile == "cold":
+        n = args.n or 3_000_000
+        dd, qd = synth.deep_like_device(n, nq, dev, sigma=DEEP_SIGMA)
+        K = max(64, n // 610)
+        G = rabitq.Index.build(dd, K, seed=2, kmeans_iters=10, kmeans_sample=256 * K)
+        del dd
+        torch.cuda.empty_cache()
+        plan = rabitq.Plan(G, 100, 128, nq, max_candidates=1 << 18, stats=True)
+        plan.queries.copy_(qd)
+        for _ in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            plan.run(nq)
+        plan.sync()
+        print(json.dumps({"profile": "cold", "n": n, "K": K, "nq": nq, "nprobe": 128,
+                          "fused_ms": float(plan.stats()[3]), "tile": plan.tile()}))
+    else:
+        w = synth.dataclasses_replace(synth.SIFT_LIKE, nq=nq)
+        data, queries = synth.make(w)
+        G = rabitq.Index.build(torch.from_numpy(data).to(dev), w.n_clusters, seed=2)
+        qd = torch.from_numpy(queries).to(dev)
+        for _ in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            G.search(qd, w.k, 64, rot_precision=rabitq.ROT_TF32, scan_path=rabitq.SCAN_TC,
+                     max_candidates=1 << 18)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "tc", "nq": nq, "nprobe": 64}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1450,6 +1494,8 @@ def main():
                     help="skip the learned-nprobe configuration (10M x 256 DEEP-shaped)")
     ap.add_argument("--deep-train-nq", type=int, default=200_000)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop study")
+    ap.add_argument("--profile", default=None, choices=["cold", "tc"],
+                    help="run a small launch for an ncu capture instead of the benchmark")
     ap.add_argument("--parallel", default="replicas", choices=["replicas", "shards"],
                     help="multi-GPU form: query replicas (default) or bucket shards")
     ap.add_argument("--epochs", type=int, default=20)
@@ -1467,6 +1513,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args)
+        return
+    if args.profile:
+        if rank == 0:
+            run_profile(args)
         return
     if args.study == "accuracy":
         if rank == 0:
