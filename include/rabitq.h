@@ -73,7 +73,8 @@ enum { RABITQ_LAYOUT_AUTO = 0, RABITQ_LAYOUT_CTA = 1, RABITQ_LAYOUT_WARP = 2 };
  * round's codes and factors are copied into shared memory by the bulk-copy
  * (TMA) engine while the block evaluates the round before (BULK), or loaded
  * by every thread on its own (OFF). AUTO follows rabitq_autotune_tiles'
- * choice, else BULK. Results are identical either way. */
+ * choice, else OFF (the faster of the two on the shapes measured). Results
+ * are identical either way. */
 enum { RABITQ_STAGING_AUTO = 0, RABITQ_STAGING_OFF = 1, RABITQ_STAGING_BULK = 2 };
 
 typedef struct {

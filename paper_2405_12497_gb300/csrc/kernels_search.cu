@@ -3275,8 +3275,8 @@ void resolve_tile(const rabitq_index* X, int k, int nprobe, int32_t* path, int32
                       : (X->tuned_layout ? X->tuned_layout
                                          : (k <= 32 ? RABITQ_LAYOUT_WARP : RABITQ_LAYOUT_CTA));
   if (*ppl == 0) *ppl = t.valid ? t.ppl : 0;
-  if (*stage == RABITQ_STAGING_AUTO)
-    *stage = t.valid && t.stage ? t.stage : RABITQ_STAGING_BULK;
+  if (*stage == RABITQ_STAGING_AUTO)  // bulk staging measured slower on GB300 (tuner only)
+    *stage = t.valid && t.stage ? t.stage : RABITQ_STAGING_OFF;
 }
 
 int search_dev(const SearchArgs& a_in, cudaStream_t s) {
