@@ -766,11 +766,38 @@ __device__ __forceinline__ float score_step(float acc, float q, float x) {
 
 // Canonical exact score of row x against the query qv (shared memory), in
 // ascending dimension order: ||q - x||^2, or -<q, x> for inner products.
-// 16-byte loads, eight in flight, when d is a multiple of 4.
+// 32-byte loads, four in flight, when d is a multiple of 8 (rows, in
+// cudaMalloc'ed arrays, then start on 32-byte boundaries); 16-byte loads,
+// eight in flight, when d is a multiple of 4.
 template <bool IP>
 __device__ __forceinline__ float row_score(const float* __restrict__ x, const float* qv, int d) {
   float acc = 0.0f;
-  if ((d & 3) == 0) {
+  if ((d & 7) == 0) {
+    int c = 0;
+    for (; c + 32 <= d; c += 32) {
+      unsigned long long v[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+                     : "=l"(v[u][0]), "=l"(v[u][1]), "=l"(v[u][2]), "=l"(v[u][3])
+                     : "l"(x + c + 8 * u));
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          acc = score_step<IP>(acc, qv[c + 8 * u + e],
+                               __int_as_float((int)(uint32_t)(v[u][e >> 1] >> (32 * (e & 1)))));
+    }
+    for (; c < d; c += 8) {
+      unsigned long long v[4];
+      asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+                   : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3])
+                   : "l"(x + c));
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        acc = score_step<IP>(acc, qv[c + e], __int_as_float((int)(uint32_t)(v[e >> 1] >> (32 * (e & 1)))));
+    }
+  } else if ((d & 3) == 0) {
     const float4* x4 = reinterpret_cast<const float4*>(x);
     const float4* q4 = reinterpret_cast<const float4*>(qv);
     int c = 0;
@@ -1108,7 +1135,7 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
   float* od = out_dist + (int64_t)q * nprobe;
   if (nc <= kProbeCandMax) {
     // canonical scores of the candidates (one thread each, the full scan's
-    // fold, 16-byte loads eight in flight)
+    // fold)
     for (int i = tid; i < nc; i += blockDim.x) {
       const int c = (int)(uint32_t)ckey[i];
       const float* x = C + (int64_t)c * d;
@@ -1293,7 +1320,11 @@ struct CodeRegs {
 
 template <int WT>
 __device__ __forceinline__ void load_code(CodeRegs<WT>& r, const uint64_t* __restrict__ code) {
-  if constexpr (WT > 0) {
+  if constexpr (WT == 4) {  // one 32-byte load (codes are 32-byte aligned)
+    asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+                 : "=l"(r.c[0]), "=l"(r.c[1]), "=l"(r.c[2]), "=l"(r.c[3])
+                 : "l"(code));
+  } else if constexpr (WT > 0) {
     if constexpr (WT % 2 == 0) {
 #pragma unroll
       for (int w = 0; w < WT; w += 2) {
@@ -1347,7 +1378,34 @@ __device__ __forceinline__ int code_ip(const CodeRegs<WT>& r, const uint64_t* __
   }
 }
 
-constexpr int kPPT = 4;  // most pairs per thread per scan round (buffer sizing)
+// <x_b, q_u> of two codes of the same probe: each plane word is read from
+// shared memory once for both (D' = 128 / 256, B_q = 4).
+template <int WT>
+__device__ __forceinline__ void code_ip2(const CodeRegs<WT>& r0, const CodeRegs<WT>& r1,
+                                         const uint64_t* pl, int& i0, int& i1) {
+  i0 = 0;
+  i1 = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    uint64_t pw[WT];
+#pragma unroll
+    for (int w = 0; w < WT; w += 2) {
+      const uint4 v = *reinterpret_cast<const uint4*>(pl + b * WT + w);
+      pw[w] = ((uint64_t)v.y << 32) | v.x;
+      pw[w + 1] = ((uint64_t)v.w << 32) | v.z;
+    }
+    int p0 = 0, p1 = 0;
+#pragma unroll
+    for (int w = 0; w < WT; ++w) {
+      p0 += __popcll(r0.c[w] & pw[w]);
+      p1 += __popcll(r1.c[w] & pw[w]);
+    }
+    i0 += p0 << b;
+    i1 += p1 << b;
+  }
+}
+
+constexpr int kPPT = 4;  // most appends per thread between two buffer upkeeps (sizing)
 
 // Pairs per thread per round: two (four cost spills at the four-CTA register
 // budget), one for codes longer than 512 bits.
@@ -1541,9 +1599,18 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
         if (wid == 0 && total > 0) stage_issue<WT>(P, S, stg, s_bar, 0, min(step, total), npc, 0, step);
       }
       int rnd = 0;
-      // each thread takes PPT consecutive pairs per round (mostly of one
-      // probe); the probe's bit-planes are read from shared memory (holding
-      // them in registers cost spills at the four-CTA register budget)
+      // Pairs of a round. Direct loads: warp w takes the block [base + 32 PPT w,
+      // base + 32 PPT (w + 1)) and lane l its pairs l, l + 32, ..., so that
+      // each load instruction of a warp covers consecutive codes; a block
+      // inside one probe (the usual case) shares that probe's position,
+      // bit-planes and bounds across the warp, and each plane word is read
+      // once for a thread's two pairs. Staged rounds: thread tid takes the
+      // stage slots tid PPT ... The warps run unsynchronized between the
+      // buffer upkeep points (every kUpkeep rounds, every round when staged);
+      // the buffers have room for the appends in between.
+      constexpr int kUpkeep = STG ? 1 : 2;
+      static_assert(kUpkeep * PPT <= kPPT, "buffer room between upkeeps");
+      const bool tracing = P.tr.pair_id != nullptr;
       for (int base = 0; base < total; base += step, ++rnd) {
         const int buf = rnd & 1;
         if constexpr (STG) {
@@ -1556,33 +1623,33 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
           if (!stage_wait(&s_bar[buf], (par >> buf) & 1u)) s_stg_fail = 1;
           par ^= 1u << buf;
         }
-        // issue every load of this thread's PPT pairs first (they are
-        // independent), then evaluate; keeps PPT code/factor loads in flight
-        const int t0 = base + tid * PPT;
-        int posv[PPT];
-        int jv[PPT];
+        // every load of this thread's PPT pairs is issued first (they are
+        // independent), then the pairs are evaluated
+        int posv[PPT], jv[PPT], tv[PPT], ipv[PPT];
         CodeRegs<WT> cr[PPT];
         float4 fv[PPT];
-        // consecutive pairs advance through a bucket: the prefix array is
-        // consulted again only at a bucket boundary
-        int pos = 0;
-        int next_b = 0;
+        bool one_probe = false;
+        if constexpr (STG) {
+          // consecutive pairs advance through a bucket: the prefix array is
+          // consulted again only at a bucket boundary
+          const int t0 = base + tid * PPT;
+          int pos = 0, next_b = 0;
 #pragma unroll
-        for (int pp = 0; pp < PPT; ++pp) {
-          const int t = t0 + pp;
-          posv[pp] = -1;
-          jv[pp] = 0;
-          if (t < total) {
-            if (pp == 0 || t >= next_b) {
-              while (S.pref[j + 1] <= t) ++j;
-              pos = S.pbeg[j] + (t - S.pref[j]);
-              next_b = S.pref[j + 1];
-            } else {
-              ++pos;
-            }
-            posv[pp] = pos;
-            jv[pp] = j;
-            if constexpr (STG) {
+          for (int pp = 0; pp < PPT; ++pp) {
+            const int t = t0 + pp;
+            posv[pp] = -1;
+            jv[pp] = 0;
+            tv[pp] = t;
+            if (t < total) {
+              if (pp == 0 || t >= next_b) {
+                while (S.pref[j + 1] <= t) ++j;
+                pos = S.pbeg[j] + (t - S.pref[j]);
+                next_b = S.pref[j + 1];
+              } else {
+                ++pos;
+              }
+              posv[pp] = pos;
+              jv[pp] = j;
               // this pair's slot in the round's stage (shared memory: plain
               // loads, not the read-only global path)
               const int r = t - base;
@@ -1594,26 +1661,68 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
                 cr[pp].c[w + 1] = ((uint64_t)v.w << 32) | v.z;
               }
               fv[pp] = reinterpret_cast<const float4*>(stg + (size_t)2 * step * (WT * 8))[buf * step + r];
-            } else {
+            }
+          }
+        } else {
+          const int blk = base + wid * (32 * PPT);
+          // the probe of the block's first pair; every lane's j is at most
+          // that probe, so after this walk j is the same in all lanes
+          if (blk < total)
+            while (S.pref[j + 1] <= blk) ++j;
+          one_probe = blk + 32 * PPT <= min(total, S.pref[j + 1]);  // warp-uniform
+          if (one_probe) {
+            const int p0 = S.pbeg[j] + (blk - S.pref[j]) + lane;
+#pragma unroll
+            for (int pp = 0; pp < PPT; ++pp) {
+              posv[pp] = p0 + 32 * pp;
+              jv[pp] = j;
+              tv[pp] = blk + 32 * pp + lane;
               load_code<WT>(cr[pp], P.codes + (size_t)(uint32_t)posv[pp] * (uint32_t)W);
               fv[pp] = __ldg(P.factors + (uint32_t)posv[pp]);
             }
+          } else {
+#pragma unroll
+            for (int pp = 0; pp < PPT; ++pp) {
+              const int t = blk + 32 * pp + lane;
+              posv[pp] = -1;
+              jv[pp] = 0;
+              tv[pp] = t;
+              if (t < total) {
+                while (S.pref[j + 1] <= t) ++j;
+                posv[pp] = S.pbeg[j] + (t - S.pref[j]);
+                jv[pp] = j;
+                load_code<WT>(cr[pp], P.codes + (size_t)(uint32_t)posv[pp] * (uint32_t)W);
+                fv[pp] = __ldg(P.factors + (uint32_t)posv[pp]);
+              }
+            }
           }
         }
-        // evaluate the estimator and its bounds for every pair of the round
+        // <x_b, q_u> of every pair (§3.3.2)
+        bool ip_done = false;
+        if constexpr (!STG && PPT == 2 && (WT == 2 || WT == 4) && BQT == 4) {
+          if (one_probe) {
+            code_ip2<WT>(cr[0], cr[1], S.planes + (size_t)j * (4 * WT), ipv[0], ipv[1]);
+            ip_done = true;
+          }
+        }
+        if (!ip_done) {
+#pragma unroll
+          for (int pp = 0; pp < PPT; ++pp)
+            ipv[pp] = posv[pp] < 0 ? 0
+                                   : code_ip<WT, BQT>(cr[pp], P.codes + (size_t)(uint32_t)posv[pp] * (uint32_t)W,
+                                                      S.planes + (size_t)jv[pp] * bq * W, W, bq);
+        }
+        // the estimator and its bounds for every pair of the round
         float distv[PPT], lbv[PPT], ubv[PPT];
-        int ipv[PPT];
         const float tau = s_tau;
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp) {
           distv[pp] = 0.0f;
           lbv[pp] = __int_as_float(0x7f800000);
           ubv[pp] = __int_as_float(0x7f800000);
-          ipv[pp] = 0;
           if (posv[pp] >= 0) {
             const int jj = jv[pp];
-            const int ip = code_ip<WT, BQT>(cr[pp], P.codes + (size_t)(uint32_t)posv[pp] * (uint32_t)W,
-                                            S.planes + (size_t)jj * bq * W, W, bq);
+            const int ip = ipv[pp];
             const float4 mt = S.pmeta[jj];
             const int psum = S.psum[jj];
             const float4 f = fv[pp];
@@ -1625,7 +1734,6 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
             distv[pp] = dist;
             lbv[pp] = __fsub_rn(dist, e);
             ubv[pp] = __fadd_rn(dist, e);
-            ipv[pp] = ip;
           }
         }
         // one packed warp scan reserves the slots of both buffers
@@ -1664,8 +1772,8 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
               s_overflow = 1;
             ++bc;
           }
-          if (P.tr.pair_id) {
-            const int64_t tt = pairs_done + t0 + pp;
+          if (tracing) {
+            const int64_t tt = pairs_done + tv[pp];
             if (tt < P.tr.pair_cap) {
               const int64_t o = q * P.tr.pair_cap + tt;
               P.tr.pair_id[o] = __ldg(P.perm + posv[pp]);
@@ -1676,12 +1784,13 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
             }
           }
         }
+        if (rnd % kUpkeep != kUpkeep - 1 && base + step < total) continue;
         // Buffer upkeep. The counters are read between two barriers: after
-        // every append of this round and before any append of the next, so
+        // every append before this point and before any append after it, so
         // that every thread takes the same branches (a warp that ran ahead
-        // into the next round must not change what a slower one reads).
+        // must not change what a slower one reads).
         __syncthreads();
-        const int room = step;
+        const int room = kUpkeep * step;
         const int ub_cnt = s_ub_cnt, c_cnt = s_cand_cnt;
         bool ovf = s_overflow != 0;
         __syncthreads();

@@ -240,7 +240,10 @@ def test_learned_beats_fixed_nprobe(R, oracle_mod):
     smallest multiplier 2^(i/32) whose calibration recall@100 reaches 0.955),
     then frozen and evaluated once on 2000 other (held-out) queries: both
     reach recall@100 >= 0.95 there, and the learned search probes fewer
-    buckets and runs faster (search plans, best of five) than the fixed one."""
+    buckets and runs faster (search plans, best of five) than the fixed one
+    on a batch of 8000 held-out queries (at a few thousand queries the
+    learned plan's own fixed cost, the network and its probe lists, is a
+    large share of a sub-millisecond search)."""
     import torch
     from paper_2405_12497_gb300 import synth
     w = synth.SIFT_LIKE
@@ -282,7 +285,8 @@ def test_learned_beats_fixed_nprobe(R, oracle_mod):
     ids_l, _ = idx.search_learned(pr, queries, 100)
     rec_f, rec_l = recall(ids_f, truth), recall(ids_l, truth)
     mean_np = idx.predict_nprobe(pr, queries).mean()
-    qd = torch.from_numpy(queries).cuda()
+    _, time_q = synth.make(w, n=200_000, nq=8000, seed_query=13, with_data=False)
+    qd = torch.from_numpy(time_q).cuda()
 
     def best_ms(plan):
         plan.queries.copy_(qd)
@@ -290,15 +294,15 @@ def test_learned_beats_fixed_nprobe(R, oracle_mod):
         for _ in range(6):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            plan.run(len(queries))
+            plan.run(len(time_q))
             e1.record()
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         plan.sync()
         return min(times[1:])
 
-    t_f = best_ms(R.Plan(idx, 100, fixed, len(queries)))
-    t_l = best_ms(R.Plan(idx, 100, 0, len(queries), predictor=pr))
+    t_f = best_ms(R.Plan(idx, 100, fixed, len(time_q)))
+    t_l = best_ms(R.Plan(idx, 100, 0, len(time_q), predictor=pr))
     print(f"fixed nprobe {fixed}: recall {rec_f:.4f}, {t_f:.3f} ms; learned (mult {mult:.3f}, "
           f"mean nprobe {mean_np:.1f}): recall {rec_l:.4f}, {t_l:.3f} ms")
     assert rec_f >= 0.95 and rec_l >= 0.95
