@@ -85,7 +85,7 @@ int alloc_index_arrays(rabitq_index* X) {
   X->kp = (X->d + 63) / 64 * 64;
   RBQ_CHECK(dev_alloc(reinterpret_cast<uint16_t**>(&X->ptb), (size_t)X->dpad * X->kp));
   RBQ_CHECK(dev_alloc(&X->ptf, (size_t)X->dpad * X->kp));
-  RBQ_CHECK(dev_alloc(&X->ctf, (size_t)X->K * X->kp));
+  RBQ_CHECK(dev_alloc(&X->ctf, (size_t)centroid_tile_rows(X->K) * X->kp));
   RBQ_CHECK(dev_alloc(&X->cn2, (size_t)X->K));
   RBQ_CHECK(dev_alloc(&X->cnorm, (size_t)X->K));
   return RABITQ_OK;

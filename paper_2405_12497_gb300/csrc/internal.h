@@ -41,8 +41,10 @@ struct rabitq_index {
   } tune[4][4] = {};
   void* ptb = nullptr;            // dpad x kp BF16
   float* ptf = nullptr;           // dpad x kp TF32-rounded FP32
-  // centroids for the tensor-core probe scores: K x kp TF32-rounded rows,
-  // and the FP32 norms ||c||^2 (canonical fold) and ||c||
+  // centroids for the tensor-core probe scores: TF32-rounded, stored in
+  // tiles of 256 rows (centroid_tile_rows(K) x kp, zero padding), each a run
+  // of 32-column stages in the core-matrix layout; and the FP32 norms
+  // ||c||^2 (canonical fold) and ||c||
   float* ctf = nullptr;
   float* cn2 = nullptr;
   float* cnorm = nullptr;
@@ -144,9 +146,13 @@ int pack_pt(rabitq_index* X, cudaStream_t s);
 int pack_centroids(rabitq_index* X, cudaStream_t s);
 // out[m][c] = <q_m, c> for all K centroids with TF32 operands on tensor
 // cores, FP32 accumulation (the probe filter's approximate scores); *err = 2
-// when a bounded wait expired
+// when a bounded wait expired. out holds probe_scratch_floats(X, M) floats:
+// the M x K products, then the queries' TF32 tiles.
 int centroid_dot_tc(const rabitq_index* X, const float* Q, int64_t M, float* out, int* err,
                     cudaStream_t s);
+size_t probe_scratch_floats(const rabitq_index* X, int64_t nq);
+// rows of the index's tiled TF32 centroid array (K padded to whole tiles)
+int64_t centroid_tile_rows(int K);
 // out[M x dpad] = Q[M x d] P (mode RABITQ_ROT_BF16 or RABITQ_ROT_TF32);
 // a bounded wait that expires sets *err = 2
 int rotate_tc(const rabitq_index* X, const float* Q, int64_t M, int mode, float* out, int* err,

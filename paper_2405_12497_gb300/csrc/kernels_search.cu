@@ -3443,7 +3443,7 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
   DevBuf cd, rq, pid, pdist, cand, err, ubout, scnt, cand2, qn, pnq2;
   if (metric_cos(X)) RBQ_CHECK(qn.alloc(sizeof(float) * qchunk * d, s));
   if (metric_ip(X)) RBQ_CHECK(pnq2.alloc(sizeof(float) * qchunk * nprobe, s));
-  RBQ_CHECK(cd.alloc(sizeof(float) * qchunk * K, s));
+  RBQ_CHECK(cd.alloc(sizeof(float) * probe_scratch_floats(X, qchunk), s));
   RBQ_CHECK(rq.alloc(sizeof(float) * qchunk * dpad, s));
   RBQ_CHECK(pid.alloc(sizeof(int32_t) * qchunk * nprobe, s));
   RBQ_CHECK(pdist.alloc(sizeof(float) * qchunk * nprobe, s));
@@ -3662,7 +3662,7 @@ Carve carve_layout(const SearchArgs& a, int64_t grid, int64_t cap, int64_t qchun
     return at;
   };
   L.o_cand = take(sizeof(int4) * grid * cap);
-  L.o_cd = take(sizeof(float) * qchunk * K);
+  L.o_cd = take(sizeof(float) * probe_scratch_floats(X, qchunk));
   L.o_rq = take(sizeof(float) * qchunk * X->dpad);
   L.o_pid = take(sizeof(int32_t) * qchunk * nprobe);
   L.o_pdist = take(sizeof(float) * qchunk * nprobe);
@@ -3919,7 +3919,7 @@ int search_dev_tc(const SearchArgs& a, cudaStream_t s) {
       err, qn, pnq2;
   if (metric_cos(X)) RBQ_CHECK(qn.alloc(sizeof(float) * qchunk * d, s));
   if (metric_ip(X)) RBQ_CHECK(pnq2.alloc(sizeof(float) * np, s));
-  RBQ_CHECK(cd.alloc(sizeof(float) * qchunk * K, s));
+  RBQ_CHECK(cd.alloc(sizeof(float) * probe_scratch_floats(X, qchunk), s));
   RBQ_CHECK(rq.alloc(sizeof(float) * qchunk * dpad, s));
   RBQ_CHECK(pid.alloc(sizeof(int32_t) * np, s));
   RBQ_CHECK(pdist.alloc(sizeof(float) * np, s));
@@ -4110,7 +4110,7 @@ int select_buckets(const rabitq_index* X, const float* Q, int64_t nq, int nsel, 
   nsel = std::min(nsel, K);
   const int64_t qchunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t(1) << 28) / K));
   DevBuf cd;
-  RBQ_CHECK(cd.alloc(sizeof(float) * qchunk * K, s));
+  RBQ_CHECK(cd.alloc(sizeof(float) * probe_scratch_floats(X, qchunk), s));
   DevBuf err;
   RBQ_CHECK(err.alloc(sizeof(int), s));
   RBQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));

@@ -11,7 +11,17 @@
 // (8 rows x 16 bytes per core matrix). One thread issues the MMAs and
 // commits them to an mbarrier; every wait is bounded and reports a timeout
 // through the error word instead of hanging.
+//
+// The probe products <q, c> for all K centroids (§4's probe, made exact by
+// the bound in probe_select) run in probe_dot_kernel: both operands are
+// stored pre-tiled in the core-matrix layout (the centroids in the index,
+// the queries by query_tile_kernel per search), so that every K stage of a
+// 128 x 256 output tile is two contiguous bulk copies. One producer warp
+// fills a ring of stages, one thread issues the MMAs into one of two TMEM
+// accumulators, and four warps write the other accumulator's products out.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
@@ -23,6 +33,8 @@ namespace {
 constexpr int kTcThreads = 128;
 constexpr int kTcM = 128;           // rows per CTA (one per TMEM lane)
 constexpr int kStageBytes = 128;    // bytes per row per K stage
+
+inline __host__ __device__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
@@ -197,19 +209,39 @@ __global__ void pack_pt_kernel(const float* __restrict__ P32, int d, int dpad, i
   ptf[i] = to_tf32(v);
 }
 
-// Centroid rows rounded to TF32 (K-major, zero-padded to Kp), and the FP32
-// norms ||c||^2 (ascending fold) and ||c|| that scale the probe filter's
-// error bound. One thread per (centroid, column); column 0 also folds the
-// norm.
+// ---- probe products
+constexpr int kPdM = 128;                        // queries per tile (TMEM lanes)
+constexpr int kPdN = 256;                        // centroids per tile (TMEM columns)
+constexpr int kPdStages = 4;                     // ring of K stages
+constexpr int kPdA = kPdM * kStageBytes;         // 16 KB: one A stage
+constexpr int kPdB = kPdN * kStageBytes;         // 32 KB: one B stage
+constexpr int kPdThreads = 192;                  // warps 0-3 epilogue, 4 producer, 5 MMA
+constexpr size_t kPdSmem = (size_t)kPdStages * (kPdA + kPdB);
+constexpr int kPdEl = kStageBytes / 4;           // TF32 elements per row per stage
+
+// Offset (floats) of element (row r, column k) of a matrix stored pre-tiled:
+// tiles of R rows, each a run of K stages of R rows x 32 TF32 in the
+// core-matrix layout (the shared-memory image of one stage).
+__device__ __forceinline__ int64_t tiled_off(int64_t r, int k, int R, int nks) {
+  const int64_t tile = r / R;
+  const int rr = (int)(r % R), st = k / kPdEl, kk = k % kPdEl;
+  return ((tile * nks + st) * (int64_t)(R * kStageBytes) + core_off(rr, kk >> 2, R)) / 4 + (kk & 3);
+}
+
+// Centroids rounded to TF32 in tiles of kPdN rows (rows past K and columns
+// past d are zero), and the FP32 norms ||c||^2 (ascending fold) and ||c||
+// that scale the probe filter's error bound. One thread per element of the
+// padded matrix; column 0 also folds the norm.
 __global__ void pack_centroids_kernel(const float* __restrict__ C, int K, int d, int Kp,
-                                      float* __restrict__ ctf, float* __restrict__ cn2,
-                                      float* __restrict__ cnorm) {
+                                      int64_t rows, float* __restrict__ ctf,
+                                      float* __restrict__ cn2, float* __restrict__ cnorm) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= (int64_t)K * Kp) return;
-  const int c = (int)(i / Kp), k = (int)(i % Kp);
-  const float* row = C + (int64_t)c * d;
-  ctf[i] = (k < d) ? to_tf32(row[k]) : 0.0f;
-  if (k == 0) {
+  if (i >= rows * Kp) return;
+  const int64_t c = i / Kp;
+  const int k = (int)(i % Kp);
+  const float* row = C + c * d;
+  ctf[tiled_off(c, k, kPdN, Kp / kPdEl)] = (c < K && k < d) ? to_tf32(row[k]) : 0.0f;
+  if (k == 0 && c < K) {
     float s2 = 0.0f;
     for (int t = 0; t < d; ++t) s2 = __fmaf_rn(row[t], row[t], s2);
     cn2[c] = s2;
@@ -217,12 +249,232 @@ __global__ void pack_centroids_kernel(const float* __restrict__ C, int K, int d,
   }
 }
 
+// Queries rounded to TF32 in tiles of kPdM rows (zero padding).
+__global__ void query_tile_kernel(const float* __restrict__ Q, int64_t M, int d, int Kp,
+                                  int64_t rows, float* __restrict__ qt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows * Kp) return;
+  const int64_t m = i / Kp;
+  const int k = (int)(i % Kp);
+  qt[tiled_off(m, k, kPdM, Kp / kPdEl)] = (m < M && k < d) ? to_tf32(__ldg(Q + m * d + k)) : 0.0f;
+}
+
+// Bounded wait that also gives up once another role of the CTA has failed.
+__device__ __forceinline__ bool pd_wait(uint32_t bar, uint32_t parity, volatile int* fail) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && *fail) return false;
+  }
+  return false;
+}
+
+// C[M x N] = Qt Ct^T over the tiles (m, n), m-major; CTA b takes the items
+// [b items / G, (b + 1) items / G). Stage it of the CTA's sequence lives in
+// ring slot it % kPdStages; tile j of the CTA accumulates in TMEM columns
+// (j & 1) * kPdN. Barriers: full (copies landed), empty (the MMAs reading
+// the slot are done), tfull (a tile's accumulator is complete), tempty (the
+// epilogue has read it). A wait that expires sets *err = 2; the roles then
+// stop, wait (bounded) for their own copies or MMAs in flight, and the CTA
+// frees its TMEM.
+__global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
+    const float* __restrict__ qt, const float* __restrict__ ct, int64_t M, int N, int nks,
+    int ntn, int64_t items, float* __restrict__ C, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint32_t s_taddr;
+  __shared__ __align__(8) uint64_t s_full[kPdStages], s_empty[kPdStages], s_tfull[2], s_tempty[2];
+  __shared__ volatile int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t G = gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * items / G, i1 = ((int64_t)blockIdx.x + 1) * items / G;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_taddr)),
+                 "r"(2 * kPdN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kPdStages; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_empty[i])), "r"(1));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_tfull[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_tempty[i])),
+                   "r"(4 * 32));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_fail = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = s_taddr;
+  const uint32_t sbase = smem_u32(smem);
+  auto slot_a = [&](uint32_t slot) { return sbase + slot * (uint32_t)(kPdA + kPdB); };
+  auto slot_b = [&](uint32_t slot) { return sbase + slot * (uint32_t)(kPdA + kPdB) + (uint32_t)kPdA; };
+
+  if (warp == 4) {  // producer: one lane issues every stage's two bulk copies
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t i = i0; i < i1 && ok; ++i) {
+        const int64_t mt = i / ntn;
+        const int nt = (int)(i % ntn);
+        const uint8_t* a_src = reinterpret_cast<const uint8_t*>(qt) + mt * nks * (int64_t)kPdA;
+        const uint8_t* b_src = reinterpret_cast<const uint8_t*>(ct) + (int64_t)nt * nks * kPdB;
+        for (int ks = 0; ks < nks; ++ks, ++it) {
+          const uint32_t slot = it % kPdStages;
+          if (it >= (uint32_t)kPdStages &&
+              !pd_wait(smem_u32(&s_empty[slot]), ((it / kPdStages) - 1) & 1u, &s_fail)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&s_full[slot]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                       "r"((uint32_t)(kPdA + kPdB))
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+              ::"r"(slot_a(slot)), "l"(a_src + (int64_t)ks * kPdA), "r"((uint32_t)kPdA), "r"(fb)
+              : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+              ::"r"(slot_b(slot)), "l"(b_src + (int64_t)ks * kPdB), "r"((uint32_t)kPdB), "r"(fb)
+              : "memory");
+        }
+      }
+      if (!ok) {
+        s_fail = 1;
+        // the copies already issued land before the CTA exits: stages
+        // it - kPdStages .. it - 1 may be in flight
+        for (uint32_t j = it > (uint32_t)kPdStages ? it - kPdStages : 0; j < it; ++j)
+          mbar_wait(smem_u32(&s_full[j % kPdStages]), (j / kPdStages) & 1u);
+      }
+    }
+  } else if (warp == 5) {  // MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(2u, kPdM, kPdN);
+      constexpr uint32_t lboA = (kPdM / 8) * 128, lboB = (kPdN / 8) * 128;
+      uint32_t it = 0, tc = 0;
+      bool ok = true, issued = false;
+      for (int64_t i = i0; i < i1 && ok; ++i, ++tc) {
+        const uint32_t buf = tc & 1u;
+        if (tc >= 2 && !pd_wait(smem_u32(&s_tempty[buf]), ((tc / 2) - 1) & 1u, &s_fail)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t dt = taddr + buf * (uint32_t)kPdN;
+        for (int ks = 0; ks < nks; ++ks, ++it) {
+          const uint32_t slot = it % kPdStages;
+          if (!pd_wait(smem_u32(&s_full[slot]), (it / kPdStages) & 1u, &s_fail)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a0 = slot_a(slot), b0 = slot_b(slot);
+#pragma unroll
+          for (int sI = 0; sI < kPdEl / 8; ++sI) {
+            const uint64_t da = make_desc(a0 + (uint32_t)(2 * sI) * lboA, lboA, 128);
+            const uint64_t db = make_desc(b0 + (uint32_t)(2 * sI) * lboB, lboB, 128);
+            const uint32_t acc = (ks > 0 || sI > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
+                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_u32(&s_empty[slot]))
+              : "memory");
+          issued = true;
+        }
+        if (!ok) break;
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&s_tfull[buf]))
+            : "memory");
+      }
+      if (!ok) {
+        s_fail = 1;
+        if (issued) {  // the last MMAs issued complete before the CTA exits
+          const uint32_t j = it - 1;
+          mbar_wait(smem_u32(&s_empty[j % kPdStages]), (j / kPdStages) & 1u);
+        }
+      }
+    }
+  } else {  // epilogue: warp w reads TMEM lanes 32w .. 32w + 31 (tile rows)
+    uint32_t tc = 0;
+    for (int64_t i = i0; i < i1; ++i, ++tc) {
+      const uint32_t buf = tc & 1u;
+      if (!pd_wait(smem_u32(&s_tfull[buf]), (tc / 2) & 1u, &s_fail)) {
+        s_fail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int64_t mt = i / ntn;
+      const int n0 = (int)(i % ntn) * kPdN;
+      const int64_t row = mt * kPdM + warp * 32 + lane;
+      const uint32_t src = taddr + ((uint32_t)(warp * 32) << 16) + buf * (uint32_t)kPdN;
+      for (int c0 = 0; c0 < kPdN; c0 += 16) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(src + (uint32_t)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const int gb = n0 + c0;
+        if (row < M) {
+          if (gb + 16 <= N && (N & 3) == 0) {  // whole chunk: four 16-byte stores
+            float4* dst = reinterpret_cast<float4*>(C + row * N + gb);
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                   __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (gb + e < N) C[row * N + gb + e] = __uint_as_float(r[e]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_tempty[buf]))
+                   : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && s_fail) atomicExch(err, 2);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(2 * kPdN));
+}
+
 }  // namespace
 
+int64_t centroid_tile_rows(int K) { return ((int64_t)K + kPdN - 1) / kPdN * kPdN; }
+
+size_t probe_scratch_floats(const rabitq_index* X, int64_t nq) {
+  const int64_t rows = (nq + kPdM - 1) / kPdM * kPdM;
+  return align_up((size_t)nq * X->K, 256) + (size_t)rows * X->kp;
+}
+
 int pack_centroids(rabitq_index* X, cudaStream_t s) {
-  const int64_t total = (int64_t)X->K * X->kp;
+  const int64_t rows = centroid_tile_rows(X->K);
+  const int64_t total = rows * X->kp;
   pack_centroids_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-      X->centroids, X->K, X->d, X->kp, X->ctf, X->cn2, X->cnorm);
+      X->centroids, X->K, X->d, X->kp, rows, X->ctf, X->cn2, X->cnorm);
   RBQ_CUDA(cudaGetLastError());
   return RABITQ_OK;
 }
@@ -230,14 +482,21 @@ int pack_centroids(rabitq_index* X, cudaStream_t s) {
 int centroid_dot_tc(const rabitq_index* X, const float* Q, int64_t M, float* out, int* err,
                     cudaStream_t s) {
   if (M <= 0) return RABITQ_OK;
-  const int N = X->K;
-  const int NT = 256;
-  const int ntiles = (N + NT - 1) / NT;
-  const size_t smem = 100 * 1024;  // at most two CTAs (256 TMEM columns each) per SM
-  dim3 grid((unsigned)((M + kTcM - 1) / kTcM), (unsigned)ntiles);
-  RBQ_CUDA(cudaFuncSetAttribute(rotate_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
-  rotate_tc_kernel<1><<<grid, kTcThreads, smem, s>>>(Q, M, X->d, X->ctf, X->kp, N, NT, out, err);
+  const int N = X->K, Kp = X->kp, nks = Kp / kPdEl;
+  const int64_t rows = (M + kPdM - 1) / kPdM * kPdM;
+  float* qt = out + align_up((size_t)M * N, 256);
+  query_tile_kernel<<<(unsigned)((rows * Kp + 255) / 256), 256, 0, s>>>(Q, M, X->d, Kp, rows, qt);
+  RBQ_CUDA(cudaGetLastError());
+  const int ntn = (N + kPdN - 1) / kPdN;
+  const int64_t items = (rows / kPdM) * ntn;
+  int dev = 0, sms = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
+  RBQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t grid = std::min<int64_t>(items, sms);
+  RBQ_CUDA(cudaFuncSetAttribute(probe_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kPdSmem));
+  probe_dot_kernel<<<(unsigned)grid, kPdThreads, kPdSmem, s>>>(qt, X->ctf, M, N, nks, ntn, items,
+                                                               out, err);
   RBQ_CUDA(cudaGetLastError());
   return RABITQ_OK;
 }
