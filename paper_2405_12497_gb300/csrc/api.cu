@@ -66,6 +66,7 @@ void free_index_arrays(rabitq_index* X) {
   cudaFree(X->ctf);
   cudaFree(X->cn2);
   cudaFree(X->cnorm);
+  cudaFree(X->cnorm_max);
 }
 
 int alloc_index_arrays(rabitq_index* X) {
@@ -88,6 +89,7 @@ int alloc_index_arrays(rabitq_index* X) {
   RBQ_CHECK(dev_alloc(&X->ctf, (size_t)centroid_tile_rows(X->K) * X->kp));
   RBQ_CHECK(dev_alloc(&X->cn2, (size_t)X->K));
   RBQ_CHECK(dev_alloc(&X->cnorm, (size_t)X->K));
+  RBQ_CHECK(dev_alloc(&X->cnorm_max, 1));
   return RABITQ_OK;
 }
 

@@ -55,6 +55,32 @@ __device__ __forceinline__ float key_float(uint32_t k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
+// The probe filter's error bound eps_c of a centroid's approximate score
+// (derived where probe_select_kernel is defined).
+// eps_c as a quadratic in ||c|| with per-query coefficients: squared
+// distances 1.05 [2a ||q|| ||c|| + b (||q|| + ||c||)^2], b = (2d + 8) 2^-23,
+// = ||c|| (kb ||c|| + ka) + kg; inner products 1.05 (a + (d + 8) 2^-22)
+// ||q|| ||c||. (Evaluated in FP32: a few units of rounding, inside the 5%.)
+struct ProbeEps {
+  float ka, kb, kg;
+  __device__ __forceinline__ ProbeEps(int ip_metric, float nq, int d) {
+    const float a = 0x1.0p-10f + (float)(d + 2) * 0x1.0p-21f;
+    if (ip_metric) {
+      ka = 1.05f * (a + (float)(d + 8) * 0x1.0p-22f) * nq;
+      kb = 0.0f;
+      kg = 0.0f;
+    } else {
+      const float b = (float)(2 * d + 8) * 0x1.0p-23f;
+      ka = 1.05f * (2.0f * a + 2.0f * b) * nq;
+      kb = 1.05f * b;
+      kg = 1.05f * b * nq * nq;
+    }
+  }
+  __device__ __forceinline__ float operator()(float nc) const {
+    return __fmaf_rn(nc, __fmaf_rn(kb, nc, ka), kg);
+  }
+};
+
 // Ascending bitonic sort of n (power of two) 64-bit keys in shared memory by
 // the whole block. Caller synchronizes before; returns synchronized.
 __device__ __forceinline__ void block_bitonic_sort_u64(unsigned long long* a, int n) {

@@ -48,6 +48,7 @@ struct rabitq_index {
   float* ctf = nullptr;
   float* cn2 = nullptr;
   float* cnorm = nullptr;
+  float* cnorm_max = nullptr;  // max ||c|| (one value)
 };
 
 // Learned probe-count predictor (kernels_mlp.cu): MLP weights with BF16
@@ -144,13 +145,26 @@ int finite_flag(const float* x, int64_t count, int* flag, cudaStream_t s);
 int pack_pt(rabitq_index* X, cudaStream_t s);
 // TF32 centroid rows and their norms (after the centroids are final)
 int pack_centroids(rabitq_index* X, cudaStream_t s);
-// out[m][c] = <q_m, c> for all K centroids with TF32 operands on tensor
-// cores, FP32 accumulation (the probe filter's approximate scores); *err = 2
-// when a bounded wait expired. out holds probe_scratch_floats(X, M) floats:
-// the M x K products, then the queries' TF32 tiles.
-int centroid_dot_tc(const rabitq_index* X, const float* Q, int64_t M, float* out, int* err,
-                    cudaStream_t s);
+// Probe filter keys of M queries against all K centroids (tensor cores,
+// TF32 operands, FP32 accumulation): keys[m][c] = the order-preserving key
+// of U_c = approximate score + eps_c, with each query's key range and
+// FP32 ||q||^2; *err = 2 when a bounded wait expired. The scratch holds
+// probe_scratch_floats(X, M) floats, viewed by probe_scratch().
+constexpr int kProbePool = 8;  // smallest keys pooled per query and 128 centroids
+struct ProbeScratch {
+  uint32_t* keys;   // M x K
+  float* qt;        // the queries' TF32 tiles
+  float* nq2;       // M
+  uint32_t* kmin;   // M: smallest key
+  uint32_t* kmax;   // M: largest key
+  uint32_t* pool;   // M x pool_n: the kProbePool smallest keys of each 128 centroids
+  int pool_n;       // kProbePool x (K / 128, rounded up to whole tiles of 256)
+  size_t floats;    // total size
+};
+ProbeScratch probe_scratch(const rabitq_index* X, int64_t nq, float* base);
 size_t probe_scratch_floats(const rabitq_index* X, int64_t nq);
+int probe_keys_tc(const rabitq_index* X, const float* Q, int64_t M, float* scratch, int* err,
+                  cudaStream_t s);
 // rows of the index's tiled TF32 centroid array (K padded to whole tiles)
 int64_t centroid_tile_rows(int K);
 // out[M x dpad] = Q[M x d] P (mode RABITQ_ROT_BF16 or RABITQ_ROT_TF32);

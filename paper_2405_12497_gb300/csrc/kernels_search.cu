@@ -895,12 +895,18 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
 // at least the nsel-th smallest upper bound is at least the nsel-th smallest
 // canonical score, and every centroid of the exact top nsel has L_c <= T --
 // the same bound-and-filter step as the paper's re-ranking (§4). T is the
-// upper edge of the histogram bin of the upper bounds that holds the nsel-th
-// smallest. The candidates with L_c <= T get their canonical scores (the fold
-// the full scan uses) and the nsel smallest (score, id) are written in order.
+// nsel-th smallest of a pool of upper bounds (the kProbePool smallest of
+// every 128 centroids, taken in the tensor-core kernel's epilogue),
+// or, when nsel exceeds the pool, the upper edge of the histogram bin of all
+// upper bounds that holds the nsel-th smallest. The candidates with
+// L_c <= T get their canonical scores (the fold the full scan uses) and the
+// nsel smallest (score, id) are written in order.
 // If the candidates exceed the shared-memory list, the row select ranks every
-// centroid by its canonical score (computed on the fly). ip: nq x K
-// approximate products (read only).
+// centroid by its canonical score (computed on the fly). keys: nq x K keys
+// of U_c, formed in the tensor-core kernel's epilogue (probe_keys_tc) with
+// eps_c from ProbeEps and each query's FP32 ||q||^2 (nq2), together with
+// the pool (pool_n keys per query) and each query's key range [kmin, kmax]
+// (read only).
 //
 // The bound: |t - x| <= 2^-11 |x| for each TF32 operand t, the products of
 // two TF32 values are exact in FP32, and the accumulation of d products in
@@ -912,55 +918,26 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
 // and the FP32 operations forming s~, U and L add a few units of
 // 2^-24 (||q|| + ||c||)^2; eps_c takes all of these with a 5% margin.
 constexpr int kProbeCandMax = 2048;  // candidates kept in shared memory
-// up to this many centroids the upper-bound keys stay in shared memory; for
-// more, the passes recompute them (keeping 64 KB of keys cost more in
-// residency than the recomputation: K = 16384 took 1.78 ms per 10k queries)
-constexpr int kProbeSmemK = 8192;
-
-// eps_c as a quadratic in ||c|| with per-query coefficients: squared
-// distances 1.05 [2a ||q|| ||c|| + b (||q|| + ||c||)^2], b = (2d + 8) 2^-23,
-// = ||c|| (kb ||c|| + ka) + kg; inner products 1.05 (a + (d + 8) 2^-22)
-// ||q|| ||c||. (Evaluated in FP32: a few units of rounding, inside the 5%.)
-struct ProbeEps {
-  float ka, kb, kg;
-  __device__ __forceinline__ ProbeEps(int ip_metric, float nq, int d) {
-    const float a = 0x1.0p-10f + (float)(d + 2) * 0x1.0p-21f;
-    if (ip_metric) {
-      ka = 1.05f * (a + (float)(d + 8) * 0x1.0p-22f) * nq;
-      kb = 0.0f;
-      kg = 0.0f;
-    } else {
-      const float b = (float)(2 * d + 8) * 0x1.0p-23f;
-      ka = 1.05f * (2.0f * a + 2.0f * b) * nq;
-      kb = 1.05f * b;
-      kg = 1.05f * b * nq * nq;
-    }
-  }
-  __device__ __forceinline__ float operator()(float nc) const {
-    return __fmaf_rn(nc, __fmaf_rn(kb, nc, ka), kg);
-  }
-};
 
 __global__ void __launch_bounds__(kThreads) probe_select_kernel(
-    const float* __restrict__ Q, int d, const float* __restrict__ ip, const float* __restrict__ C,
-    const float* __restrict__ cn2, const float* __restrict__ cnorm, int K, int metric,
-    int nprobe, const int32_t* __restrict__ nprobe_q, int sort_n, int smem_keys,
-    const int32_t* __restrict__ pre_ids, const float* __restrict__ pre_dist, int pre_n,
-    int32_t* __restrict__ out_ids, float* __restrict__ out_dist) {
+    const float* __restrict__ Q, int d, const uint32_t* __restrict__ keys,
+    const uint32_t* __restrict__ pool, int pool_n, const uint32_t* __restrict__ kmin_q,
+    const uint32_t* __restrict__ kmax_q, const float* __restrict__ nq2_q,
+    const float* __restrict__ C, const float* __restrict__ cnorm,
+    const float* __restrict__ cnorm_max, int K, int metric, int nprobe,
+    const int32_t* __restrict__ nprobe_q, int sort_n, const int32_t* __restrict__ pre_ids,
+    const float* __restrict__ pre_dist, int pre_n, int32_t* __restrict__ out_ids,
+    float* __restrict__ out_dist) {
   extern __shared__ __align__(16) unsigned char psm[];
-  // layout: q (d floats) | upper-bound keys (K, when smem_keys) | work area:
-  // the histogram, then the candidates, or the fallback's sort buffer
+  // layout: q (d floats) | work area: the pooled keys or the histogram, then
+  // the candidates, or the fallback's sort buffer
   float* qs = reinterpret_cast<float*>(psm);
-  uint32_t* uk = reinterpret_cast<uint32_t*>(psm + align_up(sizeof(float) * d, 16));
-  unsigned char* work = reinterpret_cast<unsigned char*>(uk) +
-                        (smem_keys ? align_up(sizeof(uint32_t) * K, 16) : 0);
+  unsigned char* work = psm + align_up(sizeof(float) * d, 16);
   __shared__ SelState st;
-  __shared__ float s_nq2;
   __shared__ int s_nc, s_bin;
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int nw = blockDim.x >> 5;
   const float* qg = Q + (int64_t)q * d;
-  const float* row = ip + (int64_t)q * K;
+  const uint32_t* row = keys + (int64_t)q * K;
   int nsel = nprobe;
   if (nprobe_q) nsel = min(max(nprobe_q[q], 1), nprobe);
   nsel = min(nsel, K);
@@ -975,156 +952,113 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
     }
     return;
   }
-  // ||q||^2 (any summation order: the bound needs an FP32 value, not the fold)
-  float part = 0.0f;
-  for (int i = tid; i < d; i += blockDim.x) {
-    const float v = qg[i];
-    qs[i] = v;
-    part = __fmaf_rn(v, v, part);
-  }
-  part = warp_sum_f(part);
-  if (lane == 0) st.wmin[wid] = __float_as_uint(part);
+  for (int i = tid; i < d; i += blockDim.x) qs[i] = qg[i];
   if (tid == 0) s_nc = 0;
+  const ProbeEps eps(metric, __fsqrt_rn(nq2_q[q]), d);
+  constexpr int kSelU = 8;  // keys per thread in flight in a pass
+  // the pooled keys (the kProbePool smallest of every 128 centroids;
+  // slots past the last centroid hold 0xffffffff, which no real key equals)
+  uint32_t* pk = reinterpret_cast<uint32_t*>(work);
+  __shared__ int s_np;
+  if (tid == 0) s_np = 0;
   __syncthreads();
-  if (tid == 0) {
-    float a = 0.0f;
-    for (int w = 0; w < nw; ++w) a = __fadd_rn(a, __uint_as_float((uint32_t)st.wmin[w]));
-    s_nq2 = a;
+  for (int i0 = 0; i0 < pool_n; i0 += blockDim.x) {
+    const int i = i0 + tid;
+    const uint32_t v = i < pool_n ? __ldg(pool + (int64_t)q * pool_n + i) : 0xffffffffu;
+    const bool real = v != 0xffffffffu;
+    const int slot = warp_reserve(real, &s_np);
+    if (real) pk[slot] = v;
   }
   __syncthreads();
-  const float nq2 = s_nq2, nq = __fsqrt_rn(nq2);
-  const ProbeEps eps(metric, nq, d);
-  auto approx = [row, cn2, nq2, metric](int c) {
-    const float v = row[c];
-    return metric ? -v : __fsub_rn(__fadd_rn(nq2, cn2[c]), __fmul_rn(2.0f, v));
-  };
-  auto ukey = [&](int c) {
-    return smem_keys ? uk[c]
-                     : float_key(__fadd_rn(approx(c), eps(cnorm[c])));
-  };
-  // L_c = U_c - 2 eps_c (its rounding is inside the bound's margin)
-  auto lkey = [&](int c) {
-    return float_key(
-        __fsub_rn(key_float(ukey(c)), __fmul_rn(2.0f, eps(cnorm[c]))));
-  };
-  // pass 1: the upper bounds' keys and their range; four centroids per
-  // thread per step, loads first
-  uint32_t kmin = 0xffffffffu, kmax = 0u;
-  for (int c0 = 0; c0 < K; c0 += 4 * blockDim.x) {
-    float v[4], n2[4], nn[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = c0 + u * blockDim.x + tid;
-      v[u] = 0.0f;
-      n2[u] = 0.0f;
-      nn[u] = 0.0f;
-      if (c < K) {
-        v[u] = row[c];
-        n2[u] = cn2[c];
-        nn[u] = cnorm[c];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = c0 + u * blockDim.x + tid;
-      if (c < K) {
-        const float sc = metric ? -v[u] : __fsub_rn(__fadd_rn(nq2, n2[u]), __fmul_rn(2.0f, v[u]));
-        const uint32_t key = float_key(__fadd_rn(sc, eps(nn[u])));
-        if (smem_keys) uk[c] = key;
-        kmin = key < kmin ? key : kmin;
-        kmax = key > kmax ? key : kmax;
-      }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint32_t a = __shfl_xor_sync(kFull, kmin, o), b = __shfl_xor_sync(kFull, kmax, o);
-    kmin = a < kmin ? a : kmin;
-    kmax = b > kmax ? b : kmax;
-  }
-  __syncthreads();  // (st.wmin held the norm partials)
-  if (lane == 0) {
-    st.wmin[wid] = kmin;
-    st.wmax[wid] = kmax;
-  }
-  int* hist = reinterpret_cast<int*>(work);
-  for (int i = tid; i < kHistBins; i += blockDim.x) hist[i] = 0;
-  __syncthreads();
-  kmin = 0xffffffffu;
-  kmax = 0u;
-  for (int w = 0; w < nw; ++w) {
-    kmin = (uint32_t)st.wmin[w] < kmin ? (uint32_t)st.wmin[w] : kmin;
-    kmax = (uint32_t)st.wmax[w] > kmax ? (uint32_t)st.wmax[w] : kmax;
-  }
-  // pass 2: histogram of the upper bounds over [kmin, kmax]; T = the upper
-  // edge of the bin holding the nsel-th smallest (an upper bound of it)
-  const uint64_t span = (uint64_t)(kmax - kmin) + 1u;
-  for (int c = tid; c < K; c += blockDim.x)
-    atomicAdd(&hist[(int)(((uint64_t)(ukey(c) - kmin) * (uint64_t)kHistBins) / span)], 1);
-  __syncthreads();
-  {
-    int cb[4], sum = 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      cb[u] = hist[4 * tid + u];
-      sum += cb[u];
-    }
-    int incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
-    }
-    if (lane == 31) st.warp_cnt[wid] = incl;
+  const int np_real = s_np;
+  uint32_t T;
+  if (nsel <= np_real) {
+    // T = the nsel-th smallest pooled key: the pool holds distinct
+    // centroids, so at least nsel keys are <= T, and T is at least the
+    // nsel-th smallest upper bound of all centroids
+    T = block_select<uint32_t>(pk, np_real, nsel, st);
     __syncthreads();
-    for (int w = 0; w < wid; ++w) incl += st.warp_cnt[w];
-    const int excl = incl - sum;
-    if (excl < nsel && incl >= nsel) {  // exactly one thread
-      int cum = excl;
+  } else {
+    // histogram of the keys, bin (key - kmin) >> shift (at least half of
+    // the kHistBins bins span [kmin, kmax]); T = the last key of the bin
+    // holding the nsel-th smallest (an upper bound of it)
+    const uint32_t kmin = kmin_q[q], kmax = kmax_q[q];
+    int* hist = reinterpret_cast<int*>(work);
+    for (int i = tid; i < kHistBins; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint32_t span1 = kmax - kmin;  // span - 1
+    int shift = 0;
+    while ((span1 >> shift) >= (uint32_t)kHistBins) ++shift;
+    for (int c0 = 0; c0 < K; c0 += kSelU * blockDim.x) {
+      uint32_t kv[kSelU];
+#pragma unroll
+      for (int u = 0; u < kSelU; ++u) {
+        const int c = c0 + u * blockDim.x + tid;
+        kv[u] = c < K ? __ldg(row + c) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kSelU; ++u) {
+        const int c = c0 + u * blockDim.x + tid;
+        if (c < K) atomicAdd(&hist[(kv[u] - kmin) >> shift], 1);
+      }
+    }
+    __syncthreads();
+    {
+      int cb[4], sum = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (cum + cb[u] >= nsel) {
-          s_bin = 4 * tid + u;
-          break;
+        cb[u] = hist[4 * tid + u];
+        sum += cb[u];
+      }
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane == 31) st.warp_cnt[wid] = incl;
+      __syncthreads();
+      for (int w = 0; w < wid; ++w) incl += st.warp_cnt[w];
+      const int excl = incl - sum;
+      if (excl < nsel && incl >= nsel) {  // exactly one thread
+        int cum = excl;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (cum + cb[u] >= nsel) {
+            s_bin = 4 * tid + u;
+            break;
+          }
+          cum += cb[u];
         }
-        cum += cb[u];
       }
     }
+    __syncthreads();
+    // keys of bin B are at most kmin + ((B + 1) << shift) - 1
+    const uint64_t edge = (uint64_t)kmin + ((uint64_t)(s_bin + 1) << shift) - 1u;
+    T = (uint32_t)min((uint64_t)kmax, edge);
   }
-  __syncthreads();
-  // keys of bin B are below kmin + ceil((B + 1) span / kHistBins)
-  const uint64_t edge = ((uint64_t)(s_bin + 1) * span + kHistBins - 1) / kHistBins;
-  const uint32_t T = (uint32_t)min((uint64_t)kmax, (uint64_t)kmin + edge - 1u);
-  // pass 3: candidates, L_c <= T (ids now, (score key, id) after the
-  // refine); four centroids per thread per step, loads first
+  // candidates, L_c <= T (ids now, (score key, id) after the
+  // refine), eight centroids per thread per step. L_c = U_c - 2 eps_c (its
+  // rounding is inside the bound's margin) needs ||c||; since eps_c is at
+  // most eps(max ||c||), only keys U_c <= T + 2 eps(max ||c||) (with a margin
+  // for the rounding of the subtraction) can pass, and only theirs are read.
+  const float Tf = key_float(T), e2max = __fmul_rn(2.0f, eps(__ldg(cnorm_max)));
+  const uint32_t Tpre =
+      float_key(__fadd_ru(__fadd_ru(Tf, e2max), __fmul_ru(0x1.0p-20f, __fadd_ru(fabsf(Tf), e2max))));
   unsigned long long* ckey = reinterpret_cast<unsigned long long*>(work);
-  for (int c0 = 0; c0 < K; c0 += 4 * blockDim.x) {
-    uint32_t lk4[4];
-    if (smem_keys) {
-      float nn[4];
+  for (int c0 = 0; c0 < K; c0 += kSelU * blockDim.x) {
+    uint32_t kv[kSelU];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = c0 + u * blockDim.x + tid;
-        nn[u] = c < K ? cnorm[c] : 0.0f;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = c0 + u * blockDim.x + tid;
-        lk4[u] = c < K ? float_key(__fsub_rn(key_float(uk[c]),
-                                             __fmul_rn(2.0f, eps(nn[u]))))
-                       : 0xffffffffu;
-      }
-    } else {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = c0 + u * blockDim.x + tid;
-        lk4[u] = c < K ? lkey(c) : 0xffffffffu;
-      }
+    for (int u = 0; u < kSelU; ++u) {
+      const int c = c0 + u * blockDim.x + tid;
+      kv[u] = c < K ? __ldg(row + c) : 0xffffffffu;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kSelU; ++u) {
       const int c = c0 + u * blockDim.x + tid;
-      const bool in = c < K && lk4[u] <= T;
+      bool in = false;
+      if (c < K && kv[u] <= Tpre)
+        in = float_key(__fsub_rn(key_float(kv[u]), __fmul_rn(2.0f, eps(__ldg(cnorm + c))))) <= T;
       const int slot = warp_reserve(in, &s_nc);
       if (in && slot < kProbeCandMax) ckey[slot] = (unsigned long long)(uint32_t)c;
     }
@@ -1135,7 +1069,12 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
   float* od = out_dist + (int64_t)q * nprobe;
   if (nc <= kProbeCandMax) {
     // canonical scores of the candidates (one thread each, the full scan's
-    // fold)
+    // fold); every line of their rows is requested first
+    for (int i = tid; i < nc; i += blockDim.x) {
+      const char* x = reinterpret_cast<const char*>(C + (int64_t)(uint32_t)ckey[i] * d);
+      for (int o = 0; o < d * (int)sizeof(float); o += 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(x + o));
+    }
     for (int i = tid; i < nc; i += blockDim.x) {
       const int c = (int)(uint32_t)ckey[i];
       const float* x = C + (int64_t)c * d;
@@ -1169,14 +1108,13 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
   }
 }
 
-// Shared memory of probe_select_kernel for dimension d, K centroids (keys
-// held in shared memory or not) and sort size sort_n.
-inline size_t probe_select_smem(int d, int K, int sort_n, bool smem_keys) {
-  const size_t work = std::max({sizeof(int) * kHistBins,
+// Shared memory of probe_select_kernel for dimension d, sort size sort_n and
+// pool_n pooled keys.
+inline size_t probe_select_smem(int d, int sort_n, int pool_n) {
+  const size_t work = std::max({sizeof(int) * kHistBins, sizeof(uint32_t) * (size_t)pool_n,
                                 sizeof(unsigned long long) * kProbeCandMax,
                                 sizeof(unsigned long long) * (size_t)sort_n});
-  const size_t keys = smem_keys ? align_up(sizeof(uint32_t) * K, 16) : 0;
-  return align_up(sizeof(float) * d, 16) + keys + work;
+  return align_up(sizeof(float) * d, 16) + work;
 }
 
 // Shared counters the per-query finishing step works with.
@@ -3216,7 +3154,7 @@ int fused_shape(const SearchArgs& a, FusedShape* f) {
   return RABITQ_OK;
 }
 
-// Probe lists from the tensor-core products cd (nqc x K, centroid_dot_tc):
+// Probe lists from the probe keys in cd (probe_keys_tc):
 // the nsel (= nprobe, or npq[q] clamped to it) best centroids of each query
 // by exact canonical score, ascending (score, id), in rows of nprobe. With
 // pre_ids/pre_dist (rows of pre_n such lists), a query with nsel <= pre_n
@@ -3235,14 +3173,13 @@ int probe_select(const rabitq_index* X, const float* Q, int64_t nqc, const float
   const size_t limit = (size_t)(optin - (int)fa.sharedSizeBytes);
   RBQ_CUDA(cudaFuncSetAttribute(probe_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)limit));
-  // the bounds' keys stay in shared memory when they fit beside the rest
-  const bool smem_keys =
-      X->K <= kProbeSmemK && probe_select_smem(X->d, X->K, sort_n, true) <= limit;
-  const size_t smem = probe_select_smem(X->d, X->K, sort_n, smem_keys);
+  const ProbeScratch v = probe_scratch(X, nqc, const_cast<float*>(cd));
+  const size_t smem = probe_select_smem(X->d, sort_n, v.pool_n);
   if (smem > limit) return fail(RABITQ_EINVAL, "probe selection does not fit shared memory");
   probe_select_kernel<<<(unsigned)nqc, kThreads, smem, s>>>(
-      Q, X->d, cd, X->centroids, X->cn2, X->cnorm, X->K, X->metric != RABITQ_METRIC_L2 ? 1 : 0,
-      nprobe, npq, sort_n, smem_keys ? 1 : 0, pre_ids, pre_dist, pre_n, ids, dist);
+      Q, X->d, v.keys, v.pool, v.pool_n, v.kmin, v.kmax, v.nq2, X->centroids, X->cnorm,
+      X->cnorm_max, X->K, X->metric != RABITQ_METRIC_L2 ? 1 : 0, nprobe, npq, sort_n, pre_ids,
+      pre_dist, pre_n, ids, dist);
   RBQ_CUDA(cudaGetLastError());
   return RABITQ_OK;
 }
@@ -3281,11 +3218,11 @@ int search_queries(const rabitq_index* X, const float* Q, int64_t nq, float* qn,
   return RABITQ_OK;
 }
 
-// The approximate probe scores' products <q, c> for all K centroids on
-// tensor cores (probe_select turns them into exact probe lists).
+// The probe filter's keys for all K centroids from tensor-core products
+// (probe_select turns them into exact probe lists).
 int centroid_scores(const rabitq_index* X, const float* Q, int64_t nq, float* cd, int* err,
                     cudaStream_t s) {
-  return centroid_dot_tc(X, Q, nq, cd, err, s);
+  return probe_keys_tc(X, Q, nq, cd, err, s);
 }
 
 int probe_nq2(const rabitq_index* X, const float* Q, int64_t nq, int nprobe, const int32_t* pid,
@@ -4116,7 +4053,7 @@ int select_buckets(const rabitq_index* X, const float* Q, int64_t nq, int nsel, 
   RBQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
   for (int64_t q0 = 0; q0 < nq; q0 += qchunk) {
     const int64_t m = std::min(qchunk, nq - q0);
-    RBQ_CHECK(centroid_dot_tc(X, Q + q0 * d, m, cd.as<float>(), err.as<int>(), s));
+    RBQ_CHECK(probe_keys_tc(X, Q + q0 * d, m, cd.as<float>(), err.as<int>(), s));
     RBQ_CHECK(probe_select(X, Q + q0 * d, m, cd.as<float>(), nsel, nullptr, ids + q0 * nsel,
                            dist + q0 * nsel, s));
   }

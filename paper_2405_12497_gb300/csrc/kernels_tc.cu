@@ -12,13 +12,14 @@
 // commits them to an mbarrier; every wait is bounded and reports a timeout
 // through the error word instead of hanging.
 //
-// The probe products <q, c> for all K centroids (§4's probe, made exact by
-// the bound in probe_select) run in probe_dot_kernel: both operands are
-// stored pre-tiled in the core-matrix layout (the centroids in the index,
-// the queries by query_tile_kernel per search), so that every K stage of a
+// The probe scores of all K centroids (§4's probe, made exact by the bound
+// in probe_select) run in probe_dot_kernel: both operands are stored
+// pre-tiled in the core-matrix layout (the centroids in the index, the
+// queries by query_prep_kernel per search), so that every K stage of a
 // 128 x 256 output tile is two contiguous bulk copies. One producer warp
 // fills a ring of stages, one thread issues the MMAs into one of two TMEM
-// accumulators, and four warps write the other accumulator's products out.
+// accumulators, and eight warps turn the other accumulator's products into
+// the filter's upper-bound keys.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -215,7 +216,9 @@ constexpr int kPdN = 256;                        // centroids per tile (TMEM col
 constexpr int kPdStages = 4;                     // ring of K stages
 constexpr int kPdA = kPdM * kStageBytes;         // 16 KB: one A stage
 constexpr int kPdB = kPdN * kStageBytes;         // 32 KB: one B stage
-constexpr int kPdThreads = 192;                  // warps 0-3 epilogue, 4 producer, 5 MMA
+constexpr int kPdEpi = 8;                        // epilogue warps: two per TMEM lane quarter
+constexpr int kPdThreads = (kPdEpi + 2) * 32;    // then the producer warp and the MMA warp
+constexpr int kPdCols = kPdN / 2;                // columns per epilogue warp
 constexpr size_t kPdSmem = (size_t)kPdStages * (kPdA + kPdB);
 constexpr int kPdEl = kStageBytes / 4;           // TF32 elements per row per stage
 
@@ -249,14 +252,45 @@ __global__ void pack_centroids_kernel(const float* __restrict__ C, int K, int d,
   }
 }
 
-// Queries rounded to TF32 in tiles of kPdM rows (zero padding).
-__global__ void query_tile_kernel(const float* __restrict__ Q, int64_t M, int d, int Kp,
-                                  int64_t rows, float* __restrict__ qt) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= rows * Kp) return;
-  const int64_t m = i / Kp;
-  const int k = (int)(i % Kp);
-  qt[tiled_off(m, k, kPdM, Kp / kPdEl)] = (m < M && k < d) ? to_tf32(__ldg(Q + m * d + k)) : 0.0f;
+// max_c ||c|| (one block).
+__global__ void max_norm_kernel(const float* __restrict__ cnorm, int K, float* __restrict__ out) {
+  __shared__ float wmax[32];
+  float m = 0.0f;
+  for (int c = threadIdx.x; c < K; c += blockDim.x) m = fmaxf(m, cnorm[c]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+    *out = m;
+  }
+}
+
+// One warp per query row (rows past M: zeros): the row rounded to TF32 in
+// tiles of kPdM rows, its FP32 ||q||^2 (lane-strided partial folds, then a
+// fixed butterfly; the bound needs an FP32 value of the norm, not the
+// canonical fold) and the initial range of its keys.
+__global__ void query_prep_kernel(const float* __restrict__ Q, int64_t M, int d, int Kp,
+                                  int64_t rows, float* __restrict__ qt, float* __restrict__ nq2,
+                                  uint32_t* __restrict__ kmin, uint32_t* __restrict__ kmax) {
+  const int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (m >= rows) return;
+  const int nks = Kp / kPdEl;
+  float part = 0.0f;
+  for (int k = lane; k < Kp; k += 32) {
+    const float v = (m < M && k < d) ? __ldg(Q + m * d + k) : 0.0f;
+    part = __fmaf_rn(v, v, part);
+    qt[tiled_off(m, k, kPdM, nks)] = to_tf32(v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o));
+  if (lane == 0 && m < M) {
+    nq2[m] = part;
+    kmin[m] = 0xffffffffu;
+    kmax[m] = 0u;
+  }
 }
 
 // Bounded wait that also gives up once another role of the CTA has failed.
@@ -285,11 +319,15 @@ __device__ __forceinline__ bool pd_wait(uint32_t bar, uint32_t parity, volatile 
 // frees its TMEM.
 __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
     const float* __restrict__ qt, const float* __restrict__ ct, int64_t M, int N, int nks,
-    int ntn, int64_t items, float* __restrict__ C, int* err) {
+    int ntn, int64_t items, int d, int metric, const float* __restrict__ nq2,
+    const float* __restrict__ cn2, const float* __restrict__ cnorm, uint32_t* __restrict__ keys,
+    uint32_t* __restrict__ kmin, uint32_t* __restrict__ kmax, uint32_t* __restrict__ pool,
+    int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ uint32_t s_taddr;
   __shared__ __align__(8) uint64_t s_full[kPdStages], s_empty[kPdStages], s_tfull[2], s_tempty[2];
   __shared__ volatile int s_fail;
+  __shared__ float s_cn2[kPdN], s_cnorm[kPdN];  // the current tile's centroid norms
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t G = gridDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * items / G, i1 = ((int64_t)blockIdx.x + 1) * items / G;
@@ -307,7 +345,7 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
     for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_tfull[i])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_tempty[i])),
-                   "r"(4 * 32));
+                   "r"(kPdEpi * 32));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
     s_fail = 0;
@@ -320,7 +358,7 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
   auto slot_a = [&](uint32_t slot) { return sbase + slot * (uint32_t)(kPdA + kPdB); };
   auto slot_b = [&](uint32_t slot) { return sbase + slot * (uint32_t)(kPdA + kPdB) + (uint32_t)kPdA; };
 
-  if (warp == 4) {  // producer: one lane issues every stage's two bulk copies
+  if (warp == kPdEpi) {  // producer: one lane issues every stage's two bulk copies
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
@@ -358,7 +396,7 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
           mbar_wait(smem_u32(&s_full[j % kPdStages]), (j / kPdStages) & 1u);
       }
     }
-  } else if (warp == 5) {  // MMA issue
+  } else if (warp == kPdEpi + 1) {  // MMA issue
     if (lane == 0) {
       const uint32_t idesc = make_idesc(2u, kPdM, kPdN);
       constexpr uint32_t lboA = (kPdM / 8) * 128, lboB = (kPdN / 8) * 128;
@@ -410,20 +448,50 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
         }
       }
     }
-  } else {  // epilogue: warp w reads TMEM lanes 32w .. 32w + 31 (tile rows)
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and
+    // the columns [kPdCols (w / 4), + kPdCols); the two halves keep their
+    // own pool entries. Each half stages its columns' ||c||^2 and ||c|| in
+    // shared memory (loaded before the tile's MMAs are waited for).
+    const int quarter = warp & 3, half = warp >> 2, ht = tid & 127;
+    const uint32_t bar_id = 1u + (uint32_t)half;
     uint32_t tc = 0;
     for (int64_t i = i0; i < i1; ++i, ++tc) {
       const uint32_t buf = tc & 1u;
-      if (!pd_wait(smem_u32(&s_tfull[buf]), (tc / 2) & 1u, &s_fail)) {
+      const int64_t mt = i / ntn;
+      const int nt = (int)(i % ntn);
+      const int h0 = nt * kPdN + half * kPdCols;  // first column of this half
+      const int cl = min(h0 + ht, N - 1);
+      const float ncn2 = __ldg(cn2 + cl), ncnorm = __ldg(cnorm + cl);
+      const bool ok = pd_wait(smem_u32(&s_tfull[buf]), (tc / 2) & 1u, &s_fail);
+      // one decision for the whole half (a thread that gave up stops all of
+      // them); the same barrier finds the half's previous tile read
+      uint32_t gave_up;
+      asm volatile(
+          "{\n.reg .pred p, q;\nsetp.eq.u32 q, %1, 0;\nbar.red.or.pred p, %2, 128, q;\n"
+          "selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(gave_up)
+          : "r"((uint32_t)ok), "r"(bar_id)
+          : "memory");
+      if (gave_up) {
         s_fail = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const int64_t mt = i / ntn;
-      const int n0 = (int)(i % ntn) * kPdN;
-      const int64_t row = mt * kPdM + warp * 32 + lane;
-      const uint32_t src = taddr + ((uint32_t)(warp * 32) << 16) + buf * (uint32_t)kPdN;
-      for (int c0 = 0; c0 < kPdN; c0 += 16) {
+      s_cn2[half * kPdCols + ht] = ncn2;
+      s_cnorm[half * kPdCols + ht] = ncnorm;
+      asm volatile("bar.sync %0, 128;" ::"r"(bar_id));
+      const int64_t row = mt * kPdM + quarter * 32 + lane;
+      const bool live = row < M;
+      const float q2 = live ? __ldg(nq2 + row) : 0.0f;
+      const ProbeEps eps(metric, __fsqrt_rn(q2), d);
+      uint32_t tmin = 0xffffffffu, tmax = 0u;
+      uint32_t top[kProbePool];  // the smallest keys of this row and half, ascending
+#pragma unroll
+      for (int j = 0; j < kProbePool; ++j) top[j] = 0xffffffffu;
+      const uint32_t src = taddr + ((uint32_t)(quarter * 32) << 16) + buf * (uint32_t)kPdN +
+                           (uint32_t)(half * kPdCols);
+      for (int c0 = 0; c0 < kPdCols; c0 += 16) {
         uint32_t r[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
@@ -433,20 +501,51 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
               "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
             : "r"(src + (uint32_t)c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        const int gb = n0 + c0;
-        if (row < M) {
-          if (gb + 16 <= N && (N & 3) == 0) {  // whole chunk: four 16-byte stores
-            float4* dst = reinterpret_cast<float4*>(C + row * N + gb);
+        const int gb = h0 + c0;
+        // U_c = approximate score + eps_c as an order-preserving key (the
+        // same FP32 operations as the filter's definition)
+        uint32_t u[16];
 #pragma unroll
-            for (int v = 0; v < 4; ++v)
-              dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
-                                   __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+        for (int e = 0; e < 16; ++e) {
+          const int sc_i = half * kPdCols + c0 + e;
+          const float v = __uint_as_float(r[e]);
+          const float sc = metric ? -v : __fsub_rn(__fadd_rn(q2, s_cn2[sc_i]), __fmul_rn(2.0f, v));
+          u[e] = float_key(__fadd_rn(sc, eps(s_cnorm[sc_i])));
+          if (gb + e < N) {
+            tmin = u[e] < tmin ? u[e] : tmin;
+            tmax = u[e] > tmax ? u[e] : tmax;
+            if (u[e] < top[kProbePool - 1]) {  // insert, keeping the order
+              uint32_t x = u[e];
+#pragma unroll
+              for (int j = 0; j < kProbePool; ++j) {
+                const uint32_t lo = min(top[j], x);
+                x = max(top[j], x);
+                top[j] = lo;
+              }
+            }
+          }
+        }
+        if (live) {
+          if (gb + 16 <= N && (N & 3) == 0) {  // whole chunk: four 16-byte stores
+            uint4* dst = reinterpret_cast<uint4*>(keys + row * N + gb);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) dst[v] = make_uint4(u[4 * v], u[4 * v + 1], u[4 * v + 2], u[4 * v + 3]);
           } else {
 #pragma unroll
             for (int e = 0; e < 16; ++e)
-              if (gb + e < N) C[row * N + gb + e] = __uint_as_float(r[e]);
+              if (gb + e < N) keys[row * N + gb + e] = u[e];
           }
         }
+      }
+      if (live) {
+        atomicMin(kmin + row, tmin);
+        atomicMax(kmax + row, tmax);
+        // unused slots (past the last centroid) keep the largest key, which
+        // no selection takes before the real ones
+        uint4* dst = reinterpret_cast<uint4*>(pool + row * (int64_t)(2 * ntn * kProbePool) +
+                                              (int64_t)(2 * nt + half) * kProbePool);
+        dst[0] = make_uint4(top[0], top[1], top[2], top[3]);
+        dst[1] = make_uint4(top[4], top[5], top[6], top[7]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_tempty[buf]))
@@ -465,9 +564,28 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
 
 int64_t centroid_tile_rows(int K) { return ((int64_t)K + kPdN - 1) / kPdN * kPdN; }
 
-size_t probe_scratch_floats(const rabitq_index* X, int64_t nq) {
+ProbeScratch probe_scratch(const rabitq_index* X, int64_t nq, float* base) {
   const int64_t rows = (nq + kPdM - 1) / kPdM * kPdM;
-  return align_up((size_t)nq * X->K, 256) + (size_t)rows * X->kp;
+  ProbeScratch v;
+  size_t o = align_up((size_t)nq * X->K, 256);
+  v.keys = reinterpret_cast<uint32_t*>(base);
+  v.qt = base + o;
+  o = align_up(o + (size_t)rows * X->kp, 64);
+  v.nq2 = base + o;
+  o = align_up(o + (size_t)nq, 64);
+  v.kmin = reinterpret_cast<uint32_t*>(base + o);
+  o = align_up(o + (size_t)nq, 64);
+  v.kmax = reinterpret_cast<uint32_t*>(base + o);
+  o = align_up(o + (size_t)nq, 64);
+  v.pool_n = 2 * kProbePool * (int)((X->K + kPdN - 1) / kPdN);
+  v.pool = reinterpret_cast<uint32_t*>(base + o);
+  o = align_up(o + (size_t)nq * v.pool_n, 64);
+  v.floats = o;
+  return v;
+}
+
+size_t probe_scratch_floats(const rabitq_index* X, int64_t nq) {
+  return probe_scratch(X, nq, nullptr).floats;
 }
 
 int pack_centroids(rabitq_index* X, cudaStream_t s) {
@@ -476,16 +594,19 @@ int pack_centroids(rabitq_index* X, cudaStream_t s) {
   pack_centroids_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
       X->centroids, X->K, X->d, X->kp, rows, X->ctf, X->cn2, X->cnorm);
   RBQ_CUDA(cudaGetLastError());
+  max_norm_kernel<<<1, 1024, 0, s>>>(X->cnorm, X->K, X->cnorm_max);
+  RBQ_CUDA(cudaGetLastError());
   return RABITQ_OK;
 }
 
-int centroid_dot_tc(const rabitq_index* X, const float* Q, int64_t M, float* out, int* err,
-                    cudaStream_t s) {
+int probe_keys_tc(const rabitq_index* X, const float* Q, int64_t M, float* scratch, int* err,
+                  cudaStream_t s) {
   if (M <= 0) return RABITQ_OK;
   const int N = X->K, Kp = X->kp, nks = Kp / kPdEl;
   const int64_t rows = (M + kPdM - 1) / kPdM * kPdM;
-  float* qt = out + align_up((size_t)M * N, 256);
-  query_tile_kernel<<<(unsigned)((rows * Kp + 255) / 256), 256, 0, s>>>(Q, M, X->d, Kp, rows, qt);
+  const ProbeScratch v = probe_scratch(X, M, scratch);
+  query_prep_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(Q, M, X->d, Kp, rows, v.qt,
+                                                                        v.nq2, v.kmin, v.kmax);
   RBQ_CUDA(cudaGetLastError());
   const int ntn = (N + kPdN - 1) / kPdN;
   const int64_t items = (rows / kPdM) * ntn;
@@ -495,8 +616,9 @@ int centroid_dot_tc(const rabitq_index* X, const float* Q, int64_t M, float* out
   const int64_t grid = std::min<int64_t>(items, sms);
   RBQ_CUDA(cudaFuncSetAttribute(probe_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kPdSmem));
-  probe_dot_kernel<<<(unsigned)grid, kPdThreads, kPdSmem, s>>>(qt, X->ctf, M, N, nks, ntn, items,
-                                                               out, err);
+  probe_dot_kernel<<<(unsigned)grid, kPdThreads, kPdSmem, s>>>(
+      v.qt, X->ctf, M, N, nks, ntn, items, X->d, X->metric != RABITQ_METRIC_L2 ? 1 : 0, v.nq2,
+      X->cn2, X->cnorm, v.keys, v.kmin, v.kmax, v.pool, err);
   RBQ_CUDA(cudaGetLastError());
   return RABITQ_OK;
 }
