@@ -157,7 +157,10 @@ struct ProbeScratch {
   float* nq2;       // M
   uint32_t* kmin;   // M: smallest key
   uint32_t* kmax;   // M: largest key
-  uint32_t* pool;   // M x pool_n: the kProbePool smallest keys of each 128 centroids
+  // M x pool_n: the kProbePool smallest entries of each 128 centroids,
+  // ascending: the key rounded up to a multiple of 128 | the centroid's index
+  // among the 128 (0xffffffff past the last centroid)
+  uint32_t* pool;
   int pool_n;       // kProbePool x (K / 128, rounded up to whole tiles of 256)
   size_t floats;    // total size
 };

@@ -929,12 +929,15 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
     const float* __restrict__ pre_dist, int pre_n, int32_t* __restrict__ out_ids,
     float* __restrict__ out_dist) {
   extern __shared__ __align__(16) unsigned char psm[];
-  // layout: q (d floats) | work area: the pooled keys or the histogram, then
-  // the candidates, or the fallback's sort buffer
+  // layout: q (d floats) | the pool (pool_n entries) | work area: the
+  // histogram, then the candidates, or the fallback's sort buffer
   float* qs = reinterpret_cast<float*>(psm);
-  unsigned char* work = psm + align_up(sizeof(float) * d, 16);
+  uint32_t* sp = reinterpret_cast<uint32_t*>(psm + align_up(sizeof(float) * d, 16));
+  unsigned char* work = psm + align_up(sizeof(float) * d, 16) + align_up(sizeof(uint32_t) * pool_n, 16);
   __shared__ SelState st;
-  __shared__ int s_nc, s_bin;
+  __shared__ int s_nc, s_bin, s_np, s_nsat;
+  __shared__ uint32_t s_pmin, s_pmax;
+  __shared__ int s_sat[64];  // saturated groups of 128 centroids (scanned in full)
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const float* qg = Q + (int64_t)q * d;
   const uint32_t* row = keys + (int64_t)q * K;
@@ -953,42 +956,61 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
     return;
   }
   for (int i = tid; i < d; i += blockDim.x) qs[i] = qg[i];
-  if (tid == 0) s_nc = 0;
+  if (tid == 0) {
+    s_nc = 0;
+    s_np = 0;
+    s_nsat = 0;
+    s_pmin = 0xffffffffu;
+    s_pmax = 0u;
+  }
   const ProbeEps eps(metric, __fsqrt_rn(nq2_q[q]), d);
   constexpr int kSelU = 8;  // keys per thread in flight in a pass
-  // the pooled keys (the kProbePool smallest of every 128 centroids;
-  // slots past the last centroid hold 0xffffffff, which no real key equals)
-  uint32_t* pk = reinterpret_cast<uint32_t*>(work);
-  __shared__ int s_np;
-  if (tid == 0) s_np = 0;
+  int* hist = reinterpret_cast<int*>(work);
+  for (int i = tid; i < kHistBins; i += blockDim.x) hist[i] = 0;
   __syncthreads();
-  for (int i0 = 0; i0 < pool_n; i0 += blockDim.x) {
-    const int i = i0 + tid;
-    const uint32_t v = i < pool_n ? __ldg(pool + (int64_t)q * pool_n + i) : 0xffffffffu;
-    const bool real = v != 0xffffffffu;
-    const int slot = warp_reserve(real, &s_np);
-    if (real) pk[slot] = v;
+  // the pool, with the number and range of its real entries (an entry is
+  // at least its centroid's key: the key rounded up, then the index bits)
+  {
+    int cnt = 0;
+    uint32_t pmin = 0xffffffffu, pmax = 0u;
+    for (int i = tid; i < pool_n; i += blockDim.x) {
+      const uint32_t e = __ldg(pool + (int64_t)q * pool_n + i);
+      sp[i] = e;
+      if (e != 0xffffffffu) {
+        ++cnt;
+        pmin = e < pmin ? e : pmin;
+        pmax = e > pmax ? e : pmax;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      cnt += __shfl_xor_sync(kFull, cnt, o);
+      const uint32_t a = __shfl_xor_sync(kFull, pmin, o), b = __shfl_xor_sync(kFull, pmax, o);
+      pmin = a < pmin ? a : pmin;
+      pmax = b > pmax ? b : pmax;
+    }
+    if (lane == 0) {
+      atomicAdd(&s_np, cnt);
+      atomicMin(&s_pmin, pmin);
+      atomicMax(&s_pmax, pmax);
+    }
   }
   __syncthreads();
-  const int np_real = s_np;
-  uint32_t T;
-  if (nsel <= np_real) {
-    // T = the nsel-th smallest pooled key: the pool holds distinct
-    // centroids, so at least nsel keys are <= T, and T is at least the
-    // nsel-th smallest upper bound of all centroids
-    T = block_select<uint32_t>(pk, np_real, nsel, st);
-    __syncthreads();
+  const bool from_pool = nsel <= s_np;
+  // T bounds the nsel-th smallest upper bound of all centroids from above.
+  // From the pool (distinct centroids): the last value of the histogram bin
+  // (over the pool's range) holding the nsel-th smallest entry, so at least
+  // nsel centroids have keys <= T. Otherwise: the same over all K keys.
+  const uint32_t kmin = from_pool ? s_pmin : kmin_q[q], kmax = from_pool ? s_pmax : kmax_q[q];
+  const uint32_t span1 = kmax - kmin;  // span - 1
+  int shift = 0;
+  while ((span1 >> shift) >= (uint32_t)kHistBins) ++shift;
+  if (from_pool) {
+    for (int i = tid; i < pool_n; i += blockDim.x) {
+      const uint32_t e = sp[i];
+      if (e != 0xffffffffu) atomicAdd(&hist[(e - kmin) >> shift], 1);
+    }
   } else {
-    // histogram of the keys, bin (key - kmin) >> shift (at least half of
-    // the kHistBins bins span [kmin, kmax]); T = the last key of the bin
-    // holding the nsel-th smallest (an upper bound of it)
-    const uint32_t kmin = kmin_q[q], kmax = kmax_q[q];
-    int* hist = reinterpret_cast<int*>(work);
-    for (int i = tid; i < kHistBins; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    const uint32_t span1 = kmax - kmin;  // span - 1
-    int shift = 0;
-    while ((span1 >> shift) >= (uint32_t)kHistBins) ++shift;
     for (int c0 = 0; c0 < K; c0 += kSelU * blockDim.x) {
       uint32_t kv[kSelU];
 #pragma unroll
@@ -1002,65 +1024,114 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
         if (c < K) atomicAdd(&hist[(kv[u] - kmin) >> shift], 1);
       }
     }
+  }
+  __syncthreads();
+  {
+    int cb[4], sum = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      cb[u] = hist[4 * tid + u];
+      sum += cb[u];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) st.warp_cnt[wid] = incl;
     __syncthreads();
-    {
-      int cb[4], sum = 0;
+    for (int w = 0; w < wid; ++w) incl += st.warp_cnt[w];
+    const int excl = incl - sum;
+    if (excl < nsel && incl >= nsel) {  // exactly one thread
+      int cum = excl;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        cb[u] = hist[4 * tid + u];
-        sum += cb[u];
-      }
-      int incl = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-      }
-      if (lane == 31) st.warp_cnt[wid] = incl;
-      __syncthreads();
-      for (int w = 0; w < wid; ++w) incl += st.warp_cnt[w];
-      const int excl = incl - sum;
-      if (excl < nsel && incl >= nsel) {  // exactly one thread
-        int cum = excl;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (cum + cb[u] >= nsel) {
-            s_bin = 4 * tid + u;
-            break;
-          }
-          cum += cb[u];
+        if (cum + cb[u] >= nsel) {
+          s_bin = 4 * tid + u;
+          break;
         }
+        cum += cb[u];
       }
     }
-    __syncthreads();
-    // keys of bin B are at most kmin + ((B + 1) << shift) - 1
-    const uint64_t edge = (uint64_t)kmin + ((uint64_t)(s_bin + 1) << shift) - 1u;
-    T = (uint32_t)min((uint64_t)kmax, edge);
   }
-  // candidates, L_c <= T (ids now, (score key, id) after the
-  // refine), eight centroids per thread per step. L_c = U_c - 2 eps_c (its
-  // rounding is inside the bound's margin) needs ||c||; since eps_c is at
-  // most eps(max ||c||), only keys U_c <= T + 2 eps(max ||c||) (with a margin
-  // for the rounding of the subtraction) can pass, and only theirs are read.
+  __syncthreads();
+  // keys of bin B are at most kmin + ((B + 1) << shift) - 1
+  const uint64_t edge = (uint64_t)kmin + ((uint64_t)(s_bin + 1) << shift) - 1u;
+  const uint32_t T = (uint32_t)min((uint64_t)kmax, edge);
+  // Candidates, L_c <= T (ids now, (score key, id) after the refine).
+  // L_c = U_c - 2 eps_c (its rounding is inside the bound's margin) needs
+  // ||c||; since eps_c is at most eps(max ||c||), only keys U_c <= Tpre =
+  // T + 2 eps(max ||c||) (with a margin for the rounding of the subtraction)
+  // can pass. From the pool: a group of 128 centroids whose largest pooled
+  // entry, rounded down to its key part, is <= Tpre + 128 may hold more
+  // such keys (an entry's key part exceeds its key by less than 128) and is
+  // scanned in full; the others' keys <= Tpre are all pooled, and a pooled
+  // entry whose key part is <= Tpre + 128 has its exact key read.
   const float Tf = key_float(T), e2max = __fmul_rn(2.0f, eps(__ldg(cnorm_max)));
   const uint32_t Tpre =
       float_key(__fadd_ru(__fadd_ru(Tf, e2max), __fmul_ru(0x1.0p-20f, __fadd_ru(fabsf(Tf), e2max))));
   unsigned long long* ckey = reinterpret_cast<unsigned long long*>(work);
-  for (int c0 = 0; c0 < K; c0 += kSelU * blockDim.x) {
-    uint32_t kv[kSelU];
-#pragma unroll
-    for (int u = 0; u < kSelU; ++u) {
-      const int c = c0 + u * blockDim.x + tid;
-      kv[u] = c < K ? __ldg(row + c) : 0xffffffffu;
+  __syncthreads();  // (the histogram is read)
+  auto consider = [&](bool pass_pre, int c) {
+    bool in = false;
+    if (pass_pre)
+      in = float_key(__fsub_rn(key_float(row[c]), __fmul_rn(2.0f, eps(__ldg(cnorm + c))))) <= T;
+    const int slot = warp_reserve(in, &s_nc);
+    if (in && slot < kProbeCandMax) ckey[slot] = (unsigned long long)(uint32_t)c;
+  };
+  bool scan_all = !from_pool;
+  if (from_pool) {
+    const uint64_t lim = (uint64_t)Tpre + 128u;
+    for (int i0 = 0; i0 < pool_n; i0 += blockDim.x) {
+      const int i = i0 + tid;
+      bool pre = false;
+      int c = 0;
+      if (i < pool_n) {
+        const uint32_t e = sp[i];
+        const int g = i / kProbePool, j = i % kProbePool;
+        const uint32_t last = sp[g * kProbePool + kProbePool - 1];
+        const bool sat = last != 0xffffffffu && (uint64_t)(last & ~127u) <= lim;
+        if (sat && j == 0) {
+          const int slot = atomicAdd(&s_nsat, 1);
+          if (slot < 64) s_sat[slot] = g;
+        }
+        c = g * 128 + (int)(e & 127u);
+        pre = !sat && e != 0xffffffffu && (uint64_t)(e & ~127u) <= lim;
+      }
+      consider(pre && row[c] <= Tpre, c);
     }
+    __syncthreads();
+    const int nsat = s_nsat;
+    if (nsat > 64) {
+      scan_all = true;  // many saturated groups: one pass over all keys instead
+      __syncthreads();
+      if (tid == 0) s_nc = 0;
+      __syncthreads();
+    } else {
+      for (int t = 0; t < nsat; ++t) {
+        const int g = s_sat[t];
+        for (int c0 = g * 128; c0 < min(K, g * 128 + 128); c0 += blockDim.x) {
+          const int c = c0 + tid;
+          const bool ok = c < min(K, g * 128 + 128);
+          consider(ok && row[c] <= Tpre, ok ? c : 0);
+        }
+      }
+    }
+  }
+  if (scan_all) {
+    for (int c0 = 0; c0 < K; c0 += kSelU * blockDim.x) {
+      uint32_t kv[kSelU];
 #pragma unroll
-    for (int u = 0; u < kSelU; ++u) {
-      const int c = c0 + u * blockDim.x + tid;
-      bool in = false;
-      if (c < K && kv[u] <= Tpre)
-        in = float_key(__fsub_rn(key_float(kv[u]), __fmul_rn(2.0f, eps(__ldg(cnorm + c))))) <= T;
-      const int slot = warp_reserve(in, &s_nc);
-      if (in && slot < kProbeCandMax) ckey[slot] = (unsigned long long)(uint32_t)c;
+      for (int u = 0; u < kSelU; ++u) {
+        const int c = c0 + u * blockDim.x + tid;
+        kv[u] = c < K ? __ldg(row + c) : 0xffffffffu;
+      }
+#pragma unroll
+      for (int u = 0; u < kSelU; ++u) {
+        const int c = c0 + u * blockDim.x + tid;
+        consider(c < K && kv[u] <= Tpre, c < K ? c : 0);
+      }
     }
   }
   __syncthreads();
@@ -1109,12 +1180,11 @@ __global__ void __launch_bounds__(kThreads) probe_select_kernel(
 }
 
 // Shared memory of probe_select_kernel for dimension d, sort size sort_n and
-// pool_n pooled keys.
+// pool_n pooled entries.
 inline size_t probe_select_smem(int d, int sort_n, int pool_n) {
-  const size_t work = std::max({sizeof(int) * kHistBins, sizeof(uint32_t) * (size_t)pool_n,
-                                sizeof(unsigned long long) * kProbeCandMax,
+  const size_t work = std::max({sizeof(int) * kHistBins, sizeof(unsigned long long) * kProbeCandMax,
                                 sizeof(unsigned long long) * (size_t)sort_n});
-  return align_up(sizeof(float) * d, 16) + work;
+  return align_up(sizeof(float) * d, 16) + align_up(sizeof(uint32_t) * (size_t)pool_n, 16) + work;
 }
 
 // Shared counters the per-query finishing step works with.

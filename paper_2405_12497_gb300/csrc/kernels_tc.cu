@@ -486,7 +486,10 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
       const float q2 = live ? __ldg(nq2 + row) : 0.0f;
       const ProbeEps eps(metric, __fsqrt_rn(q2), d);
       uint32_t tmin = 0xffffffffu, tmax = 0u;
-      uint32_t top[kProbePool];  // the smallest keys of this row and half, ascending
+      // the smallest pool entries of this row and half, ascending: the key
+      // rounded up to a multiple of 128, then the centroid's index in the
+      // half (7 bits)
+      uint32_t top[kProbePool];
 #pragma unroll
       for (int j = 0; j < kProbePool; ++j) top[j] = 0xffffffffu;
       const uint32_t src = taddr + ((uint32_t)(quarter * 32) << 16) + buf * (uint32_t)kPdN +
@@ -514,8 +517,9 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
           if (gb + e < N) {
             tmin = u[e] < tmin ? u[e] : tmin;
             tmax = u[e] > tmax ? u[e] : tmax;
-            if (u[e] < top[kProbePool - 1]) {  // insert, keeping the order
-              uint32_t x = u[e];
+            const uint32_t x0 = ((u[e] + 127u) & ~127u) | (uint32_t)(c0 + e);
+            if (x0 < top[kProbePool - 1]) {  // insert, keeping the order
+              uint32_t x = x0;
 #pragma unroll
               for (int j = 0; j < kProbePool; ++j) {
                 const uint32_t lo = min(top[j], x);
@@ -540,8 +544,8 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
       if (live) {
         atomicMin(kmin + row, tmin);
         atomicMax(kmax + row, tmax);
-        // unused slots (past the last centroid) keep the largest key, which
-        // no selection takes before the real ones
+        // unused slots (past the last centroid) hold 0xffffffff, which no
+        // real entry equals (finite keys are at most 0xff800000)
         uint4* dst = reinterpret_cast<uint4*>(pool + row * (int64_t)(2 * ntn * kProbePool) +
                                               (int64_t)(2 * nt + half) * kProbePool);
         dst[0] = make_uint4(top[0], top[1], top[2], top[3]);

@@ -35,8 +35,12 @@ def _check(R, oracle_mod, data, cents, Q, nprobe, metric="l2"):
         assert np.array_equal(dist[i].view(np.uint32), t["probe_dist"].view(np.uint32))
 
 
+# (33, 300, 1e-3, 100): more probes than the 24 pooled keys, so the threshold
+# comes from the histogram of all keys; (8, 16384, 1.0, 1000): most groups of
+# 128 centroids hold 8 keys under the threshold, so all keys are scanned
 @pytest.mark.parametrize("d,K,scale,nprobe", [(8, 7, 1.0, 7), (33, 300, 1e-3, 17),
-                                               (128, 1024, 200.0, 64), (100, 2000, 1e3, 1)])
+                                               (33, 300, 1e-3, 100), (128, 1024, 200.0, 64),
+                                               (100, 2000, 1e3, 1), (8, 16384, 1.0, 1000)])
 def test_probe_lists_match_full_scan(R, oracle_mod, d, K, scale, nprobe):
     rng = np.random.default_rng(d + K)
     cents = (rng.standard_normal((K, d)) * scale * rng.uniform(0.2, 2, d)).astype(np.float32)
@@ -45,6 +49,21 @@ def test_probe_lists_match_full_scan(R, oracle_mod, d, K, scale, nprobe):
     Q[0] = cents[3]              # a query on a centroid
     Q[1] = 0                     # the zero query
     _check(R, oracle_mod, data, cents, Q, nprobe)
+
+
+def test_crowded_group_is_scanned_in_full(R, oracle_mod):
+    """The 64 nearest centroids of some queries have ids 0..63 (one group of
+    128 centroids): that group's 8 pooled keys are all under the threshold,
+    so its keys are scanned in full; the other queries take their
+    candidates from the pool."""
+    rng = np.random.default_rng(11)
+    d, K = 16, 1024
+    cents = rng.standard_normal((K, d)).astype(np.float32)
+    Q = rng.standard_normal((12, d)).astype(np.float32)
+    cents[:64] = Q[2] + 0.05 * rng.standard_normal((64, d)).astype(np.float32)
+    cents[64:80] = Q[5] + 0.05 * rng.standard_normal((16, d)).astype(np.float32)
+    data = cents + 0.01 * rng.standard_normal((K, d)).astype(np.float32)
+    _check(R, oracle_mod, data, cents, Q, 40)
 
 
 def test_equidistant_centroids_take_the_exact_path(R, oracle_mod):
