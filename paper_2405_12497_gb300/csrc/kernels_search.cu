@@ -773,6 +773,15 @@ template <bool IP>
 __device__ __forceinline__ float row_score(const float* __restrict__ x, const float* qv, int d) {
   float acc = 0.0f;
   if ((d & 7) == 0) {
+    // (qv: 16-byte aligned shared memory, read as float4)
+    const float4* q4 = reinterpret_cast<const float4*>(qv);
+    auto fold8 = [&](const unsigned long long (&v)[4], int c) {
+      const float4 qa = q4[c >> 2], qb = q4[(c >> 2) + 1];
+      const float qq[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        acc = score_step<IP>(acc, qq[e], __int_as_float((int)(uint32_t)(v[e >> 1] >> (32 * (e & 1)))));
+    };
     int c = 0;
     for (; c + 32 <= d; c += 32) {
       unsigned long long v[4][4];
@@ -782,20 +791,14 @@ __device__ __forceinline__ float row_score(const float* __restrict__ x, const fl
                      : "=l"(v[u][0]), "=l"(v[u][1]), "=l"(v[u][2]), "=l"(v[u][3])
                      : "l"(x + c + 8 * u));
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          acc = score_step<IP>(acc, qv[c + 8 * u + e],
-                               __int_as_float((int)(uint32_t)(v[u][e >> 1] >> (32 * (e & 1)))));
+      for (int u = 0; u < 4; ++u) fold8(v[u], c + 8 * u);
     }
     for (; c < d; c += 8) {
       unsigned long long v[4];
       asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
                    : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3])
                    : "l"(x + c));
-#pragma unroll
-      for (int e = 0; e < 8; ++e)
-        acc = score_step<IP>(acc, qv[c + e], __int_as_float((int)(uint32_t)(v[e >> 1] >> (32 * (e & 1)))));
+      fold8(v, c);
     }
   } else if ((d & 3) == 0) {
     const float4* x4 = reinterpret_cast<const float4*>(x);
@@ -1705,15 +1708,76 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
             }
           }
         }
-        // <x_b, q_u> of every pair (§3.3.2)
-        bool ip_done = false;
+        // A block inside one probe (direct loads, D' = 128 / 256, B_q = 4):
+        // every pair valid, the probe's bounds shared, each plane word read
+        // once for both pairs, appends reserved from ballots.
+        bool evaluated = false;
         if constexpr (!STG && PPT == 2 && (WT == 2 || WT == 4) && BQT == 4) {
           if (one_probe) {
+            evaluated = true;
             code_ip2<WT>(cr[0], cr[1], S.planes + (size_t)j * (4 * WT), ipv[0], ipv[1]);
-            ip_done = true;
+            const float4 mt = S.pmeta[j];
+            const int psum = S.psum[j];
+            const float tau = s_tau;
+            float dv[2], lv[2], uv[2];
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+              const float4 f = fv[pp];
+              // estimator (§3.3.2 + Theorem 3.2) and its bound, fixed FP32 order
+              const float t1 = (float)(2 * ipv[pp] - psum);
+              const float xq = __fadd_rn(__fmul_rn(mt.x, t1), __fmul_rn(mt.y, f.w));
+              dv[pp] = __fsub_rn(__fadd_rn(f.x, mt.w), __fmul_rn(f.y, xq));
+              const float e = __fmul_rn(f.z, mt.z);
+              lv[pp] = __fsub_rn(dv[pp], e);
+              uv[pp] = __fadd_rn(dv[pp], e);
+            }
+            const unsigned lt = (1u << lane) - 1u;
+            const unsigned mu0 = __ballot_sync(kFull, uv[0] < tau);
+            const unsigned mu1 = __ballot_sync(kFull, uv[1] < tau);
+            if (mu0 | mu1) {
+              int b = 0;
+              if (lane == 0) b = atomicAdd(&s_ub_cnt, __popc(mu0) + __popc(mu1));
+              b = __shfl_sync(kFull, b, 0);
+              if (uv[0] < tau) S.ubk[b + __popc(mu0 & lt)] = float_key(uv[0]);
+              if (uv[1] < tau) S.ubk[b + __popc(mu0) + __popc(mu1 & lt)] = float_key(uv[1]);
+            }
+            const unsigned mc0 = __ballot_sync(kFull, lv[0] <= tau);
+            const unsigned mc1 = __ballot_sync(kFull, lv[1] <= tau);
+            if (mc0 | mc1) {
+              int b = 0;
+              if (lane == 0) b = atomicAdd(&s_cand_cnt, __popc(mc0) + __popc(mc1));
+              b = __shfl_sync(kFull, b, 0);
+#pragma unroll
+              for (int pp = 0; pp < 2; ++pp) {
+                if (lv[pp] <= tau) {
+                  const int slot = b + (pp == 0 ? __popc(mc0 & lt) : __popc(mc0) + __popc(mc1 & lt));
+                  if (slot < P.cand_cap)
+                    cand[slot] = make_int4(posv[pp], __float_as_int(lv[pp]), __float_as_int(dv[pp]),
+                                           __float_as_int(uv[pp]));
+                  else
+                    s_overflow = 1;
+                }
+              }
+            }
+            if (tracing) {
+#pragma unroll
+              for (int pp = 0; pp < 2; ++pp) {
+                const int64_t tt = pairs_done + tv[pp];
+                if (tt < P.tr.pair_cap) {
+                  const int64_t o = q * P.tr.pair_cap + tt;
+                  P.tr.pair_id[o] = __ldg(P.perm + posv[pp]);
+                  P.tr.pair_ip[o] = ipv[pp];
+                  P.tr.pair_est[3 * o] = dv[pp];
+                  P.tr.pair_est[3 * o + 1] = lv[pp];
+                  P.tr.pair_est[3 * o + 2] = uv[pp];
+                }
+              }
+            }
           }
         }
-        if (!ip_done) {
+        if (!evaluated) {
+        // <x_b, q_u> of every pair (§3.3.2)
+        {
 #pragma unroll
           for (int pp = 0; pp < PPT; ++pp)
             ipv[pp] = posv[pp] < 0 ? 0
@@ -1792,6 +1856,7 @@ __global__ void __launch_bounds__(kThreads, fused_min_blocks<WT>()) fused_search
             }
           }
         }
+        }  // !evaluated
         if (rnd % kUpkeep != kUpkeep - 1 && base + step < total) continue;
         // Buffer upkeep. The counters are read between two barriers: after
         // every append before this point and before any append after it, so

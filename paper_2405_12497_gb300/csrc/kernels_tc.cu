@@ -18,8 +18,8 @@
 // queries by query_prep_kernel per search), so that every K stage of a
 // 128 x 256 output tile is two contiguous bulk copies. One producer warp
 // fills a ring of stages, one thread issues the MMAs into one of two TMEM
-// accumulators, and eight warps turn the other accumulator's products into
-// the filter's upper-bound keys.
+// accumulators, and two groups of eight warps turn the accumulators'
+// products into the filter's upper-bound keys.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -216,7 +216,8 @@ constexpr int kPdN = 256;                        // centroids per tile (TMEM col
 constexpr int kPdStages = 4;                     // ring of K stages
 constexpr int kPdA = kPdM * kStageBytes;         // 16 KB: one A stage
 constexpr int kPdB = kPdN * kStageBytes;         // 32 KB: one B stage
-constexpr int kPdEpi = 8;                        // epilogue warps: two per TMEM lane quarter
+constexpr int kPdEpiG = 8;                       // warps of an epilogue group (one accumulator)
+constexpr int kPdEpi = 2 * kPdEpiG;              // epilogue warps: two groups
 constexpr int kPdThreads = (kPdEpi + 2) * 32;    // then the producer warp and the MMA warp
 constexpr int kPdCols = kPdN / 2;                // columns per epilogue warp
 constexpr size_t kPdSmem = (size_t)kPdStages * (kPdA + kPdB);
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
   __shared__ uint32_t s_taddr;
   __shared__ __align__(8) uint64_t s_full[kPdStages], s_empty[kPdStages], s_tfull[2], s_tempty[2];
   __shared__ volatile int s_fail;
-  __shared__ float s_cn2[kPdN], s_cnorm[kPdN];  // the current tile's centroid norms
+  __shared__ float s_cn2[2][kPdN], s_cnorm[2][kPdN];  // each group's tile's centroid norms
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t G = gridDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * items / G, i1 = ((int64_t)blockIdx.x + 1) * items / G;
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
     for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_tfull[i])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_tempty[i])),
-                   "r"(kPdEpi * 32));
+                   "r"(kPdEpiG * 32));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
     s_fail = 0;
@@ -449,14 +450,19 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
       }
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and
-    // the columns [kPdCols (w / 4), + kPdCols); the two halves keep their
-    // own pool entries. Each half stages its columns' ||c||^2 and ||c|| in
-    // shared memory (loaded before the tile's MMAs are waited for).
-    const int quarter = warp & 3, half = warp >> 2, ht = tid & 127;
-    const uint32_t bar_id = 1u + (uint32_t)half;
-    uint32_t tc = 0;
-    for (int64_t i = i0; i < i1; ++i, ++tc) {
+    // epilogue: group g (warps 8g .. 8g + 7) takes the CTA's tiles g, g + 2,
+    // ..., which accumulate in TMEM buffer g. Its warp w reads TMEM lanes
+    // 32 (w % 4) .. + 31 (tile rows) and the columns [kPdCols ((w / 4) % 2),
+    // + kPdCols); the two halves keep their own pool entries. Each half
+    // stages its columns' ||c||^2 and ||c|| in shared memory (loaded before
+    // the tile's MMAs are waited for).
+    const int group = warp / kPdEpiG, quarter = warp & 3, half = (warp >> 2) & 1;
+    const int ht = tid & 127;
+    const uint32_t bar_id = 1u + 2u * (uint32_t)group + (uint32_t)half;
+    float* g_cn2 = s_cn2[group];
+    float* g_cnorm = s_cnorm[group];
+    for (int64_t i = i0 + group; i < i1; i += 2) {
+      const uint32_t tc = (uint32_t)(i - i0);
       const uint32_t buf = tc & 1u;
       const int64_t mt = i / ntn;
       const int nt = (int)(i % ntn);
@@ -478,8 +484,8 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      s_cn2[half * kPdCols + ht] = ncn2;
-      s_cnorm[half * kPdCols + ht] = ncnorm;
+      g_cn2[half * kPdCols + ht] = ncn2;
+      g_cnorm[half * kPdCols + ht] = ncnorm;
       asm volatile("bar.sync %0, 128;" ::"r"(bar_id));
       const int64_t row = mt * kPdM + quarter * 32 + lane;
       const bool live = row < M;
@@ -508,23 +514,32 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
         // U_c = approximate score + eps_c as an order-preserving key (the
         // same FP32 operations as the filter's definition)
         uint32_t u[16];
+        uint32_t below = 0;  // the chunk's entries under the pool's largest
+        const uint32_t thr = top[kProbePool - 1];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int sc_i = half * kPdCols + c0 + e;
           const float v = __uint_as_float(r[e]);
-          const float sc = metric ? -v : __fsub_rn(__fadd_rn(q2, s_cn2[sc_i]), __fmul_rn(2.0f, v));
-          u[e] = float_key(__fadd_rn(sc, eps(s_cnorm[sc_i])));
+          const float sc = metric ? -v : __fsub_rn(__fadd_rn(q2, g_cn2[sc_i]), __fmul_rn(2.0f, v));
+          u[e] = float_key(__fadd_rn(sc, eps(g_cnorm[sc_i])));
           if (gb + e < N) {
             tmin = u[e] < tmin ? u[e] : tmin;
             tmax = u[e] > tmax ? u[e] : tmax;
-            const uint32_t x0 = ((u[e] + 127u) & ~127u) | (uint32_t)(c0 + e);
-            if (x0 < top[kProbePool - 1]) {  // insert, keeping the order
-              uint32_t x = x0;
+            if ((((u[e] + 127u) & ~127u) | (uint32_t)(c0 + e)) < thr) below |= 1u << e;
+          }
+        }
+        // insert them, keeping the order (only entries under the largest
+        // before the chunk can enter it)
+        if (below) {
 #pragma unroll
-              for (int j = 0; j < kProbePool; ++j) {
-                const uint32_t lo = min(top[j], x);
-                x = max(top[j], x);
-                top[j] = lo;
+          for (int e = 0; e < 16; ++e) {
+            if ((below >> e) & 1u) {
+              uint32_t x = ((u[e] + 127u) & ~127u) | (uint32_t)(c0 + e);
+#pragma unroll
+              for (int jj = 0; jj < kProbePool; ++jj) {
+                const uint32_t lo = min(top[jj], x);
+                x = max(top[jj], x);
+                top[jj] = lo;
               }
             }
           }
