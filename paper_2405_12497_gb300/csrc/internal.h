@@ -124,6 +124,13 @@ int counting_sort(const int32_t* key, int64_t n, int32_t K, int32_t* perm, int32
 // the same with caller-provided scratch of counting_sort_ws_ints(n, K) ints
 // (no allocation, so it can be captured in a CUDA graph)
 int64_t counting_sort_ws_ints(int64_t n, int32_t K);
+// Ids [0, n) grouped by key, the order within a key unspecified (a work
+// order): one block when n <= 65536 and K <= 8192, else counting_sort_ws
+// with the caller's scratch ws (counting_sort_ws_ints(n, K) ints, unused by
+// the one-block sort).
+int order_sort(const int32_t* key, int64_t n, int32_t K, int32_t* perm, int32_t* offsets,
+               int32_t* ws, cudaStream_t s);
+bool order_sort_fits(int64_t n, int32_t K);
 int counting_sort_ws(const int32_t* key, int64_t n, int32_t K, int32_t* perm, int32_t* offsets,
                      int32_t* ws, cudaStream_t s);
 int sample_rotation_dev(uint64_t seed, int32_t dpad, double* P64, float* P32, cudaStream_t s);

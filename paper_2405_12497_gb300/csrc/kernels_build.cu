@@ -128,6 +128,36 @@ __global__ void sort_scatter_kernel(const int32_t* __restrict__ key, int64_t n, 
   }
 }
 
+// Counting sort of ids [0, n) by key in one block (small n and K): counts
+// in shared memory, one scan, then each id takes the next slot of its key
+// (the order within a key is unspecified).
+constexpr int kOrderThreads = 1024;
+__global__ void __launch_bounds__(kOrderThreads) order_sort_kernel(const int32_t* __restrict__ key,
+                                                                   int n, int K,
+                                                                   int32_t* __restrict__ perm,
+                                                                   int32_t* __restrict__ offsets) {
+  extern __shared__ int ocnt[];  // K
+  for (int i = threadIdx.x; i < K; i += blockDim.x) ocnt[i] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&ocnt[key[i]], 1);
+  __syncthreads();
+  const int per = (K + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int b0 = min(K, (int)threadIdx.x * per), b1 = min(K, b0 + per);
+  int sum = 0;
+  for (int b = b0; b < b1; ++b) sum += ocnt[b];
+  int tot;
+  int run = block_exclusive_scan(sum, &tot);
+  for (int b = b0; b < b1; ++b) {
+    const int c = ocnt[b];
+    ocnt[b] = run;
+    offsets[b] = run;
+    run += c;
+  }
+  if (threadIdx.x == 0) offsets[K] = n;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[atomicAdd(&ocnt[key[i]], 1)] = i;
+}
+
 __global__ void bucket_offsets_kernel(const int32_t* __restrict__ off, int K, int nw, int64_t n,
                                       int32_t* __restrict__ offsets) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -488,6 +518,17 @@ int counting_sort_ws(const int32_t* key, int64_t n, int32_t K, int32_t* perm, in
   RBQ_CHECK(scan_ws(hist, off, cells, sums, s));
   bucket_offsets_kernel<<<blocks_for(K + 1, 256), 256, 0, s>>>(off, K, (int)nw, n, offsets);
   sort_scatter_kernel<<<blocks, 256, 0, s>>>(key, n, (int)nw, L, off, perm);
+  RBQ_CUDA(cudaGetLastError());
+  return RABITQ_OK;
+}
+
+bool order_sort_fits(int64_t n, int32_t K) { return n <= (int64_t(1) << 16) && K <= 8192; }
+
+int order_sort(const int32_t* key, int64_t n, int32_t K, int32_t* perm, int32_t* offsets,
+               int32_t* ws, cudaStream_t s) {
+  if (n <= 0) return RABITQ_OK;
+  if (!order_sort_fits(n, K)) return counting_sort_ws(key, n, K, perm, offsets, ws, s);
+  order_sort_kernel<<<1, kOrderThreads, sizeof(int) * (size_t)K, s>>>(key, (int)n, K, perm, offsets);
   RBQ_CUDA(cudaGetLastError());
   return RABITQ_OK;
 }

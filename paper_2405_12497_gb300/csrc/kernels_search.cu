@@ -3416,7 +3416,7 @@ int launch_warp(WarpFn wfn, int64_t wctas, const FusedParams& P, const WarpScrat
   work_key_kernel<<<(unsigned)((P.nq + 255) / 256), 256, 0, s>>>(
       P.probe_ids, P.nprobe_q, P.nq, P.nprobe, P.bucket_off, ws.wkey);
   RBQ_CUDA(cudaGetLastError());
-  RBQ_CHECK(counting_sort_ws(ws.wkey, P.nq, kWorkKeys, ws.worder, ws.wooff, ws.wsortws, s));
+  RBQ_CHECK(order_sort(ws.wkey, P.nq, kWorkKeys, ws.worder, ws.wooff, ws.wsortws, s));
   int* redo = ws.redo;
   FusedParams W = P;
   W.candw = ws.candw;
@@ -3622,8 +3622,12 @@ int search_dev_popc(const SearchArgs& a, cudaStream_t s) {
     if (npq) {
       order_key_kernel<<<(unsigned)((nqc + 255) / 256), 256, 0, s>>>(npq, nqc, nprobe,
                                                                     okey.as<int32_t>());
-      RBQ_CHECK(counting_sort(okey.as<int32_t>(), nqc, nprobe + 1, order.as<int32_t>(),
-                              ooff.as<int32_t>(), s));
+      if (order_sort_fits(nqc, nprobe + 1))
+        RBQ_CHECK(order_sort(okey.as<int32_t>(), nqc, nprobe + 1, order.as<int32_t>(),
+                             ooff.as<int32_t>(), nullptr, s));
+      else
+        RBQ_CHECK(counting_sort(okey.as<int32_t>(), nqc, nprobe + 1, order.as<int32_t>(),
+                                ooff.as<int32_t>(), s));
       P.order = order.as<int32_t>();
     }
     if (a.trace) {
@@ -3902,7 +3906,7 @@ int search_enqueue_carved(const SearchArgs& a, unsigned char* scratch, size_t sc
     if (npq) {
       order_key_kernel<<<(unsigned)((nqc + 255) / 256), 256, 0, s>>>(npq, nqc, nprobe, okey);
       RBQ_CUDA(cudaGetLastError());
-      RBQ_CHECK(counting_sort_ws(okey, nqc, nprobe + 1, order, ooff, sortws, s));
+      RBQ_CHECK(order_sort(okey, nqc, nprobe + 1, order, ooff, sortws, s));
       P.order = order;
     }
     const int split = a.allow_split ? split_factor(a, nqc, grid, fs) : 1;
