@@ -841,11 +841,12 @@ __device__ void rerank_rows(const FusedParams& P, const FusedSmem& S, int64_t q,
                             const int4* cand, int* top_cnt, int* surv_cnt,
                             unsigned long long kmax = ~0ull) {
   const int d = P.d;
-  // Ask L2 for every row of the set first (no registers held, no waiting):
-  // the loads below then find most rows in L2 instead of waiting on DRAM
-  // eight loads at a time.
+  // Ask L2 for the rows of the first two rounds (no registers held, no
+  // waiting): their loads then find most rows in L2 instead of waiting on
+  // DRAM four loads at a time. (Asking for a whole set of thousands of rows
+  // at once, or two rounds ahead every round, measured slower.)
   const int row_bytes = d * (int)sizeof(float);
-  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+  for (int i = threadIdx.x; i < min(count, 2 * (int)blockDim.x); i += blockDim.x) {
     const int pos = SRC == 0 ? (int)(S.estk[i] & 0xffffffffu) : (cand[i].x & 0x7fffffff);
     const char* x = reinterpret_cast<const char*>(P.data_b + (int64_t)pos * d);
     for (int o = 0; o < row_bytes; o += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(x + o));

@@ -213,7 +213,7 @@ __global__ void pack_pt_kernel(const float* __restrict__ P32, int d, int dpad, i
 // ---- probe products
 constexpr int kPdM = 128;                        // queries per tile (TMEM lanes)
 constexpr int kPdN = 256;                        // centroids per tile (TMEM columns)
-constexpr int kPdStages = 4;                     // ring of K stages
+constexpr int kPdStages = 3;                     // ring of K stages
 constexpr int kPdA = kPdM * kStageBytes;         // 16 KB: one A stage
 constexpr int kPdB = kPdN * kStageBytes;         // 32 KB: one B stage
 constexpr int kPdEpiG = 8;                       // warps of an epilogue group (one accumulator)
