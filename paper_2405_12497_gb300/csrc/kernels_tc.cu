@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
   __shared__ uint32_t s_taddr;
   __shared__ __align__(8) uint64_t s_full[kPdStages], s_empty[kPdStages], s_tfull[2], s_tempty[2];
   __shared__ volatile int s_fail;
-  __shared__ float s_cn2[2][kPdN], s_cnorm[2][kPdN];  // each group's tile's centroid norms
+  __shared__ __align__(16) float s_cn2[2][kPdN];  // each group's tile's centroid norms
+  __shared__ __align__(16) float s_cnorm[2][kPdN];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t G = gridDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * items / G, i1 = ((int64_t)blockIdx.x + 1) * items / G;
@@ -516,12 +517,20 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
         uint32_t u[16];
         uint32_t below = 0;  // the chunk's entries under the pool's largest
         const uint32_t thr = top[kProbePool - 1];
+        // the chunk's 16 norms as four 16-byte broadcast reads each
+        float n2v[16], nnv[16];
+#pragma unroll
+        for (int v4 = 0; v4 < 4; ++v4) {
+          const float4 a = reinterpret_cast<const float4*>(g_cn2 + half * kPdCols + c0)[v4];
+          const float4 b = reinterpret_cast<const float4*>(g_cnorm + half * kPdCols + c0)[v4];
+          n2v[4 * v4] = a.x; n2v[4 * v4 + 1] = a.y; n2v[4 * v4 + 2] = a.z; n2v[4 * v4 + 3] = a.w;
+          nnv[4 * v4] = b.x; nnv[4 * v4 + 1] = b.y; nnv[4 * v4 + 2] = b.z; nnv[4 * v4 + 3] = b.w;
+        }
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const int sc_i = half * kPdCols + c0 + e;
           const float v = __uint_as_float(r[e]);
-          const float sc = metric ? -v : __fsub_rn(__fadd_rn(q2, g_cn2[sc_i]), __fmul_rn(2.0f, v));
-          u[e] = float_key(__fadd_rn(sc, eps(g_cnorm[sc_i])));
+          const float sc = metric ? -v : __fsub_rn(__fadd_rn(q2, n2v[e]), __fmul_rn(2.0f, v));
+          u[e] = float_key(__fadd_rn(sc, eps(nnv[e])));
           if (gb + e < N) {
             tmin = u[e] < tmin ? u[e] : tmin;
             tmax = u[e] > tmax ? u[e] : tmax;
