@@ -643,6 +643,18 @@ void rabitq_free(rabitq_index* idx);
 /* Message of the last failure on the calling thread ("" if none). */
 const char* rabitq_last_error(void);
 
+/*
+ * rabitq_selftest_wait -- checks, on the current device, the bounded waits
+ * that every mbarrier wait of the library's tensor-core kernels uses (a
+ * library safeguard; the paper has no counterpart). One small kernel waits
+ * `polls` times on an mbarrier that nothing completes and must give up,
+ * then waits again while another warp raises the CTA's failure flag and
+ * must give up on the flag; the kernel then exits normally, so the context
+ * stays usable. Returns OK when both waits gave up; EIO when one did not;
+ * EINVAL for polls == 0; ECUDA on a launch or copy failure.
+ */
+int rabitq_selftest_wait(uint32_t polls);
+
 #ifdef __cplusplus
 }
 #endif

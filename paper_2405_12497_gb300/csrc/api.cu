@@ -164,6 +164,17 @@ void rabitq_search_opts_default(rabitq_search_opts* o) {
 
 const char* rabitq_last_error(void) { return g_err.c_str(); }
 
+int rabitq_selftest_wait(uint32_t polls) {
+  g_err.clear();
+  if (polls == 0) return fail(RABITQ_EINVAL, "rabitq_selftest_wait: polls must be positive");
+  int status = 0;
+  RBQ_CHECK(wait_selftest(polls, &status));
+  if (status != 3)
+    return fail(RABITQ_EIO, "rabitq_selftest_wait: a bounded wait did not give up (status " +
+                                std::to_string(status) + ")");
+  return RABITQ_OK;
+}
+
 int rabitq_last_stats(float* ms, int32_t cap) {
   if (!ms || cap < 0) return fail(RABITQ_EINVAL, "rabitq_last_stats: null output");
   const int m = std::min<int>(cap, g_nstats);

@@ -173,6 +173,8 @@ struct ProbeScratch {
 };
 ProbeScratch probe_scratch(const rabitq_index* X, int64_t nq, float* base);
 size_t probe_scratch_floats(const rabitq_index* X, int64_t nq);
+// runs the bounded-wait self-test kernel; *status_host gets its result bits
+int wait_selftest(uint32_t polls, int* status_host);
 int probe_keys_tc(const rabitq_index* X, const float* Q, int64_t M, float* scratch, int* err,
                   cudaStream_t s);
 // rows of the index's tiled TF32 centroid array (K padded to whole tiles)

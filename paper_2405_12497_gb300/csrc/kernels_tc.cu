@@ -295,8 +295,9 @@ __global__ void query_prep_kernel(const float* __restrict__ Q, int64_t M, int d,
 }
 
 // Bounded wait that also gives up once another role of the CTA has failed.
-__device__ __forceinline__ bool pd_wait(uint32_t bar, uint32_t parity, volatile int* fail) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool pd_wait(uint32_t bar, uint32_t parity, volatile int* fail,
+                                        uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -588,7 +589,45 @@ __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
                  "r"(2 * kPdN));
 }
 
+// Self-test of the bounded waits (two warps, nothing ever completes the
+// barrier): warp 0 waits `polls` times on an mbarrier that no one arrives on
+// and must give up (bit 0 of *status); then it waits again with no poll
+// limit that matters while warp 1 raises the CTA's failure flag, and must
+// give up on the flag (bit 1). The kernel then returns normally.
+__global__ void wait_selftest_kernel(uint32_t polls, int* status) {
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ volatile int s_fail;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_fail = 0;
+  }
+  __syncthreads();
+  int st = 0;
+  if (threadIdx.x == 0) {
+    if (!mbar_wait(smem_u32(&s_bar), 0u, polls)) st |= 1;
+    if (!pd_wait(smem_u32(&s_bar), 0u, &s_fail)) st |= 2;  // ends once warp 1 sets the flag
+    *status = st;
+  } else if (threadIdx.x == 32) {
+    const long long t0 = clock64();
+    while (clock64() - t0 < 100000) {
+    }
+    s_fail = 1;
+  }
+  __syncthreads();
+}
+
 }  // namespace
+
+int wait_selftest(uint32_t polls, int* status_host) {
+  DevBuf st;
+  RBQ_CHECK(st.alloc(sizeof(int), nullptr));
+  RBQ_CUDA(cudaMemset(st.p, 0, sizeof(int)));
+  wait_selftest_kernel<<<1, 64>>>(polls, st.as<int>());
+  RBQ_CUDA(cudaGetLastError());
+  RBQ_CUDA(cudaMemcpy(status_host, st.p, sizeof(int), cudaMemcpyDeviceToHost));
+  return RABITQ_OK;
+}
 
 int64_t centroid_tile_rows(int K) { return ((int64_t)K + kPdN - 1) / kPdN * kPdN; }
 

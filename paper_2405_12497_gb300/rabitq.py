@@ -42,7 +42,7 @@ EXPORTS = (
     "rabitq_estimate", "rabitq_autotune_tiles", "rabitq_plan_tile", "rabitq_shard_clusters",
     "rabitq_merge_topk", "rabitq_server_opts_default", "rabitq_server_create",
     "rabitq_server_add_index", "rabitq_server_submit", "rabitq_server_wait",
-    "rabitq_server_get_stats", "rabitq_server_free",
+    "rabitq_server_get_stats", "rabitq_server_free", "rabitq_selftest_wait",
 )
 
 MLP_IN, MLP_HIDDEN = 64, 256
@@ -172,6 +172,7 @@ def lib():
             "rabitq_server_wait": (C.c_int, [vp, i64, C.c_double, vp]),
             "rabitq_server_get_stats": (C.c_int, [vp, vp]),
             "rabitq_server_free": (None, [vp]),
+            "rabitq_selftest_wait": (C.c_int, [C.c_uint32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -188,6 +189,13 @@ def _check(code: int):
 
 def _np_ptr(a):
     return a.ctypes.data_as(C.c_void_p)
+
+
+def selftest_wait(polls: int = 1 << 12):
+    """Bounded-wait self-test on the current device (rabitq_selftest_wait):
+    raises RabitqError unless both of its waits gave up and the kernel
+    returned."""
+    _check(lib().rabitq_selftest_wait(int(polls)))
 
 
 def _is_torch(x) -> bool:
