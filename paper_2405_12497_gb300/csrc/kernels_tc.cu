@@ -210,7 +210,7 @@ __global__ void pack_pt_kernel(const float* __restrict__ P32, int d, int dpad, i
   ptf[i] = to_tf32(v);
 }
 
-// ---- probe products
+// ---- probe scores (products and the filter's keys)
 constexpr int kPdM = 128;                        // queries per tile (TMEM lanes)
 constexpr int kPdN = 256;                        // centroids per tile (TMEM columns)
 constexpr int kPdStages = 3;                     // ring of K stages
@@ -311,14 +311,18 @@ __device__ __forceinline__ bool pd_wait(uint32_t bar, uint32_t parity, volatile 
   return false;
 }
 
-// C[M x N] = Qt Ct^T over the tiles (m, n), m-major; CTA b takes the items
-// [b items / G, (b + 1) items / G). Stage it of the CTA's sequence lives in
-// ring slot it % kPdStages; tile j of the CTA accumulates in TMEM columns
-// (j & 1) * kPdN. Barriers: full (copies landed), empty (the MMAs reading
-// the slot are done), tfull (a tile's accumulator is complete), tempty (the
-// epilogue has read it). A wait that expires sets *err = 2; the roles then
-// stop, wait (bounded) for their own copies or MMAs in flight, and the CTA
-// frees its TMEM.
+// The products Qt Ct^T (M x N) over tiles (m, n), m-major, turned into the
+// probe filter's keys: keys[m][c] = key of U_c, each row's key range in
+// kmin / kmax (atomics), and per row and 128 columns the kProbePool smallest
+// entries (key rounded up to a multiple of 128 | column index in the 128,
+// ascending) in pool. CTA b takes the items [b items / G, (b + 1) items / G).
+// Stage it of the CTA's sequence lives in ring slot it % kPdStages; tile j of
+// the CTA accumulates in TMEM columns (j & 1) * kPdN and is drained by
+// epilogue group j & 1. Barriers: full (copies landed), empty (the MMAs
+// reading the slot are done), tfull (a tile's accumulator is complete),
+// tempty (its epilogue group has read it). A wait that expires sets
+// *err = 2; the roles then stop, wait (bounded) for their own copies or
+// MMAs in flight, and the CTA frees its TMEM.
 __global__ void __launch_bounds__(kPdThreads, 1) probe_dot_kernel(
     const float* __restrict__ qt, const float* __restrict__ ct, int64_t M, int N, int nks,
     int ntn, int64_t items, int d, int metric, const float* __restrict__ nq2,
