@@ -471,6 +471,38 @@ def test_per_query_probe_counts(oracle_mod, tiny_oracle_index, tiny_workload):
         assert np.array_equal(dist[rows], dist_c[rows])
 
 
+def test_mass_ties_resolve_by_id(oracle_mod):
+    """700 identical points: FP64 brute force says they are the 700 nearest
+    of the queries built on them, so the (distance, id) ranking of §4 makes
+    the top-k the k lowest of their ids, all at one distance (0 for the
+    point itself). Pins the tie handling of tau_ub, the pilot, the
+    survivor test and the final selection when whole key ranges are equal;
+    all points identical pins it through empty clusters and equal centroid
+    scores."""
+    rng = np.random.default_rng(21)
+    data = rng.standard_normal((4000, 128)).astype(np.float32)
+    data[1000:1700] = data[1000]
+    Q = np.stack([data[1000], data[1000] + np.float32(1e-3), data[1000] * np.float32(1.5)])
+    ex = ((Q.astype(np.float64)[:, None, :] - data.astype(np.float64)[None]) ** 2).sum(-1)
+    near = np.argsort(ex, axis=1, kind="stable")[:, :700]
+    assert (np.sort(near, axis=1) == np.arange(1000, 1700)).all()
+    X = oracle_mod.OracleIndex(data, K=24, seed=4)
+    for k, nprobe in ((100, 4), (1, 1), (128, 24)):
+        ids, dist = X.search(Q, k, nprobe)
+        assert (ids == np.arange(1000, 1000 + k)).all()
+        assert (dist == dist[:, :1]).all() and (dist[0] == 0).all()
+        assert np.allclose(dist[:, 0], ex[:, 1000], rtol=1e-5, atol=1e-9)
+    t = X.trace(Q[1], 1, 100, 4)
+    ub = t["pair_est"][t["pair_id"] >= 1000][:, 2]
+    ub = ub[t["pair_id"][t["pair_id"] >= 1000] < 1700]
+    assert t["tau_ub"] == ub[0] and (ub == ub[0]).all()
+    same = np.repeat(data[:1], 500, axis=0)
+    Y = oracle_mod.OracleIndex(same, K=4, seed=4)
+    assert np.array_equal(Y.assign, np.zeros(500, np.int64))
+    ids, dist = Y.search(np.stack([same[0], Q[2]]), 10, 1)
+    assert (ids == np.arange(10)).all() and (dist == dist[:, :1]).all() and (dist[0] == 0).all()
+
+
 def test_trace_rerank_set_definition(oracle_mod, tiny_oracle_index, tiny_workload):
     """Re-rank set = pilot (4k smallest estimates by (estimate, id) among the
     codes with LB <= k-th smallest UB) plus every code with LB <= min(k-th
