@@ -118,6 +118,37 @@ def test_all_buckets_and_padding(R, tiny_gpu_index, tiny_oracle_index, tiny_work
     assert (ids_g == -1).any() and np.isinf(dist_g[ids_g == -1]).all()
 
 
+def test_largest_k_matches_oracle(R, tiny_gpu_index, tiny_oracle_index, tiny_workload):
+    """k = 1024, the largest the API takes (and 1023): a 4096-code pilot,
+    a top-k buffer cut back to k several times during the re-rank, and
+    1024-key sorts, in every form of the CTA kernel, the bucket-major
+    tensor-core scan, split mode and a search plan."""
+    import torch
+    _, Q = tiny_workload
+    Q = Q[:40]
+    qd = torch.from_numpy(Q).cuda()
+    G = tiny_gpu_index
+    for k, nprobe in ((1024, 16), (1024, 6), (1023, 3)):
+        ids_o, dist_o = tiny_oracle_index.search(Q, k, nprobe)
+        assert (ids_o >= 0).all()
+        for kw in (dict(layout=R.LAYOUT_CTA, staging=R.STAGING_OFF),
+                   dict(layout=R.LAYOUT_CTA, staging=R.STAGING_BULK), dict(scan_path=R.SCAN_TC)):
+            ids, dist = G.search(qd, k, nprobe, **kw)
+            assert np.array_equal(ids.cpu().numpy(), ids_o), (k, nprobe, kw)
+            assert np.array_equal(dist.cpu().numpy().view(np.uint32), dist_o.view(np.uint32))
+        for nq in (1, 3):                      # small batches: split mode
+            ids, dist = G.search(Q[:nq], k, nprobe)
+            assert np.array_equal(ids, ids_o[:nq])
+            assert np.array_equal(dist.view(np.uint32), dist_o[:nq].view(np.uint32))
+    plan = R.Plan(G, 1024, 16, len(Q))
+    plan.queries.copy_(qd)
+    plan.run(len(Q))
+    plan.sync()
+    ids_o, dist_o = tiny_oracle_index.search(Q, 1024, 16)
+    assert np.array_equal(plan.ids.cpu().numpy(), ids_o)
+    assert np.array_equal(plan.dist.cpu().numpy().view(np.uint32), dist_o.view(np.uint32))
+
+
 def _ragged_case(oracle_mod, n, d, K, code_bits, seed, sample=0):
     rng = np.random.default_rng(seed)
     data = (rng.standard_normal((n, d)) * rng.uniform(0.1, 3, d)).astype(np.float32)
@@ -176,7 +207,8 @@ def test_save_load_roundtrip(R, tiny_gpu_index, tiny_workload, tmp_path):
 
 def test_invalid_search_arguments(R, tiny_gpu_index, tiny_workload):
     _, Q = tiny_workload
-    for kw in (dict(k=0, nprobe=4), dict(k=10, nprobe=17), dict(k=10, nprobe=4, bq=9),
+    for kw in (dict(k=0, nprobe=4), dict(k=1025, nprobe=4), dict(k=10, nprobe=17),
+               dict(k=10, nprobe=4, bq=9),
                dict(k=10, nprobe=4, eps0=float("nan"))):
         with pytest.raises(R.RabitqError) as e:
             tiny_gpu_index.search(Q, **kw)
