@@ -323,17 +323,10 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
   cudaStream_t s = static_cast<cudaStream_t>(opts.stream);
   const bool on_dev = trace ? true : opts.io_on_device != 0;
 
-  struct Events {  // destroyed on every return path
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
-    ~Events() {
-      if (t0) cudaEventDestroy(t0);
-      if (t1) cudaEventDestroy(t1);
-    }
-  } ev;
+  EventSet<2> ev;  // t0, t1 of the whole search (stats)
   if (opts.collect_stats) {
-    RBQ_CUDA(cudaEventCreate(&ev.t0));
-    RBQ_CUDA(cudaEventCreate(&ev.t1));
-    RBQ_CUDA(cudaEventRecord(ev.t0, s));
+    RBQ_CHECK(ev.create());
+    RBQ_CUDA(cudaEventRecord(ev[0], s));
   }
   DevBuf qb, ib, db, nb, pb;
   const float* dq = queries;
@@ -393,14 +386,14 @@ static int search_common(const rabitq_index* X, const float* queries, int64_t nq
     RBQ_CUDA(cudaMemcpyAsync(out_dist, ddist, sizeof(float) * nq * k, cudaMemcpyDeviceToHost, s));
   }
   // the total ends with the search and its output copies (before the flag read)
-  if (opts.collect_stats) RBQ_CUDA(cudaEventRecord(ev.t1, s));
+  if (opts.collect_stats) RBQ_CUDA(cudaEventRecord(ev[1], s));
   int h_fin = 0;
   RBQ_CUDA(cudaMemcpyAsync(&h_fin, fin.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   RBQ_CUDA(cudaStreamSynchronize(s));
   if (h_fin)
     return fail(RABITQ_EINVAL, "rabitq_search: a query has a non-finite value (outputs undefined)");
   if (opts.collect_stats) {
-    RBQ_CUDA(cudaEventElapsedTime(&stage[4], ev.t0, ev.t1));
+    RBQ_CUDA(cudaEventElapsedTime(&stage[4], ev[0], ev[1]));
     for (int i = 0; i < 5; ++i) g_stats[i] = stage[i];
     g_nstats = 5;
   }
@@ -469,16 +462,15 @@ int rabitq_autotune(rabitq_index* X, const float* queries, int64_t nq, int32_t k
   RBQ_CHECK(db.alloc(sizeof(float) * nq * k, s));
   opts.io_on_device = 1;
   opts.per_query_nprobe = dnp;
-  cudaEvent_t e0, e1;
-  RBQ_CUDA(cudaEventCreate(&e0));
-  RBQ_CUDA(cudaEventCreate(&e1));
+  EventSet<2> ev;
+  RBQ_CHECK(ev.create());
   float best[2] = {-1.0f, -1.0f};
   const int paths[2] = {RABITQ_SCAN_POPC, RABITQ_SCAN_TC};
   int st_all = RABITQ_OK;
   for (int p = 0; p < 2 && st_all == RABITQ_OK; ++p) {
     opts.scan_path = paths[p];
     for (int r = 0; r <= reps; ++r) {  // run 0 warms up
-      RBQ_CUDA(cudaEventRecord(e0, s));
+      RBQ_CUDA(cudaEventRecord(ev[0], s));
       const int st = search_common(X, dq, nq, k, nprobe, bq, eps0, ib.as<int64_t>(),
                                    db.as<float>(), &opts, nullptr);
       if (st == RABITQ_EOVERFLOW && paths[p] == RABITQ_SCAN_TC) {
@@ -489,15 +481,13 @@ int rabitq_autotune(rabitq_index* X, const float* queries, int64_t nq, int32_t k
         st_all = st;
         break;
       }
-      RBQ_CUDA(cudaEventRecord(e1, s));
-      RBQ_CUDA(cudaEventSynchronize(e1));
+      RBQ_CUDA(cudaEventRecord(ev[1], s));
+      RBQ_CUDA(cudaEventSynchronize(ev[1]));
       float ms = 0.0f;
-      RBQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      RBQ_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
       if (r > 0 && (best[p] < 0.0f || ms < best[p])) best[p] = ms;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (st_all != RABITQ_OK) return st_all;
   const int pick = (best[1] >= 0.0f && best[1] < best[0]) ? RABITQ_SCAN_TC : RABITQ_SCAN_POPC;
   X->tuned_path = pick;
@@ -557,15 +547,8 @@ int rabitq_autotune_tiles(rabitq_index* X, const float* queries, int64_t nq, int
     cand[nc++] = rabitq_tile{RABITQ_SCAN_POPC, RABITQ_LAYOUT_WARP, 2, RABITQ_STAGING_OFF, -1.0f};
   }
   cand[nc++] = rabitq_tile{RABITQ_SCAN_TC, 0, 0, 0, -1.0f};
-  struct Ev {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    ~Ev() {
-      if (e0) cudaEventDestroy(e0);
-      if (e1) cudaEventDestroy(e1);
-    }
-  } ev;
-  RBQ_CUDA(cudaEventCreate(&ev.e0));
-  RBQ_CUDA(cudaEventCreate(&ev.e1));
+  EventSet<2> ev;
+  RBQ_CHECK(ev.create());
   // time with the warp-layout batch rule waived (the tuned tile is then
   // taken for every batch of the class)
   for (int c = 0; c < nc; ++c) {
@@ -574,7 +557,7 @@ int rabitq_autotune_tiles(rabitq_index* X, const float* queries, int64_t nq, int
     opts.lane_pairs = cand[c].lane_pairs;
     opts.scan_staging = cand[c].staging;
     for (int r = 0; r <= reps; ++r) {  // run 0 warms up
-      RBQ_CUDA(cudaEventRecord(ev.e0, s));
+      RBQ_CUDA(cudaEventRecord(ev[0], s));
       const int st = search_common(X, dq, nq, k, nprobe, bq, eps0, ib.as<int64_t>(),
                                    db.as<float>(), &opts, nullptr);
       // the tensor-core path is ruled out by an overflow of its lists or a
@@ -585,10 +568,10 @@ int rabitq_autotune_tiles(rabitq_index* X, const float* queries, int64_t nq, int
         break;
       }
       if (st != RABITQ_OK) return st;
-      RBQ_CUDA(cudaEventRecord(ev.e1, s));
-      RBQ_CUDA(cudaEventSynchronize(ev.e1));
+      RBQ_CUDA(cudaEventRecord(ev[1], s));
+      RBQ_CUDA(cudaEventSynchronize(ev[1]));
       float ms = 0.0f;
-      RBQ_CUDA(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
+      RBQ_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
       if (r > 0 && (cand[c].time_ms < 0.0f || ms < cand[c].time_ms)) cand[c].time_ms = ms;
     }
   }

@@ -105,6 +105,25 @@ struct DevBuf {
   }
 };
 
+// N timing events, destroyed on every return path (create() may be skipped
+// when no timing is asked for).
+template <int N>
+struct EventSet {
+  cudaEvent_t e[N] = {};
+  EventSet() = default;
+  EventSet(const EventSet&) = delete;
+  EventSet& operator=(const EventSet&) = delete;
+  ~EventSet() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+  int create() {
+    for (auto& x : e) RBQ_CUDA(cudaEventCreate(&x));
+    return RABITQ_OK;
+  }
+  cudaEvent_t& operator[](int i) { return e[i]; }
+};
+
 // ---- canonical SIMT "GEMM" (kernels_gemm.cu) ----------------------------
 // C[m][n] = fold_k op(A'[m][k], B[k][n]) in ascending k, where
 // A'[m][k] = A[arow(m)][k] - (sub ? sub[srow(m)][k] : 0); arow(m) = a_rows ? a_rows[m] : m.

@@ -182,3 +182,23 @@ def test_tile_options_are_checked(R, tiny_idx, tiny_workload):
         tiny_idx.search(queries, 10, 4, lane_pairs=3)
     with pytest.raises(R.RabitqError):
         tiny_idx.search(queries, 10, 4, layout=7)
+
+
+def test_search_stats_and_their_error_path(R, tiny_workload, tiny_idx):
+    """Stage times recorded with stats on leave the results unchanged, on
+    both scan paths; a non-finite query with stats on is EINVAL and the
+    next searches (with their timing events) still run."""
+    _, queries = tiny_workload
+    for path in (R.SCAN_POPC, R.SCAN_TC):
+        want = tiny_idx.search(queries, 10, 4, scan_path=path)
+        got = tiny_idx.search(queries, 10, 4, scan_path=path, stats=True)
+        _same(got, want)
+        st = R.last_stats()
+        assert len(st) == 5 and (st >= 0).all() and st[4] > 0
+    bad = queries[:5].copy()
+    bad[1, 3] = np.inf
+    for _ in range(50):
+        with pytest.raises(R.RabitqError) as e:
+            tiny_idx.search(bad, 10, 4, stats=True)
+        assert e.value.code == R.EINVAL
+    _same(tiny_idx.search(queries, 10, 4, stats=True), tiny_idx.search(queries, 10, 4))
