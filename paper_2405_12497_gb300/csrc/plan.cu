@@ -124,8 +124,10 @@ int rabitq_plan_create(const rabitq_index* X, const rabitq_predictor* pr, int64_
     return fail(RABITQ_EINVAL, "rabitq_plan_create: lane_pairs must be 0, 1 or 2");
   if (opts.scan_staging < RABITQ_STAGING_AUTO || opts.scan_staging > RABITQ_STAGING_BULK)
     return fail(RABITQ_EINVAL, "rabitq_plan_create: unknown scan_staging");
+  int dev = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
   auto* P = new rabitq_plan();
-  RBQ_CUDA(cudaGetDevice(&P->device));
+  P->device = dev;
   SearchArgs& a = P->a;
   a.X = X;
   a.nq = nq_max;

@@ -159,6 +159,7 @@ void worker_main(rabitq_server* S) {
   for (;;) {
     std::vector<std::shared_ptr<Req>> batch;
     int64_t total = 0;
+    Slot* sl = nullptr;  // stays valid: the slot deque only grows at its end
     {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv_work.wait(lk, [S] { return S->stop || !S->queue.empty(); });
@@ -171,6 +172,7 @@ void worker_main(rabitq_server* S) {
       // the oldest request, then every queued request of the same (index,
       // k) that still fits the batch, in arrival order
       const int32_t slot = S->queue.front()->slot, k = S->queue.front()->k;
+      sl = &S->slots[slot];
       for (auto it = S->queue.begin(); it != S->queue.end();) {
         Req& r = **it;
         if (r.slot == slot && r.k == k && total + r.nq <= S->o.max_batch) {
@@ -182,8 +184,7 @@ void worker_main(rabitq_server* S) {
         }
       }
     }
-    Slot& sl = S->slots[batch.front()->slot];
-    const int st = run_batch(S, sl, batch.front()->k, batch, total);
+    const int st = run_batch(S, *sl, batch.front()->k, batch, total);
     const auto now = Clock::now();
     {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -240,6 +241,7 @@ int rabitq_server_create(const rabitq_server_opts* opts, rabitq_server** out) {
   S->pool.init(cap);
   if (cudaStreamCreateWithFlags(&S->copy_s, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&S->run_s, cudaStreamNonBlocking) != cudaSuccess) {
+    if (S->copy_s) cudaStreamDestroy(S->copy_s);
     cudaFree(S->pool_mem);
     return fail(RABITQ_ECUDA, "rabitq_server_create: stream creation failed");
   }
@@ -286,6 +288,7 @@ int rabitq_server_submit(rabitq_server* S, int32_t slot, const float* queries, i
   if (k < 1 || k > 1024) return fail(RABITQ_EINVAL, "rabitq_server_submit: need 1 <= k <= 1024");
   auto r = std::make_shared<Req>();
   r->t_submit = Clock::now();
+  int d = 0;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (slot < 0 || slot >= (int32_t)S->slots.size())
@@ -293,6 +296,7 @@ int rabitq_server_submit(rabitq_server* S, int32_t slot, const float* queries, i
     if (S->worker_status != RABITQ_OK)
       return fail(S->worker_status, "rabitq_server_submit: the server failed earlier");
     const rabitq_index* X = S->slots[slot].X;
+    d = X->d;  // (the slot list is read under the lock: add_index may grow it)
     r->bytes = req_bytes(X, nq);
     // admission: the request's queries must fit the free staging memory
     if (!S->pool.take(r->bytes, &r->off)) {
@@ -310,7 +314,6 @@ int rabitq_server_submit(rabitq_server* S, int32_t slot, const float* queries, i
     r->out_dist = out_dist;
     S->st.admitted += 1;
   }
-  const int d = S->slots[slot].X->d;
   cudaError_t e = cudaEventCreateWithFlags(&r->copied, cudaEventDisableTiming);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(S->pool_mem + r->off, queries, sizeof(float) * nq * d,

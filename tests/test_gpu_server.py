@@ -113,3 +113,49 @@ def test_server_admission_by_device_budget(R, indices):
     with pytest.raises(R.RabitqError):
         srv.submit(slot, Q[:4], 2000, ids, dist)             # k out of range
     srv.free()
+
+
+def test_server_slots_added_while_serving(R, indices):
+    """Indices added from one thread while three others submit and wait:
+    the slot list grows under the server's lock and is read there; every
+    result equals a direct search, and a slot added last serves too."""
+    (G, Q), (G2, Q2) = indices
+    srv = R.Server(max_batch=64, mem_budget=8 << 20)
+    slot0 = srv.add_index(G, nprobe=6, eps0=EPS)
+    errs, added, outs = [], [], []
+
+    def adder():
+        try:
+            for _ in range(300):
+                added.append(srv.add_index(G2, nprobe=4, eps0=EPS))
+        except Exception as e:  # noqa: BLE001 -- reported below
+            errs.append(e)
+
+    def client(c):
+        try:
+            for j in range(20):
+                o = (c * 20 + j) * 3 % 190
+                ids = np.zeros((10, 10), np.int64)
+                dist = np.zeros((10, 10), np.float32)
+                srv.wait(srv.submit(slot0, Q[o:o + 10], 10, ids, dist), 120.0)
+                outs.append((o, ids, dist))
+        except Exception as e:  # noqa: BLE001 -- reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=adder)] + [threading.Thread(target=client, args=(c,))
+                                             for c in range(3)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    assert sorted(added) == list(range(1, 301)) and len(outs) == 60
+    for o, ids, dist in outs:
+        ri, rd = G.search(Q[o:o + 10], 10, 6, eps0=EPS)
+        assert np.array_equal(ids, ri) and np.array_equal(dist.view(np.uint32), rd.view(np.uint32))
+    ids = np.zeros((5, 10), np.int64)
+    dist = np.zeros((5, 10), np.float32)
+    srv.wait(srv.submit(added[-1], Q2[:5], 10, ids, dist), 120.0)
+    ri, rd = G2.search(Q2[:5], 10, 4, eps0=EPS)
+    assert np.array_equal(ids, ri) and np.array_equal(dist.view(np.uint32), rd.view(np.uint32))
+    srv.free()
