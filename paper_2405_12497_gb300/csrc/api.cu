@@ -206,14 +206,16 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
     return fail(RABITQ_EINVAL, "rabitq_build: n_clusters too large for n");
   cudaStream_t s = static_cast<cudaStream_t>(opts.stream);
 
+  int dev = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
   auto* X = new rabitq_index();
+  X->device = dev;
   X->n = n;
   X->d = d;
   X->dpad = dpad;
   X->K = n_clusters;
   X->W = dpad / 64;
   X->metric = opts.metric;
-  RBQ_CUDA(cudaGetDevice(&X->device));
   int st = alloc_index_arrays(X);
   if (st != RABITQ_OK) {
     free_index_arrays(X);

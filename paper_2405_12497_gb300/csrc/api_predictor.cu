@@ -31,8 +31,10 @@ void free_predictor(rabitq_predictor* pr) {
 }
 
 int new_predictor(int32_t K, int32_t nprobe_max, rabitq_predictor** out) {
+  int dev = 0;
+  RBQ_CUDA(cudaGetDevice(&dev));
   auto* pr = new rabitq_predictor();
-  RBQ_CUDA(cudaGetDevice(&pr->device));
+  pr->device = dev;
   pr->K = K;
   pr->nprobe_max = nprobe_max;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&pr->params), sizeof(float) * kMlpParams);
