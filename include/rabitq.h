@@ -543,8 +543,8 @@ int rabitq_shard_clusters(const int32_t* sizes, int32_t K, int32_t S, int32_t* s
  * (may be NULL, or hold NULL entries) is a device array of n_lists device
  * pointers mapping each list's ids to global ids (ids[...] indexes
  * labels[list]); global ids must be below 2^32 - 1. n_lists * k_in <= 8192,
- * k <= 1024. Asynchronous on `stream` (no synchronization). Errors: EINVAL;
- * ECUDA.
+ * k <= 1024, nq <= 2^31 - 1. Asynchronous on `stream` (no synchronization).
+ * Errors: EINVAL; ECUDA.
  */
 int rabitq_merge_topk(const float* dist, const int64_t* ids, int32_t n_lists, int64_t nq,
                       int32_t k_in, int32_t k, const int64_t* const* labels, int32_t metric,

@@ -90,7 +90,8 @@ int rabitq_merge_topk(const float* dist, const int64_t* ids, int32_t n_lists, in
                       int32_t k_in, int32_t k, const int64_t* const* labels, int32_t metric,
                       int64_t* out_ids, float* out_dist, void* stream) {
   set_error("");
-  if (nq < 0) return fail(RABITQ_EINVAL, "rabitq_merge_topk: nq < 0");
+  if (nq < 0 || nq > 0x7fffffff)
+    return fail(RABITQ_EINVAL, "rabitq_merge_topk: need 0 <= nq <= 2^31 - 1 (one CTA per query)");
   if (nq == 0) return RABITQ_OK;
   if (!dist || !ids || !out_ids || !out_dist)
     return fail(RABITQ_EINVAL, "rabitq_merge_topk: null pointer");

@@ -65,6 +65,24 @@ def test_invalid_arguments_fail_before_device_work(L):
                                out.ctypes.data_as(C.c_void_p), None) == L.EINVAL
     m = C.c_int32(-1)
     assert lib.rabitq_index_metric(None, C.byref(m)) == L.EINVAL
+    # the merge's argument checks come before any launch (one CTA per query)
+    for nq, n_lists, k_in, k in ((-1, 2, 10, 10), (1 << 31, 2, 10, 10), (4, 2, 5000, 10),
+                                 (4, 2, 10, 1025), (4, 0, 10, 10)):
+        assert lib.rabitq_merge_topk(p, p, n_lists, nq, k_in, k, None, L.METRIC_L2, p, p,
+                                     None) == L.EINVAL
+    assert lib.rabitq_merge_topk(p, p, 2, 4, 10, 10, None, 7, p, p, None) == L.EINVAL
+    assert lib.rabitq_merge_topk(None, None, 2, 0, 10, 10, None, L.METRIC_L2, None, None,
+                                 None) == L.OK
+    sizes = np.array([5, 9, 1, 7, 3], np.int32)
+    shard_of = np.zeros(5, np.int32)
+    pts = np.zeros(2, np.int64)
+    assert lib.rabitq_shard_clusters(sizes.ctypes.data_as(C.c_void_p), 5, 2,
+                                     shard_of.ctypes.data_as(C.c_void_p),
+                                     pts.ctypes.data_as(C.c_void_p)) == L.OK
+    # largest first onto the lighter shard: 9 -> 0, 7 -> 1, 5 -> 1, 3 -> 0, 1 -> 0
+    assert shard_of.tolist() == [1, 0, 0, 1, 0] and pts.tolist() == [13, 12]
+    assert lib.rabitq_shard_clusters(sizes.ctypes.data_as(C.c_void_p), 5, 6,
+                                     shard_of.ctypes.data_as(C.c_void_p), None) == L.EINVAL
     lib.rabitq_free(None)
 
 
