@@ -133,7 +133,7 @@ int rabitq_build(const float* data, int64_t n, int32_t d, int32_t n_clusters, ui
  *   queries   nq x d float32 raw query vectors q_r
  *   nq        >= 0 (0 is a no-op)
  *   k         1..1024 neighbours per query
- *   nprobe    1..K buckets probed per query (the nearest centroids)
+ *   nprobe    1..min(K, 16384) buckets probed per query (the nearest centroids)
  *   bq        1..8 bits of the randomized query quantization (§3.3.1)
  *   eps0      >= 0, confidence parameter of the error bound (Theorem 3.2)
  *   out_ids   nq x k int64 ids, ascending by (distance, id); -1 pads
@@ -568,7 +568,7 @@ int rabitq_merge_topk(const float* dist, const int64_t* ids, int32_t n_lists, in
  *   mem_budget       staging pool bytes (default 64 MiB)
  *   batch_window_us  how long a lone queued request may wait for company
  *                    before it runs (default 0: it runs at once)
- * rabitq_server_add_index: nprobe (1..K) for a fixed probe count, or a
+ * rabitq_server_add_index: nprobe (1..min(K, 16384)) for a fixed probe count, or a
  *   predictor for learned counts (nprobe then ignored); slot receives the
  *   index's number for rabitq_server_submit.
  * rabitq_server_submit: queries (host, nq x d) are copied before it returns

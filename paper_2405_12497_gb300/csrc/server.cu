@@ -260,8 +260,8 @@ int rabitq_server_add_index(rabitq_server* S, const rabitq_index* X,
   RBQ_CHECK(check_device(X->device, "rabitq_server_add_index (index)"));
   if (pr && pr->K != X->K)
     return fail(RABITQ_EINVAL, "rabitq_server_add_index: predictor made for another bucket count");
-  if (!pr && (nprobe < 1 || nprobe > X->K))
-    return fail(RABITQ_EINVAL, "rabitq_server_add_index: need 1 <= nprobe <= K");
+  if (!pr && (nprobe < 1 || nprobe > X->K || nprobe > 16384))
+    return fail(RABITQ_EINVAL, "rabitq_server_add_index: need 1 <= nprobe <= min(K, 16384)");
   if (bq < 1 || bq > 8) return fail(RABITQ_EINVAL, "rabitq_server_add_index: need 1 <= bq <= 8");
   if (!(eps0 >= 0.0f) || !(eps0 < __builtin_inff()))
     return fail(RABITQ_EINVAL, "rabitq_server_add_index: eps0 must be finite and >= 0");
