@@ -946,7 +946,8 @@ def deep_legs(args, flush, stream, dist, hbm, src):
     # and factors) far larger than L2
     cplan = rabitq.Plan(G, w.k, 128, w.nq, bq=w.bq, eps0=w.eps0, stats=True, max_candidates=cap)
     cold = time_leg(args, cplan, qd, gt, w, flush, stream, dist, name="deep_cold")
-    for key in ("_ids", "_dist", "_npq", "_plan"):
+    c_ids, c_dist = cold.pop("_ids"), cold.pop("_dist")
+    for key in ("_npq", "_plan"):
         cold.pop(key, None)
     cold["nprobe"] = 128
     cold["tile"] = cplan.tile()
@@ -960,7 +961,8 @@ def deep_legs(args, flush, stream, dist, hbm, src):
            "legs": {"fixed": fixed, "learned": learned}, "cold_scan": cold,
            "learned_vs_fixed_qps": round(learned["value"] / fixed["value"], 4)}
     if not args.no_cpu_baseline:
-        out["parity"] = deep_parity(G, dd, qd, w, chosen, f_ids, f_dist, l_ids, l_dist, l_npq)
+        out["parity"] = deep_parity(G, dd, qd, w, chosen, f_ids, f_dist, l_ids, l_dist, l_npq,
+                                    cold=(128, c_ids, c_dist))
     G.free()
     pr.free()
     del dd, qd, cqd, tqd
@@ -968,11 +970,13 @@ def deep_legs(args, flush, stream, dist, hbm, src):
     return out
 
 
-def deep_parity(G, dd, qd, w, nprobe, f_ids, f_dist, l_ids, l_dist, l_npq, m=300):
+def deep_parity(G, dd, qd, w, nprobe, f_ids, f_dist, l_ids, l_dist, l_npq, m=300, cold=None,
+                m_cold=100):
     """The oracle on the DEEP-shaped index: its own P for the build seed, the
-    codes and factors of a 65536-point sample recomputed from the data, and
-    the first m queries of both timed legs searched by the oracle (the fixed
-    nprobe; the learned leg's per-query counts)."""
+    codes and factors of a 65536-point sample recomputed from the data, the
+    first m queries of both timed legs searched by the oracle (the fixed
+    nprobe; the learned leg's per-query counts), and the first m_cold of the
+    cold-scan leg (cold = (nprobe, ids, dist) of its timed plan)."""
     from oracle import oracle as O
     X = oracle_on_index(G, dd.cpu().numpy())
     cores = os.cpu_count() or 1
@@ -997,6 +1001,14 @@ def deep_parity(G, dd, qd, w, nprobe, f_ids, f_dist, l_ids, l_dist, l_npq, m=300
         out["learned"] = {"queries": m, "ids_equal": bool(np.array_equal(o_ids, l_ids[:m])),
                           "dist_bits_equal": bool(np.array_equal(o_dist.view(np.uint32),
                                                                  l_dist[:m].view(np.uint32)))}
+    if cold is not None:
+        npc, c_ids, c_dist = cold
+        mc = min(m_cold, len(q))
+        o_ids, o_dist = X.search(q[:mc], w.k, npc, bq=w.bq, eps0=w.eps0, threads=cores)
+        out["cold_scan"] = {"queries": mc, "nprobe": npc,
+                            "ids_equal": bool(np.array_equal(o_ids, c_ids[:mc])),
+                            "dist_bits_equal": bool(np.array_equal(o_dist.view(np.uint32),
+                                                                   c_dist[:mc].view(np.uint32)))}
     return out
 
 
