@@ -16,7 +16,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-def _noalloc(R, G, qd, k, nprobe, bq=4, eps0=1.9):
+def _noalloc(R, G, qd, k, nprobe, bq=4, eps0=1.9, npq=None):
     import torch
     nq = qd.shape[0]
     ids = torch.full((nq, k), -7, dtype=torch.int64, device=qd.device)
@@ -25,6 +25,8 @@ def _noalloc(R, G, qd, k, nprobe, bq=4, eps0=1.9):
     R.lib().rabitq_search_opts_default(C.byref(o))
     o.io_on_device = 1
     o.stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if npq is not None:  # a device int32 tensor of nq probe counts
+        o.per_query_nprobe = C.c_void_p(npq.data_ptr())
     rc = R.lib().rabitq_search_noalloc(G._h, C.c_void_p(qd.data_ptr()), nq, k, nprobe, bq, eps0,
                                        C.c_void_p(ids.data_ptr()), C.c_void_p(dist.data_ptr()),
                                        C.byref(o))
@@ -91,3 +93,31 @@ def test_noalloc_reports_non_finite_query():
     ref_ids, ref_dist = G.search(qd, 5, 2)
     assert np.array_equal(ids, ref_ids.cpu().numpy())
     assert np.array_equal(dist.view(np.uint32), ref_dist.cpu().numpy().view(np.uint32))
+
+
+def test_noalloc_matches_oracle(oracle_mod):
+    """Against the oracle directly: every metric, the largest k (1024) and
+    per-query probe counts, through the fixed scratch."""
+    import torch
+    from paper_2405_12497_gb300 import build, rabitq as R, synth
+    build.build()
+    data, Q = synth.tiny()
+    Q = Q[:40]
+    qd = torch.from_numpy(Q).cuda()
+    for metric in ("l2", "ip", "cosine"):
+        G = R.Index.build(data, 16, seed=2, metric=metric)
+        O = oracle_mod.OracleIndex(data, K=16, seed=2, metric=metric)
+        for k, nprobe in ((10, 4), (1024, 16)):
+            rc, ids, dist = _noalloc(R, G, qd, k, nprobe)
+            assert rc == R.OK, R.lib().rabitq_last_error()
+            ids_o, dist_o = O.search(Q, k, nprobe)
+            assert np.array_equal(ids, ids_o), (metric, k)
+            assert np.array_equal(dist.view(np.uint32), dist_o.view(np.uint32)), (metric, k)
+        if metric == "l2":
+            npq = ((np.arange(len(Q)) * 7) % 9 + 1).astype(np.int32)
+            rc, ids, dist = _noalloc(R, G, qd, 10, 9, npq=torch.from_numpy(npq).cuda())
+            assert rc == R.OK, R.lib().rabitq_last_error()
+            ids_o, dist_o = O.search(Q, 10, 9, per_query_nprobe=npq)
+            assert np.array_equal(ids, ids_o)
+            assert np.array_equal(dist.view(np.uint32), dist_o.view(np.uint32))
+        G.free()
