@@ -76,3 +76,23 @@ def test_sharded_search_equals_unsharded(R, oracle_mod, tiny_workload, n_shards)
             assert ((t["pair_est"][:, 1] > ex) | (t["pair_est"][:, 2] < ex)).any()
         assert same.mean() >= 0.9
     SH.free()
+
+
+@pytest.mark.parametrize("metric", ["ip", "cosine"])
+def test_sharded_inner_product_search_equals_unsharded(R, tiny_workload, metric):
+    """Inner products and cosines over shards: with eps0 = 6 no bound fails
+    (Theorem 3.2), so every shard returns the exact top-k of its probed
+    buckets and the merge by (-inner product, id) equals the unsharded
+    search row for row, values bit for bit."""
+    import torch
+    data, Q = tiny_workload
+    qd = torch.from_numpy(Q).cuda()
+    G = R.Index.build(data, 16, seed=2, metric=metric)
+    SH = R.ShardedIndex.build(torch.from_numpy(data).cuda(), 16, 3, seed=2, metric=metric)
+    for k, nprobe in ((10, 4), (100, 16)):
+        ids_s, dist_s = SH.search(qd, k, nprobe, eps0=6.0)
+        ids_g, dist_g = G.search(qd, k, nprobe, eps0=6.0)
+        assert np.array_equal(ids_s.cpu().numpy(), ids_g.cpu().numpy()), (metric, k)
+        assert np.array_equal(dist_s.cpu().numpy().view(np.uint32),
+                              dist_g.cpu().numpy().view(np.uint32))
+    SH.free()
