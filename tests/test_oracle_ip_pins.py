@@ -177,3 +177,25 @@ def test_cosine_search(oracle_mod, tiny_workload):
     idg, _ = X.search(Q, 10, 4)
     gt = np.argsort(-((Q.astype(np.float64) @ d64.T) / np.linalg.norm(d64, axis=1)), 1)[:, :10]
     assert _recall(idg, gt) >= 0.8
+
+
+@pytest.mark.parametrize("metric", ["ip", "cosine"])
+def test_ip_ties_resolve_by_id(oracle_mod, metric):
+    """300 identical points along the query hold its 300 largest inner
+    products (and cosines), by FP64 brute force: ranked by (-value, id),
+    the top-k are the k lowest of their ids, all with one value."""
+    rng = np.random.default_rng(31)
+    data = rng.standard_normal((3000, 64)).astype(np.float32)
+    q = rng.standard_normal(64).astype(np.float32)
+    data[500:800] = q * np.float32(3.0)
+    Q = np.stack([q, q * np.float32(0.5)])
+    d64 = data.astype(np.float64)
+    if metric == "cosine":
+        d64 = d64 / np.linalg.norm(d64, axis=1, keepdims=True)
+    top = np.argsort(-(Q.astype(np.float64) @ d64.T), axis=1, kind="stable")[:, :300]
+    assert (np.sort(top, axis=1) == np.arange(500, 800)).all()
+    X = oracle_mod.OracleIndex(data, K=12, seed=4, metric=metric)
+    for k in (1, 100, 300):
+        ids, v = X.search(Q, k, X.K)
+        assert (ids == np.arange(500, 500 + k)).all(), (metric, k)
+        assert (v == v[:, :1]).all()
