@@ -503,6 +503,27 @@ def test_mass_ties_resolve_by_id(oracle_mod):
     assert (ids == np.arange(10)).all() and (dist == dist[:, :1]).all() and (dist[0] == 0).all()
 
 
+def test_query_at_a_centroid_estimates_exactly(oracle_mod, tiny_oracle_index):
+    """A query equal to centroid c: its rotated residual is exactly zero, so
+    the quantizer's range is empty (Delta = 0, every q_u = 0, no plane bit
+    set), ||q_r - c|| = 0 removes both the estimator's correction and the
+    error bound, and every code of c's bucket gets LB = estimate = UB =
+    ||o_r - c||^2 (its factor F1), which is also the exact distance: the
+    result is the exact k-NN of the bucket, ranked by (distance, id)."""
+    X = tiny_oracle_index
+    for c in (0, 5, 11):
+        t = X.trace(X.centroids[c], 7, 10, 1)
+        assert t["probe_ids"][0] == c and t["probe_dist"][0] == 0
+        assert (t["meta"][0] == 0).all() and t["sum_qu"][0] == 0 and not t["planes"].any()
+        ids, est = t["pair_id"], t["pair_est"]
+        assert len(ids) == X.bucket_off[c + 1] - X.bucket_off[c]
+        ex = oracle_mod.sqdist_matrix(X.centroids[c][None], X.data[ids])[0]
+        assert np.array_equal(est[:, 0], X.factors[ids, 0]) and np.array_equal(est[:, 0], ex)
+        assert np.array_equal(est[:, 1], est[:, 0]) and np.array_equal(est[:, 2], est[:, 0])
+        order = np.lexsort((ids, ex))[:10]
+        assert np.array_equal(t["ids"], ids[order]) and np.array_equal(t["dist"], ex[order])
+
+
 def test_trace_rerank_set_definition(oracle_mod, tiny_oracle_index, tiny_workload):
     """Re-rank set = pilot (4k smallest estimates by (estimate, id) among the
     codes with LB <= k-th smallest UB) plus every code with LB <= min(k-th
