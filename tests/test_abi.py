@@ -92,3 +92,26 @@ def test_truncated_index_file_is_rejected(L, tmp_path):
     f.write_bytes(b"RABITQ\x00\x01" + b"\x00" * 20)
     h = C.c_void_p()
     assert lib.rabitq_index_load(str(f).encode(), None, C.byref(h)) == L.EIO
+
+
+def test_missing_library_fails_loudly_and_nothing_falls_back():
+    """Without the CUDA library every call raises (there is no CPU path), and
+    the package imports nothing from the oracle, in a fresh interpreter."""
+    import subprocess
+    import sys
+    code = (
+        "import sys\n"
+        "from paper_2405_12497_gb300 import rabitq as R\n"
+        "R._LIB_PATH = '/nonexistent/librabitq.so'\n"
+        "R._lib = None\n"
+        "try:\n"
+        "    R.Index.build(__import__('numpy').zeros((4, 8), 'float32'), 2, seed=1)\n"
+        "except R.RabitqError as e:\n"
+        "    assert e.code == R.ECUDA and 'not built' in str(e), e\n"
+        "else:\n"
+        "    raise SystemExit('no error without the library')\n"
+        "assert not [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]\n"
+        "print('ok')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
