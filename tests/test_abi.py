@@ -115,3 +115,21 @@ def test_missing_library_fails_loudly_and_nothing_falls_back():
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
                        timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
+
+
+def test_oracle_and_cuda_path_share_nothing():
+    """Static check of the independence rule: no file of the package (Python
+    or CUDA) names the oracle, and no oracle file names the package or its
+    sources."""
+    pkg = os.path.join(ROOT, "paper_2405_12497_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\b(import oracle|from oracle|rabitq_oracle|mlp_oracle)\b",
+                                     text), f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            text = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_2405_12497_gb300" not in text and "csrc" not in text, f
+            assert "rabitq.h" not in text and "internal.h" not in text, f
